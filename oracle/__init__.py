@@ -1,0 +1,141 @@
+"""CPU oracle for the X-engine correlator and the gain-calibration loss.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the product package.
+The C source (``mwax_oracle.c``) shares no code with the CUDA library.
+
+Parity pins for every function here live in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(_HERE, "_lib", "libmwax_oracle.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_OVERFLOW = 0, 1, 2, 3
+
+
+def build_command():
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    return ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-Wall",
+            os.path.join(_HERE, "mwax_oracle.c"), "-o", LIB]
+
+
+def build() -> None:
+    cmd = build_command()
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle build failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            build()
+        lib = ctypes.CDLL(LIB)
+        lib.oracle_decode.restype = ctypes.c_int
+        lib.oracle_decode.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p]
+        lib.oracle_correlate.restype = ctypes.c_int
+        lib.oracle_correlate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_n_baselines.restype = ctypes.c_int64
+        lib.oracle_n_baselines.argtypes = [ctypes.c_int64]
+        lib.oracle_baseline_index.restype = ctypes.c_int64
+        lib.oracle_baseline_index.argtypes = [ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_calib_loss.restype = ctypes.c_double
+        lib.oracle_calib_loss.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int]
+        lib.oracle_calib_grad.restype = ctypes.c_int
+        lib.oracle_calib_grad.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int,
+                                                                  ctypes.c_void_p, ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def threads() -> int:
+    return max(1, min(os.cpu_count() or 1, 64))
+
+
+def decode(raw: np.ndarray, sample_bits: int):
+    """Packed samples -> (re, im) int32 arrays of n samples."""
+    raw = np.ascontiguousarray(raw, np.uint8).ravel()
+    n = raw.size if sample_bits == 4 else raw.size // 2
+    re = np.empty(n, np.int32)
+    im = np.empty(n, np.int32)
+    rc = _load().oracle_decode(raw.ctypes.data, sample_bits, n, re.ctypes.data, im.ctypes.data)
+    if rc:
+        raise ValueError("unsupported sample width")
+    return re, im
+
+
+def correlate(volt: np.ndarray, sample_bits: int, n_inputs: int, n_chan: int, n_time: int,
+              want64: bool = False, n_threads: int | None = None):
+    """Oracle correlation of packed voltages [n_chan][n_time][n_inputs].
+
+    Returns int32 [n_chan, N(N+1)/2, 2] (and the int64 copy when want64).
+    Raises OverflowError when a visibility exceeds the int32 range (the
+    int64 copy is still returned through the exception's ``args[1]``)."""
+    volt = np.ascontiguousarray(volt, np.uint8)
+    bps = 1 if sample_bits == 4 else 2
+    if volt.size != n_chan * n_time * n_inputs * bps:
+        raise ValueError("voltage buffer size does not match the shape")
+    B = n_inputs * (n_inputs + 1) // 2
+    out = np.zeros((n_chan, B, 2), np.int32)
+    out64 = np.zeros((n_chan, B, 2), np.int64) if want64 else None
+    rc = _load().oracle_correlate(volt.ctypes.data, sample_bits, n_inputs, n_chan, n_time,
+                                  out.ctypes.data, out64.ctypes.data if want64 else None,
+                                  n_threads or threads())
+    if rc == ERR_OVERFLOW:
+        raise OverflowError("visibility outside the int32 range", out64)
+    if rc:
+        raise RuntimeError(f"oracle_correlate failed ({rc})")
+    return (out, out64) if want64 else out
+
+
+def n_baselines(n_inputs: int) -> int:
+    return int(_load().oracle_n_baselines(n_inputs))
+
+
+def baseline_index(i: int, j: int) -> int:
+    return int(_load().oracle_baseline_index(i, j))
+
+
+def _c128_as_pairs(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, np.complex128)
+    return a.view(np.float64)
+
+
+def calib_loss(V, M, g) -> float:
+    """FP64 loss.  V, M: complex [n_chan, N(N+1)/2]; g: complex [N]."""
+    V = np.ascontiguousarray(V, np.complex128)
+    M = np.ascontiguousarray(M, np.complex128)
+    g = np.ascontiguousarray(g, np.complex128)
+    C, B = V.shape
+    N = g.shape[0]
+    assert B == N * (N + 1) // 2 and M.shape == V.shape
+    return float(_load().oracle_calib_loss(V.ctypes.data, M.ctypes.data, g.ctypes.data, N, C))
+
+
+def calib_grad(V, M, g, n_threads: int | None = None) -> np.ndarray:
+    """FP64 gradient 2 dL/d conj(g), complex [N]."""
+    V = np.ascontiguousarray(V, np.complex128)
+    M = np.ascontiguousarray(M, np.complex128)
+    g = np.ascontiguousarray(g, np.complex128)
+    C, B = V.shape
+    N = g.shape[0]
+    assert B == N * (N + 1) // 2 and M.shape == V.shape
+    out = np.zeros(N, np.complex128)
+    rc = _load().oracle_calib_grad(V.ctypes.data, M.ctypes.data, g.ctypes.data, N, C,
+                                   out.ctypes.data, n_threads or threads())
+    if rc:
+        raise RuntimeError("oracle_calib_grad failed")
+    return out

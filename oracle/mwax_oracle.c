@@ -1,0 +1,251 @@
+/*
+ * mwax_oracle.c -- plain, slow CPU oracle for the MWA X-engine correlator and
+ * the gain-calibration loss that consumes its output.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this code:
+ * it is used by the tests, by the smoke check and by the benchmark's CPU
+ * baseline leg.  It shares no code with the CUDA library (own sample
+ * decoding, own index arithmetic, own loops).
+ *
+ * What it computes (paper Sec. 2: an FPGA correlator cross-correlates the
+ * signals of all antennas -- 512 antennas, ~130,000 baseline pairs, 768
+ * channels, 4 polarisation products -- and the stream is then integrated,
+ * calibrated and imaged):
+ *
+ *   correlation, per channel c and input pair i >= j (lower triangle with
+ *   autocorrelations), integrated over T time samples:
+ *       V_ij = sum_t x_i(t) conj(x_j(t))
+ *       Re V_ij = sum_t xr_i xr_j + xi_i xi_j
+ *       Im V_ij = sum_t xi_i xr_j - xr_i xi_j
+ *   with int64 accumulators, stored as int32 pairs at
+ *   out[c][i(i+1)/2 + j][re, im].
+ *
+ *   calibration (Sec. 2: the complex gain of each antenna element is found
+ *   by a least-squares fit against catalogue sources), in FP64:
+ *       R_ij = g_i conj(g_j) M_ij - V_ij
+ *       L(g) = sum_nu sum_{i>j} |R_ij,nu|^2          (w = 1 off-diagonal, 0 on autos)
+ *       grad_k = 2 dL/d conj(g_k)
+ *              = 2 sum_nu sum_{j != k} R_kj g_j conj(M_kj)
+ *   where R and M are extended to the upper triangle by Hermitian symmetry
+ *   (R_kj = conj(R_jk), M_kj = conj(M_jk)).  grad is the PyTorch convention
+ *   for a real loss of a complex parameter: dL/dRe g + i dL/dIm g.
+ *
+ * Sample format (the correlator input): voltages[chan][time][input];
+ *   4+4-bit: one byte, low nibble = re, high nibble = im, two's complement;
+ *   8+8-bit: two bytes, re then im, int8.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- sample decoding ---------------------------------------------------- */
+
+static int32_t nibble_to_int(uint32_t v) { return (v & 0x8u) ? (int32_t)v - 16 : (int32_t)v; }
+
+/* Decode n packed complex samples into separate re / im arrays.
+ * Returns 0, or 1 for an unsupported sample width. */
+int oracle_decode(const uint8_t *raw, int sample_bits, int64_t n, int32_t *re, int32_t *im) {
+  if (sample_bits == 4) {
+    for (int64_t k = 0; k < n; ++k) {
+      re[k] = nibble_to_int(raw[k] & 0xFu);
+      im[k] = nibble_to_int((raw[k] >> 4) & 0xFu);
+    }
+    return 0;
+  }
+  if (sample_bits == 8) {
+    for (int64_t k = 0; k < n; ++k) {
+      re[k] = (int32_t)(int8_t)raw[2 * k];
+      im[k] = (int32_t)(int8_t)raw[2 * k + 1];
+    }
+    return 0;
+  }
+  return 1;
+}
+
+/* ---- correlation -------------------------------------------------------- */
+
+typedef struct {
+  const int32_t *re, *im; /* decoded, [chan][input][time] */
+  int n_inputs, n_chan, n_time;
+  int32_t *out;   /* [chan][b][2] */
+  int64_t *out64; /* optional [chan][b][2] int64 */
+  int tid, n_threads;
+  int overflow;
+} corr_job;
+
+static void *corr_worker(void *arg) {
+  corr_job *j = (corr_job *)arg;
+  const int64_t N = j->n_inputs, T = j->n_time;
+  const int64_t B = N * (N + 1) / 2;
+  /* one unit of work = one (channel, row i) */
+  const int64_t units = (int64_t)j->n_chan * N;
+  for (int64_t u = j->tid; u < units; u += j->n_threads) {
+    const int64_t c = u / N, i = u % N;
+    const int32_t *xr_i = j->re + (c * N + i) * T;
+    const int32_t *xi_i = j->im + (c * N + i) * T;
+    for (int64_t jj = 0; jj <= i; ++jj) {
+      const int32_t *xr_j = j->re + (c * N + jj) * T;
+      const int32_t *xi_j = j->im + (c * N + jj) * T;
+      int64_t sre = 0, sim = 0;
+      for (int64_t t = 0; t < T; ++t) {
+        sre += (int64_t)xr_i[t] * xr_j[t] + (int64_t)xi_i[t] * xi_j[t];
+        sim += (int64_t)xi_i[t] * xr_j[t] - (int64_t)xr_i[t] * xi_j[t];
+      }
+      const int64_t b = i * (i + 1) / 2 + jj;
+      if (sre > INT32_MAX || sre < -(int64_t)INT32_MAX || sim > INT32_MAX ||
+          sim < -(int64_t)INT32_MAX)
+        j->overflow = 1;
+      if (j->out) {
+        j->out[(c * B + b) * 2] = (int32_t)sre;
+        j->out[(c * B + b) * 2 + 1] = (int32_t)sim;
+      }
+      if (j->out64) {
+        j->out64[(c * B + b) * 2] = sre;
+        j->out64[(c * B + b) * 2 + 1] = sim;
+      }
+    }
+  }
+  return NULL;
+}
+
+/*
+ * Correlate packed voltages[n_chan][n_time][n_inputs].
+ * out   (may be NULL): int32 [n_chan][N(N+1)/2][2]
+ * out64 (may be NULL): int64 [n_chan][N(N+1)/2][2]
+ * Returns 0; 1 bad argument; 2 out of memory; 3 a visibility exceeds the
+ * int32 range (the int64 values in out64 are still exact).
+ */
+int oracle_correlate(const uint8_t *volt, int sample_bits, int n_inputs, int n_chan, int n_time,
+                     int32_t *out, int64_t *out64, int n_threads) {
+  if (!volt || n_inputs < 0 || n_chan < 0 || n_time < 0) return 1;
+  if (sample_bits != 4 && sample_bits != 8) return 1;
+  const int64_t N = n_inputs, T = n_time, C = n_chan;
+  const int64_t n = C * T * N;
+  int32_t *re_ct = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  int32_t *im_ct = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  int32_t *re = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  int32_t *im = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+  if (!re_ct || !im_ct || !re || !im) {
+    free(re_ct); free(im_ct); free(re); free(im);
+    return 2;
+  }
+  oracle_decode(volt, sample_bits, n, re_ct, im_ct);
+  /* [chan][time][input] -> [chan][input][time] so each input's series is contiguous */
+  for (int64_t c = 0; c < C; ++c)
+    for (int64_t t = 0; t < T; ++t)
+      for (int64_t i = 0; i < N; ++i) {
+        re[(c * N + i) * T + t] = re_ct[(c * T + t) * N + i];
+        im[(c * N + i) * T + t] = im_ct[(c * T + t) * N + i];
+      }
+  free(re_ct);
+  free(im_ct);
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  corr_job jobs[256];
+  int rc = 0, started = 0;
+  for (int k = 0; k < n_threads; ++k) {
+    jobs[k] = (corr_job){re, im, n_inputs, n_chan, n_time, out, out64, k, n_threads, 0};
+    if (pthread_create(&th[k], NULL, corr_worker, &jobs[k]) != 0) { rc = 2; break; }
+    ++started;
+  }
+  for (int k = 0; k < started; ++k) {
+    pthread_join(th[k], NULL);
+    if (jobs[k].overflow) rc = rc ? rc : 3;
+  }
+  free(re);
+  free(im);
+  return rc;
+}
+
+/* ---- baseline triangle -------------------------------------------------- */
+
+int64_t oracle_n_baselines(int64_t n_inputs) { return n_inputs * (n_inputs + 1) / 2; }
+
+int64_t oracle_baseline_index(int64_t i, int64_t j) {
+  if (j < 0 || i < j) return -1;
+  return i * (i + 1) / 2 + j;
+}
+
+/* ---- calibration loss and gradient (FP64) ------------------------------- */
+
+/* complex helpers on (re, im) pairs */
+typedef struct { double re, im; } cplx;
+static cplx cmul(cplx a, cplx b) { return (cplx){a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+static cplx cconj(cplx a) { return (cplx){a.re, -a.im}; }
+static cplx csub(cplx a, cplx b) { return (cplx){a.re - b.re, a.im - b.im}; }
+static cplx cld(const double *p) { return (cplx){p[0], p[1]}; }
+
+/* R_ij for i > j at channel nu: g_i conj(g_j) M_ij - V_ij.  V, M: [chan][b][2]. */
+static cplx resid(const double *V, const double *M, const double *g, int64_t B, int64_t nu,
+                  int64_t i, int64_t j) {
+  const int64_t b = i * (i + 1) / 2 + j;
+  cplx gi = cld(g + 2 * i), gj = cld(g + 2 * j);
+  cplx m = cld(M + (nu * B + b) * 2), v = cld(V + (nu * B + b) * 2);
+  return csub(cmul(cmul(gi, cconj(gj)), m), v);
+}
+
+/* L(g) = sum_nu sum_{i>j} |R_ij,nu|^2.  Returns the loss. */
+double oracle_calib_loss(const double *V, const double *M, const double *g, int n_inputs,
+                         int n_chan) {
+  const int64_t N = n_inputs, B = N * (N + 1) / 2;
+  double L = 0.0;
+  for (int64_t nu = 0; nu < n_chan; ++nu)
+    for (int64_t i = 0; i < N; ++i)
+      for (int64_t j = 0; j < i; ++j) {
+        cplx r = resid(V, M, g, B, nu, i, j);
+        L += r.re * r.re + r.im * r.im;
+      }
+  return L;
+}
+
+typedef struct {
+  const double *V, *M, *g;
+  int n_inputs, n_chan;
+  double *grad;
+  int tid, n_threads;
+} grad_job;
+
+static void *grad_worker(void *arg) {
+  grad_job *q = (grad_job *)arg;
+  const int64_t N = q->n_inputs, B = N * (N + 1) / 2;
+  for (int64_t k = q->tid; k < N; k += q->n_threads) {
+    cplx acc = {0.0, 0.0};
+    for (int64_t nu = 0; nu < q->n_chan; ++nu)
+      for (int64_t j = 0; j < N; ++j) {
+        if (j == k) continue;
+        cplx r_kj, m_kj;
+        if (k > j) {
+          r_kj = resid(q->V, q->M, q->g, B, nu, k, j);
+          m_kj = cld(q->M + (nu * B + k * (k + 1) / 2 + j) * 2);
+        } else {
+          r_kj = cconj(resid(q->V, q->M, q->g, B, nu, j, k));
+          m_kj = cconj(cld(q->M + (nu * B + j * (j + 1) / 2 + k) * 2));
+        }
+        cplx t = cmul(cmul(r_kj, cld(q->g + 2 * j)), cconj(m_kj));
+        acc.re += t.re;
+        acc.im += t.im;
+      }
+    q->grad[2 * k] = 2.0 * acc.re;
+    q->grad[2 * k + 1] = 2.0 * acc.im;
+  }
+  return NULL;
+}
+
+/* grad[k] = 2 dL/d conj(g_k), [n_inputs][2].  Returns 0, or 2 on thread failure. */
+int oracle_calib_grad(const double *V, const double *M, const double *g, int n_inputs, int n_chan,
+                      double *grad, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  grad_job jobs[256];
+  int started = 0, rc = 0;
+  for (int k = 0; k < n_threads; ++k) {
+    jobs[k] = (grad_job){V, M, g, n_inputs, n_chan, grad, k, n_threads};
+    if (pthread_create(&th[k], NULL, grad_worker, &jobs[k]) != 0) { rc = 2; break; }
+    ++started;
+  }
+  for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+  return rc;
+}

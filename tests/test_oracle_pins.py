@@ -1,0 +1,283 @@
+"""Pins for the CPU oracle: checks against facts fixed by the mathematics of
+V_ij = sum_t x_i(t) conj(x_j(t)) (paper Sec. 2: all antenna pairs are
+cross-correlated per channel and the products integrated) and of the
+least-squares gain loss (Sec. 2: complex gain of each element), never
+against the oracle's own formula retyped.
+
+The test packs its own samples (two's complement nibbles / int8 bytes), so a
+decoding mistake in the oracle fails the brute-force comparison.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# helpers (test-side encoding, independent of the oracle)
+# ---------------------------------------------------------------------------
+def pack(re: np.ndarray, im: np.ndarray, bits: int) -> np.ndarray:
+    """re, im int arrays [C, T, N] -> packed bytes [C, T, N*bps]."""
+    re = np.asarray(re, np.int64)
+    im = np.asarray(im, np.int64)
+    if bits == 4:
+        return ((re & 0xF) | ((im & 0xF) << 4)).astype(np.uint8)
+    out = np.empty(re.shape[:-1] + (2 * re.shape[-1],), np.uint8)
+    out[..., 0::2] = (re & 0xFF).astype(np.uint8)
+    out[..., 1::2] = (im & 0xFF).astype(np.uint8)
+    return out
+
+
+def tri(full: np.ndarray) -> np.ndarray:
+    """[C, N, N] complex -> [C, N(N+1)/2, 2] int64 lower triangle, row-major."""
+    C, N, _ = full.shape
+    ii, jj = np.tril_indices(N)
+    v = full[:, ii, jj]
+    return np.stack([np.rint(v.real), np.rint(v.imag)], axis=-1).astype(np.int64)
+
+
+def brute(re, im):
+    """Library matmul on complex128 (exact for these small integers)."""
+    x = np.asarray(re, np.float64) + 1j * np.asarray(im, np.float64)  # [C, T, N]
+    full = np.einsum("cti,ctj->cij", x, np.conj(x))
+    return tri(full)
+
+
+def run_oracle(re, im, bits):
+    C, T, N = re.shape
+    _, o64 = oracle.correlate(pack(re, im, bits), bits, N, C, T, want64=True)
+    return o64
+
+
+def rand_samples(rng, C, T, N, bits):
+    m = 7 if bits == 4 else 127
+    return rng.integers(-m, m + 1, (C, T, N)), rng.integers(-m, m + 1, (C, T, N))
+
+
+# ---------------------------------------------------------------------------
+# correlation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("bits", [4, 8])
+@pytest.mark.parametrize("N,T,C", [(1, 1, 1), (2, 7, 1), (3, 8, 3), (17, 33, 2), (5, 1, 3)])
+def test_brute_force(bits, N, T, C):
+    rng = np.random.default_rng(1000 * N + 10 * T + C + bits)
+    re, im = rand_samples(rng, C, T, N, bits)
+    np.testing.assert_array_equal(run_oracle(re, im, bits), brute(re, im))
+
+
+def test_golden_conjugation_side():
+    """Two inputs, one sample: x0 = 1, x1 = i.  V_10 = x1 conj(x0) = i."""
+    g = np.loadtxt(os.path.join(GOLDEN, "conj_side.txt"), dtype=np.int64)
+    re = np.array([[[1, 0]]])
+    im = np.array([[[0, 1]]])
+    np.testing.assert_array_equal(run_oracle(re, im, 8)[0], g)
+    np.testing.assert_array_equal(run_oracle(re, im, 4)[0], g)
+
+
+def test_golden_decode():
+    """Nibble/byte decoding of hand-written packed values."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "decode4.txt"), dtype=np.int64)
+    re, im = oracle.decode(rows[:, 0].astype(np.uint8), 4)
+    np.testing.assert_array_equal(re, rows[:, 1])
+    np.testing.assert_array_equal(im, rows[:, 2])
+    rows8 = np.loadtxt(os.path.join(GOLDEN, "decode8.txt"), dtype=np.int64)
+    raw = np.stack([rows8[:, 0], rows8[:, 1]], 1).astype(np.uint8).ravel()
+    re, im = oracle.decode(raw, 8)
+    np.testing.assert_array_equal(re, rows8[:, 2])
+    np.testing.assert_array_equal(im, rows8[:, 3])
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+def test_hermitian_by_reversal(bits):
+    """Reversing the input order maps V_ij to V_{N-1-j, N-1-i}^* (Hermitian)."""
+    rng = np.random.default_rng(7 + bits)
+    re, im = rand_samples(rng, 2, 19, 9, bits)
+    a = run_oracle(re, im, bits)
+    b = run_oracle(re[..., ::-1], im[..., ::-1], bits)
+    N = 9
+    for i in range(N):
+        for j in range(i + 1):
+            ba = oracle.baseline_index(i, j)
+            bb = oracle.baseline_index(N - 1 - j, N - 1 - i)
+            np.testing.assert_array_equal(b[:, bb, 0], a[:, ba, 0])
+            np.testing.assert_array_equal(b[:, bb, 1], -a[:, ba, 1])
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+def test_autos_are_power(bits):
+    rng = np.random.default_rng(11)
+    re, im = rand_samples(rng, 3, 25, 6, bits)
+    o = run_oracle(re, im, bits)
+    power = (re.astype(np.int64) ** 2 + im.astype(np.int64) ** 2).sum(axis=1)  # [C, N]
+    for i in range(6):
+        b = oracle.baseline_index(i, i)
+        np.testing.assert_array_equal(o[:, b, 1], 0)
+        np.testing.assert_array_equal(o[:, b, 0], power[:, i])
+        assert (o[:, b, 0] >= 0).all()
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+def test_phase_invariance(bits):
+    """x -> -x and x -> i x leave every V_ij unchanged."""
+    rng = np.random.default_rng(21)
+    re, im = rand_samples(rng, 2, 13, 7, bits)
+    a = run_oracle(re, im, bits)
+    np.testing.assert_array_equal(run_oracle(-re, -im, bits), a)
+    np.testing.assert_array_equal(run_oracle(-im, re, bits), a)  # i*(re + i im) = -im + i re
+
+
+def test_zero_padding_changes_nothing():
+    rng = np.random.default_rng(5)
+    re, im = rand_samples(rng, 2, 10, 5, 4)
+    a = run_oracle(re, im, 4)
+    rp = np.zeros((2, 16, 8), np.int64)
+    ip = np.zeros((2, 16, 8), np.int64)
+    rp[:, :10, :5] = re
+    ip[:, :10, :5] = im
+    b = run_oracle(rp, ip, 4)
+    for i in range(5):
+        for j in range(i + 1):
+            np.testing.assert_array_equal(b[:, oracle.baseline_index(i, j)], a[:, oracle.baseline_index(i, j)])
+    for i in range(5, 8):
+        for j in range(i + 1):
+            np.testing.assert_array_equal(b[:, oracle.baseline_index(i, j)], 0)
+
+
+@pytest.mark.parametrize("T", [1, 2, 5, 64, 1001])
+def test_quarter_rate_tone_closed_form(T):
+    """x_i(t) = c_i i^t gives V_ij = T c_i conj(c_j) exactly (|i^t| = 1)."""
+    rng = np.random.default_rng(T)
+    N = 6
+    c = rng.integers(-7, 8, (N, 2))
+    spec = synth.Spec("q", N, 1, T, 4, seed=0, kind=synth.SYNTH_QUARTER, ci=c)
+    v = synth.fill_host(spec)
+    o = oracle.correlate(v, 4, N, 1, T)
+    cc = c[:, 0] + 1j * c[:, 1]
+    for i in range(N):
+        for j in range(i + 1):
+            e = T * cc[i] * np.conj(cc[j])
+            b = oracle.baseline_index(i, j)
+            assert o[0, b, 0] == int(e.real) and o[0, b, 1] == int(e.imag)
+
+
+def test_int32_bound_special_case():
+    """All samples (127, 127): V_ii = 32258 T.  T = 66572 is the largest
+    integration that fits int32 (2,147,479,576); T = 66573 overflows."""
+    T = 66572
+    re = np.full((1, T, 2), 127)
+    im = np.full((1, T, 2), 127)
+    o = oracle.correlate(pack(re, im, 8), 8, 2, 1, T)
+    assert o[0, 0, 0] == 2_147_479_576 == 32258 * T
+    assert o[0, 1, 0] == 2_147_479_576 and o[0, 1, 1] == 0
+    re = np.full((1, T + 1, 1), 127)
+    with pytest.raises(OverflowError):
+        oracle.correlate(pack(re, re, 8), 8, 1, 1, T + 1)
+
+
+def test_baseline_helpers():
+    assert oracle.n_baselines(512) == 131_328  # ~130,000 baseline pairs (Sec. 2)
+    assert oracle.n_baselines(1024) == 524_800
+    assert oracle.baseline_index(0, 0) == 0
+    assert oracle.baseline_index(3, 1) == 7
+    assert oracle.baseline_index(1, 2) == -1
+    seen = [oracle.baseline_index(i, j) for i in range(20) for j in range(i + 1)]
+    assert seen == list(range(oracle.n_baselines(20)))
+
+
+# ---------------------------------------------------------------------------
+# calibration loss / gradient
+# ---------------------------------------------------------------------------
+def rand_cal(rng, N, C, scale=1.0):
+    B = N * (N + 1) // 2
+    V = (rng.standard_normal((C, B)) + 1j * rng.standard_normal((C, B))) * scale
+    M = rng.standard_normal((C, B)) + 1j * rng.standard_normal((C, B))
+    g = rng.uniform(0.8, 1.2, N) * np.exp(1j * rng.uniform(0, 2 * np.pi, N))
+    return V, M, g
+
+
+def test_calib_golden_two_inputs():
+    """N = 2, one channel, g = (1, i), M_10 = 1, V_10 = 0: R_10 = i, L = 1,
+    grad = (2, 2i) (hand derivation: L = |g0|^2 |g1|^2)."""
+    V = np.zeros((1, 3), complex)
+    M = np.zeros((1, 3), complex)
+    M[0, 1] = 1.0
+    g = np.array([1.0, 1j])
+    assert oracle.calib_loss(V, M, g) == pytest.approx(1.0, abs=1e-15)
+    np.testing.assert_allclose(oracle.calib_grad(V, M, g), [2.0, 2j], atol=1e-14)
+
+
+def test_calib_zero_at_truth():
+    rng = np.random.default_rng(3)
+    N, C = 9, 4
+    _, M, g = rand_cal(rng, N, C)
+    ii, jj = np.tril_indices(N)
+    V = g[ii] * np.conj(g[jj]) * M
+    V[:, ii == jj] = 17.0  # autos carry weight 0
+    assert oracle.calib_loss(V, M, g) == pytest.approx(0.0, abs=1e-20)
+    np.testing.assert_allclose(oracle.calib_grad(V, M, g), 0.0, atol=1e-12)
+
+
+def test_calib_against_autograd():
+    """Gradient convention pinned by torch autograd on a complex128 loss."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    N, C = 7, 3
+    V, M, g = rand_cal(rng, N, C)
+    Vf = np.zeros((C, N, N), complex)
+    Mf = np.zeros((C, N, N), complex)
+    ii, jj = np.tril_indices(N)
+    Vf[:, ii, jj] = V
+    Mf[:, ii, jj] = M
+    gt = torch.tensor(g, dtype=torch.complex128, requires_grad=True)
+    Gm = gt[:, None] * torch.conj(gt)[None, :]
+    R = Gm[None] * torch.tensor(Mf) - torch.tensor(Vf)
+    mask = torch.tril(torch.ones(N, N, dtype=torch.bool), diagonal=-1)
+    L = (R.abs() ** 2)[:, mask].sum()
+    L.backward()
+    assert oracle.calib_loss(V, M, g) == pytest.approx(L.item(), rel=1e-12)
+    np.testing.assert_allclose(oracle.calib_grad(V, M, g), gt.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_calib_central_differences():
+    rng = np.random.default_rng(5)
+    N, C = 8, 3
+    V, M, g = rand_cal(rng, N, C)
+    grad = oracle.calib_grad(V, M, g)
+    h = 1e-3
+    for k in range(N):
+        for part, unit in ((0, 1.0), (1, 1j)):
+            gp = g.copy()
+            gm = g.copy()
+            gp[k] += h * unit
+            gm[k] -= h * unit
+            fd = (oracle.calib_loss(V, M, gp) - oracle.calib_loss(V, M, gm)) / (2 * h)
+            an = grad[k].real if part == 0 else grad[k].imag
+            assert fd == pytest.approx(an, rel=1e-5, abs=1e-6)
+
+
+def test_calib_phase_and_radial_identities():
+    """L(g e^{i th}) is constant -> sum Im(conj(g_k) grad_k) = 0.
+    L(a g) = a^4 A - 2 a^2 B + C (quartic, even) -> d/da at a=1 equals
+    Re sum conj(g_k) grad_k, and L(0) = sum_{i>j} |V|^2."""
+    rng = np.random.default_rng(6)
+    N, C = 10, 2
+    V, M, g = rand_cal(rng, N, C)
+    grad = oracle.calib_grad(V, M, g)
+    s = np.sum(np.conj(g) * grad)
+    assert abs(s.imag) <= 1e-10 * np.abs(np.conj(g) * grad).sum()
+    L = oracle.calib_loss(V, M, g)
+    assert oracle.calib_loss(V, M, g * np.exp(0.7j)) == pytest.approx(L, rel=1e-12)
+    alphas = np.array([0.0, 0.5, 0.9, 1.0, 1.3, 2.0])
+    Ls = np.array([oracle.calib_loss(V, M, a * g) for a in alphas])
+    coef = np.polyfit(alphas, Ls, 4)  # a^4 .. a^0
+    assert abs(coef[1]) < 1e-8 * Ls.max() and abs(coef[3]) < 1e-8 * Ls.max()
+    np.testing.assert_allclose(np.polyval(coef, alphas), Ls, rtol=1e-10)
+    dL = 4 * coef[0] + 2 * coef[2]
+    assert s.real == pytest.approx(dL, rel=1e-8)
+    ii, jj = np.tril_indices(N)
+    assert Ls[0] == pytest.approx(float((np.abs(V[:, ii != jj]) ** 2).sum()), rel=1e-12)
