@@ -1,0 +1,200 @@
+/*
+ * mwax.h -- C ABI of the GB300 X-engine correlator library (libmwax.so).
+ *
+ * The operation (paper Sec. 2): a correlator cross-correlates the
+ * channelised voltages of every antenna input pair -- for the MWA, 512
+ * antennas giving ~130,000 baselines, 768 channels and 4 polarisation
+ * products -- and the products are integrated before calibration and
+ * imaging.  For every fine channel c and input pair i >= j (the lower
+ * triangle, autocorrelations included) this library computes
+ *
+ *     V_ij(c) = sum_{t < T} x_i(c, t) * conj(x_j(c, t))
+ *     Re V_ij = sum_t xr_i xr_j + xi_i xi_j,   Im V_ij = sum_t xi_i xr_j - xr_i xi_j
+ *
+ * exactly, in integer arithmetic, and the gain-calibration loss that consumes
+ * visibilities (Sec. 2: complex antenna gains by least squares):
+ *
+ *     L(g) = sum_c sum_{i > j} | g_i conj(g_j) M_ij(c) - V_ij(c) |^2
+ *
+ * with its gradient 2 dL/d conj(g) (PyTorch's convention for a complex
+ * parameter: dL/dRe g + i dL/dIm g).
+ *
+ * Data layouts (all little-endian, all device memory unless stated):
+ *   voltages  [n_chan][n_time][n_inputs] packed complex samples:
+ *             sample_bits 4: one byte, low nibble = re, high nibble = im,
+ *                            two's complement, values in [-7, 7];
+ *             sample_bits 8: two bytes, re then im, int8 in [-127, 127].
+ *             (-8 and -128 are outside the supported range: their negation
+ *             does not fit the sample width.)
+ *   input i   = 2 * tile + pol (pol 0 = X, 1 = Y); the four polarisation
+ *             products of a tile pair are the four input pairs it contains.
+ *   baseline  b = i (i + 1) / 2 + j for i >= j (row-major lower triangle).
+ *   out       [n_chan][N(N+1)/2][2] int32 (re, im) for MWAX_KIND_EXACT,
+ *             float32 (re, im) for MWAX_KIND_FP16.
+ *   V, M      [n_chan][N(N+1)/2][2] float32 (re, im); g, grad [N][2] float32.
+ *
+ * Conventions: every function returns an mwax_status and never aborts or
+ * exits.  Device work is asynchronous on the stream given to the plan (or to
+ * the call); results are valid once that stream is synchronised.  The caller
+ * owns every buffer it passes; a plan owns its scratch, its work list, its
+ * device status word and its CUDA graph, and releases them in mwax_destroy.
+ */
+#ifndef MWAX_H
+#define MWAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MWAX_OK = 0,
+  MWAX_ERR_INVALID_ARG = 1,     /* null pointer, bad size, host pointer where device is required */
+  MWAX_ERR_SHAPE_MISMATCH = 2,  /* call shape differs from the planned shape                  */
+  MWAX_ERR_OVERFLOW_BOUND = 3,  /* n_time * 2 * max|sample|^2 exceeds INT32_MAX              */
+  MWAX_ERR_UNSUPPORTED = 4,     /* device is not sm_103 / option not available             */
+  MWAX_ERR_OOM = 5,             /* a plan allocation failed                                 */
+  MWAX_ERR_CUDA = 6,            /* a CUDA runtime call failed                               */
+  MWAX_ERR_TIMEOUT = 7          /* a bounded device-side wait gave up (see mwax_plan_status) */
+} mwax_status;
+
+typedef enum {
+  MWAX_KIND_EXACT = 0, /* integer-exact visibilities, int32 output                     */
+  MWAX_KIND_FP16 = 1   /* 8-bit samples only: FP16 inputs, FP32 accumulation, no integer
+                          flush; float32 output (reported with its error vs FP64)     */
+} mwax_kind;
+
+typedef enum {
+  MWAX_ENGINE_TENSOR = 0, /* unpack + tcgen05 tensor-core correlator + dump (default)   */
+  MWAX_ENGINE_PLAIN = 1   /* CUDA-core int32 correlator, one launch per channel         */
+} mwax_engine;
+
+/* One correlation job.  Zero-initialise, then set the shape fields; the
+ * tuning fields may stay 0 (= chosen by the plan / autotuner). */
+typedef struct {
+  int32_t n_inputs;    /* N >= 1                                               */
+  int32_t n_chan;      /* C >= 1                                               */
+  int32_t n_time;      /* T >= 1 samples per integration                       */
+  int32_t sample_bits; /* 4 or 8                                               */
+  int32_t kind;        /* mwax_kind                                            */
+  int32_t engine;      /* mwax_engine                                          */
+  int32_t flush_blocks;    /* tuning: K-blocks per exact FP32 segment (0 = largest safe) */
+  int32_t chan_group;      /* tuning: channels unpacked per pass (0 = auto)              */
+  int32_t reserved[8];     /* must be zero                                                */
+} mwax_job;
+
+/* Read-only description of a plan's choices. */
+typedef struct {
+  int32_t n_jobs;
+  int32_t engine;
+  int32_t samples_per_block; /* time samples per 128-byte operand row block           */
+  int32_t flush_blocks;      /* K-blocks accumulated in FP32 before the int32 flush   */
+  int32_t chan_group;        /* channels per unpack/correlate pass                     */
+  int32_t grid;              /* persistent CTAs of the correlate kernel                */
+  int64_t scratch_bytes;     /* device scratch owned by the plan                       */
+  int64_t work_items;        /* (job, channel, tile pair) items per call               */
+} mwax_plan_info;
+
+typedef struct mwax_plan_s *mwax_plan_t;
+
+/* ---- plans -------------------------------------------------------------- */
+
+/* Create a plan for one job on `stream` (0 = the legacy default stream).
+ * Checks the shape, the int32 bound (MWAX_ERR_OVERFLOW_BOUND when
+ * n_time * 2 * max^2 > INT32_MAX, max = 7 or 127), the device
+ * (MWAX_ERR_UNSUPPORTED unless compute capability 10.3), and allocates the
+ * plan's scratch on the current device.  *plan is NULL on failure. */
+mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t stream);
+
+/* Plan several jobs (uneven N, C, T) that are correlated together by one
+ * persistent launch per call, captured in a CUDA graph on first use. */
+mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
+                            cudaStream_t stream);
+
+/* Release everything the plan owns.  NULL is accepted. */
+mwax_status mwax_destroy(mwax_plan_t plan);
+
+mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info);
+
+/* Device time of the kernels a plan launched while timing was enabled. */
+typedef struct {
+  double unpack_ms;            /* summed device time of unpack launches            */
+  double correlate_ms;         /* summed device time of correlate launches         */
+  int64_t unpack_launches;
+  int64_t correlate_launches;  /* tensor-core launches, or plain per-channel ones  */
+} mwax_timing;
+
+/* Record (enable != 0) or stop recording CUDA events on the plan's stream
+ * around every kernel it launches.  Batch plans time their whole graph
+ * launch as one correlate launch. */
+mwax_status mwax_plan_set_timing(mwax_plan_t plan, int enable);
+
+/* Sums since the previous call; synchronises the plan's stream, then resets. */
+mwax_status mwax_plan_get_timing(mwax_plan_t plan, mwax_timing *timing);
+
+/* Device status word of the plan's last calls: MWAX_OK, or MWAX_ERR_TIMEOUT
+ * if a bounded device wait gave up (the output is then invalid).  Reading it
+ * synchronises the plan's stream; the word is cleared afterwards. */
+mwax_status mwax_plan_status(mwax_plan_t plan);
+
+/* ---- correlation -------------------------------------------------------- */
+
+/* Correlate one integration of a single-job plan.
+ * voltages: device, [n_chan][n_time][n_inputs] packed samples (see above).
+ * out:      device, [n_chan][N(N+1)/2][2], int32 (EXACT) or float32 (FP16).
+ * The shape arguments must equal the planned ones (MWAX_ERR_SHAPE_MISMATCH). */
+mwax_status mwax_correlate(mwax_plan_t plan, const void *voltages, int n_inputs, int n_chan,
+                           int n_time, void *out);
+
+/* Correlate every job of a batch plan: voltages[k] / out[k] are device
+ * pointers for job k, passed in host arrays of n_jobs entries. */
+mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages,
+                                 void *const *out);
+
+/* Same as mwax_correlate with HOST buffers (pinned or pageable): channel
+ * groups are copied in, correlated and copied out with copies overlapping
+ * compute on the plan's stream and an internal copy stream.  Returns after
+ * the output is complete in host memory. */
+mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int n_inputs,
+                                int n_chan, int n_time, void *out_host);
+
+/* ---- baseline triangle helpers (host) ------------------------------------ */
+
+/* N(N+1)/2, or -1 for n_inputs < 0. */
+int64_t mwax_n_baselines(int n_inputs);
+/* i(i+1)/2 + j for i >= j >= 0; -1 otherwise. */
+int64_t mwax_baseline_index(int i, int j);
+/* Inverse of mwax_baseline_index for b >= 0. */
+mwax_status mwax_baseline_pair(int64_t b, int *i, int *j);
+/* Largest n_time whose visibilities fit int32 exactly: floor((2^31-1) / (2 max^2)). */
+int64_t mwax_max_n_time(int sample_bits);
+const char *mwax_status_string(mwax_status s);
+
+/* ---- gain calibration (FP32) ------------------------------------------- */
+
+/* Bytes of device workspace the calibration calls need for this shape. */
+int64_t mwax_calib_workspace_bytes(int n_inputs, int n_chan);
+
+/* L(g) into *loss (device float).  Deterministic: fixed-order reductions,
+ * no floating-point atomics.  workspace: device, >= mwax_calib_workspace_bytes. */
+mwax_status mwax_calib_loss(const float *V, const float *M, const float *g, int n_inputs,
+                            int n_chan, void *workspace, float *loss, cudaStream_t stream);
+
+/* grad[k] = 2 dL/d conj(g_k) into grad (device, [n_inputs][2]). */
+mwax_status mwax_calib_grad(const float *V, const float *M, const float *g, int n_inputs,
+                            int n_chan, void *workspace, float *grad, cudaStream_t stream);
+
+/* Loss and gradient from one pass over V and M. */
+mwax_status mwax_calib_loss_grad(const float *V, const float *M, const float *g, int n_inputs,
+                                 int n_chan, void *workspace, float *loss, float *grad,
+                                 cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MWAX_H */

@@ -1,0 +1,372 @@
+"""GB300-native MWA X-engine correlator: thin Python binding of libmwax.so.
+
+The work is the X-engine of the real-time system described in "GPUs for data
+processing in the MWA" (Sec. 2): every pair of channelised antenna inputs is
+cross-correlated per fine channel and integrated, V_ij = sum_t x_i conj(x_j),
+followed by the gain-calibration loss that consumes the visibilities.  Every
+step runs in the library's CUDA kernels; this module only marshals
+arguments (device pointers from torch tensors, the current CUDA stream) and
+raises on a non-OK status.  There is no CPU fallback: without the built
+library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+MWAX_OK = 0
+STATUS = {0: "MWAX_OK", 1: "MWAX_ERR_INVALID_ARG", 2: "MWAX_ERR_SHAPE_MISMATCH",
+          3: "MWAX_ERR_OVERFLOW_BOUND", 4: "MWAX_ERR_UNSUPPORTED", 5: "MWAX_ERR_OOM",
+          6: "MWAX_ERR_CUDA", 7: "MWAX_ERR_TIMEOUT"}
+KIND_EXACT, KIND_FP16 = 0, 1
+ENGINE_TENSOR, ENGINE_PLAIN = 0, 1
+
+
+class MwaxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_status_string(status)})")
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int32), ("n_chan", ctypes.c_int32),
+                ("n_time", ctypes.c_int32), ("sample_bits", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("flush_blocks", ctypes.c_int32), ("chan_group", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_jobs", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("samples_per_block", ctypes.c_int32), ("flush_blocks", ctypes.c_int32),
+                ("chan_group", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("scratch_bytes", ctypes.c_int64), ("work_items", ctypes.c_int64)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("unpack_ms", ctypes.c_double), ("correlate_ms", ctypes.c_double),
+                ("unpack_launches", ctypes.c_int64), ("correlate_launches", ctypes.c_int64)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+# name -> (restype, argtypes); the exported C ABI of include/mwax.h
+SIGNATURES = {
+    "mwax_plan": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Job), _P]),
+    "mwax_plan_batch": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Job), _I, _P]),
+    "mwax_destroy": (_I, [_P]),
+    "mwax_plan_get_info": (_I, [_P, ctypes.POINTER(PlanInfo)]),
+    "mwax_plan_status": (_I, [_P]),
+    "mwax_plan_set_timing": (_I, [_P, _I]),
+    "mwax_plan_get_timing": (_I, [_P, ctypes.POINTER(Timing)]),
+    "mwax_correlate": (_I, [_P, _P, _I, _I, _I, _P]),
+    "mwax_correlate_batch": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "mwax_correlate_host": (_I, [_P, _P, _I, _I, _I, _P]),
+    "mwax_n_baselines": (_I64, [_I]),
+    "mwax_baseline_index": (_I64, [_I, _I]),
+    "mwax_baseline_pair": (_I, [_I64, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mwax_max_n_time": (_I64, [_I]),
+    "mwax_status_string": (ctypes.c_char_p, [_I]),
+    "mwax_calib_workspace_bytes": (_I64, [_I, _I]),
+    "mwax_calib_loss": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "mwax_calib_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "mwax_calib_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+}
+
+
+def ensure_built() -> str:
+    """Build libmwax.so for sm_103a if it is missing or stale."""
+    return _build.build()
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built "
+                               "(paper_0902_0915_gb300.ensure_built()); there is no fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _status_string(s: int) -> str:
+    try:
+        return lib().mwax_status_string(s).decode()
+    except Exception:
+        return "?"
+
+
+def _check(status: int, where: str) -> None:
+    if status != MWAX_OK:
+        raise MwaxError(status, where)
+
+
+# ---- baseline helpers --------------------------------------------------------
+def n_baselines(n_inputs: int) -> int:
+    return int(lib().mwax_n_baselines(n_inputs))
+
+
+def baseline_index(i: int, j: int) -> int:
+    return int(lib().mwax_baseline_index(i, j))
+
+
+def baseline_pair(b: int):
+    i, j = _I(), _I()
+    _check(lib().mwax_baseline_pair(b, ctypes.byref(i), ctypes.byref(j)), "mwax_baseline_pair")
+    return i.value, j.value
+
+
+def max_n_time(sample_bits: int) -> int:
+    return int(lib().mwax_max_n_time(sample_bits))
+
+
+# ---- torch plumbing ---------------------------------------------------------------
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _job(n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, engine=ENGINE_TENSOR,
+         flush_blocks=0, chan_group=0) -> Job:
+    j = Job()
+    j.n_inputs, j.n_chan, j.n_time, j.sample_bits = n_inputs, n_chan, n_time, sample_bits
+    j.kind, j.engine, j.flush_blocks, j.chan_group = kind, engine, flush_blocks, chan_group
+    return j
+
+
+class Plan:
+    """A correlation plan for one job (see include/mwax.h: mwax_plan).
+
+    voltages: CUDA uint8 tensor holding [n_chan][n_time][n_inputs] packed
+    samples (1 byte per complex sample for 4-bit, 2 bytes for 8-bit).
+    Output: int32 (exact) or float32 (FP16 kind) tensor
+    [n_chan, N(N+1)/2, 2] (re, im)."""
+
+    def __init__(self, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,
+                 engine=ENGINE_TENSOR, flush_blocks=0, chan_group=0, stream=None):
+        self.job = _job(n_inputs, n_chan, n_time, sample_bits, kind, engine, flush_blocks, chan_group)
+        self.shape = (n_inputs, n_chan, n_time)
+        self.sample_bits, self.kind, self.engine = sample_bits, kind, engine
+        self._h = _P()
+        self.stream = stream if stream is not None else _torch().cuda.current_stream()
+        _check(lib().mwax_plan(ctypes.byref(self._h), ctypes.byref(self.job), self.stream.cuda_stream),
+               "mwax_plan")
+
+    @property
+    def n_bl(self) -> int:
+        return self.shape[0] * (self.shape[0] + 1) // 2
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check(lib().mwax_plan_get_info(self._h, ctypes.byref(inf)), "mwax_plan_get_info")
+        return inf
+
+    def empty_out(self, device=None):
+        torch = _torch()
+        dt = torch.int32 if self.kind == KIND_EXACT else torch.float32
+        return torch.empty((self.shape[1], self.n_bl, 2), dtype=dt,
+                           device=device or torch.device("cuda", torch.cuda.current_device()))
+
+    def correlate(self, voltages, out=None):
+        """Asynchronous on the plan's stream; returns ``out``."""
+        torch = _torch()
+        n, c, t = self.shape
+        bps = 1 if self.sample_bits == 4 else 2
+        if voltages.dtype != torch.uint8 or not voltages.is_cuda or not voltages.is_contiguous():
+            raise ValueError("voltages must be a contiguous CUDA uint8 tensor")
+        if voltages.numel() != n * c * t * bps:
+            raise ValueError("voltages size does not match the plan shape")
+        if out is None:
+            out = self.empty_out(voltages.device)
+        _check(lib().mwax_correlate(self._h, voltages.data_ptr(), n, c, t, out.data_ptr()),
+               "mwax_correlate")
+        return out
+
+    def correlate_host(self, voltages_host, out_host):
+        """Host buffers (numpy or CPU tensors, ideally pinned); synchronous."""
+        n, c, t = self.shape
+        vp = voltages_host.ctypes.data if hasattr(voltages_host, "ctypes") else voltages_host.data_ptr()
+        op = out_host.ctypes.data if hasattr(out_host, "ctypes") else out_host.data_ptr()
+        _check(lib().mwax_correlate_host(self._h, vp, n, c, t, op), "mwax_correlate_host")
+        return out_host
+
+    def status(self) -> int:
+        """Device status word of the last calls (synchronises the stream)."""
+        return int(lib().mwax_plan_status(self._h))
+
+    def set_timing(self, on: bool = True) -> None:
+        _check(lib().mwax_plan_set_timing(self._h, 1 if on else 0), "mwax_plan_set_timing")
+
+    def timing(self) -> Timing:
+        t = Timing()
+        _check(lib().mwax_plan_get_timing(self._h, ctypes.byref(t)), "mwax_plan_get_timing")
+        return t
+
+    def close(self):
+        if self._h:
+            lib().mwax_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """Several uneven jobs correlated by one persistent launch per call,
+    replayed from a CUDA graph (see include/mwax.h: mwax_plan_batch)."""
+
+    def __init__(self, jobs, sample_bits=4, kind=KIND_EXACT, stream=None):
+        self.shapes = [tuple(j) for j in jobs]
+        self.sample_bits, self.kind = sample_bits, kind
+        arr = (Job * len(jobs))(*[_job(n, c, t, sample_bits, kind) for (n, c, t) in jobs])
+        self._h = _P()
+        self.stream = stream if stream is not None else _torch().cuda.current_stream()
+        _check(lib().mwax_plan_batch(ctypes.byref(self._h), arr, len(jobs), self.stream.cuda_stream),
+               "mwax_plan_batch")
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check(lib().mwax_plan_get_info(self._h, ctypes.byref(inf)), "mwax_plan_get_info")
+        return inf
+
+    def empty_outs(self, device=None):
+        torch = _torch()
+        dt = torch.int32 if self.kind == KIND_EXACT else torch.float32
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        return [torch.empty((c, n * (n + 1) // 2, 2), dtype=dt, device=dev) for (n, c, t) in self.shapes]
+
+    def correlate(self, voltages, outs=None):
+        if outs is None:
+            outs = self.empty_outs(voltages[0].device)
+        k = len(self.shapes)
+        vin = (_P * k)(*[v.data_ptr() for v in voltages])
+        vout = (_P * k)(*[o.data_ptr() for o in outs])
+        _check(lib().mwax_correlate_batch(self._h, vin, vout), "mwax_correlate_batch")
+        return outs
+
+    def status(self) -> int:
+        return int(lib().mwax_plan_status(self._h))
+
+    def set_timing(self, on: bool = True) -> None:
+        _check(lib().mwax_plan_set_timing(self._h, 1 if on else 0), "mwax_plan_set_timing")
+
+    def timing(self) -> Timing:
+        t = Timing()
+        _check(lib().mwax_plan_get_timing(self._h, ctypes.byref(t)), "mwax_plan_get_timing")
+        return t
+
+    def close(self):
+        if self._h:
+            lib().mwax_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def correlate(voltages, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,
+              engine=ENGINE_TENSOR):
+    """One-shot convenience: plan, correlate, destroy (synchronises)."""
+    p = Plan(n_inputs, n_chan, n_time, sample_bits, kind, engine)
+    out = p.correlate(voltages)
+    st = p.status()
+    p.close()
+    _check(st, "correlate (device status)")
+    return out
+
+
+# ---- calibration ------------------------------------------------------------------
+def calib_workspace(n_inputs: int, n_chan: int, device=None):
+    torch = _torch()
+    nb = int(lib().mwax_calib_workspace_bytes(n_inputs, n_chan))
+    if nb < 0:
+        raise ValueError("invalid calibration shape")
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+def _f32_pairs(t):
+    torch = _torch()
+    if t.dtype == torch.complex64:
+        t = torch.view_as_real(t)
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("calibration tensors must be contiguous CUDA complex64/float32 pairs")
+    return t
+
+
+def calib_loss_grad(V, M, g, workspace=None, want_loss=True, want_grad=True):
+    """(loss float32 scalar tensor or None, grad complex64 [N] or None).
+    V, M: complex64 [n_chan, N(N+1)/2]; g: complex64 [N]."""
+    torch = _torch()
+    Vr, Mr, gr = _f32_pairs(V), _f32_pairs(M), _f32_pairs(g)
+    n = gr.shape[0]
+    c = Vr.shape[0]
+    if Vr.shape != (c, n * (n + 1) // 2, 2) or Mr.shape != Vr.shape:
+        raise ValueError("V, M must be [n_chan, N(N+1)/2] for N = len(g)")
+    ws = workspace if workspace is not None else calib_workspace(n, c, V.device)
+    loss = torch.empty((), dtype=torch.float32, device=V.device) if want_loss else None
+    grad = torch.empty((n, 2), dtype=torch.float32, device=V.device) if want_grad else None
+    _check(lib().mwax_calib_loss_grad(Vr.data_ptr(), Mr.data_ptr(), gr.data_ptr(), n, c,
+                                      ws.data_ptr(), loss.data_ptr() if want_loss else None,
+                                      grad.data_ptr() if want_grad else None,
+                                      _stream_handle()), "mwax_calib_loss_grad")
+    return loss, (torch.view_as_complex(grad) if want_grad else None)
+
+
+def _make_calib_function():
+    torch = _torch()
+
+    class CalibLoss(torch.autograd.Function):
+        """L(g) = sum_nu sum_{i>j} |g_i conj(g_j) M_ij - V_ij|^2 with the
+        hand-written forward and adjoint kernels; the gradient returned for
+        g is PyTorch's complex convention dL/dRe g + i dL/dIm g.  One kernel
+        pass computes both, the gradient is kept for backward."""
+
+        @staticmethod
+        def forward(ctx, g, V, M):
+            loss, grad = calib_loss_grad(V, M, g.detach().contiguous(), want_grad=g.requires_grad)
+            ctx.save_for_backward(grad if grad is not None else torch.empty(0, device=g.device))
+            return loss
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return grad * gout, None, None
+
+    return CalibLoss
+
+
+_calib_cls = None
+
+
+def calib_loss(g, V, M):
+    """Differentiable calibration loss (torch.autograd.Function)."""
+    global _calib_cls
+    if _calib_cls is None:
+        _calib_cls = _make_calib_function()
+    return _calib_cls.apply(g, V, M)

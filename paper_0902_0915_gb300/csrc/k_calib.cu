@@ -1,0 +1,273 @@
+// k_calib.cu -- direction-independent gain-calibration loss and its adjoint.
+//
+// Paper Sec. 2: the complex gain of each antenna element is estimated by a
+// large linear least-squares fit against catalogue sources; the visibility
+// data are measured against a model and each measurement constrains the
+// gains.  The loss consumed here is
+//     R_ij(nu) = g_i conj(g_j) M_ij(nu) - V_ij(nu)
+//     L(g)     = sum_nu sum_{i>j} |R_ij(nu)|^2          (autos carry weight 0)
+//     grad_k   = 2 dL/d conj(g_k) = 2 sum_nu sum_{j != k} R_kj g_j conj(M_kj)
+// with R, M extended to the upper triangle by Hermitian symmetry.  For one
+// stored pair (i > j) the two gradient terms are
+//     to k = i:  R_ij g_j conj(M_ij)
+//     to k = j:  conj(R_ij) g_i M_ij.
+//
+// Paper Sec. 3.2 replaces scatter with gather because the GPU of the time had
+// no floating-point atomic add; the same rule gives determinism here: each
+// CTA owns a 32x32 tile of input pairs for a fixed group of channels and
+// writes its row / column / loss partial sums to a workspace, and a second
+// kernel gathers them per input in a fixed order.  No atomics, FP32 only
+// (Kahan-compensated accumulation inside a thread, fixed trees across
+// threads).  One pass reads V and M once.
+#include "mwax_internal.h"
+
+namespace mwax {
+namespace {
+
+constexpr int kCT = 32;        // inputs per calibration tile side
+constexpr int kCalThreads = 256;
+constexpr int kMaxChanGroups = 8;
+
+struct Kahan {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+int chan_groups(int n_chan) { return n_chan < kMaxChanGroups ? n_chan : kMaxChanGroups; }
+
+__device__ __forceinline__ void tile_of(int p, int &I, int &J) {
+  int i = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= p) ++i;
+  while (i * (i + 1) / 2 > p) --i;
+  I = i;
+  J = p - i * (i + 1) / 2;
+}
+
+// grid: (tiles, channel groups).  Thread (ty, tx): column j = J*32 + tx,
+// rows i = I*32 + ty + 8m, m = 0..3.
+__global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
+    const float2 *__restrict__ V, const float2 *__restrict__ M, const float2 *__restrict__ g,
+    int N, int C, int n_cg, float *__restrict__ part_loss, float2 *__restrict__ part_row,
+    float2 *__restrict__ part_col) {
+  __shared__ float2 sg_i[kCT], sg_j[kCT];
+  __shared__ float2 scol[8][kCT];
+  __shared__ float sloss[kCalThreads / 32];
+  const int tile = blockIdx.x, cg = blockIdx.y;
+  int I, J;
+  tile_of(tile, I, J);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x < kCT) {
+    const int i = I * kCT + threadIdx.x, j = J * kCT + threadIdx.x;
+    sg_i[threadIdx.x] = i < N ? g[i] : make_float2(0.f, 0.f);
+    sg_j[threadIdx.x] = j < N ? g[j] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int64_t B = (int64_t)N * (N + 1) / 2;
+  const int j = J * kCT + tx;
+  const float2 gj = sg_j[tx];
+  // channels of this group: cg, cg + n_cg, ...
+  Kahan loss, rre[4], rim[4], cre, cim;
+  for (int nu = cg; nu < C; nu += n_cg) {
+    const float2 *Vn = V + (int64_t)nu * B;
+    const float2 *Mn = M + (int64_t)nu * B;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int il = ty + 8 * m;
+      const int i = I * kCT + il;
+      if (i >= N || j >= N || j >= i) continue;
+      const int64_t b = (int64_t)i * (i + 1) / 2 + j;
+      const float2 v = Vn[b], mm = Mn[b], gi = sg_i[il];
+      // G = g_i conj(g_j)
+      const float Gr = gi.x * gj.x + gi.y * gj.y;
+      const float Gi = gi.y * gj.x - gi.x * gj.y;
+      // R = G M - V
+      const float Rr = Gr * mm.x - Gi * mm.y - v.x;
+      const float Ri = Gr * mm.y + Gi * mm.x - v.y;
+      loss.add(Rr * Rr + Ri * Ri);
+      // to row i: R g_j conj(M)
+      const float Pr = Rr * gj.x - Ri * gj.y, Pi = Rr * gj.y + Ri * gj.x;  // R g_j
+      rre[m].add(Pr * mm.x + Pi * mm.y);
+      rim[m].add(Pi * mm.x - Pr * mm.y);
+      // to column j: conj(R) g_i M
+      const float Qr = Rr * gi.x + Ri * gi.y, Qi = Rr * gi.y - Ri * gi.x;  // conj(R) g_i
+      cre.add(Qr * mm.x - Qi * mm.y);
+      cim.add(Qr * mm.y + Qi * mm.x);
+    }
+  }
+  const int out_idx = tile * n_cg + cg;
+  // rows: sum over the 32 columns (lanes) of the warp, fixed butterfly
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    float xr = rre[m].s, xi = rim[m].s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      xr += __shfl_xor_sync(0xffffffffu, xr, o);
+      xi += __shfl_xor_sync(0xffffffffu, xi, o);
+    }
+    if (tx == 0) part_row[(int64_t)out_idx * kCT + ty + 8 * m] = make_float2(xr, xi);
+  }
+  // columns: sum over the 8 warps in a fixed order
+  scol[ty][tx] = make_float2(cre.s, cim.s);
+  float l = loss.s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if (tx == 0) sloss[ty] = l;
+  __syncthreads();
+  if (ty == 0) {
+    float2 acc = scol[0][tx];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) {
+      acc.x += scol[w][tx].x;
+      acc.y += scol[w][tx].y;
+    }
+    part_col[(int64_t)out_idx * kCT + tx] = acc;
+  }
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kCalThreads / 32; ++w) s += sloss[w];
+    part_loss[out_idx] = s;
+  }
+}
+
+// grid: n_blocks + 1.  Block K < n_blocks gathers grad for inputs K*32..;
+// the last block sums the loss partials.
+__global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
+    int N, int n_blocks, int n_cg, const float *__restrict__ part_loss,
+    const float2 *__restrict__ part_row, const float2 *__restrict__ part_col,
+    float *__restrict__ loss, float2 *__restrict__ grad) {
+  const int K = blockIdx.x;
+  if (K == n_blocks) {
+    if (!loss) return;
+    __shared__ float sred[kCalThreads];
+    const int n_part = n_blocks * (n_blocks + 1) / 2 * n_cg;
+    Kahan acc;
+    for (int k = threadIdx.x; k < n_part; k += kCalThreads) acc.add(part_loss[k]);
+    sred[threadIdx.x] = acc.s;
+    __syncthreads();
+    for (int w = kCalThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sred[threadIdx.x] += sred[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = sred[0];
+    return;
+  }
+  if (!grad) return;
+  // 32 inputs x 8 partial lanes: thread (r, l) sums every 8th contribution
+  __shared__ float2 sacc[8][kCT];
+  const int r = threadIdx.x & 31, l = threadIdx.x >> 5;
+  Kahan ar, ai;
+  // tiles (K, J), J <= K contribute row partials; tiles (I, K), I >= K column partials
+  int n = 0;
+  for (int Jt = 0; Jt <= K; ++Jt) {
+    const int tile = K * (K + 1) / 2 + Jt;
+    for (int cg = 0; cg < n_cg; ++cg, ++n) {
+      if ((n & 7) != l) continue;
+      const float2 v = part_row[((int64_t)tile * n_cg + cg) * kCT + r];
+      ar.add(v.x);
+      ai.add(v.y);
+    }
+  }
+  for (int It = K; It < n_blocks; ++It) {
+    const int tile = It * (It + 1) / 2 + K;
+    for (int cg = 0; cg < n_cg; ++cg, ++n) {
+      if ((n & 7) != l) continue;
+      const float2 v = part_col[((int64_t)tile * n_cg + cg) * kCT + r];
+      ar.add(v.x);
+      ai.add(v.y);
+    }
+  }
+  sacc[l][r] = make_float2(ar.s, ai.s);
+  __syncthreads();
+  if (l == 0) {
+    float2 acc = sacc[0][r];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) {
+      acc.x += sacc[w][r].x;
+      acc.y += sacc[w][r].y;
+    }
+    const int k = K * kCT + r;
+    if (k < N) grad[k] = make_float2(2.f * acc.x, 2.f * acc.y);
+  }
+}
+
+bool dev_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Ws {
+  float *loss;
+  float2 *row, *col;
+};
+
+Ws carve(void *ws, int n_blocks, int n_cg) {
+  const int64_t tiles = (int64_t)n_blocks * (n_blocks + 1) / 2;
+  uint8_t *p = reinterpret_cast<uint8_t *>(ws);
+  Ws w;
+  w.row = reinterpret_cast<float2 *>(p);
+  p += tiles * n_cg * kCT * sizeof(float2);
+  w.col = reinterpret_cast<float2 *>(p);
+  p += tiles * n_cg * kCT * sizeof(float2);
+  w.loss = reinterpret_cast<float *>(p);
+  return w;
+}
+
+}  // namespace
+}  // namespace mwax
+
+using namespace mwax;
+
+extern "C" {
+
+int64_t mwax_calib_workspace_bytes(int n_inputs, int n_chan) {
+  if (n_inputs < 2 || n_chan < 1) return -1;
+  const int64_t nb = (n_inputs + kCT - 1) / kCT;
+  const int64_t tiles = nb * (nb + 1) / 2;
+  const int64_t cg = chan_groups(n_chan);
+  return tiles * cg * kCT * (int64_t)sizeof(float2) * 2 + tiles * cg * (int64_t)sizeof(float) + 256;
+}
+
+mwax_status mwax_calib_loss_grad(const float *V, const float *M, const float *g, int n_inputs,
+                                 int n_chan, void *workspace, float *loss, float *grad,
+                                 cudaStream_t stream) {
+  if (n_inputs < 2 || n_chan < 1 || n_inputs > 65536) return MWAX_ERR_INVALID_ARG;
+  if (!loss && !grad) return MWAX_ERR_INVALID_ARG;
+  if (!dev_ptr(V) || !dev_ptr(M) || !dev_ptr(g) || !dev_ptr(workspace)) return MWAX_ERR_INVALID_ARG;
+  if ((loss && !dev_ptr(loss)) || (grad && !dev_ptr(grad))) return MWAX_ERR_INVALID_ARG;
+  const int nb = (n_inputs + kCT - 1) / kCT;
+  const int tiles = nb * (nb + 1) / 2;
+  const int n_cg = chan_groups(n_chan);
+  Ws w = carve(workspace, nb, n_cg);
+  calib_tile_kernel<<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
+      reinterpret_cast<const float2 *>(V), reinterpret_cast<const float2 *>(M),
+      reinterpret_cast<const float2 *>(g), n_inputs, n_chan, n_cg, w.loss, w.row, w.col);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return MWAX_ERR_CUDA;
+  calib_gather_kernel<<<nb + 1, kCalThreads, 0, stream>>>(n_inputs, nb, n_cg, w.loss, w.row, w.col,
+                                                          loss, reinterpret_cast<float2 *>(grad));
+  return cudaGetLastError() == cudaSuccess ? MWAX_OK : MWAX_ERR_CUDA;
+}
+
+mwax_status mwax_calib_loss(const float *V, const float *M, const float *g, int n_inputs,
+                            int n_chan, void *workspace, float *loss, cudaStream_t stream) {
+  if (!loss) return MWAX_ERR_INVALID_ARG;
+  return mwax_calib_loss_grad(V, M, g, n_inputs, n_chan, workspace, loss, nullptr, stream);
+}
+
+mwax_status mwax_calib_grad(const float *V, const float *M, const float *g, int n_inputs,
+                            int n_chan, void *workspace, float *grad, cudaStream_t stream) {
+  if (!grad) return MWAX_ERR_INVALID_ARG;
+  return mwax_calib_loss_grad(V, M, g, n_inputs, n_chan, workspace, nullptr, grad, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,543 @@
+// k_correlate.cu -- tensor-core X-engine correlator for sm_103a (tcgen05).
+//
+// Computes, for every fine channel and every 128x128 tile pair (I >= J) of
+// the input triangle (paper Sec. 2: all antenna pairs cross-correlated per
+// channel, then integrated over the dump),
+//     Re V_ij = sum_t xr_i xr_j + xi_i xi_j
+//     Im V_ij = sum_t xi_i xr_j - xr_i xi_j
+// as a dense rank-T Hermitian update on the 5th-generation tensor cores.
+//
+// Operands come from k_unpack.cu: per input row, 128-byte blocks of
+// [re x S | im x S] exact small floats (binary16 for 8-bit samples, S = 32;
+// E4M3 for 4-bit samples, S = 64).  A block is one row of a 128-byte
+// swizzled K-major shared-memory tile, and one MMA consumes a 32-byte slice
+// of it: slices 0,1 hold re, slices 2,3 hold im.  Per block the MMA warp
+// issues eight M=128 N=128 MMAs:
+//     D_re += A[s] . B[s]                      s = 0..3
+//     D_im += A[2] . B[0] + A[3] . B[1]        (xi_i xr_j)
+//     D_im -= A[0] . B[2] + A[1] . B[3]        (xr_i xi_j; negate-B bit)
+// Every product of two sample values is an exact integer and every partial
+// sum stays an integer below 2^24 for `flush_blocks` blocks, so the FP32
+// accumulator in tensor memory is exact; at the end of each such segment
+// the epilogue warps convert it (round-to-nearest, exact) to int32 and add
+// it to int32 register totals.  The plan bounds T so the totals fit int32.
+//
+// Roles (one persistent CTA per SM, 10 warps):
+//   warp 0      TMA producer: tiles A_I and A_J of the current block into a
+//               ring of shared-memory stages (A_J skipped on diagonal tiles)
+//   warp 1      tensor-memory allocator and single-thread MMA issuer
+//   warps 2..9  epilogue: tcgen05.ld of the FP32 accumulator, int32 flush,
+//               packed lower-triangle store (the integration dump)
+// Two 256-column accumulators (re 128 | im 128) are double-buffered in the
+// 512 tensor-memory columns so the epilogue of one segment overlaps the
+// MMAs of the next.
+//
+// Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
+// kernel records MWAX_ERR_TIMEOUT in the plan's status word, stops issuing,
+// waits (bounded) for its own copies and MMAs in flight, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include "mwax_internal.h"
+
+namespace mwax {
+namespace {
+
+constexpr int kWarps = 10;
+constexpr int kThreads = kWarps * 32;
+constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
+constexpr int kStageBytes = 2 * kTileBytes;    // A + B
+constexpr int kMaxStages = 6;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAccCols = 256;  // re 128 | im 128
+constexpr int kMaxJobs = MWAX_MAX_JOBS;
+
+// One job of a (possibly batched) launch.
+struct KJob {
+  void *out;           // visibilities of the job's first channel in this launch
+  int64_t item_begin;  // first work item of this job
+  int64_t n_bl;        // N(N+1)/2
+  int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks, pad_;
+};
+
+struct KParams {
+  KJob job[kMaxJobs];
+  int32_t *status;
+  int64_t n_items;
+  unsigned long long timeout_ns;
+  int32_t n_jobs, stages;
+};
+
+struct KMaps {
+  CUtensorMap m[kMaxJobs];
+};
+
+// ---- PTX wrappers --------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with parity `parity` to complete.  Returns false
+// on timeout, or when another role has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int *abort_flag,
+                                          unsigned long long timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (globaltimer() - t0 > timeout_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B type code 0 (F16 for
+// kind::f16, E4M3 for kind::f8f6f4), K-major A and B, M = N = 128.
+__host__ __device__ constexpr uint32_t make_idesc(bool negate_b) {
+  return (1u << 4) | ((negate_b ? 1u : 0u) << 14) | ((uint32_t)(kTile >> 3) << 17) |
+         ((uint32_t)(kTile >> 4) << 24);
+}
+
+template <int BITS>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+  if constexpr (BITS == 8) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// tile pair p -> (I, J), p = I(I+1)/2 + J, I >= J
+__device__ __forceinline__ void pair_of(int p, int &I, int &J) {
+  int i = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= p) ++i;
+  while (i * (i + 1) / 2 > p) --i;
+  I = i;
+  J = p - i * (i + 1) / 2;
+}
+
+// Work item -> (job, channel, I, J).  Items are numbered job by job.
+struct Item {
+  int job, c, I, J;
+};
+__device__ __forceinline__ Item decode_item(const KParams &p, int64_t item) {
+  int j = 0;
+  while (j + 1 < p.n_jobs && item >= p.job[j + 1].item_begin) ++j;
+  const int64_t local = item - p.job[j].item_begin;
+  Item it;
+  it.job = j;
+  it.c = (int)(local / p.job[j].n_pairs);
+  pair_of((int)(local % p.job[j].n_pairs), it.I, it.J);
+  return it;
+}
+
+__device__ __forceinline__ void raise_timeout(volatile int *abort_flag, int32_t *status) {
+  *abort_flag = 1;
+  atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
+}
+
+// Lane 0 waits; the result is broadcast so the warp takes one branch.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned long long timeout_ns, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = mbar_wait(bar, parity, abort_flag, timeout_ns) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <int BITS, int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+    correlate_tc_kernel(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~static_cast<uintptr_t>(1023));
+  const int S = p.stages;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * kStageBytes);
+  // full[0..S) empty[S..2S) tfull[2S..2S+2) tempty[2S+2..2S+4) drain[2S+4]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + S + s); };
+  auto tfull = [&](int b) { return smem_u32(bars + 2 * S + b); };
+  auto tempty = [&](int b) { return smem_u32(bars + 2 * S + 2 + b); };
+  const uint32_t drain = smem_u32(bars + 2 * S + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long tmo = p.timeout_ns;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 8);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0)
+      for (int j = 0; j < p.n_jobs; ++j)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[j]))
+                     : "memory");
+    int64_t issued = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      const Item it = decode_item(p, item);
+      const KJob &jb = p.job[it.job];
+      const CUtensorMap *map = &maps.m[it.job];
+      const int yA = (it.c * jb.n_tiles + it.I) * kTile, yB = (it.c * jb.n_tiles + it.J) * kTile;
+      const uint32_t bytes = (it.I == it.J) ? kTileBytes : kStageBytes;
+      for (int kb = 0; kb < jb.kb; ++kb) {
+        const int stage = (int)(issued % S);
+        const uint32_t phase = (uint32_t)((issued / S) & 1);
+        if (!warp_wait(empty(stage), phase ^ 1u, abort_flag, tmo, lane)) {
+          if (lane == 0) raise_timeout(abort_flag, p.status);
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
+          mbar_arrive_expect_tx(full(stage), bytes);
+          tma_load_2d(a, map, kb * kRowBytes, yA, full(stage));
+          if (it.I != it.J) tma_load_2d(a + kTileBytes, map, kb * kRowBytes, yB, full(stage));
+        }
+        __syncwarp();
+        ++issued;
+      }
+    }
+    // wait (bounded) until every copy this warp issued has landed
+    if (lane == 0) {
+      const int64_t first = issued > S ? issued - S : 0;
+      for (int64_t n = first; n < issued; ++n)
+        mbar_wait(full((int)(n % S)), (uint32_t)((n / S) & 1), nullptr, tmo);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t idesc = make_idesc(false);
+    constexpr uint32_t idesc_neg = make_idesc(true);
+    int64_t consumed = 0;
+    uint32_t seg = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      const Item it = decode_item(p, item);
+      const KJob &jb = p.job[it.job];
+      const int F = jb.flush_blocks, KB = jb.kb;
+      for (int kb = 0; kb < KB; ++kb) {
+        const bool seg_start = (kb % F) == 0;
+        const uint32_t buf = seg & 1u;
+        if (seg_start) {
+          if (!warp_wait(tempty(buf), ((seg >> 1) & 1u) ^ 1u, abort_flag, tmo, lane)) {
+            if (lane == 0) raise_timeout(abort_flag, p.status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        const int stage = (int)(consumed % S);
+        const uint32_t phase = (uint32_t)((consumed / S) & 1);
+        if (!warp_wait(full(stage), phase, abort_flag, tmo, lane)) {
+          if (lane == 0) raise_timeout(abort_flag, p.status);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
+          const uint32_t b = (it.I == it.J) ? a : a + kTileBytes;
+          const uint32_t d_re = tmem_base + buf * kAccCols;
+          const uint32_t d_im = d_re + kTile;
+          const uint32_t acc0 = seg_start ? 0u : 1u;
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+            tc_mma<BITS>(d_re, sw128_desc(a + 32 * s), sw128_desc(b + 32 * s), idesc,
+                         s == 0 ? acc0 : 1u);
+          tc_mma<BITS>(d_im, sw128_desc(a + 64), sw128_desc(b + 0), idesc, acc0);
+          tc_mma<BITS>(d_im, sw128_desc(a + 96), sw128_desc(b + 32), idesc, 1u);
+          tc_mma<BITS>(d_im, sw128_desc(a + 0), sw128_desc(b + 64), idesc_neg, 1u);
+          tc_mma<BITS>(d_im, sw128_desc(a + 32), sw128_desc(b + 96), idesc_neg, 1u);
+          tc_commit(empty(stage));
+        }
+        __syncwarp();
+        ++consumed;
+        const bool seg_end = ((kb % F) == F - 1) || (kb == KB - 1);
+        if (seg_end) {
+          if (lane == 0) tc_commit(tfull(buf));
+          __syncwarp();
+          ++seg;
+        }
+      }
+    }
+    // no MMA may be in flight when tensor memory is freed
+    if (lane == 0) {
+      tc_commit(drain);
+      mbar_wait(drain, 0, nullptr, tmo);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: flush + integration dump ----------------
+    const int q = warp & 3;         // tensor-memory lane quadrant of this warp
+    const int h = (warp - 2) >> 2;  // column half: local columns [64h, 64h + 64)
+    uint32_t seg = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      const Item it = decode_item(p, item);
+      const KJob &jb = p.job[it.job];
+      const int F = jb.flush_blocks;
+      const int n_seg = (jb.kb + F - 1) / F;
+      uint32_t tot[128];  // [0,64): re of columns 64h+k, [64,128): im
+#pragma unroll
+      for (int k = 0; k < 128; ++k) tot[k] = 0u;
+      for (int sidx = 0; sidx < n_seg; ++sidx) {
+        const uint32_t buf = seg & 1u;
+        if (!warp_wait(tfull(buf), (seg >> 1) & 1u, abort_flag, tmo, lane)) {
+          if (lane == 0) raise_timeout(abort_flag, p.status);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + buf * kAccCols;
+#pragma unroll
+        for (int chunk = 0; chunk < 4; ++chunk) {
+          const uint32_t col = chunk < 2 ? (uint32_t)(64 * h + 32 * chunk)
+                                         : (uint32_t)(kTile + 64 * h + 32 * (chunk - 2));
+          uint32_t v[32];
+          tc_ld32(trow + col, v);
+          tc_wait_ld();
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            if constexpr (KIND == MWAX_KIND_EXACT) {
+              const int x = __float2int_rn(__uint_as_float(v[k]));
+              tot[chunk * 32 + k] = (uint32_t)((int)tot[chunk * 32 + k] + x);
+            } else {
+              tot[chunk * 32 + k] = v[k];
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty(buf));
+        ++seg;
+      }
+      if (!ok) break;
+      // packed lower-triangle store: row i, columns j in [J*128 + 64h, +64), j <= i
+      const int i = it.I * kTile + q * 32 + lane;
+      if (i < jb.n_inputs) {
+        const int64_t rowb = (int64_t)i * (i + 1) / 2;
+        uint32_t *out = reinterpret_cast<uint32_t *>(jb.out) + (int64_t)it.c * jb.n_bl * 2;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+          const int j = it.J * kTile + 64 * h + k;
+          if (j < jb.n_inputs && j <= i) {
+            const uint2 val = make_uint2(tot[k], tot[64 + k]);
+            *reinterpret_cast<uint2 *>(out + 2 * (rowb + j)) = val;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// ---- host side ------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+template <int BITS, int KIND>
+cudaError_t set_smem_attr(int bytes) {
+  return cudaFuncSetAttribute(correlate_tc_kernel<BITS, KIND>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace
+
+int correlate_tc_max_stages() { return kMaxStages; }
+
+int correlate_tc_smem_bytes(int stages) {
+  return 1024 + stages * kStageBytes + (2 * stages + 5) * 8 + 16;
+}
+
+cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages) {
+  const int bytes = correlate_tc_smem_bytes(stages);
+  if (sample_bits == 4) return set_smem_attr<4, MWAX_KIND_EXACT>(bytes);
+  if (kind == MWAX_KIND_FP16) return set_smem_attr<8, MWAX_KIND_FP16>(bytes);
+  return set_smem_attr<8, MWAX_KIND_EXACT>(bytes);
+}
+
+cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
+                                cudaStream_t s) {
+  if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;
+  if (cfg.stages < 2 || cfg.stages > kMaxStages) return cudaErrorInvalidValue;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
+  if (!encode) return cudaErrorNotSupported;
+  KMaps maps;
+  KParams kp;
+  memset(&maps, 0, sizeof(maps));
+  memset(&kp, 0, sizeof(kp));
+  int64_t items = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const TcJob &job = jobs[j];
+    if (job.flush_blocks < 1 || job.kb < 1 || job.n_tiles < 1) return cudaErrorInvalidValue;
+    const cuuint64_t rows = (cuuint64_t)job.n_chan * job.n_tiles * kTile;
+    cuuint64_t dims[2] = {(cuuint64_t)job.kb * kRowBytes, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)job.kb * kRowBytes};
+    cuuint32_t box[2] = {(cuuint32_t)kRowBytes, (cuuint32_t)kTile};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&maps.m[j], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                        const_cast<uint8_t *>(job.op), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    KJob &kj = kp.job[j];
+    kj.out = job.out;
+    kj.item_begin = items;
+    kj.n_bl = job.n_bl;
+    kj.n_inputs = job.n_inputs;
+    kj.n_tiles = job.n_tiles;
+    kj.n_pairs = job.n_pairs;
+    kj.kb = job.kb;
+    kj.flush_blocks = job.flush_blocks;
+    items += (int64_t)job.n_chan * job.n_pairs;
+  }
+  kp.status = cfg.status;
+  kp.n_items = items;
+  kp.timeout_ns = cfg.timeout_ns;
+  kp.n_jobs = n_jobs;
+  kp.stages = cfg.stages;
+  if (items <= 0) return cudaSuccess;
+  const int grid = (int)(items < cfg.grid ? items : cfg.grid);
+  const int smem = correlate_tc_smem_bytes(cfg.stages);
+  if (cfg.sample_bits == 4)
+    correlate_tc_kernel<4, MWAX_KIND_EXACT><<<grid, kThreads, smem, s>>>(maps, kp);
+  else if (cfg.kind == MWAX_KIND_FP16)
+    correlate_tc_kernel<8, MWAX_KIND_FP16><<<grid, kThreads, smem, s>>>(maps, kp);
+  else
+    correlate_tc_kernel<8, MWAX_KIND_EXACT><<<grid, kThreads, smem, s>>>(maps, kp);
+  return cudaGetLastError();
+}
+
+}  // namespace mwax

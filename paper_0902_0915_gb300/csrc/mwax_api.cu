@@ -1,0 +1,576 @@
+// mwax_api.cu -- plans, argument checks and the C entry points of libmwax.
+//
+// A plan fixes the shape of one or more correlation jobs, checks the int32
+// bound, picks the tiling (samples per operand block, FP32 segment length,
+// channel groups), allocates the operand scratch and the device status
+// word, and launches the kernels on its stream:
+//   tensor engine: per channel group, unpack (k_unpack.cu) then one
+//                  persistent tcgen05 launch (k_correlate.cu);
+//   plain engine:  one CUDA-core launch per channel (k_plain.cu).
+// Batch plans run every job's unpack and then ONE persistent correlate
+// launch over all jobs' work items, captured in a CUDA graph on first use.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "mwax_internal.h"
+
+namespace mwax {
+namespace {
+
+constexpr int64_t kExactWindow = int64_t(1) << 24;  // integers exact in FP32
+constexpr int64_t kDefaultScratchBudget = int64_t(8) << 30;
+constexpr unsigned long long kDefaultTimeoutNs = 2000000000ull;  // 2 s per wait
+
+struct JobState {
+  mwax_job job;
+  int n_tiles = 0, n_pairs = 0, spb = 0, kb = 0, flush_blocks = 1, chan_group = 1;
+  int64_t n_bl = 0;
+  int64_t op_chan_bytes = 0;  // operand bytes of one channel
+  int64_t in_chan_bytes = 0;  // packed input bytes of one channel
+  int64_t out_chan_bytes = 0;
+  uint8_t *op = nullptr;  // batch plans: operand buffer for all channels of this job
+};
+
+}  // namespace
+}  // namespace mwax
+
+struct mwax_plan_s {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool batch = false;
+  int engine = MWAX_ENGINE_TENSOR;
+  int sample_bits = 4;
+  int kind = MWAX_KIND_EXACT;
+  int stages = 6;
+  unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
+  std::vector<mwax::JobState> jobs;
+  uint8_t *scratch = nullptr;  // single-job plans: operand buffer for one channel group
+  int64_t scratch_bytes = 0;
+  int32_t *status = nullptr;
+  // batch graph
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const void *> graph_in;
+  std::vector<void *> graph_out;
+  // host path
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  uint8_t *stage_in[2] = {nullptr, nullptr};
+  uint8_t *stage_out[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+              ev_out[2] = {nullptr, nullptr};
+  int64_t stage_in_bytes = 0, stage_out_bytes = 0;
+  // kernel timing (events on the launching stream)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec {
+    int kind;  // 0 unpack, 1 correlate
+    int start, stop;
+  };
+  std::vector<Rec> recs;
+};
+
+namespace mwax {
+namespace {
+
+mwax_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MWAX_OK;
+  if (e == cudaErrorMemoryAllocation) return MWAX_ERR_OOM;
+  return MWAX_ERR_CUDA;
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mwax_status check_job(const mwax_job &j) {
+  if (j.n_inputs < 1 || j.n_chan < 1 || j.n_time < 1) return MWAX_ERR_INVALID_ARG;
+  if (j.sample_bits != 4 && j.sample_bits != 8) return MWAX_ERR_INVALID_ARG;
+  if (j.kind != MWAX_KIND_EXACT && j.kind != MWAX_KIND_FP16) return MWAX_ERR_INVALID_ARG;
+  if (j.engine != MWAX_ENGINE_TENSOR && j.engine != MWAX_ENGINE_PLAIN) return MWAX_ERR_INVALID_ARG;
+  if (j.flush_blocks < 0 || j.chan_group < 0) return MWAX_ERR_INVALID_ARG;
+  for (int k = 0; k < 8; ++k)
+    if (j.reserved[k] != 0) return MWAX_ERR_INVALID_ARG;
+  if (j.kind == MWAX_KIND_FP16 && (j.sample_bits != 8 || j.engine != MWAX_ENGINE_TENSOR))
+    return MWAX_ERR_UNSUPPORTED;
+  if (j.n_inputs > 65536) return MWAX_ERR_UNSUPPORTED;
+  if (j.kind == MWAX_KIND_EXACT && (int64_t)j.n_time > mwax_max_n_time(j.sample_bits))
+    return MWAX_ERR_OVERFLOW_BOUND;
+  return MWAX_OK;
+}
+
+void derive(JobState &s) {
+  const mwax_job &j = s.job;
+  s.n_tiles = (j.n_inputs + kTile - 1) / kTile;
+  s.n_pairs = s.n_tiles * (s.n_tiles + 1) / 2;
+  s.spb = samples_per_block(j.sample_bits);
+  s.kb = (j.n_time + s.spb - 1) / s.spb;
+  const int64_t m = sample_max(j.sample_bits);
+  // largest segment whose partial sums provably stay inside the exact window
+  const int64_t per_block = (int64_t)s.spb * 2 * m * m;
+  int64_t f = kExactWindow / per_block;
+  if (j.kind == MWAX_KIND_FP16) f = s.kb;
+  if (j.flush_blocks > 0) f = j.flush_blocks;
+  s.flush_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(f, s.kb));
+  s.n_bl = (int64_t)j.n_inputs * (j.n_inputs + 1) / 2;
+  s.op_chan_bytes = (int64_t)s.n_tiles * kTile * s.kb * kRowBytes;
+  s.in_chan_bytes = (int64_t)j.n_time * j.n_inputs * bytes_per_sample(j.sample_bits);
+  s.out_chan_bytes = s.n_bl * 8;
+  int64_t g = j.chan_group > 0 ? j.chan_group : kDefaultScratchBudget / s.op_chan_bytes;
+  s.chan_group = (int)std::max<int64_t>(1, std::min<int64_t>(g, j.n_chan));
+}
+
+mwax_status init_device(mwax_plan_s *p, cudaStream_t stream) {
+  if (cudaGetDevice(&p->device) != cudaSuccess) return MWAX_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) return MWAX_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return MWAX_ERR_UNSUPPORTED;
+  p->sm_count = prop.multiProcessorCount;
+  p->stream = stream;
+  if (const char *e = getenv("MWAX_TIMEOUT_MS")) {
+    long v = atol(e);
+    if (v > 0) p->timeout_ns = (unsigned long long)v * 1000000ull;
+  }
+  cudaError_t e = cudaMalloc(&p->status, sizeof(int32_t));
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(cudaMemsetAsync(p->status, 0, sizeof(int32_t), stream));
+}
+
+// Event pair around one launch when timing is on.
+struct TimedLaunch {
+  mwax_plan_s *p;
+  int kind, start = -1;
+  cudaStream_t st;
+  TimedLaunch(mwax_plan_s *plan, int k, cudaStream_t s) : p(plan), kind(k), st(s) {
+    if (!p->timing) return;
+    start = next_event();
+    if (start >= 0) cudaEventRecord(p->ev_pool[start], st);
+  }
+  int next_event() {
+    const int used = (int)p->recs.size() * 2 + (start >= 0 ? 1 : 0);
+    while ((int)p->ev_pool.size() <= used) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      p->ev_pool.push_back(e);
+    }
+    return used;
+  }
+  void done() {
+    if (start < 0) return;
+    const int stop = next_event();
+    if (stop < 0) return;
+    cudaEventRecord(p->ev_pool[stop], st);
+    p->recs.push_back({kind, start, stop});
+    start = -1;
+  }
+};
+
+TcLaunch launch_cfg(const mwax_plan_s *p) {
+  TcLaunch c;
+  c.sample_bits = p->sample_bits;
+  c.kind = p->kind;
+  c.grid = p->sm_count;
+  c.stages = p->stages;
+  c.status = p->status;
+  c.timeout_ns = p->timeout_ns;
+  return c;
+}
+
+// Channels [c0, c0+nc) of a single-job tensor plan: unpack into the scratch,
+// then one persistent correlate launch.
+mwax_status run_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
+                      void *out_c0, cudaStream_t st) {
+  TimedLaunch tu(p, 0, st);
+  cudaError_t e = launch_unpack(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
+                                s.kb, c0, nc, p->scratch, st);
+  tu.done();
+  if (e != cudaSuccess) return cuda_status(e);
+  TcJob tj;
+  tj.op = p->scratch;
+  tj.out = out_c0;
+  tj.n_inputs = s.job.n_inputs;
+  tj.n_tiles = s.n_tiles;
+  tj.n_pairs = s.n_pairs;
+  tj.kb = s.kb;
+  tj.flush_blocks = s.flush_blocks;
+  tj.n_chan = nc;
+  tj.n_bl = s.n_bl;
+  TimedLaunch tc(p, 1, st);
+  e = launch_correlate_tc(&tj, 1, launch_cfg(p), st);
+  tc.done();
+  return cuda_status(e);
+}
+
+mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cudaStream_t st) {
+  const JobState &s = p->jobs[0];
+  if (p->engine == MWAX_ENGINE_PLAIN) {
+    for (int c = 0; c < s.job.n_chan; ++c) {
+      TimedLaunch tl(p, 1, st);
+      cudaError_t e = launch_plain_channel(volt + (int64_t)c * s.in_chan_bytes, s.job.sample_bits,
+                                           s.job.n_inputs, s.job.n_time,
+                                           reinterpret_cast<int32_t *>(out) + (int64_t)c * s.n_bl * 2,
+                                           st);
+      tl.done();
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    return MWAX_OK;
+  }
+  for (int64_t c0 = 0; c0 < s.job.n_chan; c0 += s.chan_group) {
+    const int nc = (int)std::min<int64_t>(s.chan_group, s.job.n_chan - c0);
+    mwax_status r = run_group(p, s, volt, c0, nc,
+                              reinterpret_cast<uint8_t *>(out) + c0 * s.out_chan_bytes, st);
+    if (r != MWAX_OK) return r;
+  }
+  return MWAX_OK;
+}
+
+void free_plan(mwax_plan_s *p) {
+  if (!p) return;
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (auto &s : p->jobs)
+    if (s.op) cudaFree(s.op);
+  if (p->scratch) cudaFree(p->scratch);
+  if (p->status) cudaFree(p->status);
+  for (int k = 0; k < 2; ++k) {
+    if (p->stage_in[k]) cudaFree(p->stage_in[k]);
+    if (p->stage_out[k]) cudaFree(p->stage_out[k]);
+    if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
+    if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
+    if (p->ev_out[k]) cudaEventDestroy(p->ev_out[k]);
+  }
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->h2d) cudaStreamDestroy(p->h2d);
+  if (p->d2h) cudaStreamDestroy(p->d2h);
+  delete p;
+}
+
+}  // namespace
+}  // namespace mwax
+
+using namespace mwax;
+
+extern "C" {
+
+const char *mwax_status_string(mwax_status s) {
+  switch (s) {
+    case MWAX_OK: return "ok";
+    case MWAX_ERR_INVALID_ARG: return "invalid argument";
+    case MWAX_ERR_SHAPE_MISMATCH: return "shape differs from the plan";
+    case MWAX_ERR_OVERFLOW_BOUND: return "n_time * 2 * max^2 exceeds the int32 range";
+    case MWAX_ERR_UNSUPPORTED: return "unsupported device or option";
+    case MWAX_ERR_OOM: return "device allocation failed";
+    case MWAX_ERR_CUDA: return "CUDA runtime error";
+    case MWAX_ERR_TIMEOUT: return "a bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+int64_t mwax_n_baselines(int n_inputs) {
+  if (n_inputs < 0) return -1;
+  return (int64_t)n_inputs * (n_inputs + 1) / 2;
+}
+
+int64_t mwax_baseline_index(int i, int j) {
+  if (j < 0 || i < j) return -1;
+  return (int64_t)i * (i + 1) / 2 + j;
+}
+
+mwax_status mwax_baseline_pair(int64_t b, int *i, int *j) {
+  if (b < 0 || !i || !j) return MWAX_ERR_INVALID_ARG;
+  // largest i with i(i+1)/2 <= b, by bisection on exact integers
+  int64_t lo = 0, hi = 3037000499LL;  // hi(hi+1)/2 fits int64
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo + 1) / 2;
+    if (mid * (mid + 1) / 2 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  if (lo > 2147483647LL) return MWAX_ERR_INVALID_ARG;
+  *i = (int)lo;
+  *j = (int)(b - lo * (lo + 1) / 2);
+  return MWAX_OK;
+}
+
+int64_t mwax_max_n_time(int sample_bits) {
+  if (sample_bits != 4 && sample_bits != 8) return -1;
+  const int64_t m = sample_max(sample_bits);
+  return (int64_t)2147483647 / (2 * m * m);
+}
+
+mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t stream) {
+  if (!plan) return MWAX_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (!job) return MWAX_ERR_INVALID_ARG;
+  mwax_status r = check_job(*job);
+  if (r != MWAX_OK) return r;
+  mwax_plan_s *p = new (std::nothrow) mwax_plan_s();
+  if (!p) return MWAX_ERR_OOM;
+  r = init_device(p, stream);
+  if (r != MWAX_OK) {
+    free_plan(p);
+    return r;
+  }
+  JobState s;
+  s.job = *job;
+  derive(s);
+  p->jobs.push_back(s);
+  p->engine = job->engine;
+  p->sample_bits = job->sample_bits;
+  p->kind = job->kind;
+  if (p->engine == MWAX_ENGINE_TENSOR) {
+    p->scratch_bytes = s.op_chan_bytes * s.chan_group;
+    cudaError_t e = cudaMalloc(&p->scratch, (size_t)p->scratch_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)p->scratch_bytes, stream);
+    if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages);
+    if (e != cudaSuccess) {
+      free_plan(p);
+      return cuda_status(e);
+    }
+  }
+  *plan = p;
+  return MWAX_OK;
+}
+
+mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
+                            cudaStream_t stream) {
+  if (!plan) return MWAX_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (!jobs || n_jobs < 1 || n_jobs > MWAX_MAX_JOBS) return MWAX_ERR_INVALID_ARG;
+  for (int k = 0; k < n_jobs; ++k) {
+    mwax_status r = check_job(jobs[k]);
+    if (r != MWAX_OK) return r;
+    if (jobs[k].engine != MWAX_ENGINE_TENSOR) return MWAX_ERR_UNSUPPORTED;
+    if (jobs[k].sample_bits != jobs[0].sample_bits || jobs[k].kind != jobs[0].kind)
+      return MWAX_ERR_UNSUPPORTED;  // one kernel instantiation per launch
+  }
+  mwax_plan_s *p = new (std::nothrow) mwax_plan_s();
+  if (!p) return MWAX_ERR_OOM;
+  mwax_status r = init_device(p, stream);
+  if (r != MWAX_OK) {
+    free_plan(p);
+    return r;
+  }
+  p->batch = true;
+  p->sample_bits = jobs[0].sample_bits;
+  p->kind = jobs[0].kind;
+  for (int k = 0; k < n_jobs; ++k) {
+    JobState s;
+    s.job = jobs[k];
+    derive(s);
+    cudaError_t e = cudaMalloc(&s.op, (size_t)(s.op_chan_bytes * s.job.n_chan));
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(s.op, 0, (size_t)(s.op_chan_bytes * s.job.n_chan), stream);
+    p->jobs.push_back(s);
+    p->scratch_bytes += s.op_chan_bytes * s.job.n_chan;
+    if (e != cudaSuccess) {
+      free_plan(p);
+      return cuda_status(e);
+    }
+  }
+  cudaError_t e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  *plan = p;
+  return MWAX_OK;
+}
+
+mwax_status mwax_destroy(mwax_plan_t plan) {
+  if (!plan) return MWAX_OK;
+  const cudaError_t e = cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+  return cuda_status(e);
+}
+
+mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
+  if (!plan || !info) return MWAX_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  const JobState &s = plan->jobs[0];
+  info->n_jobs = (int32_t)plan->jobs.size();
+  info->engine = plan->engine;
+  info->samples_per_block = s.spb;
+  info->flush_blocks = s.flush_blocks;
+  info->chan_group = plan->batch ? s.job.n_chan : s.chan_group;
+  info->grid = plan->sm_count;
+  info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
+  int64_t items = 0;
+  for (const auto &j : plan->jobs) items += (int64_t)j.job.n_chan * j.n_pairs;
+  info->work_items = items;
+  return MWAX_OK;
+}
+
+mwax_status mwax_plan_status(mwax_plan_t plan) {
+  if (!plan) return MWAX_ERR_INVALID_ARG;
+  int32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, plan->status, sizeof(v), cudaMemcpyDeviceToHost, plan->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->status, 0, sizeof(int32_t), plan->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return (mwax_status)v;
+}
+
+mwax_status mwax_correlate(mwax_plan_t plan, const void *voltages, int n_inputs, int n_chan,
+                           int n_time, void *out) {
+  if (!plan || plan->batch) return MWAX_ERR_INVALID_ARG;
+  const JobState &s = plan->jobs[0];
+  if (n_inputs != s.job.n_inputs || n_chan != s.job.n_chan || n_time != s.job.n_time)
+    return MWAX_ERR_SHAPE_MISMATCH;
+  if (!is_device_ptr(voltages) || !is_device_ptr(out)) return MWAX_ERR_INVALID_ARG;
+  return correlate_device(plan, reinterpret_cast<const uint8_t *>(voltages), out, plan->stream);
+}
+
+mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, void *const *out) {
+  if (!plan || !plan->batch || !voltages || !out) return MWAX_ERR_INVALID_ARG;
+  const int nj = (int)plan->jobs.size();
+  for (int k = 0; k < nj; ++k)
+    if (!is_device_ptr(voltages[k]) || !is_device_ptr(out[k])) return MWAX_ERR_INVALID_ARG;
+  bool same = plan->graph != nullptr;
+  for (int k = 0; k < nj && same; ++k)
+    same = plan->graph_in[k] == voltages[k] && plan->graph_out[k] == out[k];
+  if (!same) {
+    if (plan->graph) {
+      cudaGraphExecDestroy(plan->graph);
+      plan->graph = nullptr;
+    }
+    // capture: every job's unpack, then one persistent launch over all items
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    std::vector<TcJob> tj(nj);
+    for (int k = 0; k < nj && e == cudaSuccess; ++k) {
+      const JobState &s = plan->jobs[k];
+      e = launch_unpack(reinterpret_cast<const uint8_t *>(voltages[k]), s.job.sample_bits,
+                        s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, 0, s.job.n_chan, s.op, cs);
+      tj[k].op = s.op;
+      tj[k].out = out[k];
+      tj[k].n_inputs = s.job.n_inputs;
+      tj[k].n_tiles = s.n_tiles;
+      tj[k].n_pairs = s.n_pairs;
+      tj[k].kb = s.kb;
+      tj[k].flush_blocks = s.flush_blocks;
+      tj[k].n_chan = s.job.n_chan;
+      tj[k].n_bl = s.n_bl;
+    }
+    if (e == cudaSuccess) e = launch_correlate_tc(tj.data(), nj, launch_cfg(plan), cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      plan->graph = nullptr;
+      return cuda_status(e);
+    }
+    plan->graph_in.assign(voltages, voltages + nj);
+    plan->graph_out.assign(out, out + nj);
+  }
+  TimedLaunch tg(plan, 1, plan->stream);
+  cudaError_t e = cudaGraphLaunch(plan->graph, plan->stream);
+  tg.done();
+  return cuda_status(e);
+}
+
+mwax_status mwax_plan_set_timing(mwax_plan_t plan, int enable) {
+  if (!plan) return MWAX_ERR_INVALID_ARG;
+  plan->timing = enable != 0;
+  return MWAX_OK;
+}
+
+mwax_status mwax_plan_get_timing(mwax_plan_t plan, mwax_timing *t) {
+  if (!plan || !t) return MWAX_ERR_INVALID_ARG;
+  memset(t, 0, sizeof(*t));
+  cudaError_t e = cudaStreamSynchronize(plan->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (const auto &r : plan->recs) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, plan->ev_pool[r.start], plan->ev_pool[r.stop]);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (r.kind == 0) {
+      t->unpack_ms += ms;
+      t->unpack_launches += 1;
+    } else {
+      t->correlate_ms += ms;
+      t->correlate_launches += 1;
+    }
+  }
+  plan->recs.clear();
+  return MWAX_OK;
+}
+
+mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int n_inputs,
+                                int n_chan, int n_time, void *out_host) {
+  if (!plan || plan->batch || !voltages_host || !out_host) return MWAX_ERR_INVALID_ARG;
+  JobState &s = plan->jobs[0];
+  if (n_inputs != s.job.n_inputs || n_chan != s.job.n_chan || n_time != s.job.n_time)
+    return MWAX_ERR_SHAPE_MISMATCH;
+  const int G = s.chan_group;
+  cudaError_t e = cudaSuccess;
+  if (!plan->h2d) {
+    plan->stage_in_bytes = s.in_chan_bytes * G;
+    plan->stage_out_bytes = s.out_chan_bytes * G;
+    e = cudaStreamCreateWithFlags(&plan->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&plan->stage_in[k], (size_t)plan->stage_in_bytes);
+      if (e == cudaSuccess) e = cudaMalloc(&plan->stage_out[k], (size_t)plan->stage_out_bytes);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_in[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_comp[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_out[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  const uint8_t *hin = reinterpret_cast<const uint8_t *>(voltages_host);
+  uint8_t *hout = reinterpret_cast<uint8_t *>(out_host);
+  // the copy streams must not start before earlier work on the plan's stream
+  e = cudaEventRecord(plan->ev_comp[0], plan->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->h2d, plan->ev_comp[0], 0);
+  int64_t gi = 0;
+  for (int64_t c0 = 0; c0 < n_chan && e == cudaSuccess; c0 += G, ++gi) {
+    const int k = (int)(gi & 1);
+    const int nc = (int)std::min<int64_t>(G, n_chan - c0);
+    // input stage k is free once the compute of group gi-2 finished
+    if (gi >= 2) e = cudaStreamWaitEvent(plan->h2d, plan->ev_comp[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(plan->stage_in[k], hin + c0 * s.in_chan_bytes, nc * s.in_chan_bytes,
+                          cudaMemcpyHostToDevice, plan->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_in[k], plan->h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->stream, plan->ev_in[k], 0);
+    // output stage k is free once its copy-out of group gi-2 finished
+    if (e == cudaSuccess && gi >= 2) e = cudaStreamWaitEvent(plan->stream, plan->ev_out[k], 0);
+    if (e != cudaSuccess) break;
+    mwax_status r;
+    if (plan->engine == MWAX_ENGINE_PLAIN) {
+      r = MWAX_OK;
+      for (int c = 0; c < nc && r == MWAX_OK; ++c)
+        r = cuda_status(launch_plain_channel(
+            plan->stage_in[k] + (int64_t)c * s.in_chan_bytes, s.job.sample_bits, s.job.n_inputs,
+            s.job.n_time, reinterpret_cast<int32_t *>(plan->stage_out[k]) + (int64_t)c * s.n_bl * 2,
+            plan->stream));
+    } else {
+      r = run_group(plan, s, plan->stage_in[k], 0, nc, plan->stage_out[k], plan->stream);
+    }
+    if (r != MWAX_OK) return r;
+    e = cudaEventRecord(plan->ev_comp[k], plan->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->d2h, plan->ev_comp[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hout + c0 * s.out_chan_bytes, plan->stage_out[k], nc * s.out_chan_bytes,
+                          cudaMemcpyDeviceToHost, plan->d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[k], plan->d2h);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(plan->d2h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+  return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// mwax_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mwax.h"
+
+namespace mwax {
+
+// Tensor-core tiling: a tile is 128 inputs (the MMA M and N extent); an
+// operand row block is 128 bytes, one 128-byte swizzle row, holding S
+// samples of re followed by S samples of im for one input.
+constexpr int kTile = 128;
+constexpr int kRowBytes = 128;
+
+inline int samples_per_block(int sample_bits) { return sample_bits == 4 ? 64 : 32; }
+inline int bytes_per_sample(int sample_bits) { return sample_bits == 4 ? 1 : 2; }
+inline int sample_max(int sample_bits) { return sample_bits == 4 ? 7 : 127; }
+
+// ---- plain CUDA-core correlator (one launch per channel) ------------------
+cudaError_t launch_plain_channel(const uint8_t *volt_chan, int sample_bits, int n_inputs,
+                                 int n_time, int32_t *out_chan, cudaStream_t s);
+
+// ---- unpack: packed samples -> tensor-core operand rows --------------------
+// volt: [n_chan_total][T][N] packed; op: [n_chan][n_tiles*128][kb][128 B].
+cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
+                          int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
+                          cudaStream_t s);
+
+// ---- tensor-core correlator -------------------------------------------------
+#define MWAX_MAX_JOBS 8
+
+struct TcJob {
+  const uint8_t *op;  // operand rows [n_chan][n_tiles*128][kb][128 B]
+  void *out;          // visibilities of the first of these n_chan channels
+  int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks, n_chan;
+  int64_t n_bl;
+};
+
+struct TcLaunch {
+  int sample_bits;
+  int kind;  // mwax_kind
+  int grid;
+  int stages;
+  int32_t *status;
+  unsigned long long timeout_ns;
+};
+
+// Encodes one TMA descriptor per job and launches the persistent kernel over
+// the concatenated work items (job by job, channel-major, tile pairs inside).
+cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
+                                cudaStream_t s);
+int correlate_tc_smem_bytes(int stages);
+int correlate_tc_max_stages();
+cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages);
+
+}  // namespace mwax

@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function include/mwax.h declares; host-only entry points work on the CPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mwax.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mwax_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("mwax_plan", "mwax_correlate", "mwax_destroy", "mwax_baseline_index",
+              "mwax_plan_batch", "mwax_correlate_batch", "mwax_calib_loss", "mwax_calib_grad"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(mwax_lib):
+    lib = ctypes.CDLL(mwax_lib.LIB_PATH)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", mwax_lib.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (mwax_[a-z_]+)\b", out))
+    assert set(declared_functions()) <= exported
+    assert set(mwax_lib.SIGNATURES) == set(declared_functions())
+
+
+def test_host_helpers(mwax_lib):
+    mw = mwax_lib
+    assert mw.n_baselines(512) == 131328
+    assert mw.n_baselines(1024) == 524800
+    assert mw.baseline_index(3, 1) == 7
+    assert mw.baseline_index(1, 3) == -1
+    for b in (0, 1, 2, 7, 524799, 131327):
+        i, j = mw.baseline_pair(b)
+        assert mw.baseline_index(i, j) == b and 0 <= j <= i
+    assert mw.max_n_time(8) == 66572
+    assert mw.max_n_time(4) == 21913098
+    assert mw.max_n_time(5) == -1
+
+
+def test_plan_rejects_bad_jobs_before_touching_the_device(mwax_lib):
+    """Argument and int32-bound checks happen before any CUDA call, so they
+    return their status on a machine without a GPU."""
+    mw = mwax_lib
+    L = mw.lib()
+    h = ctypes.c_void_p()
+
+    def plan(**kw):
+        j = mw._job(**kw)
+        return L.mwax_plan(ctypes.byref(h), ctypes.byref(j), None)
+
+    assert plan(n_inputs=4, n_chan=1, n_time=66573, sample_bits=8) == 3  # OVERFLOW_BOUND
+    assert plan(n_inputs=0, n_chan=1, n_time=10, sample_bits=8) == 1
+    assert plan(n_inputs=4, n_chan=1, n_time=10, sample_bits=6) == 1
+    assert plan(n_inputs=4, n_chan=1, n_time=10, sample_bits=4, kind=1) == 4  # FP16 needs 8-bit
+    assert L.mwax_plan(None, None, None) == 1
+    assert h.value is None
+    assert L.mwax_destroy(None) == 0

@@ -1,0 +1,231 @@
+"""GPU parity of the correlator against the CPU oracle, through the C ABI.
+
+Integer visibilities must match the oracle bit for bit.  Inputs are filled
+on the device by the shared generator and regenerated on the host for the
+oracle (never copied back from the GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_exact, device_volt, oracle_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mw(mwax_lib):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return mwax_lib
+
+
+def run(mw, spec, engine, **kw):
+    import torch
+
+    v = device_volt(spec)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, spec.sample_bits, engine=engine, **kw)
+    out = p.correlate(v)
+    st = p.status()
+    torch.cuda.synchronize()
+    assert st == 0, f"device status {st}"
+    res = out.cpu().numpy()
+    p.close()
+    return res
+
+
+# ---------------------------------------------------------------------------
+def test_device_generator_matches_host(mw):
+    import torch
+
+    for spec, chans in ((synth.spec_c0(), None), (synth.spec_c1().with_(n_time=300), (0, 767)),
+                        (synth.spec_c2().with_(n_time=100), (5, 3071))):
+        if chans is None:
+            d = device_volt(spec).cpu().numpy()
+            h = synth.fill_host(spec).ravel()
+            np.testing.assert_array_equal(d, h)
+        else:
+            for c in chans:
+                d = device_volt(spec, chan0=c, n_chan=1).cpu().numpy()
+                h = synth.fill_host(spec, chans=[c]).ravel()
+                np.testing.assert_array_equal(d, h)
+    torch.cuda.synchronize()
+
+
+SMALL = [(1, 1, 1), (2, 7, 1), (3, 8, 3), (17, 33, 2), (64, 100, 3), (129, 65, 2), (130, 64, 1),
+         (257, 40, 1)]
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+@pytest.mark.parametrize("N,T,C", SMALL)
+def test_plain_small(mw, bits, N, T, C):
+    spec = synth.Spec("s", N, C, T, bits, seed=N * 131 + T, sigma=2 if bits == 4 else 40,
+                      tone_amp=0.3)
+    assert_exact(run(mw, spec, mw.ENGINE_PLAIN), oracle_for(spec, range(C)), f"plain {N},{T},{C}")
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+@pytest.mark.parametrize("N,T,C", SMALL)
+def test_tensor_small(mw, bits, N, T, C):
+    spec = synth.Spec("s", N, C, T, bits, seed=N * 131 + T + 7, sigma=2 if bits == 4 else 40,
+                      tone_amp=0.3)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tc {N},{T},{C}")
+
+
+def test_c0_both_engines(mw):
+    spec = synth.spec_c0()
+    ref = oracle_for(spec, range(spec.n_chan))
+    assert_exact(run(mw, spec, mw.ENGINE_PLAIN), ref, "plain c0")
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), ref, "tensor c0")
+
+
+@pytest.mark.parametrize("bits,flush", [(8, 1), (8, 2), (8, 5), (4, 1), (4, 3)])
+def test_tensor_flush_segments(mw, bits, flush):
+    """Short FP32 segments: many int32 flushes per item, ragged last segment."""
+    spec = synth.Spec("f", 200, 2, 1000, bits, seed=flush + bits, sigma=2 if bits == 4 else 60)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, flush_blocks=flush), oracle_for(spec, range(2)),
+                 f"flush {flush}")
+
+
+def test_tensor_multiple_channel_groups(mw):
+    spec = synth.Spec("g", 140, 7, 130, 4, seed=3, sigma=2)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, chan_group=3), oracle_for(spec, range(7)), "groups")
+
+
+@pytest.mark.parametrize("bits", [4, 8])
+def test_exact_window_big_then_small(mw, bits):
+    """Accumulator near the top of its segment window, then +-1 addends: any
+    loss of low-order bits in the tensor-core accumulation shows up."""
+    T = 20000 if bits == 4 else 2000
+    split = 19000 if bits == 4 else 500
+    spec = synth.Spec("bs", 130, 2, T, bits, seed=11, kind=synth.SYNTH_BIGSMALL, t_split=split)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(2)), "big-small")
+
+
+def test_exact_random_max_magnitude(mw):
+    spec = synth.Spec("rm", 256, 2, 3000, 8, seed=12, kind=synth.SYNTH_RANDMAX)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(2)), "randmax")
+
+
+def test_int32_bound_at_max_integration(mw):
+    """All samples (127, 127) at the largest allowed T: V_ii = 2,147,479,576."""
+    T = mw.max_n_time(8)
+    spec = synth.Spec("cmax", 3, 1, T, 8, seed=0, kind=synth.SYNTH_CONST, c_re=127, c_im=127)
+    out = run(mw, spec, mw.ENGINE_TENSOR)
+    assert out[0, 0, 0] == 2_147_479_576 and out[0, 0, 1] == 0
+    assert_exact(out, oracle_for(spec, [0]), "bound")
+    out = run(mw, spec, mw.ENGINE_PLAIN)
+    assert out[0, 0, 0] == 2_147_479_576
+
+
+def test_quarter_tone_closed_form(mw):
+    N, T = 150, 999
+    rng = np.random.default_rng(2)
+    c = rng.integers(-7, 8, (N, 2))
+    spec = synth.Spec("q", N, 1, T, 4, seed=0, kind=synth.SYNTH_QUARTER, ci=c)
+    out = run(mw, spec, mw.ENGINE_TENSOR)[0]
+    cc = c[:, 0] + 1j * c[:, 1]
+    ii, jj = np.tril_indices(N)
+    e = T * cc[ii] * np.conj(cc[jj])
+    np.testing.assert_array_equal(out[:, 0], e.real.astype(np.int64))
+    np.testing.assert_array_equal(out[:, 1], e.imag.astype(np.int64))
+
+
+def test_fp16_variant_error(mw):
+    """FP16 inputs, FP32 accumulation without integer flushes: error against
+    the exact (int64 = FP64-exact) oracle stays within the FP32 summation
+    bound 2T * 2^-24 (autos-normalised)."""
+    import torch
+
+    spec = synth.Spec("h", 128, 2, 10000, 8, seed=21, sigma=20)
+    v = device_volt(spec)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, kind=mw.KIND_FP16)
+    out = p.correlate(v)
+    assert p.status() == 0
+    got = out.cpu().numpy().astype(np.float64)
+    _, ref = oracle_for(spec, range(2), want64=True)
+    N = spec.n_inputs
+    ii, jj = np.tril_indices(N)
+    auto = ref[:, [oracle.baseline_index(i, i) for i in range(N)], 0].astype(np.float64)
+    norm = np.sqrt(auto[:, ii] * auto[:, jj])
+    err = np.abs(got - ref).max(axis=2) / norm
+    assert err.max() <= 2 * spec.n_time * 2.0**-24
+    p.close()
+    torch.cuda.synchronize()
+
+
+def test_batch_uneven_jobs(mw):
+    import torch
+
+    jobs = [(48, 4, 200), (128, 3, 500), (300, 2, 1000), (130, 2, 70)]
+    specs = [synth.Spec(f"b{k}", n, c, t, 4, seed=40 + k, sigma=2, tone_amp=0.3)
+             for k, (n, c, t) in enumerate(jobs)]
+    bp = mw.BatchPlan(jobs, sample_bits=4)
+    vs = [device_volt(s) for s in specs]
+    outs = bp.correlate(vs)
+    outs = bp.correlate(vs, outs)  # graph replay
+    assert bp.status() == 0
+    for s, o in zip(specs, outs):
+        assert_exact(o.cpu().numpy(), oracle_for(s, range(s.n_chan)), s.name)
+    bp.close()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_host_buffers(mw, engine):
+    import torch
+
+    spec = synth.spec_c0()
+    h = torch.from_numpy(synth.fill_host(spec).ravel()).pin_memory()
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, engine=engine, chan_group=7)
+    out = torch.empty((spec.n_chan, spec.n_inputs * (spec.n_inputs + 1) // 2, 2),
+                      dtype=torch.int32).pin_memory()
+    p.correlate_host(h, out)
+    assert p.status() == 0
+    assert_exact(out.numpy(), oracle_for(spec, range(spec.n_chan)), "host path")
+    p.close()
+
+
+def test_shape_mismatch_and_host_pointer_rejected(mw):
+    import torch
+
+    p = mw.Plan(8, 2, 10, 4)
+    v = torch.zeros(8 * 2 * 10, dtype=torch.uint8, device="cuda")
+    out = p.empty_out()
+    assert mw.lib().mwax_correlate(p._h, v.data_ptr(), 8, 3, 10, out.data_ptr()) == 2
+    hv = torch.zeros(8 * 2 * 10, dtype=torch.uint8)
+    assert mw.lib().mwax_correlate(p._h, hv.data_ptr(), 8, 2, 10, out.data_ptr()) == 1
+    p.close()
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, in the launch configuration the benchmark times,
+# checked on sampled channels the oracle recomputes one by one
+# ---------------------------------------------------------------------------
+def _full_size(mw, spec, chans, **kw):
+    import torch
+
+    v = device_volt(spec)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, spec.sample_bits, **kw)
+    out = p.correlate(v)
+    assert p.status() == 0
+    del v
+    got = out[list(chans)].cpu().numpy()
+    del out
+    p.close()
+    torch.cuda.empty_cache()
+    assert_exact(got, oracle_for(spec, chans), spec.name)
+
+
+def test_full_size_c1_sampled(mw):
+    spec = synth.spec_c1()
+    _full_size(mw, spec, [0, 1, 383, 766, 767])
+
+
+def test_full_size_c2_sampled(mw):
+    spec = synth.spec_c2()
+    rng = np.random.default_rng(2)
+    chans = sorted(set([0, spec.n_chan - 1] + rng.choice(spec.n_chan, 6, replace=False).tolist()))
+    _full_size(mw, spec, chans)
