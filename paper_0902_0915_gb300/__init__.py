@@ -311,11 +311,15 @@ def calib_workspace(n_inputs: int, n_chan: int, device=None):
 
 
 def _f32_pairs(t):
+    """complex64 (or float32 [..., 2]) CUDA tensor -> contiguous float32 pairs."""
     torch = _torch()
+    if not t.is_cuda:
+        raise ValueError("calibration tensors must be CUDA tensors")
+    t = t.contiguous()
     if t.dtype == torch.complex64:
         t = torch.view_as_real(t)
-    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
-        raise ValueError("calibration tensors must be contiguous CUDA complex64/float32 pairs")
+    if t.dtype != torch.float32 or t.shape[-1] != 2:
+        raise ValueError("calibration tensors must be complex64 or float32 (re, im) pairs")
     return t
 
 

@@ -37,7 +37,8 @@ def problem(N, C, seed, noise=0.05, gain_err=0.05):
     V = g_true[ii] * np.conj(g_true[jj]) * M
     V = V + noise * np.abs(M).mean() * (rng.standard_normal((C, B)) + 1j * rng.standard_normal((C, B)))
     g = g_true * (1 + gain_err * (rng.standard_normal(N) + 1j * rng.standard_normal(N)))
-    return V.astype(np.complex64), M.astype(np.complex64), g.astype(np.complex64)
+    return (np.ascontiguousarray(V, np.complex64), np.ascontiguousarray(M, np.complex64),
+            np.ascontiguousarray(g, np.complex64))
 
 
 def gpu_loss_grad(mw, V, M, g):
