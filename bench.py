@@ -227,6 +227,11 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: every rank correlates its own full workload; strong: the "
+                         "workload's channels are split across ranks")
+    ap.add_argument("--chan", type=int, default=0,
+                    help="override the channel count (small cases for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -234,6 +239,9 @@ def main():
 
     mk, desc = workloads()[args.workload]
     spec = mk()
+    if args.chan > 0:
+        spec = spec.with_(n_chan=args.chan)
+        desc = f"{desc}; channels reduced to {args.chan}"
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,12 +259,23 @@ def main():
     mw.ensure_built()
     if not os.path.exists(synth.CUDA_LIB):
         synth.build()
-    # weak scaling: every rank correlates its own full workload (its own band)
-    rspec = spec.with_(seed=spec.seed + 1000 * rank) if rank else spec
+    from paper_0902_0915_gb300.shard import channel_range
+
+    if args.scaling == "weak":
+        # every rank correlates its own full workload (its own band)
+        rspec = spec.with_(seed=spec.seed + 1000 * rank) if rank else spec
+        chan0 = 0
+    else:
+        # the workload's channels split into contiguous ranges, no exchange
+        chan0, chan1 = channel_range(spec.n_chan, rank, world)
+        rspec = spec.with_(n_chan=chan1 - chan0)
     stream = torch.cuda.current_stream(dev)
     vol = torch.empty(rspec.n_chan * rspec.n_time * rspec.n_inputs * rspec.bytes_per_sample,
                       dtype=torch.uint8, device=dev)
-    synth.fill_device(rspec, vol)
+    if args.scaling == "weak":
+        synth.fill_device(rspec, vol)
+    else:
+        synth.fill_device(spec, vol, chan0=chan0, n_chan=rspec.n_chan)
     engine = mw.ENGINE_TENSOR if args.engine == "tensor" else mw.ENGINE_PLAIN
     plan = mw.Plan(rspec.n_inputs, rspec.n_chan, rspec.n_time, rspec.sample_bits, engine=engine,
                    stream=stream)
@@ -291,7 +310,8 @@ def main():
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     ms_per_step = elapsed_ms / args.steps
     units = cmacs(rspec)
-    value = units * world / (ms_per_step / 1e3) / 1e12
+    total_units = units * world if args.scaling == "weak" else cmacs(spec)
+    value = total_units / (ms_per_step / 1e3) / 1e12
     rtf = sky_seconds(rspec) / (ms_per_step / 1e3)
 
     peaks, peak_src = load_peaks()
@@ -316,7 +336,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "TCMAC/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": args.scaling, "vs_baseline": None,
         "dtype": "f16" if rspec.sample_bits == 8 else "e4m3",
         "data": "synthetic (seeded Philox4x64-10 channelised voltages, generated in HBM)",
         "config": {"workload": f"{args.workload}: {desc}", "n_inputs": rspec.n_inputs,
@@ -370,7 +390,7 @@ def main():
                 plan.correlate_host(hin, hout)
             dt = (time.perf_counter() - t0) / n_e2e
             dt = max_over_ranks(dt, world)
-            line["e2e"] = {"value": units * world / dt / 1e12, "unit": "TCMAC/s",
+            line["e2e"] = {"value": total_units / dt / 1e12, "unit": "TCMAC/s",
                            "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b,
                            "ms_per_step": dt * 1e3, "steps": n_e2e}
 

@@ -1,0 +1,75 @@
+"""Multi-rank channel sharding on CPU (gloo, world size 2 and 3): every rank
+correlates its own contiguous channel range, rank 0 gathers the blocks, and
+the concatenation equals the single-process result bit for bit.  The
+correlation on each rank is the CPU oracle here; on GPUs it is the library,
+with the same partition (bench.py --scaling strong)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_0902_0915_gb300.shard import all_ranges, channel_range
+
+
+def test_ranges_partition_the_channels():
+    for n in (0, 1, 7, 768, 3072):
+        for w in (1, 2, 3, 8):
+            rs = all_ranges(n, w)
+            assert rs[0][0] == 0 and rs[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+            sizes = [b - a for a, b in rs]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        channel_range(10, 2, 2)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    spec = synth.spec_c0().with_(n_chan=11, n_time=200)
+    c0, c1 = channel_range(spec.n_chan, rank, world)
+    v = synth.fill_host(spec, chans=list(range(c0, c1)), threads=1)
+    out = oracle.correlate(v, spec.sample_bits, spec.n_inputs, c1 - c0, spec.n_time, n_threads=1)
+    blocks = [None] * world
+    dist.all_gather_object(blocks, out)
+    if rank == 0:
+        q.put(np.concatenate(blocks, axis=0))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_equals_single(world):
+    import torch.multiprocessing as mp
+
+    import oracle
+    import synth
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    spec = synth.spec_c0().with_(n_chan=11, n_time=200)
+    ref = oracle.correlate(synth.fill_host(spec), 4, spec.n_inputs, spec.n_chan, spec.n_time)
+    np.testing.assert_array_equal(got, ref)
