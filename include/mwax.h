@@ -193,6 +193,30 @@ mwax_status mwax_calib_loss_grad(const float *V, const float *M, const float *g,
                                  int n_chan, void *workspace, float *loss, float *grad,
                                  cudaStream_t stream);
 
+/* ---- allocation-free calibration -------------------------------------------
+ * No counterpart in the paper.  For callers that must not allocate device
+ * memory when they evaluate the loss -- a real-time loop in which
+ * cudaMalloc/cudaFree would synchronise the device and add unbounded latency
+ * to every integration, or an application whose device memory all belongs
+ * to another allocator.  Same result as mwax_calib_loss_grad, but the
+ * partial sums go to a fixed array of mwax_calib_static_workspace_bytes()
+ * (4 MiB) inside the library that every GPU which loads it keeps until the
+ * process exits; this call allocates nothing.
+ *   - Shapes whose mwax_calib_workspace_bytes(n_inputs, n_chan) exceeds the
+ *     array are rejected with MWAX_ERR_INVALID_ARG before any launch
+ *     (1024 inputs need about 2.2 MB, for any n_chan).
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls on a device share the array: calls that overlap on the GPU
+ *     (different streams without ordering between them) race and give wrong
+ *     results.  The array keeps the last call's contents; each call writes
+ *     every slot it reads, so nothing needs clearing between calls.
+ * loss and/or grad (device; one may be NULL) as in mwax_calib_loss_grad. */
+int64_t mwax_calib_static_workspace_bytes(void);
+mwax_status mwax_calib_loss_grad_static(const float *V, const float *M, const float *g,
+                                        int n_inputs, int n_chan, float *loss, float *grad,
+                                        cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

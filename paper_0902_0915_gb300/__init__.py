@@ -78,6 +78,8 @@ SIGNATURES = {
     "mwax_calib_loss": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     "mwax_calib_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     "mwax_calib_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "mwax_calib_static_workspace_bytes": (_I64, []),
+    "mwax_calib_loss_grad_static": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
 }
 
 

@@ -19,6 +19,8 @@
 // kernel gathers them per input in a fixed order.  No atomics, FP32 only
 // (Kahan-compensated accumulation inside a thread, fixed trees across
 // threads).  One pass reads V and M once.
+#include <mutex>
+
 #include "mwax_internal.h"
 
 namespace mwax {
@@ -271,3 +273,56 @@ mwax_status mwax_calib_grad(const float *V, const float *M, const float *g, int 
 }
 
 }  // extern "C"
+
+// ---- allocation-free variant ---------------------------------------------------
+// Some callers cannot allocate device memory at the point where they evaluate
+// the loss: a real-time loop (like the MWA's) where cudaMalloc/cudaFree would
+// add device-wide synchronisation and unbounded latency to every integration,
+// or a host application whose device memory is entirely owned by another
+// allocator.  For them, the partial sums live in this fixed array instead of
+// a caller-provided workspace.  Every GPU that loads the library holds the
+// array until the process exits.
+namespace mwax {
+namespace {
+
+constexpr int64_t kStaticWsBytes = int64_t(4) << 20;  // 4 MiB: 1024 inputs need ~2.2 MB
+static __device__ __align__(256) uint8_t g_calib_static_ws[kStaticWsBytes];
+
+constexpr int kMaxStaticDevices = 256;
+std::mutex g_static_ws_mu;
+void *g_static_ws_addr[kMaxStaticDevices];
+
+// Device address of the array on the current device, looked up once per
+// device (host code cannot use the array's name as a device pointer).
+cudaError_t static_ws_address(void **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxStaticDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_ws_mu);
+  if (!g_static_ws_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_calib_static_ws);
+    if (e != cudaSuccess) return e;
+    g_static_ws_addr[dev] = p;
+  }
+  *out = g_static_ws_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace mwax
+
+extern "C" int64_t mwax_calib_static_workspace_bytes(void) { return mwax::kStaticWsBytes; }
+
+extern "C" mwax_status mwax_calib_loss_grad_static(const float *V, const float *M, const float *g,
+                                                   int n_inputs, int n_chan, float *loss,
+                                                   float *grad, cudaStream_t stream) {
+  const int64_t need = mwax_calib_workspace_bytes(n_inputs, n_chan);
+  if (need < 0 || need > mwax::kStaticWsBytes) return MWAX_ERR_INVALID_ARG;
+  void *ws = nullptr;
+  if (mwax::static_ws_address(&ws) != cudaSuccess) return MWAX_ERR_CUDA;
+  // Every partial-sum slot the gather kernel reads is written first by the
+  // tile kernel of the same call, so nothing in the array needs clearing.
+  return mwax_calib_loss_grad(V, M, g, n_inputs, n_chan, ws, loss, grad, stream);
+}
