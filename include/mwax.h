@@ -84,7 +84,10 @@ typedef struct {
   int32_t engine;      /* mwax_engine                                          */
   int32_t flush_blocks;    /* tuning: K-blocks per exact FP32 segment (0 = largest safe) */
   int32_t chan_group;      /* tuning: channels unpacked per pass (0 = auto)              */
-  int32_t reserved[8];     /* must be zero                                                */
+  int32_t stages;          /* tuning: shared-memory pipeline stages, 2..6 (0 = auto)     */
+  int32_t prefetch;        /* tuning: K-blocks of L2 prefetch ahead, 1..64 (0 = auto,
+                              which is none; -1 = none)                                   */
+  int32_t reserved[6];     /* must be zero                                                */
 } mwax_job;
 
 /* Read-only description of a plan's choices. */
@@ -95,6 +98,8 @@ typedef struct {
   int32_t flush_blocks;      /* K-blocks accumulated in FP32 before the int32 flush   */
   int32_t chan_group;        /* channels per unpack/correlate pass                     */
   int32_t grid;              /* persistent CTAs of the correlate kernel                */
+  int32_t stages;            /* shared-memory pipeline stages                          */
+  int32_t prefetch;          /* K-blocks of L2 prefetch ahead of the TMA loads         */
   int64_t scratch_bytes;     /* device scratch owned by the plan                       */
   int64_t work_items;        /* (job, channel, tile pair) items per call               */
 } mwax_plan_info;

@@ -37,13 +37,15 @@ class Job(ctypes.Structure):
                 ("n_time", ctypes.c_int32), ("sample_bits", ctypes.c_int32),
                 ("kind", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("flush_blocks", ctypes.c_int32), ("chan_group", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("n_jobs", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("samples_per_block", ctypes.c_int32), ("flush_blocks", ctypes.c_int32),
                 ("chan_group", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64), ("work_items", ctypes.c_int64)]
 
 
@@ -149,10 +151,11 @@ def _stream_handle(stream=None) -> int:
 
 
 def _job(n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, engine=ENGINE_TENSOR,
-         flush_blocks=0, chan_group=0) -> Job:
+         flush_blocks=0, chan_group=0, stages=0, prefetch=0) -> Job:
     j = Job()
     j.n_inputs, j.n_chan, j.n_time, j.sample_bits = n_inputs, n_chan, n_time, sample_bits
     j.kind, j.engine, j.flush_blocks, j.chan_group = kind, engine, flush_blocks, chan_group
+    j.stages, j.prefetch = stages, prefetch
     return j
 
 
@@ -165,8 +168,10 @@ class Plan:
     [n_chan, N(N+1)/2, 2] (re, im)."""
 
     def __init__(self, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,
-                 engine=ENGINE_TENSOR, flush_blocks=0, chan_group=0, stream=None):
-        self.job = _job(n_inputs, n_chan, n_time, sample_bits, kind, engine, flush_blocks, chan_group)
+                 engine=ENGINE_TENSOR, flush_blocks=0, chan_group=0, stages=0, prefetch=0,
+                 stream=None):
+        self.job = _job(n_inputs, n_chan, n_time, sample_bits, kind, engine, flush_blocks,
+                        chan_group, stages, prefetch)
         self.shape = (n_inputs, n_chan, n_time)
         self.sample_bits, self.kind, self.engine = sample_bits, kind, engine
         self._h = _P()

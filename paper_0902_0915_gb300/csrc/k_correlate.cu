@@ -7,8 +7,8 @@
 //     Im V_ij = sum_t xi_i xr_j - xr_i xi_j
 // as a dense rank-T Hermitian update on the 5th-generation tensor cores.
 //
-// Operands come from k_unpack.cu: per input row, 128-byte blocks of
-// [re x S | im x S] exact small floats (binary16 for 8-bit samples, S = 32;
+// Operands come from k_unpack.cu: for every block of S time samples and every
+// input, a 128-byte row [re x S | im x S] of exact small floats (binary16 for 8-bit samples, S = 32;
 // E4M3 for 4-bit samples, S = 64).  A block is one row of a 128-byte
 // swizzled K-major shared-memory tile, and one MMA consumes a 32-byte slice
 // of it: slices 0,1 hold re, slices 2,3 hold im.  Per block the MMA warp
@@ -47,8 +47,9 @@ namespace {
 
 constexpr int kWarps = 10;
 constexpr int kThreads = kWarps * 32;
+constexpr int kEpiWarp0 = 2;                   // warps 2..9: epilogue
 constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
-constexpr int kStageBytes = 2 * kTileBytes;    // A + B
+constexpr int kStageBytes = 2 * kTileBytes;    // A_I | A_J
 constexpr int kMaxStages = 6;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;  // re 128 | im 128
@@ -67,7 +68,7 @@ struct KParams {
   int32_t *status;
   int64_t n_items;
   unsigned long long timeout_ns;
-  int32_t n_jobs, stages;
+  int32_t n_jobs, stages, prefetch;
 };
 
 struct KMaps {
@@ -131,6 +132,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
+// Fire-and-forget L2 prefetch of one box of the tensor (no completion tracking).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -157,7 +166,8 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 }
 
 // Instruction descriptor: FP32 accumulate, A/B type code 0 (F16 for
-// kind::f16, E4M3 for kind::f8f6f4), K-major A and B, M = N = 128.
+// kind::f16, E4M3 for kind::f8f6f4), optional negation of B, K-major A and
+// B, M = N = 128.
 __host__ __device__ constexpr uint32_t make_idesc(bool negate_b) {
   return (1u << 4) | ((negate_b ? 1u : 0u) << 14) | ((uint32_t)(kTile >> 3) << 17) |
          ((uint32_t)(kTile >> 4) << 24);
@@ -252,6 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long tmo = p.timeout_ns;
+  const uint32_t smem_base = smem_u32(smem);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -284,52 +295,83 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < p.n_jobs; ++j)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[j]))
                      : "memory");
+    // stage / phase advance incrementally: no division in the per-block path
+    int stage = 0;
+    uint32_t phase = 0;
     int64_t issued = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
       const Item it = decode_item(p, item);
       const KJob &jb = p.job[it.job];
       const CUtensorMap *map = &maps.m[it.job];
-      const int yA = (it.c * jb.n_tiles + it.I) * kTile, yB = (it.c * jb.n_tiles + it.J) * kTile;
-      const uint32_t bytes = (it.I == it.J) ? kTileBytes : kStageBytes;
+      // operand rows: [chan][kb][row][128 B]; block kb of tile I starts at row
+      // (c * KB + kb) * n_rows + I * 128
+      const int n_rows = jb.n_tiles * kTile;
+      const int y0 = it.c * jb.kb * n_rows;
+      const int yA = y0 + it.I * kTile, yB = y0 + it.J * kTile;
+      const bool diag = it.I == it.J;
+      const uint32_t bytes = diag ? kTileBytes : 2 * kTileBytes;  // TMA bytes of this stage
+      // warm L2 for the first blocks of the item; later blocks are prefetched
+      // `prefetch` blocks ahead of their TMA load (first-touch misses go to DRAM)
+      const int pf = p.prefetch;
+      if (lane == 0)
+        for (int kb = 0; kb < pf && kb < jb.kb; ++kb) {
+          tma_prefetch_2d(map, 0, yA + kb * n_rows);
+          if (!diag) tma_prefetch_2d(map, 0, yB + kb * n_rows);
+        }
       for (int kb = 0; kb < jb.kb; ++kb) {
-        const int stage = (int)(issued % S);
-        const uint32_t phase = (uint32_t)((issued / S) & 1);
+        if (lane == 0 && pf > 0 && kb + pf < jb.kb) {
+          tma_prefetch_2d(map, 0, yA + (kb + pf) * n_rows);
+          if (!diag) tma_prefetch_2d(map, 0, yB + (kb + pf) * n_rows);
+        }
         if (!warp_wait(empty(stage), phase ^ 1u, abort_flag, tmo, lane)) {
           if (lane == 0) raise_timeout(abort_flag, p.status);
           ok = false;
           break;
         }
         if (lane == 0) {
-          const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
+          const uint32_t a = smem_base + (uint32_t)stage * kStageBytes;
           mbar_arrive_expect_tx(full(stage), bytes);
-          tma_load_2d(a, map, kb * kRowBytes, yA, full(stage));
-          if (it.I != it.J) tma_load_2d(a + kTileBytes, map, kb * kRowBytes, yB, full(stage));
+          tma_load_2d(a, map, 0, yA + kb * n_rows, full(stage));
+          if (!diag) tma_load_2d(a + kTileBytes, map, 0, yB + kb * n_rows, full(stage));
         }
         __syncwarp();
         ++issued;
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
       }
     }
     // wait (bounded) until every copy this warp issued has landed
     if (lane == 0) {
-      const int64_t first = issued > S ? issued - S : 0;
-      for (int64_t n = first; n < issued; ++n)
-        mbar_wait(full((int)(n % S)), (uint32_t)((n / S) & 1), nullptr, tmo);
+      int st = stage;
+      uint32_t ph = phase;
+      for (int64_t k = 0; k < issued && k < S; ++k) {
+        if (--st < 0) {
+          st = S - 1;
+          ph ^= 1u;
+        }
+        mbar_wait(full(st), ph, nullptr, tmo);
+      }
     }
     __syncwarp();
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t idesc = make_idesc(false);
     constexpr uint32_t idesc_neg = make_idesc(true);
-    int64_t consumed = 0;
+    int stage = 0;
+    uint32_t phase = 0;
     uint32_t seg = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
       const Item it = decode_item(p, item);
       const KJob &jb = p.job[it.job];
       const int F = jb.flush_blocks, KB = jb.kb;
+      const bool diag = it.I == it.J;
+      int in_seg = 0;  // blocks already accumulated in the current segment
       for (int kb = 0; kb < KB; ++kb) {
-        const bool seg_start = (kb % F) == 0;
+        const bool seg_start = in_seg == 0;
         const uint32_t buf = seg & 1u;
         if (seg_start) {
           if (!warp_wait(tempty(buf), ((seg >> 1) & 1u) ^ 1u, abort_flag, tmo, lane)) {
@@ -339,8 +381,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
         }
-        const int stage = (int)(consumed % S);
-        const uint32_t phase = (uint32_t)((consumed / S) & 1);
         if (!warp_wait(full(stage), phase, abort_flag, tmo, lane)) {
           if (lane == 0) raise_timeout(abort_flag, p.status);
           ok = false;
@@ -348,28 +388,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         if (lane == 0) {
-          const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
-          const uint32_t b = (it.I == it.J) ? a : a + kTileBytes;
+          const uint32_t a = smem_base + (uint32_t)stage * kStageBytes;
+          // descriptors of the 32-byte K slices: start address advances by 2 units of 16 B
+          const uint64_t da = sw128_desc(a);
+          const uint64_t db = diag ? da : sw128_desc(a + kTileBytes);
           const uint32_t d_re = tmem_base + buf * kAccCols;
           const uint32_t d_im = d_re + kTile;
           const uint32_t acc0 = seg_start ? 0u : 1u;
-#pragma unroll
-          for (int s = 0; s < 4; ++s)
-            tc_mma<BITS>(d_re, sw128_desc(a + 32 * s), sw128_desc(b + 32 * s), idesc,
-                         s == 0 ? acc0 : 1u);
-          tc_mma<BITS>(d_im, sw128_desc(a + 64), sw128_desc(b + 0), idesc, acc0);
-          tc_mma<BITS>(d_im, sw128_desc(a + 96), sw128_desc(b + 32), idesc, 1u);
-          tc_mma<BITS>(d_im, sw128_desc(a + 0), sw128_desc(b + 64), idesc_neg, 1u);
-          tc_mma<BITS>(d_im, sw128_desc(a + 32), sw128_desc(b + 96), idesc_neg, 1u);
+          tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
+          tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
+          tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
+          tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
+          tc_mma<BITS>(d_im, da + 4, db + 0, idesc, acc0);
+          tc_mma<BITS>(d_im, da + 6, db + 2, idesc, 1u);
+          tc_mma<BITS>(d_im, da + 0, db + 4, idesc_neg, 1u);
+          tc_mma<BITS>(d_im, da + 2, db + 6, idesc_neg, 1u);
           tc_commit(empty(stage));
         }
         __syncwarp();
-        ++consumed;
-        const bool seg_end = ((kb % F) == F - 1) || (kb == KB - 1);
-        if (seg_end) {
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+        if (++in_seg == F || kb == KB - 1) {
           if (lane == 0) tc_commit(tfull(buf));
           __syncwarp();
           ++seg;
+          in_seg = 0;
         }
       }
     }
@@ -381,8 +426,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ---------------- epilogue: flush + integration dump ----------------
-    const int q = warp & 3;         // tensor-memory lane quadrant of this warp
-    const int h = (warp - 2) >> 2;  // column half: local columns [64h, 64h + 64)
+    const int q = warp & 3;                 // tensor-memory lane quadrant of this warp
+    const int h = (warp - kEpiWarp0) >> 2;  // column half: local columns [64h, 64h + 64)
     uint32_t seg = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
@@ -502,9 +547,11 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   for (int j = 0; j < n_jobs; ++j) {
     const TcJob &job = jobs[j];
     if (job.flush_blocks < 1 || job.kb < 1 || job.n_tiles < 1) return cudaErrorInvalidValue;
-    const cuuint64_t rows = (cuuint64_t)job.n_chan * job.n_tiles * kTile;
-    cuuint64_t dims[2] = {(cuuint64_t)job.kb * kRowBytes, rows};
-    cuuint64_t strides[1] = {(cuuint64_t)job.kb * kRowBytes};
+    // [chan][kb][row][128 B] viewed as rows of 128 bytes
+    const cuuint64_t rows = (cuuint64_t)job.n_chan * job.kb * job.n_tiles * kTile;
+    if (rows > 0x7FFFFFFFull) return cudaErrorInvalidValue;  // TMA row coordinate is int32
+    cuuint64_t dims[2] = {(cuuint64_t)kRowBytes, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kRowBytes};
     cuuint32_t box[2] = {(cuuint32_t)kRowBytes, (cuuint32_t)kTile};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(&maps.m[j], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
@@ -528,6 +575,7 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   kp.timeout_ns = cfg.timeout_ns;
   kp.n_jobs = n_jobs;
   kp.stages = cfg.stages;
+  kp.prefetch = cfg.prefetch;
   if (items <= 0) return cudaSuccess;
   const int grid = (int)(items < cfg.grid ? items : cfg.grid);
   const int smem = correlate_tc_smem_bytes(cfg.stages);

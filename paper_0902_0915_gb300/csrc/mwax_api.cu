@@ -47,6 +47,7 @@ struct mwax_plan_s {
   int sample_bits = 4;
   int kind = MWAX_KIND_EXACT;
   int stages = 6;
+  int prefetch = 0;
   unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
   std::vector<mwax::JobState> jobs;
   uint8_t *scratch = nullptr;  // single-job plans: operand buffer for one channel group
@@ -98,7 +99,9 @@ mwax_status check_job(const mwax_job &j) {
   if (j.kind != MWAX_KIND_EXACT && j.kind != MWAX_KIND_FP16) return MWAX_ERR_INVALID_ARG;
   if (j.engine != MWAX_ENGINE_TENSOR && j.engine != MWAX_ENGINE_PLAIN) return MWAX_ERR_INVALID_ARG;
   if (j.flush_blocks < 0 || j.chan_group < 0) return MWAX_ERR_INVALID_ARG;
-  for (int k = 0; k < 8; ++k)
+  if (j.stages < 0 || j.stages == 1 || j.stages > correlate_tc_max_stages()) return MWAX_ERR_INVALID_ARG;
+  if (j.prefetch < -1 || j.prefetch > 64) return MWAX_ERR_INVALID_ARG;
+  for (int k = 0; k < 6; ++k)
     if (j.reserved[k] != 0) return MWAX_ERR_INVALID_ARG;
   if (j.kind == MWAX_KIND_FP16 && (j.sample_bits != 8 || j.engine != MWAX_ENGINE_TENSOR))
     return MWAX_ERR_UNSUPPORTED;
@@ -180,6 +183,7 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
   c.kind = p->kind;
   c.grid = p->sm_count;
   c.stages = p->stages;
+  c.prefetch = p->prefetch;
   c.status = p->status;
   c.timeout_ns = p->timeout_ns;
   return c;
@@ -325,6 +329,8 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
   p->engine = job->engine;
   p->sample_bits = job->sample_bits;
   p->kind = job->kind;
+  if (job->stages > 0) p->stages = job->stages;
+  if (job->prefetch != 0) p->prefetch = job->prefetch < 0 ? 0 : job->prefetch;
   if (p->engine == MWAX_ENGINE_TENSOR) {
     p->scratch_bytes = s.op_chan_bytes * s.chan_group;
     cudaError_t e = cudaMalloc(&p->scratch, (size_t)p->scratch_bytes);
@@ -361,6 +367,8 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
   p->batch = true;
   p->sample_bits = jobs[0].sample_bits;
   p->kind = jobs[0].kind;
+  if (jobs[0].stages > 0) p->stages = jobs[0].stages;
+  if (jobs[0].prefetch != 0) p->prefetch = jobs[0].prefetch < 0 ? 0 : jobs[0].prefetch;
   for (int k = 0; k < n_jobs; ++k) {
     JobState s;
     s.job = jobs[k];
@@ -401,6 +409,8 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   info->flush_blocks = s.flush_blocks;
   info->chan_group = plan->batch ? s.job.n_chan : s.chan_group;
   info->grid = plan->sm_count;
+  info->stages = plan->stages;
+  info->prefetch = plan->prefetch;
   info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
   int64_t items = 0;
   for (const auto &j : plan->jobs) items += (int64_t)j.job.n_chan * j.n_pairs;

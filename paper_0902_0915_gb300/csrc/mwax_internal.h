@@ -23,7 +23,7 @@ cudaError_t launch_plain_channel(const uint8_t *volt_chan, int sample_bits, int 
                                  int n_time, int32_t *out_chan, cudaStream_t s);
 
 // ---- unpack: packed samples -> tensor-core operand rows --------------------
-// volt: [n_chan_total][T][N] packed; op: [n_chan][n_tiles*128][kb][128 B].
+// volt: [n_chan_total][T][N] packed; op: [n_chan][kb][n_tiles*128][128 B].
 cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
                           int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
                           cudaStream_t s);
@@ -32,7 +32,7 @@ cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, in
 #define MWAX_MAX_JOBS 8
 
 struct TcJob {
-  const uint8_t *op;  // operand rows [n_chan][n_tiles*128][kb][128 B]
+  const uint8_t *op;  // operand rows [n_chan][kb][n_tiles*128][128 B]
   void *out;          // visibilities of the first of these n_chan channels
   int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks, n_chan;
   int64_t n_bl;
@@ -43,6 +43,7 @@ struct TcLaunch {
   int kind;  // mwax_kind
   int grid;
   int stages;
+  int prefetch;  // K-blocks of L2 prefetch ahead of the TMA loads (0 = none)
   int32_t *status;
   unsigned long long timeout_ns;
 };
