@@ -215,13 +215,275 @@ def run_reference(args, spec, desc, world, rank):
 
 
 # ---------------------------------------------------------------------------
+def fp16_variant(mw, spec, vol, stream, args):
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, kind=mw.KIND_FP16, stream=stream)
+    fout = p.empty_out()
+    p.correlate(vol, fout)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    reps = 3
+    for _ in range(reps):
+        p.correlate(vol, fout)
+    b.record(stream)
+    b.synchronize()
+    if p.status() != 0:
+        raise RuntimeError("FP16 variant: device status not OK")
+    ms = a.elapsed_time(b) / reps
+    chans = [0, spec.n_chan - 1]
+    got = fout[chans].double().cpu().numpy()
+    p.close()
+    _, ref = oracle.correlate(synth.fill_host(spec, chans=chans), 8, spec.n_inputs, len(chans),
+                              spec.n_time, want64=True)
+    ref = ref.astype(np.float64)
+    N = spec.n_inputs
+    ii, jj = np.tril_indices(N)
+    autos = ref[:, [i * (i + 1) // 2 + i for i in range(N)], 0]
+    norm = np.sqrt(autos[:, ii] * autos[:, jj])
+    err = np.abs(got - ref).max(axis=2)
+    big = np.abs(ref).max(axis=2) >= 0.01 * norm
+    return {"value": cmacs(spec) / (ms / 1e3) / 1e12, "unit": "TCMAC/s", "ms_per_step": ms,
+            "max_rel_err_autos_normalised": float((err / norm).max()),
+            "max_abs_err": float(err.max()),
+            "max_rel_err_where_abs_ge_1pct_of_autos": float((err[big] / np.abs(ref).max(axis=2)[big]).max()),
+            "fp32_bound_2T_eps": 2 * spec.n_time * 2.0 ** -24,
+            "channels_checked": chans, "reference": "int64 oracle (exact, equal to FP64)"}
+
+
+def run_batch(args):
+    """c3: four uneven sub-array jobs in one persistent launch per call,
+    replayed from a CUDA graph, against the plain per-channel form."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    import paper_0902_0915_gb300 as mw
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    specs = [synth.spec_c3(j) for j in range(4)]
+    desc = "batched jobs " + ", ".join(f"({s.n_inputs} in, {s.n_chan} ch, T={s.n_time})" for s in specs) + ", 4+4-bit"
+    units = sum(cmacs(s) for s in specs)
+    if args.impl == "reference":
+        times, done = [], 0.0
+        for k in range(args.steps + args.warmup):
+            s = specs[k % 4]
+            c = (k * 7) % s.n_chan
+            v = synth.fill_host(s, chans=[c])
+            t0 = time.perf_counter()
+            oracle.correlate(v, 4, s.n_inputs, 1, s.n_time)
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                times.append(dt)
+                done += cmacs(s) / s.n_chan
+        value = done / sum(times) / 1e12
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "TCMAC/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": sum(times) / len(times) * 1e3, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                          "config": {"workload": f"c3: {desc}", "step": "one channel of one job per step"},
+                          "cpu_baseline": {"value": value, "unit": "TCMAC/s", "cores": oracle.threads(),
+                                           "kind": "oracle", "sample": "one channel per step, jobs in turn"},
+                          "e2e": {"value": value, "unit": "TCMAC/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    mw.ensure_built()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    vols = []
+    for s in specs:
+        v = torch.empty(s.n_chan * s.n_time * s.n_inputs, dtype=torch.uint8, device="cuda")
+        synth.fill_device(s, v)
+        vols.append(v)
+    jobs = [(s.n_inputs, s.n_chan, s.n_time) for s in specs]
+    outs = [torch.empty((s.n_chan, s.n_inputs * (s.n_inputs + 1) // 2, 2), dtype=torch.int32,
+                        device="cuda") for s in specs]
+    tune, rep = {}, None
+    if not args.no_tune:
+        tune, rep = mw.autotune_batch(jobs, vols, outs, sample_bits=4, stream=stream)
+    bp = mw.BatchPlan(jobs, sample_bits=4, stream=stream, **tune)
+    for _ in range(args.warmup):
+        bp.correlate(vols, outs)
+    assert bp.status() == 0
+    bp.set_timing(True)
+    clocks = Clocks(0)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        bp.correlate(vols, outs)
+    b.record(stream)
+    b.synchronize()
+    clk = clocks.stop()
+    tim = bp.timing()
+    assert bp.status() == 0
+    ms = a.elapsed_time(b) / args.steps
+    peaks, src = load_peaks()
+    peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    achieved = 8.0 * units * args.steps / (tim.correlate_ms / 1e3) / 1e12 if tim.correlate_ms else None
+    line = {"metric": METRIC, "value": units / (ms / 1e3) / 1e12, "unit": "TCMAC/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
+            "data": "synthetic (seeded Philox4x64-10 channelised voltages, generated in HBM)",
+            "config": {"workload": f"c3: {desc}", "launch": "per call: 4 unpacks + 1 persistent correlate, one CUDA graph",
+                       "tuning": tune, "exact": "int32 visibilities, bit-exact",
+                       "l2": "inputs 68 GB > 129 MB L2"},
+            "roofline": None if achieved is None else {
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "correlate_tc_kernel (batched launch)",
+                "peak_source": f"2 x bf16 sustained ({src})",
+                "kernel_ms_per_launch": tim.correlate_ms / max(1, tim.correlate_launches),
+                "unpack_ms_per_step": tim.unpack_ms / args.steps},
+            "gpu_launches": int(5 * args.steps), "clocks": clk}
+    if rep is not None:
+        line["config"]["autotune"] = {"candidates": rep.candidates, "best_ms": rep.best_ms,
+                                      "default_ms": rep.default_ms}
+    bp.close()
+    if not args.no_plain:
+        total = 0.0
+        per_job = []
+        for s, v, o in zip(specs, vols, outs):
+            p = mw.Plan(s.n_inputs, s.n_chan, s.n_time, 4, engine=mw.ENGINE_PLAIN, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.correlate(v, o)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            per_job.append(t)
+            total += t
+            p.close()
+        line["plain"] = {"ms_per_step": total, "value": units / (total / 1e3) / 1e12, "unit": "TCMAC/s",
+                         "per_job_ms": per_job, "launches_per_step": sum(s.n_chan for s in specs),
+                         "batched_speedup": total / ms}
+    if not args.no_cpu:
+        t_total, n_done = 0.0, 0.0
+        for k, s in enumerate(specs):
+            v = synth.fill_host(s, chans=[0])
+            t0 = time.perf_counter()
+            oracle.correlate(v, 4, s.n_inputs, 1, s.n_time)
+            t_total += time.perf_counter() - t0
+            n_done += cmacs(s) / s.n_chan
+        line["cpu_baseline"] = {"value": n_done / t_total / 1e12, "unit": "TCMAC/s", "cores": oracle.threads(),
+                                "kind": "oracle", "sample": "channel 0 of each job"}
+    print(json.dumps(line), flush=True)
+
+
+def model_visibilities(spec, chans, device):
+    """M_ij(c) = sum_s S_s exp(i (phi_is - phi_js)) for the source geometry of
+    `spec`, lower triangle [len(chans), N(N+1)/2] complex64 (setup only)."""
+    import numpy as np
+    import torch
+
+    N = spec.n_inputs
+    ii, jj = np.tril_indices(N)
+    ii = torch.from_numpy(ii).to(device)
+    jj = torch.from_numpy(jj).to(device)
+    rate = torch.from_numpy(spec.src_rate.astype(np.float64)).to(device)  # [N, S] uint32 turns per channel
+    flux = torch.from_numpy(np.asarray(spec.src_flux, np.float64)).to(device)
+    out = torch.empty((len(chans), ii.numel()), dtype=torch.complex64, device=device)
+    for k, c in enumerate(chans):
+        turns = torch.remainder(rate * float(c + spec.chan_base), 2.0 ** 32) / 2.0 ** 32
+        e = torch.exp(2j * np.pi * turns)  # [N, S]
+        full = (e * flux) @ e.conj().T
+        out[k] = full[ii, jj].to(torch.complex64)
+    return out
+
+
+def run_calib(args):
+    """c4: calibration loss and adjoint (one pass) on correlator output."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    import paper_0902_0915_gb300 as mw
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    spec = synth.spec_c4()
+    N, C, T = spec.n_inputs, spec.n_chan, spec.n_time
+    B = N * (N + 1) // 2
+    desc = f"calibration loss+adjoint, {N} inputs x {C} ch, V from T={T} 8-bit correlation, 20-source model"
+    metric = "calibration loss+gradient throughput (baseline-channel terms/s), FP32"
+    mw.ensure_built()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    vol = torch.empty(C * T * N * 2, dtype=torch.uint8, device=dev)
+    synth.fill_device(spec, vol)
+    plan = mw.Plan(N, C, T, 8, stream=stream)
+    vis = plan.correlate(vol)
+    assert plan.status() == 0
+    plan.close()
+    del vol
+    scale2 = 2.0 * spec.meta["scale"] ** 2
+    V = torch.complex(vis[..., 0].float(), vis[..., 1].float()) / (T * scale2)
+    del vis
+    M = model_visibilities(spec, list(range(C)), dev)
+    g_true = torch.from_numpy(np.asarray(spec.gains, np.complex64)).to(dev)
+    rng = np.random.default_rng(4)
+    g = (g_true * torch.from_numpy((1 + 0.05 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))).astype(np.complex64)).to(dev)).contiguous()
+    ws = mw.calib_workspace(N, C, dev)
+    for _ in range(args.warmup):
+        loss, grad = mw.calib_loss_grad(V, M, g, ws)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        loss, grad = mw.calib_loss_grad(V, M, g, ws)
+    b.record(stream)
+    b.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    terms = B * C
+    bytes_step = 2 * 8 * B * C + 16 * N
+    peaks, src = load_peaks()
+    achieved = bytes_step / (ms / 1e3) / 1e9
+    line = {"metric": metric, "value": terms / (ms / 1e3) / 1e9, "unit": "Gterms/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (V from correlating seeded c4-style voltages; point-source model)",
+            "config": {"workload": f"c4: {desc}", "l2": f"V + M {2 * 8 * B * C / 1e9:.1f} GB > L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "kernel": "calib_tile_kernel + calib_gather_kernel (one step)",
+                         "peak_source": src},
+            "loss": float(loss), "gpu_launches": 2 * args.steps, "clocks": clk}
+    if not args.no_cpu:
+        sub = list(range(0, C, C // 8))[:8]
+        V64 = V[sub].cpu().numpy().astype(np.complex128)
+        M64 = M[sub].cpu().numpy().astype(np.complex128)
+        g64 = g.cpu().numpy().astype(np.complex128)
+        t0 = time.perf_counter()
+        oracle.calib_loss(V64, M64, g64)
+        oracle.calib_grad(V64, M64, g64)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": B * len(sub) / dt / 1e9, "unit": "Gterms/s", "cores": oracle.threads(),
+                                "kind": "oracle", "sample": f"{len(sub)} of {C} channels (FP64 loss + gradient)"}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mwax", choices=["mwax", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0", "c3", "c4"])
     ap.add_argument("--engine", default="tensor", choices=["tensor", "plain"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -232,10 +494,17 @@ def main():
                          "workload's channels are split across ranks")
     ap.add_argument("--chan", type=int, default=0,
                     help="override the channel count (small cases for profiling)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-variant report")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     import synth
+
+    if args.workload == "c3":
+        return run_batch(args)
+    if args.workload == "c4":
+        return run_calib(args)
 
     mk, desc = workloads()[args.workload]
     spec = mk()
@@ -277,9 +546,14 @@ def main():
     else:
         synth.fill_device(spec, vol, chan0=chan0, n_chan=rspec.n_chan)
     engine = mw.ENGINE_TENSOR if args.engine == "tensor" else mw.ENGINE_PLAIN
+    n_bl = rspec.n_inputs * (rspec.n_inputs + 1) // 2
+    out = torch.empty((rspec.n_chan, n_bl, 2), dtype=torch.int32, device=dev)
+    tune, tune_rep = {}, None
+    if engine == mw.ENGINE_TENSOR and not args.no_tune:
+        tune, tune_rep = mw.autotune(vol, out, rspec.n_inputs, rspec.n_chan, rspec.n_time,
+                                     rspec.sample_bits, stream=stream)
     plan = mw.Plan(rspec.n_inputs, rspec.n_chan, rspec.n_time, rspec.sample_bits, engine=engine,
-                   stream=stream)
-    out = plan.empty_out(dev)
+                   stream=stream, **tune)
     for _ in range(args.warmup):
         plan.correlate(vol, out)
     if plan.status() != 0:
@@ -344,6 +618,11 @@ def main():
                    "engine": args.engine, "exact": "int32 visibilities, bit-exact",
                    "l2": f"inputs {vol.numel() / 1e9:.1f} GB > 129 MB L2 (no flush needed)",
                    "chan_group": info.chan_group, "flush_blocks": info.flush_blocks,
+                   "mma_shape": info.mma_shape, "stages": info.stages, "prefetch": info.prefetch,
+                   "pipeline": info.pipeline,
+                   "autotune": None if tune_rep is None else {
+                       "candidates": tune_rep.candidates, "from_cache": bool(tune_rep.from_cache),
+                       "best_ms": tune_rep.best_ms, "default_ms": tune_rep.default_ms},
                    "parallelism": f"channels, {world} GPU(s), no collective"},
         "rtf": rtf,
         "roofline": roofline,
@@ -367,6 +646,11 @@ def main():
         line["plain"] = {"ms_per_step": pms, "value": units / (pms / 1e3) / 1e12, "unit": "TCMAC/s",
                          "launches_per_step": rspec.n_chan}
         pp.close()
+
+    # FP16-in / FP32-accumulate variant (8-bit samples): time and error vs the
+    # exact integer oracle (= FP64-exact) on two sampled channels
+    if rank == 0 and not args.no_fp16 and engine == mw.ENGINE_TENSOR and rspec.sample_bits == 8:
+        line["fp16_variant"] = fp16_variant(mw, rspec, vol, stream, args)
 
     # end to end through the public API with host buffers (pinned), N GPUs
     if not args.no_e2e:

@@ -87,7 +87,13 @@ typedef struct {
   int32_t stages;          /* tuning: shared-memory pipeline stages, 2..6 (0 = auto)     */
   int32_t prefetch;        /* tuning: K-blocks of L2 prefetch ahead, 1..64 (0 = auto,
                               which is none; -1 = none)                                   */
-  int32_t reserved[6];     /* must be zero                                                */
+  int32_t mma_shape;       /* tuning: 1 = M128xN128 MMAs (Re, Im separately), 2 = M128xN256
+                              MMAs with [Re | Im] at once (0 = auto)                     */
+  int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
+                              plan's stream, 2 = overlap the unpack of the next group with
+                              the correlation of the current one on a second stream (two
+                              scratch buffers); 0 = auto (1)                              */
+  int32_t reserved[4];     /* must be zero                                                */
 } mwax_job;
 
 /* Read-only description of a plan's choices. */
@@ -100,6 +106,8 @@ typedef struct {
   int32_t grid;              /* persistent CTAs of the correlate kernel                */
   int32_t stages;            /* shared-memory pipeline stages                          */
   int32_t prefetch;          /* K-blocks of L2 prefetch ahead of the TMA loads         */
+  int32_t mma_shape;         /* 1 = N128, 2 = N256                                     */
+  int32_t pipeline;          /* 1 = sequential, 2 = overlapped unpack/correlate        */
   int64_t scratch_bytes;     /* device scratch owned by the plan                       */
   int64_t work_items;        /* (job, channel, tile pair) items per call               */
 } mwax_plan_info;
@@ -116,7 +124,9 @@ typedef struct mwax_plan_s *mwax_plan_t;
 mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t stream);
 
 /* Plan several jobs (uneven N, C, T) that are correlated together by one
- * persistent launch per call, captured in a CUDA graph on first use. */
+ * persistent launch per call.  On first use (and whenever the buffers
+ * change) the calls are captured into two CUDA graphs: every job's unpack,
+ * then the single persistent correlate launch over all jobs' work items. */
 mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
                             cudaStream_t stream);
 
@@ -134,8 +144,9 @@ typedef struct {
 } mwax_timing;
 
 /* Record (enable != 0) or stop recording CUDA events on the plan's stream
- * around every kernel it launches.  Batch plans time their whole graph
- * launch as one correlate launch. */
+ * around every kernel it launches.  A batch plan replays two CUDA graphs per
+ * call -- all jobs' unpack launches, then the one persistent correlate
+ * launch -- and times each graph launch as one unpack / correlate launch. */
 mwax_status mwax_plan_set_timing(mwax_plan_t plan, int enable);
 
 /* Sums since the previous call; synchronises the plan's stream, then resets. */
@@ -145,6 +156,31 @@ mwax_status mwax_plan_get_timing(mwax_plan_t plan, mwax_timing *timing);
  * if a bounded device wait gave up (the output is then invalid).  Reading it
  * synchronises the plan's stream; the word is cleared afterwards. */
 mwax_status mwax_plan_status(mwax_plan_t plan);
+
+/* ---- autotuning ------------------------------------------------------------ */
+
+typedef struct {
+  int32_t candidates;  /* configurations timed                                        */
+  int32_t from_cache;  /* 1 when the choice was read from the MWAX_TUNE_CACHE file     */
+  double best_ms;      /* device time of one call with the chosen configuration        */
+  double default_ms;   /* device time with the default configuration (first candidate) */
+} mwax_tune_report;
+
+/* Choose the tuning fields of a tensor-engine job (mma_shape, stages,
+ * prefetch, pipeline, chan_group) by timing candidate configurations with
+ * CUDA events on `voltages` / `out` (device buffers of the job's shape,
+ * contents of `out` are overwritten) on `stream`.  Writes the choice into
+ * *job and, when the environment variable MWAX_TUNE_CACHE names a file,
+ * appends it there keyed by device name, SM count and job shape; a later
+ * mwax_plan of a job whose tuning fields are all zero applies the cached
+ * choice.  Synchronises `stream`.  Plain-engine jobs are left unchanged. */
+mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaStream_t stream,
+                          mwax_tune_report *report);
+
+/* The same for a batch: one shared choice of mma_shape, stages and prefetch
+ * for all jobs (voltages[k], out[k] as for mwax_correlate_batch). */
+mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *voltages,
+                                void *const *out, cudaStream_t stream, mwax_tune_report *report);
 
 /* ---- correlation -------------------------------------------------------- */
 

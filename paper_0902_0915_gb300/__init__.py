@@ -38,7 +38,8 @@ class Job(ctypes.Structure):
                 ("kind", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("flush_blocks", ctypes.c_int32), ("chan_group", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("mma_shape", ctypes.c_int32), ("pipeline", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -46,12 +47,18 @@ class PlanInfo(ctypes.Structure):
                 ("samples_per_block", ctypes.c_int32), ("flush_blocks", ctypes.c_int32),
                 ("chan_group", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
+                ("mma_shape", ctypes.c_int32), ("pipeline", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64), ("work_items", ctypes.c_int64)]
 
 
 class Timing(ctypes.Structure):
     _fields_ = [("unpack_ms", ctypes.c_double), ("correlate_ms", ctypes.c_double),
                 ("unpack_launches", ctypes.c_int64), ("correlate_launches", ctypes.c_int64)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -68,6 +75,9 @@ SIGNATURES = {
     "mwax_plan_status": (_I, [_P]),
     "mwax_plan_set_timing": (_I, [_P, _I]),
     "mwax_plan_get_timing": (_I, [_P, ctypes.POINTER(Timing)]),
+    "mwax_autotune": (_I, [ctypes.POINTER(Job), _P, _P, _P, ctypes.POINTER(TuneReport)]),
+    "mwax_autotune_batch": (_I, [ctypes.POINTER(Job), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P,
+                                 ctypes.POINTER(TuneReport)]),
     "mwax_correlate": (_I, [_P, _P, _I, _I, _I, _P]),
     "mwax_correlate_batch": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "mwax_correlate_host": (_I, [_P, _P, _I, _I, _I, _P]),
@@ -151,11 +161,11 @@ def _stream_handle(stream=None) -> int:
 
 
 def _job(n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, engine=ENGINE_TENSOR,
-         flush_blocks=0, chan_group=0, stages=0, prefetch=0) -> Job:
+         flush_blocks=0, chan_group=0, stages=0, prefetch=0, mma_shape=0, pipeline=0) -> Job:
     j = Job()
     j.n_inputs, j.n_chan, j.n_time, j.sample_bits = n_inputs, n_chan, n_time, sample_bits
     j.kind, j.engine, j.flush_blocks, j.chan_group = kind, engine, flush_blocks, chan_group
-    j.stages, j.prefetch = stages, prefetch
+    j.stages, j.prefetch, j.mma_shape, j.pipeline = stages, prefetch, mma_shape, pipeline
     return j
 
 
@@ -169,9 +179,9 @@ class Plan:
 
     def __init__(self, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,
                  engine=ENGINE_TENSOR, flush_blocks=0, chan_group=0, stages=0, prefetch=0,
-                 stream=None):
+                 mma_shape=0, pipeline=0, stream=None):
         self.job = _job(n_inputs, n_chan, n_time, sample_bits, kind, engine, flush_blocks,
-                        chan_group, stages, prefetch)
+                        chan_group, stages, prefetch, mma_shape, pipeline)
         self.shape = (n_inputs, n_chan, n_time)
         self.sample_bits, self.kind, self.engine = sample_bits, kind, engine
         self._h = _P()
@@ -245,10 +255,12 @@ class BatchPlan:
     """Several uneven jobs correlated by one persistent launch per call,
     replayed from a CUDA graph (see include/mwax.h: mwax_plan_batch)."""
 
-    def __init__(self, jobs, sample_bits=4, kind=KIND_EXACT, stream=None):
+    def __init__(self, jobs, sample_bits=4, kind=KIND_EXACT, stream=None, mma_shape=0, stages=0,
+                 prefetch=0):
         self.shapes = [tuple(j) for j in jobs]
         self.sample_bits, self.kind = sample_bits, kind
-        arr = (Job * len(jobs))(*[_job(n, c, t, sample_bits, kind) for (n, c, t) in jobs])
+        arr = (Job * len(jobs))(*[_job(n, c, t, sample_bits, kind, mma_shape=mma_shape,
+                                       stages=stages, prefetch=prefetch) for (n, c, t) in jobs])
         self._h = _P()
         self.stream = stream if stream is not None else _torch().cuda.current_stream()
         _check(lib().mwax_plan_batch(ctypes.byref(self._h), arr, len(jobs), self.stream.cuda_stream),
@@ -295,6 +307,31 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+TUNE_FIELDS = ("mma_shape", "stages", "prefetch", "pipeline", "chan_group")
+
+
+def autotune(voltages, out, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, stream=None):
+    """Time candidate configurations on these device buffers; returns
+    (dict of tuning fields, TuneReport).  See include/mwax.h: mwax_autotune."""
+    j = _job(n_inputs, n_chan, n_time, sample_bits, kind)
+    rep = TuneReport()
+    _check(lib().mwax_autotune(ctypes.byref(j), voltages.data_ptr(), out.data_ptr(),
+                               _stream_handle(stream), ctypes.byref(rep)), "mwax_autotune")
+    return {k: getattr(j, k) for k in TUNE_FIELDS}, rep
+
+
+def autotune_batch(jobs, voltages, outs, sample_bits=4, kind=KIND_EXACT, stream=None):
+    """Batch variant: one shared (mma_shape, stages, prefetch) for all jobs."""
+    k = len(jobs)
+    arr = (Job * k)(*[_job(n, c, t, sample_bits, kind) for (n, c, t) in jobs])
+    vin = (_P * k)(*[v.data_ptr() for v in voltages])
+    vout = (_P * k)(*[o.data_ptr() for o in outs])
+    rep = TuneReport()
+    _check(lib().mwax_autotune_batch(arr, k, vin, vout, _stream_handle(stream), ctypes.byref(rep)),
+           "mwax_autotune_batch")
+    return {f: getattr(arr[0], f) for f in ("mma_shape", "stages", "prefetch")}, rep
 
 
 def correlate(voltages, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,

@@ -45,12 +45,20 @@
 namespace mwax {
 namespace {
 
-constexpr int kWarps = 10;
-constexpr int kThreads = kWarps * 32;
-constexpr int kEpiWarp0 = 2;                   // warps 2..9: epilogue
 constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
-constexpr int kStageBytes = 2 * kTileBytes;    // A_I | A_J
-constexpr int kMaxStages = 6;
+
+// Two MMA shapes.  Narrow: eight M=128 N=128 MMAs per block (Re and Im
+// separately, negate-B bit for the minus sign).  Wide: four M=128 N=256 MMAs
+// per block against B = [A_J ; B'_J], B'_J = [-im_j | re_j] built in shared
+// memory by two extra warps.
+template <bool WIDE>
+struct Shape {
+  static constexpr int warps = WIDE ? 12 : 10;
+  static constexpr int conv_warps = WIDE ? 2 : 0;   // warps 2 .. 2+conv_warps-1
+  static constexpr int epi0 = 2 + conv_warps;       // 8 epilogue warps from here
+  static constexpr int stage_bytes = (WIDE ? 3 : 2) * kTileBytes;
+  static constexpr int max_stages = WIDE ? 4 : 6;
+};
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;  // re 128 | im 128
 constexpr int kMaxJobs = MWAX_MAX_JOBS;
@@ -167,9 +175,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
 
 // Instruction descriptor: FP32 accumulate, A/B type code 0 (F16 for
 // kind::f16, E4M3 for kind::f8f6f4), optional negation of B, K-major A and
-// B, M = N = 128.
-__host__ __device__ constexpr uint32_t make_idesc(bool negate_b) {
-  return (1u << 4) | ((negate_b ? 1u : 0u) << 14) | ((uint32_t)(kTile >> 3) << 17) |
+// B, M = 128, N = n.
+__host__ __device__ constexpr uint32_t make_idesc(bool negate_b, int n) {
+  return (1u << 4) | ((negate_b ? 1u : 0u) << 14) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(kTile >> 4) << 24);
 }
 
@@ -243,22 +251,25 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-template <int BITS, int KIND>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int BITS, int KIND, bool WIDE>
+__global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
     correlate_tc_kernel(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p) {
+  using Sh = Shape<WIDE>;
+  constexpr int kStageBytes = Sh::stage_bytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~static_cast<uintptr_t>(1023));
   const int S = p.stages;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * kStageBytes);
-  // full[0..S) empty[S..2S) tfull[2S..2S+2) tempty[2S+2..2S+4) drain[2S+4]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
+  // full[0..S) empty[S..2S) bfull[2S..3S) tfull[3S..3S+2) tempty[3S+2..3S+4) drain[3S+4]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * S + 5);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + S + s); };
-  auto tfull = [&](int b) { return smem_u32(bars + 2 * S + b); };
-  auto tempty = [&](int b) { return smem_u32(bars + 2 * S + 2 + b); };
-  const uint32_t drain = smem_u32(bars + 2 * S + 4);
+  auto bfull = [&](int s) { return smem_u32(bars + 2 * S + s); };
+  auto tfull = [&](int b) { return smem_u32(bars + 3 * S + b); };
+  auto tempty = [&](int b) { return smem_u32(bars + 3 * S + 2 + b); };
+  const uint32_t drain = smem_u32(bars + 3 * S + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long tmo = p.timeout_ns;
@@ -268,6 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < S; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
+      mbar_init(bfull(s), Sh::conv_warps > 0 ? Sh::conv_warps : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
@@ -358,8 +370,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = make_idesc(false);
-    constexpr uint32_t idesc_neg = make_idesc(true);
+    constexpr uint32_t idesc = make_idesc(false, WIDE ? 2 * kTile : kTile);
+    constexpr uint32_t idesc_neg = make_idesc(true, kTile);
     int stage = 0;
     uint32_t phase = 0;
     uint32_t seg = 0;
@@ -381,7 +393,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
         }
-        if (!warp_wait(full(stage), phase, abort_flag, tmo, lane)) {
+        if (!warp_wait(full(stage), phase, abort_flag, tmo, lane) ||
+            (WIDE && !warp_wait(bfull(stage), phase, abort_flag, tmo, lane))) {
           if (lane == 0) raise_timeout(abort_flag, p.status);
           ok = false;
           break;
@@ -393,16 +406,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint64_t da = sw128_desc(a);
           const uint64_t db = diag ? da : sw128_desc(a + kTileBytes);
           const uint32_t d_re = tmem_base + buf * kAccCols;
-          const uint32_t d_im = d_re + kTile;
           const uint32_t acc0 = seg_start ? 0u : 1u;
-          tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
-          tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
-          tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
-          tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
-          tc_mma<BITS>(d_im, da + 4, db + 0, idesc, acc0);
-          tc_mma<BITS>(d_im, da + 6, db + 2, idesc, 1u);
-          tc_mma<BITS>(d_im, da + 0, db + 4, idesc_neg, 1u);
-          tc_mma<BITS>(d_im, da + 2, db + 6, idesc_neg, 1u);
+          if constexpr (WIDE) {
+            // B = [A_J ; B'_J]: columns 0..127 give Re, 128..255 give Im
+            tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
+            tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
+            tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
+            tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
+          } else {
+            const uint32_t d_im = d_re + kTile;
+            tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
+            tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
+            tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
+            tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
+            tc_mma<BITS>(d_im, da + 4, db + 0, idesc, acc0);
+            tc_mma<BITS>(d_im, da + 6, db + 2, idesc, 1u);
+            tc_mma<BITS>(d_im, da + 0, db + 4, idesc_neg, 1u);
+            tc_mma<BITS>(d_im, da + 2, db + 6, idesc_neg, 1u);
+          }
           tc_commit(empty(stage));
         }
         __syncwarp();
@@ -424,10 +445,61 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain, 0, nullptr, tmo);
     }
     __syncwarp();
+  } else if (WIDE && warp < Sh::epi0) {
+    // ---------------- B' builder (wide shape) ----------------
+    // B'_J row r = [-im_j | re_j]: 16-byte chunk c of the (128-byte swizzled)
+    // row is chunk c ^ 4 of the A_J row, negated for c < 4.  Thread t copies
+    // chunk c = t & 7 of rows (t >> 3) + 8m, m = 0..15, so its swizzle term
+    // (row & 7) and its negation flag are fixed; all 16 loads are issued
+    // before the stores.
+    constexpr uint32_t neg = BITS == 8 ? 0x80008000u : 0x80808080u;  // packed sign bits
+    const int ct = (warp - 2) * 32 + lane;                           // 0 .. 63
+    const int c = ct & 7, r0 = ct >> 3, sw = r0 & 7;
+    const uint32_t flip = c < 4 ? neg : 0u;
+    const int src_off = r0 * kRowBytes + (((c ^ 4) ^ sw) << 4);
+    const int dst_off = r0 * kRowBytes + ((c ^ sw) << 4);
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      const Item it = decode_item(p, item);
+      const KJob &jb = p.job[it.job];
+      const bool diag = it.I == it.J;
+      for (int kb = 0; kb < jb.kb; ++kb) {
+        if (!warp_wait(full(stage), phase, abort_flag, tmo, lane)) {
+          if (lane == 0) raise_timeout(abort_flag, p.status);
+          ok = false;
+          break;
+        }
+        const uint8_t *src = smem + (size_t)stage * kStageBytes + (diag ? 0 : kTileBytes);
+        uint8_t *dst = smem + (size_t)stage * kStageBytes + (diag ? kTileBytes : 2 * kTileBytes);
+        uint4 v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+          v[m] = *reinterpret_cast<const uint4 *>(src + src_off + m * 8 * kRowBytes);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          uint4 w = v[m];
+          w.x ^= flip;
+          w.y ^= flip;
+          w.z ^= flip;
+          w.w ^= flip;
+          *reinterpret_cast<uint4 *>(dst + dst_off + m * 8 * kRowBytes) = w;
+        }
+        // generic-proxy writes -> visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bfull(stage));
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
   } else {
     // ---------------- epilogue: flush + integration dump ----------------
-    const int q = warp & 3;                 // tensor-memory lane quadrant of this warp
-    const int h = (warp - kEpiWarp0) >> 2;  // column half: local columns [64h, 64h + 64)
+    const int q = warp & 3;               // tensor-memory lane quadrant of this warp
+    const int h = (warp - Sh::epi0) >> 2;  // column half: local columns [64h, 64h + 64)
     uint32_t seg = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
@@ -512,31 +584,52 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-template <int BITS, int KIND>
+template <int BITS, int KIND, bool WIDE>
 cudaError_t set_smem_attr(int bytes) {
-  return cudaFuncSetAttribute(correlate_tc_kernel<BITS, KIND>,
+  return cudaFuncSetAttribute(correlate_tc_kernel<BITS, KIND, WIDE>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <bool WIDE>
+cudaError_t prepare_shape(int sample_bits, int kind, int bytes) {
+  if (sample_bits == 4) return set_smem_attr<4, MWAX_KIND_EXACT, WIDE>(bytes);
+  if (kind == MWAX_KIND_FP16) return set_smem_attr<8, MWAX_KIND_FP16, WIDE>(bytes);
+  return set_smem_attr<8, MWAX_KIND_EXACT, WIDE>(bytes);
+}
+
+template <bool WIDE>
+void launch_shape(int sample_bits, int kind, int grid, int smem, cudaStream_t s, const KMaps &maps,
+                  const KParams &kp) {
+  const int threads = Shape<WIDE>::warps * 32;
+  if (sample_bits == 4)
+    correlate_tc_kernel<4, MWAX_KIND_EXACT, WIDE><<<grid, threads, smem, s>>>(maps, kp);
+  else if (kind == MWAX_KIND_FP16)
+    correlate_tc_kernel<8, MWAX_KIND_FP16, WIDE><<<grid, threads, smem, s>>>(maps, kp);
+  else
+    correlate_tc_kernel<8, MWAX_KIND_EXACT, WIDE><<<grid, threads, smem, s>>>(maps, kp);
 }
 
 }  // namespace
 
-int correlate_tc_max_stages() { return kMaxStages; }
-
-int correlate_tc_smem_bytes(int stages) {
-  return 1024 + stages * kStageBytes + (2 * stages + 5) * 8 + 16;
+int correlate_tc_max_stages(int wide) {
+  return wide ? Shape<true>::max_stages : Shape<false>::max_stages;
 }
 
-cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages) {
-  const int bytes = correlate_tc_smem_bytes(stages);
-  if (sample_bits == 4) return set_smem_attr<4, MWAX_KIND_EXACT>(bytes);
-  if (kind == MWAX_KIND_FP16) return set_smem_attr<8, MWAX_KIND_FP16>(bytes);
-  return set_smem_attr<8, MWAX_KIND_EXACT>(bytes);
+int correlate_tc_smem_bytes(int stages, int wide) {
+  const int stage_bytes = wide ? Shape<true>::stage_bytes : Shape<false>::stage_bytes;
+  return 1024 + stages * stage_bytes + (3 * stages + 5) * 8 + 16;
+}
+
+cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int wide) {
+  const int bytes = correlate_tc_smem_bytes(stages, wide);
+  return wide ? prepare_shape<true>(sample_bits, kind, bytes)
+              : prepare_shape<false>(sample_bits, kind, bytes);
 }
 
 cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
                                 cudaStream_t s) {
   if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;
-  if (cfg.stages < 2 || cfg.stages > kMaxStages) return cudaErrorInvalidValue;
+  if (cfg.stages < 2 || cfg.stages > correlate_tc_max_stages(cfg.wide)) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
   if (!encode) return cudaErrorNotSupported;
   KMaps maps;
@@ -578,13 +671,11 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   kp.prefetch = cfg.prefetch;
   if (items <= 0) return cudaSuccess;
   const int grid = (int)(items < cfg.grid ? items : cfg.grid);
-  const int smem = correlate_tc_smem_bytes(cfg.stages);
-  if (cfg.sample_bits == 4)
-    correlate_tc_kernel<4, MWAX_KIND_EXACT><<<grid, kThreads, smem, s>>>(maps, kp);
-  else if (cfg.kind == MWAX_KIND_FP16)
-    correlate_tc_kernel<8, MWAX_KIND_FP16><<<grid, kThreads, smem, s>>>(maps, kp);
+  const int smem = correlate_tc_smem_bytes(cfg.stages, cfg.wide);
+  if (cfg.wide)
+    launch_shape<true>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
   else
-    correlate_tc_kernel<8, MWAX_KIND_EXACT><<<grid, kThreads, smem, s>>>(maps, kp);
+    launch_shape<false>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
   return cudaGetLastError();
 }
 

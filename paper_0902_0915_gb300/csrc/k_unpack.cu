@@ -189,14 +189,16 @@ __global__ void __launch_bounds__(128) unpack4_line_kernel(const uint8_t *__rest
 
 cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
                           int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
-                          cudaStream_t s) {
+                          int variant_req, cudaStream_t s) {
   const int n_rows = n_tiles * kTile;
   if (n_chan <= 0) return cudaSuccess;
-  // variant: 0 = automatic, 1 = shared-memory transpose, 2 = full-line
-  static const int variant = [] {
+  // variant: 0 = automatic, 1 = shared-memory transpose, 2 = full-line;
+  // MWAX_UNPACK overrides the automatic choice (tuning experiments)
+  static const int env_variant = [] {
     const char *e = getenv("MWAX_UNPACK");
     return e ? atoi(e) : 0;
   }();
+  const int variant = variant_req != 0 ? variant_req : env_variant;
   const bool line8 = variant == 2;
   const bool line4 = variant != 1;
   if (line8 && sample_bits == 8 && n_inputs % 2 == 0 && kb <= 65535 && n_chan <= 65535) {

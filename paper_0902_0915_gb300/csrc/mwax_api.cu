@@ -48,13 +48,20 @@ struct mwax_plan_s {
   int kind = MWAX_KIND_EXACT;
   int stages = 6;
   int prefetch = 0;
+  int wide = 0;
   unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
   std::vector<mwax::JobState> jobs;
   uint8_t *scratch = nullptr;  // single-job plans: operand buffer for one channel group
+  uint8_t *scratch2 = nullptr;  // second buffer when unpack and correlate overlap
   int64_t scratch_bytes = 0;
+  // overlapped pipeline: unpack of group g+1 (aux stream) runs beside the
+  // persistent correlate of group g (plan stream)
+  bool overlap = false;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_unpacked[2] = {nullptr, nullptr}, ev_freed[2] = {nullptr, nullptr};
   int32_t *status = nullptr;
-  // batch graph
-  cudaGraphExec_t graph = nullptr;
+  // batch graphs: every job's unpack, then the one persistent correlate launch
+  cudaGraphExec_t graph = nullptr, graph2 = nullptr;
   std::vector<const void *> graph_in;
   std::vector<void *> graph_out;
   // host path
@@ -69,9 +76,10 @@ struct mwax_plan_s {
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
     int kind;  // 0 unpack, 1 correlate
-    int start, stop;
+    cudaEvent_t start, stop;
   };
   std::vector<Rec> recs;
+
 };
 
 namespace mwax {
@@ -99,9 +107,12 @@ mwax_status check_job(const mwax_job &j) {
   if (j.kind != MWAX_KIND_EXACT && j.kind != MWAX_KIND_FP16) return MWAX_ERR_INVALID_ARG;
   if (j.engine != MWAX_ENGINE_TENSOR && j.engine != MWAX_ENGINE_PLAIN) return MWAX_ERR_INVALID_ARG;
   if (j.flush_blocks < 0 || j.chan_group < 0) return MWAX_ERR_INVALID_ARG;
-  if (j.stages < 0 || j.stages == 1 || j.stages > correlate_tc_max_stages()) return MWAX_ERR_INVALID_ARG;
+  if (j.mma_shape < 0 || j.mma_shape > 2) return MWAX_ERR_INVALID_ARG;
+  if (j.pipeline < 0 || j.pipeline > 2) return MWAX_ERR_INVALID_ARG;
+  if (j.stages < 0 || j.stages == 1 || j.stages > correlate_tc_max_stages(j.mma_shape == 2))
+    return MWAX_ERR_INVALID_ARG;
   if (j.prefetch < -1 || j.prefetch > 64) return MWAX_ERR_INVALID_ARG;
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < 4; ++k)
     if (j.reserved[k] != 0) return MWAX_ERR_INVALID_ARG;
   if (j.kind == MWAX_KIND_FP16 && (j.sample_bits != 8 || j.engine != MWAX_ENGINE_TENSOR))
     return MWAX_ERR_UNSUPPORTED;
@@ -172,7 +183,7 @@ struct TimedLaunch {
     const int stop = next_event();
     if (stop < 0) return;
     cudaEventRecord(p->ev_pool[stop], st);
-    p->recs.push_back({kind, start, stop});
+    p->recs.push_back({kind, p->ev_pool[start], p->ev_pool[stop]});
     start = -1;
   }
 };
@@ -184,22 +195,25 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
   c.grid = p->sm_count;
   c.stages = p->stages;
   c.prefetch = p->prefetch;
+  c.wide = p->wide;
   c.status = p->status;
   c.timeout_ns = p->timeout_ns;
   return c;
 }
 
-// Channels [c0, c0+nc) of a single-job tensor plan: unpack into the scratch,
-// then one persistent correlate launch.
-mwax_status run_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
-                      void *out_c0, cudaStream_t st) {
+mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
+                         uint8_t *op, int variant, cudaStream_t st) {
   TimedLaunch tu(p, 0, st);
   cudaError_t e = launch_unpack(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
-                                s.kb, c0, nc, p->scratch, st);
+                                s.kb, c0, nc, op, variant, st);
   tu.done();
-  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(e);
+}
+
+mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op, int nc,
+                            void *out_c0, cudaStream_t st) {
   TcJob tj;
-  tj.op = p->scratch;
+  tj.op = op;
   tj.out = out_c0;
   tj.n_inputs = s.job.n_inputs;
   tj.n_tiles = s.n_tiles;
@@ -209,9 +223,18 @@ mwax_status run_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, in
   tj.n_chan = nc;
   tj.n_bl = s.n_bl;
   TimedLaunch tc(p, 1, st);
-  e = launch_correlate_tc(&tj, 1, launch_cfg(p), st);
+  cudaError_t e = launch_correlate_tc(&tj, 1, launch_cfg(p), st);
   tc.done();
   return cuda_status(e);
+}
+
+// Channels [c0, c0+nc) of a single-job tensor plan, one after the other on
+// `st`: unpack into the scratch, then one persistent correlate launch.
+mwax_status run_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
+                      void *out_c0, cudaStream_t st) {
+  mwax_status r = unpack_group(p, s, volt, c0, nc, p->scratch, 0, st);
+  if (r != MWAX_OK) return r;
+  return correlate_group(p, s, p->scratch, nc, out_c0, st);
 }
 
 mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cudaStream_t st) {
@@ -228,11 +251,36 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
     }
     return MWAX_OK;
   }
-  for (int64_t c0 = 0; c0 < s.job.n_chan; c0 += s.chan_group) {
+  uint8_t *out8 = reinterpret_cast<uint8_t *>(out);
+  if (!p->overlap) {
+    for (int64_t c0 = 0; c0 < s.job.n_chan; c0 += s.chan_group) {
+      const int nc = (int)std::min<int64_t>(s.chan_group, s.job.n_chan - c0);
+      mwax_status r = run_group(p, s, volt, c0, nc, out8 + c0 * s.out_chan_bytes, st);
+      if (r != MWAX_OK) return r;
+    }
+    return MWAX_OK;
+  }
+  // Overlapped: the unpack of group g+1 runs on the aux stream into the other
+  // scratch buffer while group g correlates.  The unpack kernel (128 threads,
+  // no shared memory) fits beside the persistent correlate CTA on each SM and
+  // uses the DRAM bandwidth the correlate leaves idle.
+  uint8_t *buf[2] = {p->scratch, p->scratch2};
+  cudaError_t e = cudaEventRecord(p->ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_start, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  int64_t g = 0;
+  for (int64_t c0 = 0; c0 < s.job.n_chan; c0 += s.chan_group, ++g) {
+    const int k = (int)(g & 1);
     const int nc = (int)std::min<int64_t>(s.chan_group, s.job.n_chan - c0);
-    mwax_status r = run_group(p, s, volt, c0, nc,
-                              reinterpret_cast<uint8_t *>(out) + c0 * s.out_chan_bytes, st);
+    if (g >= 2 && (e = cudaStreamWaitEvent(p->aux, p->ev_freed[k], 0)) != cudaSuccess)
+      return cuda_status(e);
+    mwax_status r = unpack_group(p, s, volt, c0, nc, buf[k], 2, p->aux);
     if (r != MWAX_OK) return r;
+    if ((e = cudaEventRecord(p->ev_unpacked[k], p->aux)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaStreamWaitEvent(st, p->ev_unpacked[k], 0)) != cudaSuccess) return cuda_status(e);
+    r = correlate_group(p, s, buf[k], nc, out8 + c0 * s.out_chan_bytes, st);
+    if (r != MWAX_OK) return r;
+    if ((e = cudaEventRecord(p->ev_freed[k], st)) != cudaSuccess) return cuda_status(e);
   }
   return MWAX_OK;
 }
@@ -240,18 +288,25 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
 void free_plan(mwax_plan_s *p) {
   if (!p) return;
   if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->graph2) cudaGraphExecDestroy(p->graph2);
   for (auto &s : p->jobs)
     if (s.op) cudaFree(s.op);
   if (p->scratch) cudaFree(p->scratch);
+  if (p->scratch2) cudaFree(p->scratch2);
   if (p->status) cudaFree(p->status);
+  if (p->aux) cudaStreamDestroy(p->aux);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
   for (int k = 0; k < 2; ++k) {
     if (p->stage_in[k]) cudaFree(p->stage_in[k]);
     if (p->stage_out[k]) cudaFree(p->stage_out[k]);
     if (p->ev_in[k]) cudaEventDestroy(p->ev_in[k]);
     if (p->ev_comp[k]) cudaEventDestroy(p->ev_comp[k]);
     if (p->ev_out[k]) cudaEventDestroy(p->ev_out[k]);
+    if (p->ev_unpacked[k]) cudaEventDestroy(p->ev_unpacked[k]);
+    if (p->ev_freed[k]) cudaEventDestroy(p->ev_freed[k]);
   }
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+
   if (p->h2d) cudaStreamDestroy(p->h2d);
   if (p->d2h) cudaStreamDestroy(p->d2h);
   delete p;
@@ -322,6 +377,9 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
     free_plan(p);
     return r;
   }
+  mwax_job tuned = *job;
+  apply_tune_cache(&tuned);
+  job = &tuned;
   JobState s;
   s.job = *job;
   derive(s);
@@ -329,13 +387,26 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
   p->engine = job->engine;
   p->sample_bits = job->sample_bits;
   p->kind = job->kind;
-  if (job->stages > 0) p->stages = job->stages;
+  p->wide = job->mma_shape == 2;
+  p->stages = job->stages > 0 ? job->stages : correlate_tc_max_stages(p->wide);
   if (job->prefetch != 0) p->prefetch = job->prefetch < 0 ? 0 : job->prefetch;
   if (p->engine == MWAX_ENGINE_TENSOR) {
-    p->scratch_bytes = s.op_chan_bytes * s.chan_group;
-    cudaError_t e = cudaMalloc(&p->scratch, (size_t)p->scratch_bytes);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)p->scratch_bytes, stream);
-    if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages);
+    const int64_t one = s.op_chan_bytes * s.chan_group;
+    p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan;
+    p->scratch_bytes = one * (p->overlap ? 2 : 1);
+    cudaError_t e = cudaMalloc(&p->scratch, (size_t)one);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)one, stream);
+    if (e == cudaSuccess && p->overlap) {
+      e = cudaMalloc(&p->scratch2, (size_t)one);
+      if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch2, 0, (size_t)one, stream);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&p->ev_unpacked[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_freed[k], cudaEventDisableTiming);
+      }
+    }
+    if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->wide);
     if (e != cudaSuccess) {
       free_plan(p);
       return cuda_status(e);
@@ -367,7 +438,8 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
   p->batch = true;
   p->sample_bits = jobs[0].sample_bits;
   p->kind = jobs[0].kind;
-  if (jobs[0].stages > 0) p->stages = jobs[0].stages;
+  p->wide = jobs[0].mma_shape == 2;
+  p->stages = jobs[0].stages > 0 ? jobs[0].stages : correlate_tc_max_stages(p->wide);
   if (jobs[0].prefetch != 0) p->prefetch = jobs[0].prefetch < 0 ? 0 : jobs[0].prefetch;
   for (int k = 0; k < n_jobs; ++k) {
     JobState s;
@@ -383,7 +455,7 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
       return cuda_status(e);
     }
   }
-  cudaError_t e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages);
+  cudaError_t e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->wide);
   if (e != cudaSuccess) {
     free_plan(p);
     return cuda_status(e);
@@ -410,6 +482,8 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   info->chan_group = plan->batch ? s.job.n_chan : s.chan_group;
   info->grid = plan->sm_count;
   info->stages = plan->stages;
+  info->mma_shape = plan->wide ? 2 : 1;
+  info->pipeline = plan->overlap ? 2 : 1;
   info->prefetch = plan->prefetch;
   info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
   int64_t items = 0;
@@ -443,25 +517,18 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
   const int nj = (int)plan->jobs.size();
   for (int k = 0; k < nj; ++k)
     if (!is_device_ptr(voltages[k]) || !is_device_ptr(out[k])) return MWAX_ERR_INVALID_ARG;
-  bool same = plan->graph != nullptr;
+  bool same = plan->graph != nullptr && plan->graph2 != nullptr;
   for (int k = 0; k < nj && same; ++k)
     same = plan->graph_in[k] == voltages[k] && plan->graph_out[k] == out[k];
   if (!same) {
-    if (plan->graph) {
-      cudaGraphExecDestroy(plan->graph);
-      plan->graph = nullptr;
-    }
-    // capture: every job's unpack, then one persistent launch over all items
-    cudaStream_t cs;
-    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_status(e);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (cudaGraphExec_t *ge : {&plan->graph, &plan->graph2})
+      if (*ge) {
+        cudaGraphExecDestroy(*ge);
+        *ge = nullptr;
+      }
     std::vector<TcJob> tj(nj);
-    for (int k = 0; k < nj && e == cudaSuccess; ++k) {
+    for (int k = 0; k < nj; ++k) {
       const JobState &s = plan->jobs[k];
-      e = launch_unpack(reinterpret_cast<const uint8_t *>(voltages[k]), s.job.sample_bits,
-                        s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, 0, s.job.n_chan, s.op, cs);
       tj[k].op = s.op;
       tj[k].out = out[k];
       tj[k].n_inputs = s.job.n_inputs;
@@ -472,22 +539,47 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
       tj[k].n_chan = s.job.n_chan;
       tj[k].n_bl = s.n_bl;
     }
-    if (e == cudaSuccess) e = launch_correlate_tc(tj.data(), nj, launch_cfg(plan), cs);
-    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    // graph 1: every job's unpack; graph 2: one persistent launch over all items
+    for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (part == 0) {
+        for (int k = 0; k < nj && e == cudaSuccess; ++k) {
+          const JobState &s = plan->jobs[k];
+          e = launch_unpack(reinterpret_cast<const uint8_t *>(voltages[k]), s.job.sample_bits,
+                            s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, 0, s.job.n_chan, s.op, 0,
+                            cs);
+        }
+      } else if (e == cudaSuccess) {
+        e = launch_correlate_tc(tj.data(), nj, launch_cfg(plan), cs);
+      }
+      cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(part == 0 ? &plan->graph : &plan->graph2, g, 0);
+      if (g) cudaGraphDestroy(g);
+    }
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
-      plan->graph = nullptr;
+      for (cudaGraphExec_t *ge : {&plan->graph, &plan->graph2})
+        if (*ge) {
+          cudaGraphExecDestroy(*ge);
+          *ge = nullptr;
+        }
       return cuda_status(e);
     }
     plan->graph_in.assign(voltages, voltages + nj);
     plan->graph_out.assign(out, out + nj);
   }
-  TimedLaunch tg(plan, 1, plan->stream);
+  TimedLaunch tu(plan, 0, plan->stream);
   cudaError_t e = cudaGraphLaunch(plan->graph, plan->stream);
-  tg.done();
+  tu.done();
+  if (e != cudaSuccess) return cuda_status(e);
+  TimedLaunch tc(plan, 1, plan->stream);
+  e = cudaGraphLaunch(plan->graph2, plan->stream);
+  tc.done();
   return cuda_status(e);
 }
 
@@ -504,7 +596,7 @@ mwax_status mwax_plan_get_timing(mwax_plan_t plan, mwax_timing *t) {
   if (e != cudaSuccess) return cuda_status(e);
   for (const auto &r : plan->recs) {
     float ms = 0.f;
-    e = cudaEventElapsedTime(&ms, plan->ev_pool[r.start], plan->ev_pool[r.stop]);
+    e = cudaEventElapsedTime(&ms, r.start, r.stop);
     if (e != cudaSuccess) return cuda_status(e);
     if (r.kind == 0) {
       t->unpack_ms += ms;

@@ -24,9 +24,11 @@ cudaError_t launch_plain_channel(const uint8_t *volt_chan, int sample_bits, int 
 
 // ---- unpack: packed samples -> tensor-core operand rows --------------------
 // volt: [n_chan_total][T][N] packed; op: [n_chan][kb][n_tiles*128][128 B].
+// variant: 0 = automatic, 1 = shared-memory transpose, 2 = full-line (no
+// shared memory, 128 threads: fits beside a running correlate CTA).
 cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
                           int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
-                          cudaStream_t s);
+                          int variant, cudaStream_t s);
 
 // ---- tensor-core correlator -------------------------------------------------
 #define MWAX_MAX_JOBS 8
@@ -44,6 +46,7 @@ struct TcLaunch {
   int grid;
   int stages;
   int prefetch;  // K-blocks of L2 prefetch ahead of the TMA loads (0 = none)
+  int wide;      // 1: N=256 MMAs with B' built in shared memory; 0: N=128 MMAs
   int32_t *status;
   unsigned long long timeout_ns;
 };
@@ -52,8 +55,11 @@ struct TcLaunch {
 // the concatenated work items (job by job, channel-major, tile pairs inside).
 cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
                                 cudaStream_t s);
-int correlate_tc_smem_bytes(int stages);
-int correlate_tc_max_stages();
-cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages);
+int correlate_tc_smem_bytes(int stages, int wide);
+int correlate_tc_max_stages(int wide);
+cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int wide);
+
+// Fill the tuning fields of an all-auto job from the MWAX_TUNE_CACHE file.
+void apply_tune_cache(mwax_job *job);
 
 }  // namespace mwax

@@ -66,12 +66,17 @@ def test_plain_small(mw, bits, N, T, C):
     assert_exact(run(mw, spec, mw.ENGINE_PLAIN), oracle_for(spec, range(C)), f"plain {N},{T},{C}")
 
 
+SHAPES = [1, 2]  # M128xN128 (Re, Im separately) and M128xN256 ([Re | Im] per MMA)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("bits", [4, 8])
 @pytest.mark.parametrize("N,T,C", SMALL)
-def test_tensor_small(mw, bits, N, T, C):
+def test_tensor_small(mw, bits, N, T, C, shape):
     spec = synth.Spec("s", N, C, T, bits, seed=N * 131 + T + 7, sigma=2 if bits == 4 else 40,
                       tone_amp=0.3)
-    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tc {N},{T},{C}")
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, mma_shape=shape), oracle_for(spec, range(C)),
+                 f"tc {N},{T},{C}")
 
 
 def test_c0_both_engines(mw):
@@ -81,12 +86,13 @@ def test_c0_both_engines(mw):
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR), ref, "tensor c0")
 
 
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("bits,flush", [(8, 1), (8, 2), (8, 5), (4, 1), (4, 3)])
-def test_tensor_flush_segments(mw, bits, flush):
+def test_tensor_flush_segments(mw, bits, flush, shape):
     """Short FP32 segments: many int32 flushes per item, ragged last segment."""
     spec = synth.Spec("f", 200, 2, 1000, bits, seed=flush + bits, sigma=2 if bits == 4 else 60)
-    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, flush_blocks=flush), oracle_for(spec, range(2)),
-                 f"flush {flush}")
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, flush_blocks=flush, mma_shape=shape),
+                 oracle_for(spec, range(2)), f"flush {flush}")
 
 
 def test_tensor_multiple_channel_groups(mw):
@@ -94,19 +100,23 @@ def test_tensor_multiple_channel_groups(mw):
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR, chan_group=3), oracle_for(spec, range(7)), "groups")
 
 
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("bits", [4, 8])
-def test_exact_window_big_then_small(mw, bits):
+def test_exact_window_big_then_small(mw, bits, shape):
     """Accumulator near the top of its segment window, then +-1 addends: any
     loss of low-order bits in the tensor-core accumulation shows up."""
     T = 20000 if bits == 4 else 2000
     split = 19000 if bits == 4 else 500
     spec = synth.Spec("bs", 130, 2, T, bits, seed=11, kind=synth.SYNTH_BIGSMALL, t_split=split)
-    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(2)), "big-small")
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, mma_shape=shape), oracle_for(spec, range(2)),
+                 "big-small")
 
 
-def test_exact_random_max_magnitude(mw):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_exact_random_max_magnitude(mw, shape):
     spec = synth.Spec("rm", 256, 2, 3000, 8, seed=12, kind=synth.SYNTH_RANDMAX)
-    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(2)), "randmax")
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, mma_shape=shape), oracle_for(spec, range(2)),
+                 "randmax")
 
 
 def test_int32_bound_at_max_integration(mw):
@@ -219,13 +229,15 @@ def _full_size(mw, spec, chans, **kw):
     assert_exact(got, oracle_for(spec, chans), spec.name)
 
 
-def test_full_size_c1_sampled(mw):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_full_size_c1_sampled(mw, shape):
     spec = synth.spec_c1()
-    _full_size(mw, spec, [0, 1, 383, 766, 767])
+    _full_size(mw, spec, [0, 1, 383, 766, 767], mma_shape=shape)
 
 
-def test_full_size_c2_sampled(mw):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_full_size_c2_sampled(mw, shape):
     spec = synth.spec_c2()
     rng = np.random.default_rng(2)
     chans = sorted(set([0, spec.n_chan - 1] + rng.choice(spec.n_chan, 6, replace=False).tolist()))
-    _full_size(mw, spec, chans)
+    _full_size(mw, spec, chans, mma_shape=shape)

@@ -1,0 +1,80 @@
+"""Autotuner and pipeline options: every tuning choice keeps the result
+bit-exact; the tuner's choice is cached and re-applied."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import assert_exact, device_volt, oracle_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mw(mwax_lib):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return mwax_lib
+
+
+def test_autotune_choice_is_exact_and_cached(mw, tmp_path, monkeypatch):
+    import torch
+
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("MWAX_TUNE_CACHE", str(cache))
+    spec = synth.Spec("t", 300, 9, 700, 8, seed=5, sigma=40)
+    v = device_volt(spec)
+    out = torch.empty((spec.n_chan, spec.n_inputs * (spec.n_inputs + 1) // 2, 2), dtype=torch.int32,
+                      device="cuda")
+    fields, rep = mw.autotune(v, out, spec.n_inputs, spec.n_chan, spec.n_time, 8)
+    assert rep.candidates >= 4 and rep.from_cache == 0 and rep.best_ms > 0
+    assert fields["mma_shape"] in (1, 2) and fields["stages"] >= 2
+    assert cache.read_text().strip()
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, **fields)
+    got = p.correlate(v)
+    assert p.status() == 0
+    assert_exact(got.cpu().numpy(), oracle_for(spec, range(spec.n_chan)), "tuned")
+    p.close()
+    fields2, rep2 = mw.autotune(v, out, spec.n_inputs, spec.n_chan, spec.n_time, 8)
+    assert rep2.from_cache == 1 and fields2 == fields
+    # an all-auto plan picks the cached choice up
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8)
+    inf = p.info()
+    assert inf.mma_shape == fields["mma_shape"] and inf.stages == fields["stages"]
+    p.close()
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_overlapped_pipeline_is_exact(mw, shape):
+    """Unpack of the next channel group on a second stream beside the
+    correlation of the current one (two scratch buffers)."""
+    spec = synth.Spec("o", 260, 7, 300, 8, seed=8, sigma=50)
+    v = device_volt(spec)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, chan_group=2, pipeline=2, mma_shape=shape)
+    assert p.info().pipeline == 2
+    out = p.correlate(v)
+    out = p.correlate(v, out)
+    assert p.status() == 0
+    assert_exact(out.cpu().numpy(), oracle_for(spec, range(spec.n_chan)), "overlap")
+    p.close()
+
+
+def test_batch_autotune_and_graph_timing(mw):
+    import torch
+
+    jobs = [(64, 5, 300), (200, 3, 400)]
+    specs = [synth.Spec(f"bt{k}", n, c, t, 4, seed=60 + k, sigma=2) for k, (n, c, t) in enumerate(jobs)]
+    vs = [device_volt(s) for s in specs]
+    outs = [torch.empty((c, n * (n + 1) // 2, 2), dtype=torch.int32, device="cuda") for (n, c, t) in jobs]
+    fields, rep = mw.autotune_batch(jobs, vs, outs)
+    assert rep.candidates >= 3 and rep.best_ms > 0
+    bp = mw.BatchPlan(jobs, **fields)
+    bp.set_timing(True)
+    outs = bp.correlate(vs, outs)
+    t = bp.timing()
+    assert t.correlate_launches == 1 and t.unpack_launches == 1 and t.correlate_ms > 0 and t.unpack_ms > 0
+    assert bp.status() == 0
+    for s, o in zip(specs, outs):
+        assert_exact(o.cpu().numpy(), oracle_for(s, range(s.n_chan)), s.name)
+    bp.close()
