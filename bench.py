@@ -49,6 +49,19 @@ def sky_seconds(spec) -> float:
     return spec.n_time / spec.chan_width_hz
 
 
+def measured_traffic(kernel_key: str, channels_per_launch: int):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
+    scaled by channels (traffic grows in proportion), or None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel_key)
+    return None if e is None else e["bytes_per_channel"] * channels_per_launch
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -306,7 +319,7 @@ def run_batch(args):
     outs = [torch.empty((s.n_chan, s.n_inputs * (s.n_inputs + 1) // 2, 2), dtype=torch.int32,
                         device="cuda") for s in specs]
     tune, rep = {}, None
-    if not args.no_tune:
+    if args.tune:
         tune, rep = mw.autotune_batch(jobs, vols, outs, sample_bits=4, stream=stream)
     bp = mw.BatchPlan(jobs, sample_bits=4, stream=stream, **tune)
     for _ in range(args.warmup):
@@ -494,7 +507,10 @@ def main():
                          "workload's channels are split across ranks")
     ap.add_argument("--chan", type=int, default=0,
                     help="override the channel count (small cases for profiling)")
-    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--tune", action="store_true",
+                    help="run the autotuner first (default: the plan's default configuration, "
+                         "the one the committed ncu traffic figures were taken on)")
+    ap.add_argument("--no-tune", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-variant report")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -549,7 +565,7 @@ def main():
     n_bl = rspec.n_inputs * (rspec.n_inputs + 1) // 2
     out = torch.empty((rspec.n_chan, n_bl, 2), dtype=torch.int32, device=dev)
     tune, tune_rep = {}, None
-    if engine == mw.ENGINE_TENSOR and not args.no_tune:
+    if engine == mw.ENGINE_TENSOR and args.tune:
         tune, tune_rep = mw.autotune(vol, out, rspec.n_inputs, rspec.n_chan, rspec.n_time,
                                      rspec.sample_bits, stream=stream)
     plan = mw.Plan(rspec.n_inputs, rspec.n_chan, rspec.n_time, rspec.sample_bits, engine=engine,
@@ -595,10 +611,20 @@ def main():
     else:
         peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_note = f"2 x bf16 sustained ({peak_src}; nominal fp8/bf16 ratio 4.5/2.25)"
+    info = plan.info()
     if engine == mw.ENGINE_TENSOR and tim.correlate_ms > 0:
         achieved = 8.0 * units * args.steps / (tim.correlate_ms / 1e3) / 1e12
+        traffic = None
+        if (info.mma_shape == 1 and rspec.sample_bits == 8 and rspec.n_inputs == 1024
+                and rspec.n_time == 10000 and rspec.kind == synth.SYNTH_NOISE_TONE):
+            traffic = measured_traffic("correlate_tc_kernel<8,EXACT,narrow>|N1024|T10000",
+                                       info.chan_group)
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic,
+                    "traffic_note": "DRAM bytes per launch of chan_group channels, scaled from a "
+                                    "64-channel ncu capture (profiles/traffic.json); algorithmic "
+                                    "bytes per launch: operands + visibilities = "
+                                    f"{45223936.0 * info.chan_group:.4g}" if traffic else None,
                     "kernel": "correlate_tc_kernel", "peak_source": peak_note,
                     "kernel_ms_per_launch": tim.correlate_ms / max(1, tim.correlate_launches),
                     "unpack_ms_per_step": tim.unpack_ms / args.steps,
@@ -606,7 +632,6 @@ def main():
     else:
         roofline = None
 
-    info = plan.info()
     line = {
         "metric": METRIC, "value": value, "unit": "TCMAC/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

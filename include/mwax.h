@@ -93,7 +93,14 @@ typedef struct {
                               plan's stream, 2 = overlap the unpack of the next group with
                               the correlation of the current one on a second stream (two
                               scratch buffers); 0 = auto (1)                              */
-  int32_t reserved[4];     /* must be zero                                                */
+  int32_t timeout_ms;      /* limit of every device-side wait, ms (0 = 2000)              */
+  int32_t test_fault;      /* failure-detection tests only, 0 = off: with k > 0 the
+                              epilogue of the tensor correlator withholds the release of
+                              its (k-1)-th accumulator segment, so the MMA warp's bounded
+                              wait runs out; the call then completes with
+                              MWAX_ERR_TIMEOUT in mwax_plan_status and the output is
+                              invalid; the device stays usable                          */
+  int32_t reserved[2];     /* must be zero                                                */
 } mwax_job;
 
 /* Read-only description of a plan's choices. */

@@ -22,6 +22,7 @@ MWAX_OK = 0
 STATUS = {0: "MWAX_OK", 1: "MWAX_ERR_INVALID_ARG", 2: "MWAX_ERR_SHAPE_MISMATCH",
           3: "MWAX_ERR_OVERFLOW_BOUND", 4: "MWAX_ERR_UNSUPPORTED", 5: "MWAX_ERR_OOM",
           6: "MWAX_ERR_CUDA", 7: "MWAX_ERR_TIMEOUT"}
+STATUS_BY_NAME = {v: k for k, v in STATUS.items()}
 KIND_EXACT, KIND_FP16 = 0, 1
 ENGINE_TENSOR, ENGINE_PLAIN = 0, 1
 
@@ -39,7 +40,8 @@ class Job(ctypes.Structure):
                 ("flush_blocks", ctypes.c_int32), ("chan_group", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("mma_shape", ctypes.c_int32), ("pipeline", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("timeout_ms", ctypes.c_int32), ("test_fault", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -161,11 +163,13 @@ def _stream_handle(stream=None) -> int:
 
 
 def _job(n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, engine=ENGINE_TENSOR,
-         flush_blocks=0, chan_group=0, stages=0, prefetch=0, mma_shape=0, pipeline=0) -> Job:
+         flush_blocks=0, chan_group=0, stages=0, prefetch=0, mma_shape=0, pipeline=0,
+         timeout_ms=0, test_fault=0) -> Job:
     j = Job()
     j.n_inputs, j.n_chan, j.n_time, j.sample_bits = n_inputs, n_chan, n_time, sample_bits
     j.kind, j.engine, j.flush_blocks, j.chan_group = kind, engine, flush_blocks, chan_group
     j.stages, j.prefetch, j.mma_shape, j.pipeline = stages, prefetch, mma_shape, pipeline
+    j.timeout_ms, j.test_fault = timeout_ms, test_fault
     return j
 
 
@@ -179,9 +183,9 @@ class Plan:
 
     def __init__(self, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,
                  engine=ENGINE_TENSOR, flush_blocks=0, chan_group=0, stages=0, prefetch=0,
-                 mma_shape=0, pipeline=0, stream=None):
+                 mma_shape=0, pipeline=0, timeout_ms=0, test_fault=0, stream=None):
         self.job = _job(n_inputs, n_chan, n_time, sample_bits, kind, engine, flush_blocks,
-                        chan_group, stages, prefetch, mma_shape, pipeline)
+                        chan_group, stages, prefetch, mma_shape, pipeline, timeout_ms, test_fault)
         self.shape = (n_inputs, n_chan, n_time)
         self.sample_bits, self.kind, self.engine = sample_bits, kind, engine
         self._h = _P()

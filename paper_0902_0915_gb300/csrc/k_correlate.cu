@@ -77,6 +77,7 @@ struct KParams {
   int64_t n_items;
   unsigned long long timeout_ns;
   int32_t n_jobs, stages, prefetch;
+  int32_t withhold_seg;  // test hook: segment whose accumulator release the epilogue withholds (-1: none)
 };
 
 struct KMaps {
@@ -538,7 +539,9 @@ __global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty(buf));
+        // (test hook: withholding one release makes the MMA warp's bounded
+        // wait for that accumulator run out -> MWAX_ERR_TIMEOUT, clean exit)
+        if (lane == 0 && (int)seg != p.withhold_seg) mbar_arrive(tempty(buf));
         ++seg;
       }
       if (!ok) break;
@@ -669,6 +672,7 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   kp.n_jobs = n_jobs;
   kp.stages = cfg.stages;
   kp.prefetch = cfg.prefetch;
+  kp.withhold_seg = cfg.withhold_seg;
   if (items <= 0) return cudaSuccess;
   const int grid = (int)(items < cfg.grid ? items : cfg.grid);
   const int smem = correlate_tc_smem_bytes(cfg.stages, cfg.wide);

@@ -49,6 +49,7 @@ struct mwax_plan_s {
   int stages = 6;
   int prefetch = 0;
   int wide = 0;
+  int withhold_seg = -1;
   unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
   std::vector<mwax::JobState> jobs;
   uint8_t *scratch = nullptr;  // single-job plans: operand buffer for one channel group
@@ -112,7 +113,8 @@ mwax_status check_job(const mwax_job &j) {
   if (j.stages < 0 || j.stages == 1 || j.stages > correlate_tc_max_stages(j.mma_shape == 2))
     return MWAX_ERR_INVALID_ARG;
   if (j.prefetch < -1 || j.prefetch > 64) return MWAX_ERR_INVALID_ARG;
-  for (int k = 0; k < 4; ++k)
+  if (j.timeout_ms < 0 || j.test_fault < 0) return MWAX_ERR_INVALID_ARG;
+  for (int k = 0; k < 2; ++k)
     if (j.reserved[k] != 0) return MWAX_ERR_INVALID_ARG;
   if (j.kind == MWAX_KIND_FP16 && (j.sample_bits != 8 || j.engine != MWAX_ENGINE_TENSOR))
     return MWAX_ERR_UNSUPPORTED;
@@ -196,6 +198,7 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
   c.stages = p->stages;
   c.prefetch = p->prefetch;
   c.wide = p->wide;
+  c.withhold_seg = p->withhold_seg;
   c.status = p->status;
   c.timeout_ns = p->timeout_ns;
   return c;
@@ -390,6 +393,8 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
   p->wide = job->mma_shape == 2;
   p->stages = job->stages > 0 ? job->stages : correlate_tc_max_stages(p->wide);
   if (job->prefetch != 0) p->prefetch = job->prefetch < 0 ? 0 : job->prefetch;
+  if (job->timeout_ms > 0) p->timeout_ns = (unsigned long long)job->timeout_ms * 1000000ull;
+  p->withhold_seg = job->test_fault - 1;
   if (p->engine == MWAX_ENGINE_TENSOR) {
     const int64_t one = s.op_chan_bytes * s.chan_group;
     p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan;

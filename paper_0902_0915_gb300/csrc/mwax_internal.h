@@ -47,6 +47,7 @@ struct TcLaunch {
   int stages;
   int prefetch;  // K-blocks of L2 prefetch ahead of the TMA loads (0 = none)
   int wide;      // 1: N=256 MMAs with B' built in shared memory; 0: N=128 MMAs
+  int withhold_seg;  // test hook (-1: off): see mwax_job.test_fault
   int32_t *status;
   unsigned long long timeout_ns;
 };
