@@ -90,9 +90,9 @@ typedef struct {
   int32_t mma_shape;       /* tuning: 1 = M128xN128 MMAs (Re, Im separately), 2 = M128xN256
                               MMAs with [Re | Im] at once (0 = auto)                     */
   int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
-                              plan's stream, 2 = overlap the unpack of the next group with
-                              the correlation of the current one on a second stream (two
-                              scratch buffers); 0 = auto (1)                              */
+                              plan's stream, 2 = unpack the next group on `unpack_sms`
+                              SMs (second stream, second scratch buffer) while the current
+                              group correlates on the other SMs; 0 = auto (1)            */
   int32_t timeout_ms;      /* limit of every device-side wait, ms (0 = 2000)              */
   int32_t test_fault;      /* failure-detection tests only, 0 = off: with k > 0 the
                               epilogue of the tensor correlator withholds the release of
@@ -100,7 +100,9 @@ typedef struct {
                               wait runs out; the call then completes with
                               MWAX_ERR_TIMEOUT in mwax_plan_status and the output is
                               invalid; the device stays usable                          */
-  int32_t reserved[2];     /* must be zero                                                */
+  int32_t unpack_sms;      /* tuning, pipeline 2 only: SMs given to the persistent unpack
+                              while the correlate runs on the others (0 = 20)           */
+  int32_t reserved[1];     /* must be zero                                                */
 } mwax_job;
 
 /* Read-only description of a plan's choices. */

@@ -41,7 +41,7 @@ class Job(ctypes.Structure):
                 ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("mma_shape", ctypes.c_int32), ("pipeline", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("test_fault", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("unpack_sms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -164,12 +164,12 @@ def _stream_handle(stream=None) -> int:
 
 def _job(n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, engine=ENGINE_TENSOR,
          flush_blocks=0, chan_group=0, stages=0, prefetch=0, mma_shape=0, pipeline=0,
-         timeout_ms=0, test_fault=0) -> Job:
+         timeout_ms=0, test_fault=0, unpack_sms=0) -> Job:
     j = Job()
     j.n_inputs, j.n_chan, j.n_time, j.sample_bits = n_inputs, n_chan, n_time, sample_bits
     j.kind, j.engine, j.flush_blocks, j.chan_group = kind, engine, flush_blocks, chan_group
     j.stages, j.prefetch, j.mma_shape, j.pipeline = stages, prefetch, mma_shape, pipeline
-    j.timeout_ms, j.test_fault = timeout_ms, test_fault
+    j.timeout_ms, j.test_fault, j.unpack_sms = timeout_ms, test_fault, unpack_sms
     return j
 
 
@@ -183,9 +183,11 @@ class Plan:
 
     def __init__(self, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,
                  engine=ENGINE_TENSOR, flush_blocks=0, chan_group=0, stages=0, prefetch=0,
-                 mma_shape=0, pipeline=0, timeout_ms=0, test_fault=0, stream=None):
+                 mma_shape=0, pipeline=0, timeout_ms=0, test_fault=0, unpack_sms=0,
+                 stream=None):
         self.job = _job(n_inputs, n_chan, n_time, sample_bits, kind, engine, flush_blocks,
-                        chan_group, stages, prefetch, mma_shape, pipeline, timeout_ms, test_fault)
+                        chan_group, stages, prefetch, mma_shape, pipeline, timeout_ms, test_fault,
+                        unpack_sms)
         self.shape = (n_inputs, n_chan, n_time)
         self.sample_bits, self.kind, self.engine = sample_bits, kind, engine
         self._h = _P()

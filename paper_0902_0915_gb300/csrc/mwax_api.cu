@@ -50,6 +50,7 @@ struct mwax_plan_s {
   int prefetch = 0;
   int wide = 0;
   int withhold_seg = -1;
+  int unpack_sms = 20;  // overlapped pipeline: SMs given to the persistent unpack
   unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
   std::vector<mwax::JobState> jobs;
   uint8_t *scratch = nullptr;  // single-job plans: operand buffer for one channel group
@@ -113,8 +114,8 @@ mwax_status check_job(const mwax_job &j) {
   if (j.stages < 0 || j.stages == 1 || j.stages > correlate_tc_max_stages(j.mma_shape == 2))
     return MWAX_ERR_INVALID_ARG;
   if (j.prefetch < -1 || j.prefetch > 64) return MWAX_ERR_INVALID_ARG;
-  if (j.timeout_ms < 0 || j.test_fault < 0) return MWAX_ERR_INVALID_ARG;
-  for (int k = 0; k < 2; ++k)
+  if (j.timeout_ms < 0 || j.test_fault < 0 || j.unpack_sms < 0) return MWAX_ERR_INVALID_ARG;
+  for (int k = 0; k < 1; ++k)
     if (j.reserved[k] != 0) return MWAX_ERR_INVALID_ARG;
   if (j.kind == MWAX_KIND_FP16 && (j.sample_bits != 8 || j.engine != MWAX_ENGINE_TENSOR))
     return MWAX_ERR_UNSUPPORTED;
@@ -194,7 +195,8 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
   TcLaunch c;
   c.sample_bits = p->sample_bits;
   c.kind = p->kind;
-  c.grid = p->sm_count;
+  // with the overlapped pipeline the correlate leaves unpack_sms SMs to the unpack
+  c.grid = p->overlap ? p->sm_count - p->unpack_sms : p->sm_count;
   c.stages = p->stages;
   c.prefetch = p->prefetch;
   c.wide = p->wide;
@@ -204,11 +206,36 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
   return c;
 }
 
+// Unpack variant: MWAX_UNPACK overrides (1 shared-memory transpose, 2
+// full-line, 3 TMA-staged input, 4 TMA both ways); automatic = TMA both ways
+// for 8-bit shapes that allow it, else the per-width default.
+int unpack_choice(const JobState &s) {
+  static const int env = [] {
+    const char *e = getenv("MWAX_UNPACK");
+    return e ? atoi(e) : 0;
+  }();
+  if (env >= 1 && env <= 4) return env;
+  if (unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs)) return 4;
+  return 0;
+}
+
 mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
-                         uint8_t *op, int variant, cudaStream_t st) {
+                         uint8_t *op, int ctas, cudaStream_t st) {
   TimedLaunch tu(p, 0, st);
-  cudaError_t e = launch_unpack(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
-                                s.kb, c0, nc, op, variant, st);
+  cudaError_t e;
+  const int v = unpack_choice(s);
+  if (v == 4 && unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs))
+    e = launch_unpack_tma2(volt, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, c0, nc, op,
+                           ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
+  else if (v == 3 && unpack_tma_supported(s.job.sample_bits, s.job.n_inputs))
+    e = launch_unpack_tma(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, c0,
+                          nc, op, ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
+  else if (ctas > 0)
+    e = launch_unpack_persistent(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
+                                 s.kb, c0, nc, op, ctas, st);
+  else
+    e = launch_unpack(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, c0,
+                      nc, op, v, st);
   tu.done();
   return cuda_status(e);
 }
@@ -277,7 +304,7 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
     const int nc = (int)std::min<int64_t>(s.chan_group, s.job.n_chan - c0);
     if (g >= 2 && (e = cudaStreamWaitEvent(p->aux, p->ev_freed[k], 0)) != cudaSuccess)
       return cuda_status(e);
-    mwax_status r = unpack_group(p, s, volt, c0, nc, buf[k], 2, p->aux);
+    mwax_status r = unpack_group(p, s, volt, c0, nc, buf[k], p->unpack_sms, p->aux);
     if (r != MWAX_OK) return r;
     if ((e = cudaEventRecord(p->ev_unpacked[k], p->aux)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaStreamWaitEvent(st, p->ev_unpacked[k], 0)) != cudaSuccess) return cuda_status(e);
@@ -397,7 +424,10 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
   p->withhold_seg = job->test_fault - 1;
   if (p->engine == MWAX_ENGINE_TENSOR) {
     const int64_t one = s.op_chan_bytes * s.chan_group;
-    p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan;
+    const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : s.job.n_inputs % 4 == 0;
+    if (job->unpack_sms > 0) p->unpack_sms = job->unpack_sms;
+    p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan && even &&
+                 p->unpack_sms < p->sm_count;
     p->scratch_bytes = one * (p->overlap ? 2 : 1);
     cudaError_t e = cudaMalloc(&p->scratch, (size_t)one);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)one, stream);

@@ -79,6 +79,17 @@ def test_tensor_small(mw, bits, N, T, C, shape):
                  f"tc {N},{T},{C}")
 
 
+@pytest.mark.parametrize("bits", [4, 8])
+@pytest.mark.parametrize("N,T,C", [(16, 33, 3), (48, 1000, 2), (120, 64, 3), (272, 97, 2),
+                                   (1024, 70, 1), (1000, 45, 2)])
+def test_tensor_tma_unpack_shapes(mw, bits, N, T, C):
+    """Shapes the TMA-staged unpack takes (N a multiple of 16, raw time block
+    <= 64 KB), with a ragged last time block."""
+    spec = synth.Spec("tma", N, C, T, bits, seed=N + T + bits, sigma=2 if bits == 4 else 40,
+                      tone_amp=0.3)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tma {N},{T},{C}")
+
+
 def test_c0_both_engines(mw):
     spec = synth.spec_c0()
     ref = oracle_for(spec, range(spec.n_chan))

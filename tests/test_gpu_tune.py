@@ -45,13 +45,16 @@ def test_autotune_choice_is_exact_and_cached(mw, tmp_path, monkeypatch):
     p.close()
 
 
+@pytest.mark.parametrize("N,bits", [(260, 8), (256, 8), (256, 4)])
 @pytest.mark.parametrize("shape", [1, 2])
-def test_overlapped_pipeline_is_exact(mw, shape):
-    """Unpack of the next channel group on a second stream beside the
-    correlation of the current one (two scratch buffers)."""
-    spec = synth.Spec("o", 260, 7, 300, 8, seed=8, sigma=50)
+def test_overlapped_pipeline_is_exact(mw, shape, N, bits):
+    """Unpack of the next channel group on a few SMs (second stream, second
+    scratch buffer) beside the correlation of the current one; N = 256 takes
+    the TMA-staged unpack, N = 260 the register-staged one."""
+    spec = synth.Spec("o", N, 7, 300, bits, seed=8, sigma=50 if bits == 8 else 2)
     v = device_volt(spec)
-    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, chan_group=2, pipeline=2, mma_shape=shape)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, bits, chan_group=2, pipeline=2,
+                mma_shape=shape, unpack_sms=12)
     assert p.info().pipeline == 2
     out = p.correlate(v)
     out = p.correlate(v, out)
