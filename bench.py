@@ -62,6 +62,33 @@ def measured_traffic(kernel_key: str, channels_per_launch: int):
     return None if e is None else e["bytes_per_channel"] * channels_per_launch
 
 
+def unpack_bytes_per_channel(spec) -> float:
+    """Algorithmic bytes the unpack moves per channel: packed samples read plus
+    operand rows written ([time block][row][128 B], rows padded to 128)."""
+    per_block = 32 if spec.sample_bits == 8 else 64
+    kb = -(-spec.n_time // per_block)
+    n_rows = -(-spec.n_inputs // 128) * 128
+    packed = spec.n_inputs * spec.n_time * (2 if spec.sample_bits == 8 else 1)
+    return float(packed + n_rows * kb * 128)
+
+
+def unpack_roofline(spec, info, tim, steps, peaks, peak_src):
+    """HBM roofline of the unpack kernel (the second kernel of a step)."""
+    per_ch = unpack_bytes_per_channel(spec)
+    achieved = per_ch * spec.n_chan * steps / (tim.unpack_ms / 1e3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    traffic = None
+    if (spec.sample_bits == 8 and spec.n_inputs == 1024 and spec.n_time == 10000
+            and os.environ.get("MWAX_UNPACK") is None):
+        traffic = measured_traffic("unpack8_tma2_kernel|N1024|T10000", info.chan_group)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_launch": per_ch * info.chan_group,
+            "kernel": "unpack8_tma2_kernel" if spec.sample_bits == 8 else "unpack4_line_kernel",
+            "peak_source": f"HBM copy ({peak_src})",
+            "ms_per_launch": tim.unpack_ms / max(1, tim.unpack_launches)}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -629,6 +656,8 @@ def main():
                     "kernel_ms_per_launch": tim.correlate_ms / max(1, tim.correlate_launches),
                     "unpack_ms_per_step": tim.unpack_ms / args.steps,
                     "correlate_ms_per_step": tim.correlate_ms / args.steps}
+        if tim.unpack_ms > 0:
+            roofline["unpack"] = unpack_roofline(rspec, info, tim, args.steps, peaks, peak_src)
     else:
         roofline = None
 

@@ -233,14 +233,7 @@ __global__ void __launch_bounds__(512) unpack4_persist_kernel(const uint8_t *__r
 
 constexpr int kPersistSmem = 64 * 1024;  // > what a correlate CTA leaves free on an SM
 
-// ---- TMA-staged persistent path -------------------------------------------------
-// One task = one time block of one channel: its raw samples (32 rows of N
-// 8-bit complex samples, or 64 rows of N 4-bit ones) are one contiguous piece
-// of the input, fetched with a single bulk copy into one of two shared-memory
-// buffers while the CTA converts the other.  Threads then read 4-byte words
-// (2 or 4 inputs at one time sample) from shared memory -- conflict-free --
-// and write whole operand rows.  Bytes in flight come from the copy engine,
-// not from registers, so a few SMs sustain the stream.
+// ---- TMA path -----------------------------------------------------------------
 constexpr int kTmaThreads = 512;
 constexpr int kTmaBufBytes = 64 * 1024;
 
@@ -263,162 +256,6 @@ __device__ __forceinline__ bool u_wait(uint32_t bar, uint32_t parity, unsigned l
     if (ok) return true;
     if (u_globaltimer() - t0 > tmo) return false;
   }
-}
-
-template <int BITS>
-__global__ void __launch_bounds__(kTmaThreads, 1)
-    unpack_tma_kernel(const uint8_t *__restrict__ volt, uint8_t *__restrict__ op, int N, int T,
-                      int n_rows, int kb, int64_t chan0, int n_chan, int32_t *status,
-                      unsigned long long tmo) {
-  constexpr int S = BITS == 4 ? 64 : 32;      // samples per block
-  constexpr int BPS = BITS == 4 ? 1 : 2;      // bytes per sample
-  extern __shared__ __align__(128) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bar[2];
-  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bar[0]);
-  const int64_t tasks = (int64_t)n_chan * kb;
-  const int64_t row_bytes = (int64_t)N * BPS;
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  // bytes of the raw block of task k (rows past T are not fetched)
-  auto issue = [&](int64_t k, int buf) {
-    const int c = (int)(k / kb), tb = (int)(k % kb);
-    const int rows = min(S, T - tb * S);
-    const uint32_t bytes = (uint32_t)(rows * row_bytes);
-    const uint8_t *src = volt + ((chan0 + c) * (int64_t)T + (int64_t)tb * S) * row_bytes;
-    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(sm + buf * kTmaBufBytes);
-    const uint32_t b = bar0 + 8 * buf;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(b)
-        : "memory");
-  };
-  int64_t k = blockIdx.x;
-  if (threadIdx.x == 0 && k < tasks) issue(k, 0);
-  uint32_t phase[2] = {0u, 0u};
-  bool ok = true;
-  int pending = -1;  // buffer with a copy issued but not yet waited for
-  for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
-    const int buf = it & 1;
-    // prefetch the next task into the other buffer (freed by the barrier below)
-    pending = -1;
-    if (k + gridDim.x < tasks) {
-      if (threadIdx.x == 0) issue(k + gridDim.x, buf ^ 1);
-      pending = buf ^ 1;
-    }
-    if (!u_wait(bar0 + 8 * buf, phase[buf], tmo)) {
-      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
-      ok = false;
-    }
-    phase[buf] ^= 1u;
-    if (ok) {
-      const int c = (int)(k / kb), tb = (int)(k % kb);
-      const int rows = min(S, T - tb * S);
-      const uint8_t *raw = sm + buf * kTmaBufBytes;
-      uint8_t *slab = op + (((int64_t)c * kb + tb) * n_rows) * kRowBytes;
-      if constexpr (BITS == 8) {
-        for (int ip = threadIdx.x; ip < n_rows / 2; ip += kTmaThreads) {
-          const int i0 = 2 * ip;
-          uint32_t w[32];
-#pragma unroll
-          for (int r = 0; r < 32; ++r)
-            w[r] = (i0 < N && r < rows) ? *reinterpret_cast<const uint32_t *>(raw + r * row_bytes + i0 * 2)
-                                        : 0u;
-          uint8_t *row_a = slab + (int64_t)i0 * kRowBytes;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            uint32_t ra[4], ia[4], rb[4], ib[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const uint32_t x = w[8 * q + 2 * e], y = w[8 * q + 2 * e + 1];
-              ra[e] = s8pair_to_h2(__byte_perm(x, y, 0x4400));
-              ia[e] = s8pair_to_h2(__byte_perm(x, y, 0x5511));
-              rb[e] = s8pair_to_h2(__byte_perm(x, y, 0x6622));
-              ib[e] = s8pair_to_h2(__byte_perm(x, y, 0x7733));
-            }
-            *reinterpret_cast<uint4 *>(row_a + 16 * q) = make_uint4(ra[0], ra[1], ra[2], ra[3]);
-            *reinterpret_cast<uint4 *>(row_a + 64 + 16 * q) = make_uint4(ia[0], ia[1], ia[2], ia[3]);
-            *reinterpret_cast<uint4 *>(row_a + kRowBytes + 16 * q) = make_uint4(rb[0], rb[1], rb[2], rb[3]);
-            *reinterpret_cast<uint4 *>(row_a + kRowBytes + 64 + 16 * q) =
-                make_uint4(ib[0], ib[1], ib[2], ib[3]);
-          }
-        }
-      } else {
-        // 4 inputs x 32 samples (half h of the block) per task unit
-        for (int u = threadIdx.x; u < (n_rows / 4) * 2; u += kTmaThreads) {
-          const int iq = u >> 1, h = u & 1;
-          const int i0 = 4 * iq;
-          uint32_t re[32], im[32];
-#pragma unroll
-          for (int r = 0; r < 32; ++r) {
-            const int rr = 32 * h + r;
-            const uint32_t w = (i0 < N && rr < rows)
-                                   ? *reinterpret_cast<const uint32_t *>(raw + rr * row_bytes + i0)
-                                   : 0u;
-            re[r] = nib4_to_e4m3(w);
-            im[r] = nib4_to_e4m3(w >> 4);
-          }
-          uint8_t *row = slab + (int64_t)i0 * kRowBytes + 32 * h;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t sel = (uint32_t)(q | ((q + 4) << 4));
-            uint32_t vr[8], vi[8];
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-              vr[g] = __byte_perm(__byte_perm(re[4 * g], re[4 * g + 1], sel),
-                                  __byte_perm(re[4 * g + 2], re[4 * g + 3], sel), 0x5410);
-              vi[g] = __byte_perm(__byte_perm(im[4 * g], im[4 * g + 1], sel),
-                                  __byte_perm(im[4 * g + 2], im[4 * g + 3], sel), 0x5410);
-            }
-            uint8_t *dst = row + q * kRowBytes;
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
-            *reinterpret_cast<uint4 *>(dst + 16) = make_uint4(vr[4], vr[5], vr[6], vr[7]);
-            *reinterpret_cast<uint4 *>(dst + 64) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
-            *reinterpret_cast<uint4 *>(dst + 80) = make_uint4(vi[4], vi[5], vi[6], vi[7]);
-          }
-        }
-      }
-    }
-    __syncthreads();  // buffer `buf` is free for the copy issued next iteration
-  }
-  // after a timeout, the prefetch into the other buffer may still be in flight:
-  // wait (bounded) for it before the CTA's shared memory goes away
-  if (!ok && pending >= 0 && threadIdx.x == 0) u_wait(bar0 + 8 * pending, phase[pending], tmo);
-  __syncthreads();
-}
-
-}  // namespace
-
-cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
-                                     int n_time, int n_tiles, int kb, int64_t chan0, int n_chan,
-                                     uint8_t *op, int ctas, cudaStream_t s) {
-  const int n_rows = n_tiles * kTile;
-  if (n_chan <= 0) return cudaSuccess;
-  if (ctas < 1 || (sample_bits == 8 && n_inputs % 2) || (sample_bits == 4 && n_inputs % 4))
-    return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(unpack8_persist_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(unpack4_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kPersistSmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  if (sample_bits == 8)
-    unpack8_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
-                                                           chan0, n_chan);
-  else
-    unpack4_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
-                                                           chan0, n_chan);
-  return cudaGetLastError();
 }
 
 // 8-bit samples, TMA both ways: the raw time block comes in with one bulk
@@ -523,18 +360,46 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   __syncthreads();
 }
 
+}  // namespace
+
+cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
+                                     int n_time, int n_tiles, int kb, int64_t chan0, int n_chan,
+                                     uint8_t *op, int ctas, cudaStream_t s) {
+  const int n_rows = n_tiles * kTile;
+  if (n_chan <= 0) return cudaSuccess;
+  if (ctas < 1 || (sample_bits == 8 && n_inputs % 2) || (sample_bits == 4 && n_inputs % 4))
+    return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(unpack8_persist_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(unpack4_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kPersistSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (sample_bits == 8)
+    unpack8_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
+                                                           chan0, n_chan);
+  else
+    unpack4_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
+                                                           chan0, n_chan);
+  return cudaGetLastError();
+}
+
 bool unpack_tma2_supported(int sample_bits, int n_inputs) {
   const int n_rows = (n_inputs + kTile - 1) / kTile * kTile;
   return sample_bits == 8 && n_inputs % 8 == 0 && 64 * n_inputs <= kTmaBufBytes &&
          n_rows * kRowBytes <= kStageOutBytes;
 }
 
-cudaError_t launch_unpack_tma2(const uint8_t *volt, int n_inputs, int n_time, int n_tiles, int kb,
-                               int64_t chan0, int n_chan, uint8_t *op, int ctas, int32_t *status,
-                               unsigned long long timeout_ns, cudaStream_t s) {
+cudaError_t launch_unpack_tma2(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
+                               int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op, int ctas,
+                               int32_t *status, unsigned long long timeout_ns, cudaStream_t s) {
   const int n_rows = n_tiles * kTile;
   if (n_chan <= 0) return cudaSuccess;
-  if (ctas < 1 || !unpack_tma2_supported(8, n_inputs)) return cudaErrorInvalidValue;
+  if (ctas < 1 || !unpack_tma2_supported(sample_bits, n_inputs)) return cudaErrorInvalidValue;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *ptr = nullptr;
@@ -566,37 +431,6 @@ cudaError_t launch_unpack_tma2(const uint8_t *volt, int n_inputs, int n_time, in
   }
   unpack8_tma2_kernel<<<ctas, kTmaThreads, smem, s>>>(map, volt, n_inputs, n_time, n_rows, kb, chan0,
                                                       n_chan, status, timeout_ns);
-  return cudaGetLastError();
-}
-
-bool unpack_tma_supported(int sample_bits, int n_inputs) {
-  const int64_t block = (int64_t)(sample_bits == 4 ? 64 : 64) * n_inputs;  // 32 x 2 B or 64 x 1 B
-  return n_inputs % 16 == 0 && block <= kTmaBufBytes;
-}
-
-cudaError_t launch_unpack_tma(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
-                              int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op, int ctas,
-                              int32_t *status, unsigned long long timeout_ns, cudaStream_t s) {
-  const int n_rows = n_tiles * kTile;
-  if (n_chan <= 0) return cudaSuccess;
-  if (ctas < 1 || !unpack_tma_supported(sample_bits, n_inputs)) return cudaErrorInvalidValue;
-  const int smem = 2 * kTmaBufBytes;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(unpack_tma_kernel<8>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(unpack_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  if (sample_bits == 8)
-    unpack_tma_kernel<8><<<ctas, kTmaThreads, smem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
-                                                         chan0, n_chan, status, timeout_ns);
-  else
-    unpack_tma_kernel<4><<<ctas, kTmaThreads, smem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
-                                                         chan0, n_chan, status, timeout_ns);
   return cudaGetLastError();
 }
 

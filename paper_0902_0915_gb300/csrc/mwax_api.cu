@@ -207,14 +207,14 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
 }
 
 // Unpack variant: MWAX_UNPACK overrides (1 shared-memory transpose, 2
-// full-line, 3 TMA-staged input, 4 TMA both ways); automatic = TMA both ways
-// for 8-bit shapes that allow it, else the per-width default.
+// full-line, 4 TMA both ways); automatic = TMA both ways for 8-bit shapes that
+// allow it, else the full-line kernel (4-bit) or the shared-memory transpose.
 int unpack_choice(const JobState &s) {
   static const int env = [] {
     const char *e = getenv("MWAX_UNPACK");
     return e ? atoi(e) : 0;
   }();
-  if (env >= 1 && env <= 4) return env;
+  if (env == 1 || env == 2 || env == 4) return env;
   if (unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs)) return 4;
   return 0;
 }
@@ -225,11 +225,8 @@ mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt,
   cudaError_t e;
   const int v = unpack_choice(s);
   if (v == 4 && unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs))
-    e = launch_unpack_tma2(volt, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, c0, nc, op,
-                           ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
-  else if (v == 3 && unpack_tma_supported(s.job.sample_bits, s.job.n_inputs))
-    e = launch_unpack_tma(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, c0,
-                          nc, op, ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
+    e = launch_unpack_tma2(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb,
+                           c0, nc, op, ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
   else if (ctas > 0)
     e = launch_unpack_persistent(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
                                  s.kb, c0, nc, op, ctas, st);
@@ -584,9 +581,14 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
       if (part == 0) {
         for (int k = 0; k < nj && e == cudaSuccess; ++k) {
           const JobState &s = plan->jobs[k];
-          e = launch_unpack(reinterpret_cast<const uint8_t *>(voltages[k]), s.job.sample_bits,
-                            s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, 0, s.job.n_chan, s.op, 0,
-                            cs);
+          const uint8_t *v = reinterpret_cast<const uint8_t *>(voltages[k]);
+          if (unpack_choice(s) == 4)
+            e = launch_unpack_tma2(v, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
+                                   s.kb, 0, s.job.n_chan, s.op, plan->sm_count, plan->status,
+                                   plan->timeout_ns, cs);
+          else
+            e = launch_unpack(v, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, 0,
+                              s.job.n_chan, s.op, 0, cs);
         }
       } else if (e == cudaSuccess) {
         e = launch_correlate_tc(tj.data(), nj, launch_cfg(plan), cs);

@@ -38,21 +38,13 @@ cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n
                                      int n_time, int n_tiles, int kb, int64_t chan0, int n_chan,
                                      uint8_t *op, int ctas, cudaStream_t s);
 
-// TMA-staged persistent unpack (one bulk copy per channel time block into a
-// double-buffered 64 KB shared-memory ring).  Needs N % 16 == 0 and a raw
-// time block of at most 64 KB (N <= 1024).  A bounded wait that runs out
-// writes MWAX_ERR_TIMEOUT to *status.
-bool unpack_tma_supported(int sample_bits, int n_inputs);
-cudaError_t launch_unpack_tma(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
-                              int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op, int ctas,
-                              int32_t *status, unsigned long long timeout_ns, cudaStream_t s);
-
 // 8-bit samples with TMA both ways (bulk copy in, swizzled staging tile, TMA
-// tensor stores out).  Needs N % 8 == 0 and N <= 1024.
+// tensor stores out).  Needs N % 8 == 0 and N <= 1024.  (For 4-bit samples
+// the nibble conversion is heavier and the full-line kernel is faster.)
 bool unpack_tma2_supported(int sample_bits, int n_inputs);
-cudaError_t launch_unpack_tma2(const uint8_t *volt, int n_inputs, int n_time, int n_tiles, int kb,
-                               int64_t chan0, int n_chan, uint8_t *op, int ctas, int32_t *status,
-                               unsigned long long timeout_ns, cudaStream_t s);
+cudaError_t launch_unpack_tma2(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
+                               int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op, int ctas,
+                               int32_t *status, unsigned long long timeout_ns, cudaStream_t s);
 
 // ---- tensor-core correlator -------------------------------------------------
 #define MWAX_MAX_JOBS 8
