@@ -23,9 +23,11 @@
 // it to int32 register totals.  The plan bounds T so the totals fit int32.
 //
 // Roles (one persistent CTA per SM, 10 warps):
-//   warp 0      TMA producer: tiles A_I and A_J of the current block into a
-//               ring of shared-memory stages (A_J skipped on diagonal tiles)
-//   warp 1      tensor-memory allocator and single-thread MMA issuer
+//   warp 0      single-thread TMA producer: tiles A_I and A_J of the next
+//               K blocks into a ring of shared-memory stages (two blocks per
+//               stage for the narrow shape; A_J skipped on diagonal tiles)
+//   warp 1      tensor-memory allocator and single-thread MMA issuer (one
+//               full-barrier wait and one commit per stage)
 //   warps 2..9  epilogue: tcgen05.ld of the FP32 accumulator, int32 flush,
 //               packed lower-triangle store (the integration dump)
 // Two 256-column accumulators (re 128 | im 128) are double-buffered in the
@@ -51,13 +53,19 @@ constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
 // separately, negate-B bit for the minus sign).  Wide: four M=128 N=256 MMAs
 // per block against B = [A_J ; B'_J], B'_J = [-im_j | re_j] built in shared
 // memory by two extra warps.
+// A shared-memory stage holds `kps` consecutive K blocks behind one pair of
+// full/empty barriers.  An mbarrier wait costs the single issuing thread
+// about as much as two MMA issues, so the narrow shape takes two blocks
+// (16 MMAs) per wait and per commit.
 template <bool WIDE>
 struct Shape {
   static constexpr int warps = WIDE ? 12 : 10;
   static constexpr int conv_warps = WIDE ? 2 : 0;   // warps 2 .. 2+conv_warps-1
   static constexpr int epi0 = 2 + conv_warps;       // 8 epilogue warps from here
-  static constexpr int stage_bytes = (WIDE ? 3 : 2) * kTileBytes;
-  static constexpr int max_stages = WIDE ? 4 : 6;
+  static constexpr int kps = WIDE ? 1 : 2;          // K blocks per stage
+  static constexpr int block_bytes = (WIDE ? 3 : 2) * kTileBytes;  // [A | B (| B')] of one block
+  static constexpr int stage_bytes = kps * block_bytes;
+  static constexpr int max_stages = WIDE ? 4 : 3;
 };
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;  // re 128 | im 128
@@ -239,6 +247,11 @@ __device__ __forceinline__ Item decode_item(const KParams &p, int64_t item) {
   return it;
 }
 
+// Named barrier `id` over `threads` threads (whole warps); waiting warps sleep.
+__device__ __forceinline__ void named_bar_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
 __device__ __forceinline__ void raise_timeout(volatile int *abort_flag, int32_t *status) {
   *abort_flag = 1;
   atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
@@ -265,6 +278,7 @@ __global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
   // full[0..S) empty[S..2S) bfull[2S..3S) tfull[3S..3S+2) tempty[3S+2..3S+4) drain[3S+4]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * S + 5);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  volatile int *epi_flag = abort_flag + 1;  // [2]: result of the epilogue's accumulator wait
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + S + s); };
   auto bfull = [&](int s) { return smem_u32(bars + 2 * S + s); };
@@ -303,61 +317,61 @@ __global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
-    if (lane == 0)
+    // ---------------- TMA producer (one thread) ----------------
+    if (lane == 0) {
       for (int j = 0; j < p.n_jobs; ++j)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[j]))
                      : "memory");
-    // stage / phase advance incrementally: no division in the per-block path
-    int stage = 0;
-    uint32_t phase = 0;
-    int64_t issued = 0;
-    bool ok = true;
-    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
-      const Item it = decode_item(p, item);
-      const KJob &jb = p.job[it.job];
-      const CUtensorMap *map = &maps.m[it.job];
-      // operand rows: [chan][kb][row][128 B]; block kb of tile I starts at row
-      // (c * KB + kb) * n_rows + I * 128
-      const int n_rows = jb.n_tiles * kTile;
-      const int y0 = it.c * jb.kb * n_rows;
-      const int yA = y0 + it.I * kTile, yB = y0 + it.J * kTile;
-      const bool diag = it.I == it.J;
-      const uint32_t bytes = diag ? kTileBytes : 2 * kTileBytes;  // TMA bytes of this stage
-      // warm L2 for the first blocks of the item; later blocks are prefetched
-      // `prefetch` blocks ahead of their TMA load (first-touch misses go to DRAM)
-      const int pf = p.prefetch;
-      if (lane == 0)
+      // stage / phase advance incrementally: no division in the per-stage path
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t issued = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        const Item it = decode_item(p, item);
+        const KJob &jb = p.job[it.job];
+        const CUtensorMap *map = &maps.m[it.job];
+        // operand rows: [chan][kb][row][128 B]; block kb of tile I starts at row
+        // (c * KB + kb) * n_rows + I * 128
+        const int n_rows = jb.n_tiles * kTile;
+        const int y0 = it.c * jb.kb * n_rows;
+        const int yA = y0 + it.I * kTile, yB = y0 + it.J * kTile;
+        const bool diag = it.I == it.J;
+        const uint32_t blk_bytes = diag ? kTileBytes : 2 * kTileBytes;  // TMA bytes per block
+        // warm L2 for the first blocks of the item; later blocks are prefetched
+        // `prefetch` blocks ahead of their TMA load (first-touch misses go to DRAM)
+        const int pf = p.prefetch;
         for (int kb = 0; kb < pf && kb < jb.kb; ++kb) {
           tma_prefetch_2d(map, 0, yA + kb * n_rows);
           if (!diag) tma_prefetch_2d(map, 0, yB + kb * n_rows);
         }
-      for (int kb = 0; kb < jb.kb; ++kb) {
-        if (lane == 0 && pf > 0 && kb + pf < jb.kb) {
-          tma_prefetch_2d(map, 0, yA + (kb + pf) * n_rows);
-          if (!diag) tma_prefetch_2d(map, 0, yB + (kb + pf) * n_rows);
-        }
-        if (!warp_wait(empty(stage), phase ^ 1u, abort_flag, tmo, lane)) {
-          if (lane == 0) raise_timeout(abort_flag, p.status);
-          ok = false;
-          break;
-        }
-        if (lane == 0) {
+        for (int kb = 0; kb < jb.kb; kb += Sh::kps) {
+          const int nb = min(Sh::kps, jb.kb - kb);
+          if (pf > 0)
+            for (int j = 0; j < nb && kb + j + pf < jb.kb; ++j) {
+              tma_prefetch_2d(map, 0, yA + (kb + j + pf) * n_rows);
+              if (!diag) tma_prefetch_2d(map, 0, yB + (kb + j + pf) * n_rows);
+            }
+          if (!mbar_wait(empty(stage), phase ^ 1u, abort_flag, tmo)) {
+            raise_timeout(abort_flag, p.status);
+            ok = false;
+            break;
+          }
           const uint32_t a = smem_base + (uint32_t)stage * kStageBytes;
-          mbar_arrive_expect_tx(full(stage), bytes);
-          tma_load_2d(a, map, 0, yA + kb * n_rows, full(stage));
-          if (!diag) tma_load_2d(a + kTileBytes, map, 0, yB + kb * n_rows, full(stage));
-        }
-        __syncwarp();
-        ++issued;
-        if (++stage == S) {
-          stage = 0;
-          phase ^= 1u;
+          mbar_arrive_expect_tx(full(stage), (uint32_t)nb * blk_bytes);
+          for (int j = 0; j < nb; ++j) {
+            const uint32_t aj = a + (uint32_t)(j * Sh::block_bytes);
+            tma_load_2d(aj, map, 0, yA + (kb + j) * n_rows, full(stage));
+            if (!diag) tma_load_2d(aj + kTileBytes, map, 0, yB + (kb + j) * n_rows, full(stage));
+          }
+          ++issued;
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
       }
-    }
-    // wait (bounded) until every copy this warp issued has landed
-    if (lane == 0) {
+      // wait (bounded) until every copy this thread issued has landed
       int st = stage;
       uint32_t ph = phase;
       for (int64_t k = 0; k < issued && k < S; ++k) {
@@ -370,78 +384,78 @@ __global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = make_idesc(false, WIDE ? 2 * kTile : kTile);
-    constexpr uint32_t idesc_neg = make_idesc(true, kTile);
-    int stage = 0;
-    uint32_t phase = 0;
-    uint32_t seg = 0;
-    bool ok = true;
-    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
-      const Item it = decode_item(p, item);
-      const KJob &jb = p.job[it.job];
-      const int F = jb.flush_blocks, KB = jb.kb;
-      const bool diag = it.I == it.J;
-      int in_seg = 0;  // blocks already accumulated in the current segment
-      for (int kb = 0; kb < KB; ++kb) {
-        const bool seg_start = in_seg == 0;
-        const uint32_t buf = seg & 1u;
-        if (seg_start) {
-          if (!warp_wait(tempty(buf), ((seg >> 1) & 1u) ^ 1u, abort_flag, tmo, lane)) {
-            if (lane == 0) raise_timeout(abort_flag, p.status);
+    // ---------------- MMA issuer (one thread) ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(false, WIDE ? 2 * kTile : kTile);
+      constexpr uint32_t idesc_neg = make_idesc(true, kTile);
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t seg = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        const Item it = decode_item(p, item);
+        const KJob &jb = p.job[it.job];
+        const int F = jb.flush_blocks, KB = jb.kb;
+        const bool diag = it.I == it.J;
+        int in_seg = 0;  // blocks already accumulated in the current segment
+        for (int kb = 0; kb < KB; kb += Sh::kps) {
+          const int nb = min(Sh::kps, KB - kb);
+          if (!mbar_wait(full(stage), phase, abort_flag, tmo) ||
+              (WIDE && !mbar_wait(bfull(stage), phase, abort_flag, tmo))) {
+            raise_timeout(abort_flag, p.status);
             ok = false;
             break;
           }
           tc_fence_after();
-        }
-        if (!warp_wait(full(stage), phase, abort_flag, tmo, lane) ||
-            (WIDE && !warp_wait(bfull(stage), phase, abort_flag, tmo, lane))) {
-          if (lane == 0) raise_timeout(abort_flag, p.status);
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        if (lane == 0) {
-          const uint32_t a = smem_base + (uint32_t)stage * kStageBytes;
-          // descriptors of the 32-byte K slices: start address advances by 2 units of 16 B
-          const uint64_t da = sw128_desc(a);
-          const uint64_t db = diag ? da : sw128_desc(a + kTileBytes);
-          const uint32_t d_re = tmem_base + buf * kAccCols;
-          const uint32_t acc0 = seg_start ? 0u : 1u;
-          if constexpr (WIDE) {
-            // B = [A_J ; B'_J]: columns 0..127 give Re, 128..255 give Im
-            tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
-            tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
-            tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
-            tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
-          } else {
-            const uint32_t d_im = d_re + kTile;
-            tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
-            tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
-            tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
-            tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
-            tc_mma<BITS>(d_im, da + 4, db + 0, idesc, acc0);
-            tc_mma<BITS>(d_im, da + 6, db + 2, idesc, 1u);
-            tc_mma<BITS>(d_im, da + 0, db + 4, idesc_neg, 1u);
-            tc_mma<BITS>(d_im, da + 2, db + 6, idesc_neg, 1u);
+          for (int j = 0; j < nb; ++j) {
+            const bool seg_start = in_seg == 0;
+            const uint32_t buf = seg & 1u;
+            if (seg_start) {
+              if (!mbar_wait(tempty(buf), ((seg >> 1) & 1u) ^ 1u, abort_flag, tmo)) {
+                raise_timeout(abort_flag, p.status);
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            const uint32_t a = smem_base + (uint32_t)stage * kStageBytes + (uint32_t)(j * Sh::block_bytes);
+            // descriptors of the 32-byte K slices: start address advances by 2 units of 16 B
+            const uint64_t da = sw128_desc(a);
+            const uint64_t db = diag ? da : sw128_desc(a + kTileBytes);
+            const uint32_t d_re = tmem_base + buf * kAccCols;
+            const uint32_t acc0 = seg_start ? 0u : 1u;
+            if constexpr (WIDE) {
+              // B = [A_J ; B'_J]: columns 0..127 give Re, 128..255 give Im
+              tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
+              tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
+              tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
+              tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
+            } else {
+              const uint32_t d_im = d_re + kTile;
+              tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
+              tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
+              tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
+              tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
+              tc_mma<BITS>(d_im, da + 4, db + 0, idesc, acc0);
+              tc_mma<BITS>(d_im, da + 6, db + 2, idesc, 1u);
+              tc_mma<BITS>(d_im, da + 0, db + 4, idesc_neg, 1u);
+              tc_mma<BITS>(d_im, da + 2, db + 6, idesc_neg, 1u);
+            }
+            if (++in_seg == F || kb + j == KB - 1) {
+              tc_commit(tfull(buf));
+              ++seg;
+              in_seg = 0;
+            }
           }
+          if (!ok) break;
           tc_commit(empty(stage));
-        }
-        __syncwarp();
-        if (++stage == S) {
-          stage = 0;
-          phase ^= 1u;
-        }
-        if (++in_seg == F || kb == KB - 1) {
-          if (lane == 0) tc_commit(tfull(buf));
-          __syncwarp();
-          ++seg;
-          in_seg = 0;
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
       }
-    }
-    // no MMA may be in flight when tensor memory is freed
-    if (lane == 0) {
+      // no MMA may be in flight when tensor memory is freed
       tc_commit(drain);
       mbar_wait(drain, 0, nullptr, tmo);
     }
@@ -513,8 +527,17 @@ __global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
       for (int k = 0; k < 128; ++k) tot[k] = 0u;
       for (int sidx = 0; sidx < n_seg; ++sidx) {
         const uint32_t buf = seg & 1u;
-        if (!warp_wait(tfull(buf), (seg >> 1) & 1u, abort_flag, tmo, lane)) {
-          if (lane == 0) raise_timeout(abort_flag, p.status);
+        // one thread polls the accumulator barrier; the other epilogue warps
+        // sleep on a named barrier instead of spinning (their issue slots are
+        // shared with the MMA and producer warps).  The result goes through a
+        // two-entry flag so every epilogue warp takes the same branch.
+        if (warp == Sh::epi0 && lane == 0) {
+          const bool got = mbar_wait(tfull(buf), (seg >> 1) & 1u, abort_flag, tmo);
+          if (!got) raise_timeout(abort_flag, p.status);
+          epi_flag[seg & 1u] = got ? 1 : 0;
+        }
+        named_bar_sync(1, 8 * 32);
+        if (!epi_flag[seg & 1u]) {
           ok = false;
           break;
         }
@@ -620,7 +643,7 @@ int correlate_tc_max_stages(int wide) {
 
 int correlate_tc_smem_bytes(int stages, int wide) {
   const int stage_bytes = wide ? Shape<true>::stage_bytes : Shape<false>::stage_bytes;
-  return 1024 + stages * stage_bytes + (3 * stages + 5) * 8 + 16;
+  return 1024 + stages * stage_bytes + (3 * stages + 5) * 8 + 32;
 }
 
 cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int wide) {

@@ -127,6 +127,12 @@ double time_batch(const std::vector<mwax_job> &jobs, const void *const *volt, vo
   return ms;
 }
 
+bool valid(const Cand &c) {
+  const bool shape_ok = c.mma_shape == 0 || c.mma_shape == 1 || c.mma_shape == 2;
+  const int max_st = correlate_tc_max_stages(c.mma_shape == 2);
+  return shape_ok && (c.stages == 0 || (c.stages >= 2 && c.stages <= max_st));
+}
+
 bool all_auto(const mwax_job &j) {
   return j.mma_shape == 0 && j.stages == 0 && j.prefetch == 0 && j.pipeline == 0 &&
          j.chan_group == 0;
@@ -139,7 +145,9 @@ void apply_tune_cache(mwax_job *j) {
   if (!all_auto(*j) || j->engine != MWAX_ENGINE_TENSOR) return;
   Cand c;
   double ms;
-  if (cache_lookup(tune_key(*j), &c, &ms)) apply(j, c);
+  // a cached choice that this build cannot run (e.g. more stages than the
+  // shape allows) is ignored
+  if (cache_lookup(tune_key(*j), &c, &ms) && valid(c)) apply(j, c);
 }
 
 }  // namespace mwax
@@ -160,7 +168,7 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
   const std::string key = tune_key(*job);
   Cand best;
   double best_ms = 0;
-  if (cache_lookup(key, &best, &best_ms)) {
+  if (cache_lookup(key, &best, &best_ms) && valid(best)) {
     apply(job, best);
     rep.from_cache = 1;
     rep.best_ms = best_ms;
@@ -171,7 +179,7 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
   apply(&base, Cand{0, 0, 0, 0, 0});
   const int reps = 2;
   const std::vector<Cand> cands = {
-      {1, 6, -1, 1, 0}, {1, 4, -1, 1, 0}, {1, 6, 8, 1, 0}, {1, 6, -1, 2, 0},
+      {1, 3, -1, 1, 0}, {1, 2, -1, 1, 0}, {1, 3, 8, 1, 0}, {1, 3, -1, 2, 0},
       {2, 4, -1, 1, 0}, {2, 3, -1, 1, 0}, {2, 4, 8, 1, 0}, {2, 4, -1, 2, 0},
   };
   best_ms = -1.0;
@@ -201,7 +209,7 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
   mwax_tune_report rep;
   memset(&rep, 0, sizeof(rep));
   std::vector<mwax_job> base(jobs, jobs + n_jobs);
-  const std::vector<Cand> cands = {{1, 6, -1, 0, 0}, {1, 4, -1, 0, 0}, {1, 6, 8, 0, 0},
+  const std::vector<Cand> cands = {{1, 3, -1, 0, 0}, {1, 2, -1, 0, 0}, {1, 3, 8, 0, 0},
                                    {2, 4, -1, 0, 0}, {2, 3, -1, 0, 0}, {2, 4, 8, 0, 0}};
   Cand best{0, 0, 0, 0, 0};
   double best_ms = -1.0;
