@@ -57,6 +57,9 @@ def _load():
         lib.oracle_calib_grad.restype = ctypes.c_int
         lib.oracle_calib_grad.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int,
                                                                   ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_calib_als_target.restype = ctypes.c_int
+        lib.oracle_calib_als_target.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int,
+                                                                        ctypes.c_void_p, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -139,3 +142,39 @@ def calib_grad(V, M, g, n_threads: int | None = None) -> np.ndarray:
     if rc:
         raise RuntimeError("oracle_calib_grad failed")
     return out
+
+
+def calib_als_target(V, M, g, n_threads: int | None = None) -> np.ndarray:
+    """FP64 alternating least-squares target h, complex [N]: h_k minimises the
+    loss over g_k with every other gain fixed at g (h_k = g_k where the
+    normal equation is empty)."""
+    V = np.ascontiguousarray(V, np.complex128)
+    M = np.ascontiguousarray(M, np.complex128)
+    g = np.ascontiguousarray(g, np.complex128)
+    C, B = V.shape
+    N = g.shape[0]
+    assert B == N * (N + 1) // 2 and M.shape == V.shape
+    out = np.zeros(N, np.complex128)
+    rc = _load().oracle_calib_als_target(V.ctypes.data, M.ctypes.data, g.ctypes.data, N, C,
+                                         out.ctypes.data, n_threads or threads())
+    if rc:
+        raise RuntimeError("oracle_calib_als_target failed")
+    return out
+
+
+def calib_solve(V, M, g0, n_iter: int, n_threads: int | None = None):
+    """FP64 gain solve: ``n_iter`` alternating least-squares sweeps from g0.
+
+    Sweep t (t = 1, 2, ...) computes the target h from the current gains for
+    every input at once and then sets g = h when t is odd and g = (g + h) / 2
+    when t is even; the averaging on every second sweep is the damping of
+    Salvini & Wijnholds (2014), which stops the simultaneous update from
+    oscillating between two points.  Returns (g, losses) with losses[t] the
+    loss of the gains entering sweep t + 1."""
+    g = np.array(g0, np.complex128)
+    losses = []
+    for t in range(1, n_iter + 1):
+        losses.append(calib_loss(V, M, g))
+        h = calib_als_target(V, M, g, n_threads)
+        g = h if t % 2 == 1 else 0.5 * (g + h)
+    return g, np.array(losses)

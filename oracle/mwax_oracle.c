@@ -30,6 +30,16 @@
  *   (R_kj = conj(R_jk), M_kj = conj(M_jk)).  grad is the PyTorch convention
  *   for a real loss of a complex parameter: dL/dRe g + i dL/dIm g.
  *
+ *   gain solve (Sec. 2: the gains come from an iterative least-squares fit
+ *   in which every measurement constrains the gains): with every gain but
+ *   g_k held fixed, L is a linear least-squares problem in g_k, minimised by
+ *       h_k = num_k / den_k
+ *       num_k = sum_nu sum_{j != k} V_kj g_j conj(M_kj)
+ *       den_k = sum_nu sum_{j != k} |g_j|^2 |M_kj|^2
+ *   (V_kj, M_kj extended by Hermitian symmetry; h_k = g_k when den_k = 0).
+ *   oracle_calib_als_target computes h for all k from one g; the iteration
+ *   that uses it lives in the Python wrapper.
+ *
  * Sample format (the correlator input): voltages[chan][time][input];
  *   4+4-bit: one byte, low nibble = re, high nibble = im, two's complement;
  *   8+8-bit: two bytes, re then im, int8.
@@ -244,6 +254,75 @@ int oracle_calib_grad(const double *V, const double *M, const double *g, int n_i
   for (int k = 0; k < n_threads; ++k) {
     jobs[k] = (grad_job){V, M, g, n_inputs, n_chan, grad, k, n_threads};
     if (pthread_create(&th[k], NULL, grad_worker, &jobs[k]) != 0) { rc = 2; break; }
+    ++started;
+  }
+  for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+  return rc;
+}
+
+/* ---- alternating least-squares gain target (FP64) ----------------------- */
+
+typedef struct {
+  const double *V, *M, *g;
+  int n_inputs, n_chan;
+  double *h;
+  int tid, n_threads;
+} als_job;
+
+/* V_kj and M_kj for any k != j, from the stored lower triangle. */
+static void pair_vm(const double *V, const double *M, int64_t B, int64_t nu, int64_t k, int64_t j,
+                    cplx *v, cplx *m) {
+  if (k > j) {
+    const int64_t b = k * (k + 1) / 2 + j;
+    *v = cld(V + (nu * B + b) * 2);
+    *m = cld(M + (nu * B + b) * 2);
+  } else {
+    const int64_t b = j * (j + 1) / 2 + k;
+    *v = cconj(cld(V + (nu * B + b) * 2));
+    *m = cconj(cld(M + (nu * B + b) * 2));
+  }
+}
+
+static void *als_worker(void *arg) {
+  als_job *q = (als_job *)arg;
+  const int64_t N = q->n_inputs, B = N * (N + 1) / 2;
+  for (int64_t k = q->tid; k < N; k += q->n_threads) {
+    cplx num = {0.0, 0.0};
+    double den = 0.0;
+    for (int64_t nu = 0; nu < q->n_chan; ++nu)
+      for (int64_t j = 0; j < N; ++j) {
+        if (j == k) continue;
+        cplx v, m;
+        pair_vm(q->V, q->M, B, nu, k, j, &v, &m);
+        const cplx gj = cld(q->g + 2 * j);
+        const cplx t = cmul(cmul(v, gj), cconj(m));
+        num.re += t.re;
+        num.im += t.im;
+        den += (gj.re * gj.re + gj.im * gj.im) * (m.re * m.re + m.im * m.im);
+      }
+    if (den > 0.0) {
+      q->h[2 * k] = num.re / den;
+      q->h[2 * k + 1] = num.im / den;
+    } else {
+      q->h[2 * k] = q->g[2 * k];
+      q->h[2 * k + 1] = q->g[2 * k + 1];
+    }
+  }
+  return NULL;
+}
+
+/* h[k] = argmin over g_k of L with the other gains fixed at g, [n_inputs][2].
+ * Returns 0, or 2 on thread failure. */
+int oracle_calib_als_target(const double *V, const double *M, const double *g, int n_inputs,
+                            int n_chan, double *h, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  als_job jobs[256];
+  int started = 0, rc = 0;
+  for (int k = 0; k < n_threads; ++k) {
+    jobs[k] = (als_job){V, M, g, n_inputs, n_chan, h, k, n_threads};
+    if (pthread_create(&th[k], NULL, als_worker, &jobs[k]) != 0) { rc = 2; break; }
     ++started;
   }
   for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);

@@ -281,3 +281,86 @@ def test_calib_phase_and_radial_identities():
     assert s.real == pytest.approx(dL, rel=1e-8)
     ii, jj = np.tril_indices(N)
     assert Ls[0] == pytest.approx(float((np.abs(V[:, ii != jj]) ** 2).sum()), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# gain solve (alternating least squares)
+# ---------------------------------------------------------------------------
+def full_hermitian(X, N):
+    """[C, B] lower triangle -> [C, N, N] with X_ji = conj(X_ij)."""
+    C = X.shape[0]
+    F = np.zeros((C, N, N), complex)
+    ii, jj = np.tril_indices(N)
+    F[:, ii, jj] = X
+    F[:, jj, ii] = np.conj(X)
+    return F
+
+
+def test_als_target_is_per_input_least_squares():
+    """h_k equals numpy's least-squares solution of min_x sum |x conj(g_j) M_kj - V_kj|^2
+    over channels and j != k, built from the full Hermitian matrices."""
+    rng = np.random.default_rng(21)
+    N, C = 7, 3
+    V, M, g = rand_cal(rng, N, C)
+    h = oracle.calib_als_target(V, M, g)
+    Vf, Mf = full_hermitian(V, N), full_hermitian(M, N)
+    for k in range(N):
+        js = [j for j in range(N) if j != k]
+        a = (np.conj(g[js])[None, :] * Mf[:, k, js]).ravel()
+        b = Vf[:, k, js].ravel()
+        x = np.linalg.lstsq(a[:, None], b, rcond=None)[0][0]
+        assert h[k] == pytest.approx(x, rel=1e-12)
+
+
+def test_als_target_zeroes_its_gradient_component():
+    """Replacing g_k by h_k (others fixed) makes the k-th gradient component vanish."""
+    rng = np.random.default_rng(22)
+    N, C = 9, 4
+    V, M, g = rand_cal(rng, N, C)
+    h = oracle.calib_als_target(V, M, g)
+    scale = np.abs(oracle.calib_grad(V, M, g)).max()
+    for k in range(N):
+        gk = g.copy()
+        gk[k] = h[k]
+        assert abs(oracle.calib_grad(V, M, gk)[k]) <= 1e-11 * scale
+
+
+def test_als_fixed_point_at_truth():
+    rng = np.random.default_rng(23)
+    N, C = 11, 3
+    _, M, g = rand_cal(rng, N, C)
+    ii, jj = np.tril_indices(N)
+    V = g[ii] * np.conj(g[jj]) * M
+    V[:, ii == jj] = -5.0  # autos carry weight 0
+    np.testing.assert_allclose(oracle.calib_als_target(V, M, g), g, rtol=1e-13)
+
+
+def test_solve_golden_two_inputs():
+    """N = 2, V_10 = 2i, M_10 = 1, g0 = (1, 1), by hand: sweep 1 (plain) gives
+    h = (conj(V_10) g_1 / |g_1|^2, V_10 g_0 / |g_0|^2) = (-2i, 2i); sweep 2 gives
+    h = (1, 1) from (-2i, 2i) and averages to (0.5 - i, 0.5 + i)."""
+    V = np.zeros((1, 3), complex)
+    M = np.zeros((1, 3), complex)
+    V[0, 1], M[0, 1] = 2j, 1.0
+    g1, l1 = oracle.calib_solve(V, M, np.array([1.0, 1.0]), 1)
+    np.testing.assert_allclose(g1, [-2j, 2j], atol=1e-15)
+    assert l1[0] == pytest.approx(abs(1 - 2j) ** 2)
+    g2, _ = oracle.calib_solve(V, M, np.array([1.0, 1.0]), 2)
+    np.testing.assert_allclose(g2, [0.5 - 1j, 0.5 + 1j], atol=1e-15)
+
+
+def test_solve_recovers_true_gains():
+    """Noise-free data: the solve converges to the true gains up to one global
+    phase (the loss cannot see it), and the loss falls to rounding level."""
+    rng = np.random.default_rng(24)
+    N, C = 16, 5
+    _, M, g_true = rand_cal(rng, N, C)
+    ii, jj = np.tril_indices(N)
+    V = g_true[ii] * np.conj(g_true[jj]) * M
+    g0 = g_true * (1 + 0.2 * (rng.standard_normal(N) + 1j * rng.standard_normal(N)))
+    g, losses = oracle.calib_solve(V, M, g0, 60)
+    ph = np.vdot(g, g_true)
+    g_al = g * ph / abs(ph)
+    assert np.abs(g_al - g_true).max() <= 1e-9 * np.abs(g_true).max()
+    assert losses[-1] <= 1e-16 * losses[0]
+    assert oracle.calib_loss(V, M, g) <= 1e-20 * losses[0]
