@@ -502,6 +502,28 @@ def run_calib(args):
                          "kernel": "calib_tile_kernel + calib_gather_kernel (one step)",
                          "peak_source": src},
             "loss": float(loss), "gpu_launches": 2 * args.steps, "clocks": clk}
+    # gain solve: alternating least-squares sweeps from the same starting gains
+    n_sweeps = 10
+    ws_solve = torch.empty(int(mw.lib().mwax_calib_solve_workspace_bytes(N, C)), dtype=torch.uint8,
+                           device=dev)
+    mw.calib_solve(V, M, g, 1, ws_solve)  # warm-up
+    torch.cuda.synchronize()
+    a.record(stream)
+    g_sol, hist = mw.calib_solve(V, M, g, n_sweeps, ws_solve)
+    b.record(stream)
+    b.synchronize()
+    ms_sweep = a.elapsed_time(b) / n_sweeps
+    loss_final, _ = mw.calib_loss_grad(V, M, g_sol, ws, want_grad=False)
+    achieved_s = bytes_step / (ms_sweep / 1e3) / 1e9
+    line["solve"] = {"sweeps": n_sweeps, "ms_per_sweep": ms_sweep,
+                     "value": terms / (ms_sweep / 1e3) / 1e9, "unit": "Gterms/s per sweep",
+                     "loss_start": float(hist[0]), "loss_after": float(loss_final),
+                     "roofline": {"bound": "hbm", "achieved": achieved_s, "peak": float(peaks["hbm_gbs"]),
+                                  "unit": "GB/s", "frac": achieved_s / float(peaks["hbm_gbs"]),
+                                  "traffic": None,
+                                  "kernel": "calib_tile_kernel<den> + calib_gather_kernel<solve> (one sweep)",
+                                  "peak_source": src},
+                     "gpu_launches": 2 * n_sweeps}
     if not args.no_cpu:
         sub = list(range(0, C, C // 8))[:8]
         V64 = V[sub].cpu().numpy().astype(np.complex128)
@@ -513,6 +535,12 @@ def run_calib(args):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": B * len(sub) / dt / 1e9, "unit": "Gterms/s", "cores": oracle.threads(),
                                 "kind": "oracle", "sample": f"{len(sub)} of {C} channels (FP64 loss + gradient)"}
+        t0 = time.perf_counter()
+        oracle.calib_solve(V64, M64, g64, 1)
+        dt = time.perf_counter() - t0
+        line["solve"]["cpu_baseline"] = {"value": B * len(sub) / dt / 1e9, "unit": "Gterms/s per sweep",
+                                         "cores": oracle.threads(), "kind": "oracle",
+                                         "sample": f"1 sweep on {len(sub)} of {C} channels (FP64)"}
     print(json.dumps(line), flush=True)
 
 

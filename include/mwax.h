@@ -243,6 +243,31 @@ mwax_status mwax_calib_loss_grad(const float *V, const float *M, const float *g,
                                  int n_chan, void *workspace, float *loss, float *grad,
                                  cudaStream_t stream);
 
+/* ---- gain solve (FP32) ---------------------------------------------------
+ * Paper Sec. 2: the complex gain of every element comes from an iterative
+ * least-squares fit of the data against a model of catalogue sources.  With
+ * every gain but g_k fixed, the loss above is a linear least-squares problem
+ * in g_k, minimised by
+ *     h_k = sum V_kj g_j conj(M_kj) / sum |g_j|^2 |M_kj|^2   (j != k, all nu;
+ *                                                             h_k = g_k if the
+ *                                                             denominator is 0)
+ * One sweep computes h for every input from the same g (one pass over V and
+ * M, the loss/adjoint pass plus one accumulator) and then sets g = h on odd
+ * sweeps and g = (g + h) / 2 on even sweeps (sweeps counted from 1; the
+ * damping of Salvini & Wijnholds 2014).  The loss does not see a global phase
+ * of g; the sweep keeps the phase of the starting point.
+ *   g:         device [n_inputs][2], starting gains in, gains after n_iter
+ *              sweeps out (updated in place).
+ *   workspace: device, >= mwax_calib_solve_workspace_bytes(n_inputs, n_chan).
+ *   loss_hist: device float[n_iter] or NULL; loss_hist[t] = L of the gains
+ *              entering sweep t + 1 (computed by that sweep's pass).
+ * V, M as in mwax_calib_loss.  Asynchronous on `stream`; deterministic (fixed
+ * reduction order).  n_iter = 0 launches nothing.  Returns INVALID_ARG for
+ * bad shapes, host or null pointers. */
+int64_t mwax_calib_solve_workspace_bytes(int n_inputs, int n_chan);
+mwax_status mwax_calib_solve(const float *V, const float *M, float *g, int n_inputs, int n_chan,
+                             int n_iter, void *workspace, float *loss_hist, cudaStream_t stream);
+
 /* ---- allocation-free calibration -------------------------------------------
  * No counterpart in the paper.  For callers that must not allocate device
  * memory when they evaluate the loss -- a real-time loop in which

@@ -92,6 +92,8 @@ SIGNATURES = {
     "mwax_calib_loss": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     "mwax_calib_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
     "mwax_calib_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "mwax_calib_solve_workspace_bytes": (_I64, [_I, _I]),
+    "mwax_calib_solve": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "mwax_calib_static_workspace_bytes": (_I64, []),
     "mwax_calib_loss_grad_static": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
 }
@@ -390,6 +392,32 @@ def calib_loss_grad(V, M, g, workspace=None, want_loss=True, want_grad=True):
                                       grad.data_ptr() if want_grad else None,
                                       _stream_handle()), "mwax_calib_loss_grad")
     return loss, (torch.view_as_complex(grad) if want_grad else None)
+
+
+def calib_solve(V, M, g0, n_iter: int, workspace=None, loss_history: bool = True):
+    """Gain solve: ``n_iter`` alternating least-squares sweeps from ``g0``
+    (complex64 [N], not modified).  Returns (g complex64 [N], losses float32
+    [n_iter] or None) with losses[t] the loss of the gains entering sweep t+1."""
+    torch = _torch()
+    Vr, Mr = _f32_pairs(V), _f32_pairs(M)
+    g = _f32_pairs(g0).clone()
+    n = g.shape[0]
+    c = Vr.shape[0]
+    if Vr.shape != (c, n * (n + 1) // 2, 2) or Mr.shape != Vr.shape:
+        raise ValueError("V, M must be [n_chan, N(N+1)/2] for N = len(g0)")
+    if n_iter < 0:
+        raise ValueError("n_iter must be >= 0")
+    if workspace is None:
+        nb = int(lib().mwax_calib_solve_workspace_bytes(n, c))
+        if nb < 0:
+            raise ValueError("invalid calibration shape")
+        workspace = torch.empty(nb, dtype=torch.uint8, device=V.device)
+    hist = (torch.empty(max(n_iter, 1), dtype=torch.float32, device=V.device)
+            if loss_history else None)
+    _check(lib().mwax_calib_solve(Vr.data_ptr(), Mr.data_ptr(), g.data_ptr(), n, c, n_iter,
+                                  workspace.data_ptr(), hist.data_ptr() if hist is not None else None,
+                                  _stream_handle()), "mwax_calib_solve")
+    return torch.view_as_complex(g), (hist[:n_iter] if hist is not None else None)
 
 
 def _make_calib_function():

@@ -19,6 +19,18 @@
 // kernel gathers them per input in a fixed order.  No atomics, FP32 only
 // (Kahan-compensated accumulation inside a thread, fixed trees across
 // threads).  One pass reads V and M once.
+//
+// Gain solve (alternating least squares): with every gain but g_k fixed, L
+// is a linear least-squares problem in g_k whose minimiser is
+//     h_k = num_k / den_k,  num_k = sum V_kj g_j conj(M_kj),
+//                           den_k = sum |g_j|^2 |M_kj|^2   (j != k, all nu)
+// and since grad_k / 2 = g_k den_k - num_k,  h_k = g_k - (grad_k / 2) / den_k.
+// One sweep is therefore the loss/adjoint pass with one more accumulator
+// (den) per row and column, followed by a gather that applies the update in
+// place: g = h on odd sweeps, g = (g + h) / 2 on even sweeps (the damping of
+// Salvini & Wijnholds 2014, which keeps the simultaneous update from
+// oscillating).  Working from the residual keeps the FP32 update accurate
+// near convergence, where num and g den nearly cancel.
 #include <mutex>
 
 #include "mwax_internal.h"
@@ -51,13 +63,16 @@ __device__ __forceinline__ void tile_of(int p, int &I, int &J) {
 }
 
 // grid: (tiles, channel groups).  Thread (ty, tx): column j = J*32 + tx,
-// rows i = I*32 + ty + 8m, m = 0..3.
+// rows i = I*32 + ty + 8m, m = 0..3.  DEN: also the per-row and per-column
+// sums of |g_other|^2 |M|^2 (the gain solve's normal-equation weight).
+template <bool DEN>
 __global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
     const float2 *__restrict__ V, const float2 *__restrict__ M, const float2 *__restrict__ g,
     int N, int C, int n_cg, float *__restrict__ part_loss, float2 *__restrict__ part_row,
-    float2 *__restrict__ part_col) {
+    float2 *__restrict__ part_col, float *__restrict__ part_rden, float *__restrict__ part_cden) {
   __shared__ float2 sg_i[kCT], sg_j[kCT];
   __shared__ float2 scol[8][kCT];
+  __shared__ float scden[8][kCT];
   __shared__ float sloss[kCalThreads / 32];
   const int tile = blockIdx.x, cg = blockIdx.y;
   int I, J;
@@ -73,7 +88,8 @@ __global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
   const int j = J * kCT + tx;
   const float2 gj = sg_j[tx];
   // channels of this group: cg, cg + n_cg, ...
-  Kahan loss, rre[4], rim[4], cre, cim;
+  Kahan loss, rre[4], rim[4], cre, cim, rden[4], cden;
+  const float gj2 = gj.x * gj.x + gj.y * gj.y;
   for (int nu = cg; nu < C; nu += n_cg) {
     const float2 *Vn = V + (int64_t)nu * B;
     const float2 *Mn = M + (int64_t)nu * B;
@@ -99,6 +115,11 @@ __global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
       const float Qr = Rr * gi.x + Ri * gi.y, Qi = Rr * gi.y - Ri * gi.x;  // conj(R) g_i
       cre.add(Qr * mm.x - Qi * mm.y);
       cim.add(Qr * mm.y + Qi * mm.x);
+      if constexpr (DEN) {
+        const float m2 = mm.x * mm.x + mm.y * mm.y;
+        rden[m].add(gj2 * m2);                            // row i: |g_j|^2 |M_ij|^2
+        cden.add((gi.x * gi.x + gi.y * gi.y) * m2);       // column j: |g_i|^2 |M_ij|^2
+      }
     }
   }
   const int out_idx = tile * n_cg + cg;
@@ -112,9 +133,16 @@ __global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
       xi += __shfl_xor_sync(0xffffffffu, xi, o);
     }
     if (tx == 0) part_row[(int64_t)out_idx * kCT + ty + 8 * m] = make_float2(xr, xi);
+    if constexpr (DEN) {
+      float d = rden[m].s;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (tx == 0) part_rden[(int64_t)out_idx * kCT + ty + 8 * m] = d;
+    }
   }
   // columns: sum over the 8 warps in a fixed order
   scol[ty][tx] = make_float2(cre.s, cim.s);
+  if constexpr (DEN) scden[ty][tx] = cden.s;
   float l = loss.s;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
@@ -128,6 +156,12 @@ __global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
       acc.y += scol[w][tx].y;
     }
     part_col[(int64_t)out_idx * kCT + tx] = acc;
+    if constexpr (DEN) {
+      float d = scden[0][tx];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) d += scden[w][tx];
+      part_cden[(int64_t)out_idx * kCT + tx] = d;
+    }
   }
   if (threadIdx.x == 0) {
     float s = 0.f;
@@ -137,11 +171,15 @@ __global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
 }
 
 // grid: n_blocks + 1.  Block K < n_blocks gathers grad for inputs K*32..;
-// the last block sums the loss partials.
+// the last block sums the loss partials.  SOLVE: instead of grad, apply one
+// gain-solve sweep to g in place (each block reads and writes only its own
+// 32 gains): g = h (avg == 0) or g = (g + h) / 2 (avg == 1).
+template <bool SOLVE>
 __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
     int N, int n_blocks, int n_cg, const float *__restrict__ part_loss,
     const float2 *__restrict__ part_row, const float2 *__restrict__ part_col,
-    float *__restrict__ loss, float2 *__restrict__ grad) {
+    const float *__restrict__ part_rden, const float *__restrict__ part_cden,
+    float *__restrict__ loss, float2 *__restrict__ grad, float2 *__restrict__ g_io, int avg) {
   const int K = blockIdx.x;
   if (K == n_blocks) {
     if (!loss) return;
@@ -158,11 +196,12 @@ __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
     if (threadIdx.x == 0) *loss = sred[0];
     return;
   }
-  if (!grad) return;
+  if (!SOLVE && !grad) return;
   // 32 inputs x 8 partial lanes: thread (r, l) sums every 8th contribution
   __shared__ float2 sacc[8][kCT];
+  __shared__ float sden[8][kCT];
   const int r = threadIdx.x & 31, l = threadIdx.x >> 5;
-  Kahan ar, ai;
+  Kahan ar, ai, ad;
   // tiles (K, J), J <= K contribute row partials; tiles (I, K), I >= K column partials
   int n = 0;
   for (int Jt = 0; Jt <= K; ++Jt) {
@@ -172,6 +211,7 @@ __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
       const float2 v = part_row[((int64_t)tile * n_cg + cg) * kCT + r];
       ar.add(v.x);
       ai.add(v.y);
+      if constexpr (SOLVE) ad.add(part_rden[((int64_t)tile * n_cg + cg) * kCT + r]);
     }
   }
   for (int It = K; It < n_blocks; ++It) {
@@ -181,9 +221,11 @@ __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
       const float2 v = part_col[((int64_t)tile * n_cg + cg) * kCT + r];
       ar.add(v.x);
       ai.add(v.y);
+      if constexpr (SOLVE) ad.add(part_cden[((int64_t)tile * n_cg + cg) * kCT + r]);
     }
   }
   sacc[l][r] = make_float2(ar.s, ai.s);
+  if constexpr (SOLVE) sden[l][r] = ad.s;
   __syncthreads();
   if (l == 0) {
     float2 acc = sacc[0][r];
@@ -193,7 +235,21 @@ __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
       acc.y += sacc[w][r].y;
     }
     const int k = K * kCT + r;
-    if (k < N) grad[k] = make_float2(2.f * acc.x, 2.f * acc.y);
+    if constexpr (SOLVE) {
+      float den = sden[0][r];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) den += sden[w][r];
+      if (k < N && den > 0.f) {
+        // h = g - (grad / 2) / den; acc holds grad / 2
+        const float2 gk = g_io[k];
+        const float inv = 1.f / den;
+        float2 h = make_float2(gk.x - acc.x * inv, gk.y - acc.y * inv);
+        if (avg) h = make_float2(0.5f * (gk.x + h.x), 0.5f * (gk.y + h.y));
+        g_io[k] = h;
+      }
+    } else {
+      if (k < N) grad[k] = make_float2(2.f * acc.x, 2.f * acc.y);
+    }
   }
 }
 
@@ -210,9 +266,12 @@ bool dev_ptr(const void *p) {
 struct Ws {
   float *loss;
   float2 *row, *col;
+  float *rden, *cden;  // gain solve only
 };
 
-Ws carve(void *ws, int n_blocks, int n_cg) {
+// Layout: row and column partials, loss partials, then (gain solve) the row
+// and column den partials.
+Ws carve(void *ws, int n_blocks, int n_cg, bool solve) {
   const int64_t tiles = (int64_t)n_blocks * (n_blocks + 1) / 2;
   uint8_t *p = reinterpret_cast<uint8_t *>(ws);
   Ws w;
@@ -221,6 +280,10 @@ Ws carve(void *ws, int n_blocks, int n_cg) {
   w.col = reinterpret_cast<float2 *>(p);
   p += tiles * n_cg * kCT * sizeof(float2);
   w.loss = reinterpret_cast<float *>(p);
+  p += (tiles * n_cg * (int64_t)sizeof(float) + 255) / 256 * 256;
+  w.rden = solve ? reinterpret_cast<float *>(p) : nullptr;
+  p += tiles * n_cg * kCT * sizeof(float);
+  w.cden = solve ? reinterpret_cast<float *>(p) : nullptr;
   return w;
 }
 
@@ -249,15 +312,50 @@ mwax_status mwax_calib_loss_grad(const float *V, const float *M, const float *g,
   const int nb = (n_inputs + kCT - 1) / kCT;
   const int tiles = nb * (nb + 1) / 2;
   const int n_cg = chan_groups(n_chan);
-  Ws w = carve(workspace, nb, n_cg);
-  calib_tile_kernel<<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
+  Ws w = carve(workspace, nb, n_cg, false);
+  calib_tile_kernel<false><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
       reinterpret_cast<const float2 *>(V), reinterpret_cast<const float2 *>(M),
-      reinterpret_cast<const float2 *>(g), n_inputs, n_chan, n_cg, w.loss, w.row, w.col);
+      reinterpret_cast<const float2 *>(g), n_inputs, n_chan, n_cg, w.loss, w.row, w.col, nullptr,
+      nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return MWAX_ERR_CUDA;
-  calib_gather_kernel<<<nb + 1, kCalThreads, 0, stream>>>(n_inputs, nb, n_cg, w.loss, w.row, w.col,
-                                                          loss, reinterpret_cast<float2 *>(grad));
+  calib_gather_kernel<false><<<nb + 1, kCalThreads, 0, stream>>>(
+      n_inputs, nb, n_cg, w.loss, w.row, w.col, nullptr, nullptr, loss,
+      reinterpret_cast<float2 *>(grad), nullptr, 0);
   return cudaGetLastError() == cudaSuccess ? MWAX_OK : MWAX_ERR_CUDA;
+}
+
+int64_t mwax_calib_solve_workspace_bytes(int n_inputs, int n_chan) {
+  if (n_inputs < 2 || n_chan < 1) return -1;
+  const int64_t nb = (n_inputs + kCT - 1) / kCT;
+  const int64_t tiles = nb * (nb + 1) / 2;
+  const int64_t cg = chan_groups(n_chan);
+  return tiles * cg * kCT * (int64_t)sizeof(float2) * 2 +
+         (tiles * cg * (int64_t)sizeof(float) + 255) / 256 * 256 +
+         tiles * cg * kCT * (int64_t)sizeof(float) * 2 + 256;
+}
+
+mwax_status mwax_calib_solve(const float *V, const float *M, float *g, int n_inputs, int n_chan,
+                             int n_iter, void *workspace, float *loss_hist, cudaStream_t stream) {
+  if (n_inputs < 2 || n_chan < 1 || n_inputs > 65536 || n_iter < 0) return MWAX_ERR_INVALID_ARG;
+  if (!dev_ptr(V) || !dev_ptr(M) || !dev_ptr(g) || !dev_ptr(workspace)) return MWAX_ERR_INVALID_ARG;
+  if (loss_hist && !dev_ptr(loss_hist)) return MWAX_ERR_INVALID_ARG;
+  const int nb = (n_inputs + kCT - 1) / kCT;
+  const int tiles = nb * (nb + 1) / 2;
+  const int n_cg = chan_groups(n_chan);
+  Ws w = carve(workspace, nb, n_cg, true);
+  float2 *g2 = reinterpret_cast<float2 *>(g);
+  for (int t = 1; t <= n_iter; ++t) {
+    calib_tile_kernel<true><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
+        reinterpret_cast<const float2 *>(V), reinterpret_cast<const float2 *>(M), g2, n_inputs,
+        n_chan, n_cg, w.loss, w.row, w.col, w.rden, w.cden);
+    if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
+    calib_gather_kernel<true><<<nb + 1, kCalThreads, 0, stream>>>(
+        n_inputs, nb, n_cg, w.loss, w.row, w.col, w.rden, w.cden,
+        loss_hist ? loss_hist + (t - 1) : nullptr, nullptr, g2, (t % 2 == 0) ? 1 : 0);
+    if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
+  }
+  return MWAX_OK;
 }
 
 mwax_status mwax_calib_loss(const float *V, const float *M, const float *g, int n_inputs,

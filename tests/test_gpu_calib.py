@@ -140,3 +140,76 @@ def test_calib_full_size(mw):
     V, M, g = big_problem(1024, 768, seed=4)
     loss, grad = gpu_loss_grad(mw, V, M, g)
     check(V, M, g, loss, grad)
+
+
+# ---------------------------------------------------------------------------
+# gain solve (alternating least-squares sweeps)
+# ---------------------------------------------------------------------------
+def gpu_solve(mw, V, M, g0, n_iter):
+    import torch
+
+    g, hist = mw.calib_solve(torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda(),
+                             torch.from_numpy(g0).cuda(), n_iter)
+    torch.cuda.synchronize()
+    return g.cpu().numpy(), (hist.cpu().numpy() if hist is not None else None)
+
+
+def check_solve(V, M, g0, n_iter, g_gpu, hist, tol_g):
+    """Iterates within tol_g (max-norm, relative to max |g|) of the FP64
+    oracle's from the same start; the first loss within 1e-5 (the FP32 loss
+    tolerance), later ones within 1e-4 (they are losses of slightly different
+    iterates, and near a minimum the loss is flat in the gains)."""
+    V64, M64, g064 = V.astype(np.complex128), M.astype(np.complex128), g0.astype(np.complex128)
+    g64, l64 = oracle.calib_solve(V64, M64, g064, n_iter)
+    assert np.abs(g_gpu - g64).max() <= tol_g * np.abs(g64).max(), np.abs(g_gpu - g64).max()
+    assert hist.shape == (n_iter,)
+    assert abs(hist[0] - l64[0]) <= 1e-5 * l64[0]
+    np.testing.assert_allclose(hist, l64, rtol=1e-4)
+    return g64, l64
+
+
+@pytest.mark.parametrize("N,C,n_iter", [(2, 1, 1), (33, 3, 1), (33, 3, 2), (70, 5, 5), (130, 9, 4)])
+def test_solve_small(mw, N, C, n_iter):
+    V, M, g0 = problem(N, C, seed=100 + N + C)
+    g, hist = gpu_solve(mw, V, M, g0, n_iter)
+    check_solve(V, M, g0, n_iter, g, hist, tol_g=1e-4)
+
+
+def test_solve_zero_sweeps_leaves_gains(mw):
+    V, M, g0 = problem(40, 2, seed=9)
+    g, hist = gpu_solve(mw, V, M, g0, 0)
+    np.testing.assert_array_equal(g, g0)
+    assert hist.shape == (0,)
+
+
+def test_solve_deterministic(mw):
+    V, M, g0 = problem(100, 6, seed=10)
+    a = gpu_solve(mw, V, M, g0, 3)
+    b = gpu_solve(mw, V, M, g0, 3)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_solve_recovers_true_gains(mw):
+    """Noise-free data in float32: the gains come back to FP32 accuracy up to
+    one global phase, and the loss falls by many orders of magnitude."""
+    rng = np.random.default_rng(11)
+    N, C = 64, 8
+    B = N * (N + 1) // 2
+    ii, jj = np.tril_indices(N)
+    M = (rng.standard_normal((C, B)) + 1j * rng.standard_normal((C, B))).astype(np.complex64)
+    g_true = rng.uniform(0.8, 1.2, N) * np.exp(1j * rng.uniform(0, 2 * np.pi, N))
+    V = (g_true[ii] * np.conj(g_true[jj]) * M).astype(np.complex64)
+    g0 = (g_true * (1 + 0.2 * (rng.standard_normal(N) + 1j * rng.standard_normal(N)))).astype(np.complex64)
+    g, hist = gpu_solve(mw, V, M, g0, 40)
+    ph = np.vdot(g, g_true)
+    err = np.abs(g * ph / abs(ph) - g_true).max() / np.abs(g_true).max()
+    assert err <= 2e-5, err
+    assert hist[-1] <= 1e-8 * hist[0]
+
+
+def test_solve_full_size(mw):
+    """1024 inputs x 768 channels: two sweeps against the FP64 oracle."""
+    V, M, g0 = big_problem(1024, 768, seed=12)
+    g, hist = gpu_solve(mw, V, M, g0, 2)
+    check_solve(V, M, g0, 2, g, hist, tol_g=1e-4)
