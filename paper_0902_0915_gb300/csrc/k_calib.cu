@@ -66,7 +66,7 @@ __device__ __forceinline__ void tile_of(int p, int &I, int &J) {
 // rows i = I*32 + ty + 8m, m = 0..3.  DEN: also the per-row and per-column
 // sums of |g_other|^2 |M|^2 (the gain solve's normal-equation weight).
 template <bool DEN>
-__global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
+__global__ void __launch_bounds__(kCalThreads, 3) calib_tile_kernel(
     const float2 *__restrict__ V, const float2 *__restrict__ M, const float2 *__restrict__ g,
     int N, int C, int n_cg, float *__restrict__ part_loss, float2 *__restrict__ part_row,
     float2 *__restrict__ part_col, float *__restrict__ part_rden, float *__restrict__ part_cden) {
@@ -87,39 +87,62 @@ __global__ void __launch_bounds__(kCalThreads) calib_tile_kernel(
   const int64_t B = (int64_t)N * (N + 1) / 2;
   const int j = J * kCT + tx;
   const float2 gj = sg_j[tx];
-  // channels of this group: cg, cg + n_cg, ...
+  // rows of this thread that hold a stored off-diagonal pair (fixed over channels)
+  bool valid[4];
+  int64_t boff[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int i = I * kCT + ty + 8 * m;
+    valid[m] = i < N && j < N && j < i;
+    boff[m] = valid[m] ? (int64_t)i * (i + 1) / 2 + j : 0;
+  }
+  // channels of this group: cg, cg + n_cg, ...  The next channel's V and M
+  // are loaded while the current one is processed (two channels in flight).
   Kahan loss, rre[4], rim[4], cre, cim, rden[4], cden;
   const float gj2 = gj.x * gj.x + gj.y * gj.y;
-  for (int nu = cg; nu < C; nu += n_cg) {
+  float2 v[4], mm[4];
+  auto load = [&](int nu, float2 (&vv)[4], float2 (&mv)[4]) {
     const float2 *Vn = V + (int64_t)nu * B;
     const float2 *Mn = M + (int64_t)nu * B;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const int il = ty + 8 * m;
-      const int i = I * kCT + il;
-      if (i >= N || j >= N || j >= i) continue;
-      const int64_t b = (int64_t)i * (i + 1) / 2 + j;
-      const float2 v = Vn[b], mm = Mn[b], gi = sg_i[il];
+      vv[m] = valid[m] ? __ldcs(Vn + boff[m]) : make_float2(0.f, 0.f);
+      mv[m] = valid[m] ? __ldcs(Mn + boff[m]) : make_float2(0.f, 0.f);
+    }
+  };
+  if (cg < C) load(cg, v, mm);
+  for (int nu = cg; nu < C; nu += n_cg) {
+    float2 vn[4] = {}, mn[4] = {};
+    if (nu + n_cg < C) load(nu + n_cg, vn, mn);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (!valid[m]) continue;
+      const float2 gi = sg_i[ty + 8 * m];
       // G = g_i conj(g_j)
       const float Gr = gi.x * gj.x + gi.y * gj.y;
       const float Gi = gi.y * gj.x - gi.x * gj.y;
       // R = G M - V
-      const float Rr = Gr * mm.x - Gi * mm.y - v.x;
-      const float Ri = Gr * mm.y + Gi * mm.x - v.y;
+      const float Rr = Gr * mm[m].x - Gi * mm[m].y - v[m].x;
+      const float Ri = Gr * mm[m].y + Gi * mm[m].x - v[m].y;
       loss.add(Rr * Rr + Ri * Ri);
       // to row i: R g_j conj(M)
       const float Pr = Rr * gj.x - Ri * gj.y, Pi = Rr * gj.y + Ri * gj.x;  // R g_j
-      rre[m].add(Pr * mm.x + Pi * mm.y);
-      rim[m].add(Pi * mm.x - Pr * mm.y);
+      rre[m].add(Pr * mm[m].x + Pi * mm[m].y);
+      rim[m].add(Pi * mm[m].x - Pr * mm[m].y);
       // to column j: conj(R) g_i M
       const float Qr = Rr * gi.x + Ri * gi.y, Qi = Rr * gi.y - Ri * gi.x;  // conj(R) g_i
-      cre.add(Qr * mm.x - Qi * mm.y);
-      cim.add(Qr * mm.y + Qi * mm.x);
+      cre.add(Qr * mm[m].x - Qi * mm[m].y);
+      cim.add(Qr * mm[m].y + Qi * mm[m].x);
       if constexpr (DEN) {
-        const float m2 = mm.x * mm.x + mm.y * mm.y;
+        const float m2 = mm[m].x * mm[m].x + mm[m].y * mm[m].y;
         rden[m].add(gj2 * m2);                            // row i: |g_j|^2 |M_ij|^2
         cden.add((gi.x * gi.x + gi.y * gi.y) * m2);       // column j: |g_i|^2 |M_ij|^2
       }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      v[m] = vn[m];
+      mm[m] = mn[m];
     }
   }
   const int out_idx = tile * n_cg + cg;
