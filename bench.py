@@ -72,6 +72,18 @@ def unpack_bytes_per_channel(spec) -> float:
     return float(packed + n_rows * kb * 128)
 
 
+def unpack_kernel_name(spec) -> str:
+    """The unpack kernel the plan picks for this shape (TMA both ways where the
+    raw rows are whole 16-byte units and the tile fits, else the fallbacks)."""
+    n = spec.n_inputs
+    if os.environ.get("MWAX_UNPACK") is None and n <= 1024:
+        if spec.sample_bits == 8 and n % 8 == 0:
+            return "unpack8_tma2_kernel"
+        if spec.sample_bits == 4 and n % 16 == 0:
+            return "unpack4_tma2_kernel"
+    return "unpack_kernel<8>" if spec.sample_bits == 8 else "unpack4_line_kernel"
+
+
 def unpack_roofline(spec, info, tim, steps, peaks, peak_src):
     """HBM roofline of the unpack kernel (the second kernel of a step)."""
     per_ch = unpack_bytes_per_channel(spec)
@@ -84,7 +96,7 @@ def unpack_roofline(spec, info, tim, steps, peaks, peak_src):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": per_ch * info.chan_group,
-            "kernel": "unpack8_tma2_kernel" if spec.sample_bits == 8 else "unpack4_line_kernel",
+            "kernel": unpack_kernel_name(spec),
             "peak_source": f"HBM copy ({peak_src})",
             "ms_per_launch": tim.unpack_ms / max(1, tim.unpack_launches)}
 
@@ -451,6 +463,8 @@ def run_calib(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     spec = synth.spec_c4()
+    if args.chan:
+        spec = spec.with_(n_chan=args.chan)
     N, C, T = spec.n_inputs, spec.n_chan, spec.n_time
     B = N * (N + 1) // 2
     desc = f"calibration loss+adjoint, {N} inputs x {C} ch, V from T={T} 8-bit correlation, 20-source model"

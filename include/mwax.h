@@ -196,12 +196,15 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
 /* Correlate one integration of a single-job plan.
  * voltages: device, [n_chan][n_time][n_inputs] packed samples (see above).
  * out:      device, [n_chan][N(N+1)/2][2], int32 (EXACT) or float32 (FP16).
+ * Both must start on a 16-byte boundary (any cudaMalloc / torch allocation
+ * does); otherwise MWAX_ERR_INVALID_ARG and nothing is launched.
  * The shape arguments must equal the planned ones (MWAX_ERR_SHAPE_MISMATCH). */
 mwax_status mwax_correlate(mwax_plan_t plan, const void *voltages, int n_inputs, int n_chan,
                            int n_time, void *out);
 
 /* Correlate every job of a batch plan: voltages[k] / out[k] are device
- * pointers for job k, passed in host arrays of n_jobs entries. */
+ * pointers for job k (16-byte aligned, as for mwax_correlate), passed in host
+ * arrays of n_jobs entries. */
 mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages,
                                  void *const *out);
 

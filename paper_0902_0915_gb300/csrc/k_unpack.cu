@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "mwax_internal.h"
 
 namespace mwax {
@@ -360,6 +362,122 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   __syncthreads();
 }
 
+// 4-bit samples, TMA both ways.  Same pipeline as the 8-bit kernel; a raw
+// time block is 64 samples x N inputs (one byte each).  Thread t converts
+// inputs 4q .. 4q+3 (q = t mod n_rows/4) for half h = t / (n_rows/4) of the
+// block (samples 32h .. 32h+31), in two quarters of 16 samples: 16 four-byte
+// loads (conflict-free across the warp), nibbles -> E4M3 by byte permutes, and
+// one 16-byte chunk of re and one of im for each of its four rows.  At step k lane q writes row 4q + ((k + q/2) mod 4), so
+// the 8 lanes of a store phase hit 8 different swizzle groups (no bank
+// conflicts).  Block size and shared memory follow N, so small N runs
+// several CTAs per SM.
+__global__ void __launch_bounds__(kTmaThreads)
+    unpack4_tma2_kernel(const __grid_constant__ CUtensorMap out_map, const uint8_t *__restrict__ volt,
+                        int N, int T, int n_rows, int kb, int64_t chan0, int n_chan, int32_t *status,
+                        unsigned long long tmo) {
+  extern __shared__ __align__(1024) uint8_t sm_base[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
+                                            ~static_cast<uintptr_t>(1023));
+  uint8_t *stage = sm;                                  // swizzled operand tile, 1024-B aligned
+  uint8_t *raw = sm + (int64_t)n_rows * kRowBytes;      // raw time block (64 x N bytes)
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  const int64_t tasks = (int64_t)n_chan * kb;
+  const int quads = n_rows / 4;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t k) {
+    const int c = (int)(k / kb), tb = (int)(k % kb);
+    const int rows = min(64, T - tb * 64);
+    const uint32_t bytes = (uint32_t)(rows * N);
+    const uint8_t *src = volt + ((chan0 + c) * (int64_t)T + (int64_t)tb * 64) * N;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(raw)),
+        "l"(src), "r"(bytes), "r"(b)
+        : "memory");
+  };
+  int64_t k = blockIdx.x;
+  if (threadIdx.x == 0 && k < tasks) issue(k);
+  uint32_t phase = 0;
+  bool ok = true;
+  const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
+  const int q = (int)threadIdx.x % quads, h = (int)threadIdx.x / quads;
+  const int i0 = 4 * q;
+  for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
+    if (!u_wait(b, phase, tmo)) {
+      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    // the previous task's TMA stores must have finished reading the staging tile
+    if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncthreads();
+    const int c = (int)(k / kb), tb = (int)(k % kb);
+    const int rows = min(64, T - tb * 64);
+    if (h < 2) {
+#pragma unroll
+      for (int qq = 0; qq < 2; ++qq) {  // 16-sample quarter: one 16-byte chunk per row for re, one for im
+        uint32_t re[16], im[16];        // byte m = E4M3 of input i0+m at sample 32h + 16qq + r
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int sidx = 32 * h + 16 * qq + r;
+          const uint32_t w = (i0 < N && sidx < rows)
+                                 ? *reinterpret_cast<const uint32_t *>(raw + sidx * N + i0)
+                                 : 0u;
+          re[r] = nib4_to_e4m3(w);
+          im[r] = nib4_to_e4m3(w >> 4);
+        }
+        const int cre = 2 * h + qq, cim = 4 + 2 * h + qq;  // chunk indices in the row
+#pragma unroll
+        for (int step = 0; step < 4; ++step) {
+          const int kk = (step + (q >> 1)) & 3;  // which of the four rows this lane writes now
+          const uint32_t sel = (uint32_t)(kk | ((kk + 4) << 4));
+          uint32_t vr[4], vi[4];
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            vr[g] = __byte_perm(__byte_perm(re[4 * g], re[4 * g + 1], sel),
+                                __byte_perm(re[4 * g + 2], re[4 * g + 3], sel), 0x5410);
+            vi[g] = __byte_perm(__byte_perm(im[4 * g], im[4 * g + 1], sel),
+                                __byte_perm(im[4 * g + 2], im[4 * g + 3], sel), 0x5410);
+          }
+          const int row = i0 + kk;
+          const int sw = row & 7;
+          uint8_t *dst = stage + (int64_t)row * kRowBytes;
+          *reinterpret_cast<uint4 *>(dst + ((cre ^ sw) << 4)) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
+          *reinterpret_cast<uint4 *>(dst + ((cim ^ sw) << 4)) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // the raw buffer is free: fetch the next block while this one is stored
+      if (k + gridDim.x < tasks) issue(k + gridDim.x);
+      const int y0 = (int)(((int64_t)c * kb + tb) * n_rows);
+      for (int r0 = 0; r0 < n_rows; r0 += kStoreBox)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                reinterpret_cast<uint64_t>(&out_map)),
+            "r"(0), "r"(y0 + r0), "r"(stage_u32 + r0 * kRowBytes)
+            : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (!ok) u_wait(b, phase, tmo);
+  }
+  __syncthreads();
+}
+
 }  // namespace
 
 cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
@@ -390,8 +508,11 @@ cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n
 
 bool unpack_tma2_supported(int sample_bits, int n_inputs) {
   const int n_rows = (n_inputs + kTile - 1) / kTile * kTile;
-  return sample_bits == 8 && n_inputs % 8 == 0 && 64 * n_inputs <= kTmaBufBytes &&
-         n_rows * kRowBytes <= kStageOutBytes;
+  if (n_inputs < 1 || n_rows * kRowBytes > kStageOutBytes) return false;
+  // raw rows must be whole 16-byte units for the bulk copy: 2N (8-bit) or N (4-bit) bytes
+  if (sample_bits == 8) return n_inputs % 8 == 0 && 64 * n_inputs <= kTmaBufBytes;
+  if (sample_bits == 4) return n_inputs % 16 == 0 && 64 * n_inputs <= kTmaBufBytes;
+  return false;
 }
 
 cudaError_t launch_unpack_tma2(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
@@ -421,16 +542,34 @@ cudaError_t launch_unpack_tma2(const uint8_t *volt, int sample_bits, int n_input
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const int smem = 1024 + kStageOutBytes + kTmaBufBytes;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(unpack8_tma2_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  if (sample_bits == 8) {
+    const int smem = 1024 + kStageOutBytes + kTmaBufBytes;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(unpack8_tma2_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    unpack8_tma2_kernel<<<ctas, kTmaThreads, smem, s>>>(map, volt, n_inputs, n_time, n_rows, kb,
+                                                        chan0, n_chan, status, timeout_ns);
+    return cudaGetLastError();
   }
-  unpack8_tma2_kernel<<<ctas, kTmaThreads, smem, s>>>(map, volt, n_inputs, n_time, n_rows, kb, chan0,
-                                                      n_chan, status, timeout_ns);
+  // 4-bit: two threads per input quad, staging and raw buffers sized to N;
+  // `ctas` is per-SM-count scaled by how many such CTAs fit on an SM
+  const int threads = n_rows / 2;  // 2 halves x n_rows/4 quads; multiple of 64, <= 512
+  const int smem = 1024 + n_rows * kRowBytes + 64 * n_inputs;
+  static bool attr4_set = false;
+  if (!attr4_set) {
+    cudaError_t e = cudaFuncSetAttribute(unpack4_tma2_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         1024 + kStageOutBytes + kTmaBufBytes);
+    if (e != cudaSuccess) return e;
+    attr4_set = true;
+  }
+  const int per_sm = std::max(1, std::min(4, (227 * 1024) / smem));
+  unpack4_tma2_kernel<<<ctas * per_sm, threads, smem, s>>>(map, volt, n_inputs, n_time, n_rows, kb,
+                                                           chan0, n_chan, status, timeout_ns);
   return cudaGetLastError();
 }
 

@@ -207,24 +207,30 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
 }
 
 // Unpack variant: MWAX_UNPACK overrides (1 shared-memory transpose, 2
-// full-line, 4 TMA both ways); automatic = TMA both ways for 8-bit shapes that
-// allow it, else the full-line kernel (4-bit) or the shared-memory transpose.
-int unpack_choice(const JobState &s) {
+// full-line, 4 TMA both ways); automatic = TMA both ways for shapes that allow
+// it (and whose sample buffer starts on a 16-byte boundary, which the bulk
+// copy needs), else the full-line kernel (4-bit) or the shared-memory
+// transpose.
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int unpack_choice(const JobState &s, const void *volt) {
   static const int env = [] {
     const char *e = getenv("MWAX_UNPACK");
     return e ? atoi(e) : 0;
   }();
-  if (env == 1 || env == 2 || env == 4) return env;
-  if (unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs)) return 4;
-  return 0;
+  const bool tma_ok = unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs) &&
+                      (reinterpret_cast<uintptr_t>(volt) & 15u) == 0;
+  if (env == 4) return tma_ok ? 4 : 0;
+  if (env == 1 || env == 2) return env;
+  return tma_ok ? 4 : 0;
 }
 
 mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
                          uint8_t *op, int ctas, cudaStream_t st) {
   TimedLaunch tu(p, 0, st);
   cudaError_t e;
-  const int v = unpack_choice(s);
-  if (v == 4 && unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs))
+  const int v = unpack_choice(s, volt);
+  if (v == 4)
     e = launch_unpack_tma2(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb,
                            c0, nc, op, ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
   else if (ctas > 0)
@@ -541,6 +547,7 @@ mwax_status mwax_correlate(mwax_plan_t plan, const void *voltages, int n_inputs,
   if (n_inputs != s.job.n_inputs || n_chan != s.job.n_chan || n_time != s.job.n_time)
     return MWAX_ERR_SHAPE_MISMATCH;
   if (!is_device_ptr(voltages) || !is_device_ptr(out)) return MWAX_ERR_INVALID_ARG;
+  if (!aligned16(voltages) || !aligned16(out)) return MWAX_ERR_INVALID_ARG;
   return correlate_device(plan, reinterpret_cast<const uint8_t *>(voltages), out, plan->stream);
 }
 
@@ -548,7 +555,9 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
   if (!plan || !plan->batch || !voltages || !out) return MWAX_ERR_INVALID_ARG;
   const int nj = (int)plan->jobs.size();
   for (int k = 0; k < nj; ++k)
-    if (!is_device_ptr(voltages[k]) || !is_device_ptr(out[k])) return MWAX_ERR_INVALID_ARG;
+    if (!is_device_ptr(voltages[k]) || !is_device_ptr(out[k]) || !aligned16(voltages[k]) ||
+        !aligned16(out[k]))
+      return MWAX_ERR_INVALID_ARG;
   bool same = plan->graph != nullptr && plan->graph2 != nullptr;
   for (int k = 0; k < nj && same; ++k)
     same = plan->graph_in[k] == voltages[k] && plan->graph_out[k] == out[k];
@@ -582,7 +591,7 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
         for (int k = 0; k < nj && e == cudaSuccess; ++k) {
           const JobState &s = plan->jobs[k];
           const uint8_t *v = reinterpret_cast<const uint8_t *>(voltages[k]);
-          if (unpack_choice(s) == 4)
+          if (unpack_choice(s, v) == 4)
             e = launch_unpack_tma2(v, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
                                    s.kb, 0, s.job.n_chan, s.op, plan->sm_count, plan->status,
                                    plan->timeout_ns, cs);

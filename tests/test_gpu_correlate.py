@@ -81,10 +81,12 @@ def test_tensor_small(mw, bits, N, T, C, shape):
 
 @pytest.mark.parametrize("bits", [4, 8])
 @pytest.mark.parametrize("N,T,C", [(16, 33, 3), (48, 1000, 2), (120, 64, 3), (272, 97, 2),
-                                   (1024, 70, 1), (1000, 45, 2)])
+                                   (1024, 70, 1), (1000, 45, 2), (256, 130, 3), (128, 64, 2),
+                                   (304, 200, 2)])
 def test_tensor_tma_unpack_shapes(mw, bits, N, T, C):
-    """Shapes the TMA-staged unpack takes (N a multiple of 16, raw time block
-    <= 64 KB), with a ragged last time block."""
+    """Shapes the TMA both-ways unpack takes (N a multiple of 8 for 8-bit and
+    of 16 for 4-bit samples, up to 1024 inputs) and shapes that fall back to
+    the other kernels, with ragged last time blocks."""
     spec = synth.Spec("tma", N, C, T, bits, seed=N + T + bits, sigma=2 if bits == 4 else 40,
                       tone_amp=0.3)
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tma {N},{T},{C}")
@@ -219,6 +221,23 @@ def test_shape_mismatch_and_host_pointer_rejected(mw):
     hv = torch.zeros(8 * 2 * 10, dtype=torch.uint8)
     assert mw.lib().mwax_correlate(p._h, hv.data_ptr(), 8, 2, 10, out.data_ptr()) == 1
     p.close()
+
+
+def test_unaligned_buffers_rejected(mw):
+    """Device buffers that do not start on a 16-byte boundary are refused
+    before any launch (the unpack and dump kernels use vector accesses)."""
+    import torch
+
+    p = mw.Plan(16, 2, 64, 4)
+    v = torch.zeros(16 * 2 * 64 + 16, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(p.empty_out().numel() + 4, dtype=torch.int32, device="cuda")
+    L = mw.lib()
+    assert L.mwax_correlate(p._h, v.data_ptr() + 1, 16, 2, 64, out.data_ptr()) == 1
+    assert L.mwax_correlate(p._h, v.data_ptr(), 16, 2, 64, out.data_ptr() + 4) == 1
+    assert L.mwax_correlate(p._h, v.data_ptr(), 16, 2, 64, out.data_ptr()) == 0
+    assert p.status() == 0
+    p.close()
+    torch.cuda.synchronize()
 
 
 # ---------------------------------------------------------------------------
