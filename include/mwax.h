@@ -90,9 +90,9 @@ typedef struct {
   int32_t mma_shape;       /* tuning: 1 = M128xN128 MMAs (Re, Im separately), 2 = M128xN256
                               MMAs with [Re | Im] at once (0 = auto)                     */
   int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
-                              plan's stream, 2 = unpack the next group on `unpack_sms`
-                              SMs (second stream, second scratch buffer) while the current
-                              group correlates on the other SMs; 0 = auto (1)            */
+                              plan's stream, 2 = unpack the next group (second stream,
+                              second scratch buffer) while the current group correlates,
+                              see unpack_sms; 0 = auto (1)                               */
   int32_t timeout_ms;      /* limit of every device-side wait, ms (0 = 2000)              */
   int32_t test_fault;      /* failure-detection tests only, 0 = off: with k > 0 the
                               epilogue of the tensor correlator withholds the release of
@@ -100,8 +100,10 @@ typedef struct {
                               wait runs out; the call then completes with
                               MWAX_ERR_TIMEOUT in mwax_plan_status and the output is
                               invalid; the device stays usable                          */
-  int32_t unpack_sms;      /* tuning, pipeline 2 only: SMs given to the persistent unpack
-                              while the correlate runs on the others (0 = 20)           */
+  int32_t unpack_sms;      /* tuning, pipeline 2 only: 0 = the unpack runs as one small
+                              CTA beside the correlate CTA on every SM (8-bit samples,
+                              n_inputs a multiple of 8; other shapes use 20); k > 0 = k
+                              SMs run the unpack while the correlate runs on the others */
   int32_t reserved[1];     /* must be zero                                                */
 } mwax_job;
 

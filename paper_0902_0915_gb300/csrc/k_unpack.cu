@@ -478,6 +478,112 @@ __global__ void __launch_bounds__(kTmaThreads)
   __syncthreads();
 }
 
+// 8-bit samples, small footprint: one task is one 128-input tile of one
+// 32-sample time block.  A 2D TMA load brings the raw box (32 samples x 256
+// bytes, rows 2N bytes apart; inputs past N read as zeros) into shared memory,
+// each of the 128 threads converts one operand row into a 128-byte-swizzled
+// 16 KB staging tile, and one TMA tensor store writes the tile.  About 25 KB
+// of shared memory and at most 80 registers a thread, so a CTA fits on an SM
+// beside a resident correlate CTA and the unpack of the next channel group
+// can run while the current group correlates.
+constexpr int kTileThreads = 128;
+constexpr int kTileRawBytes = 32 * 256;
+
+__global__ void __launch_bounds__(kTileThreads, 6)
+    unpack8_tile_kernel(const __grid_constant__ CUtensorMap in_map,
+                        const __grid_constant__ CUtensorMap out_map, int N, int T, int n_tiles,
+                        int kb, int64_t chan0, int n_chan, int32_t *status,
+                        unsigned long long tmo) {
+  extern __shared__ __align__(1024) uint8_t sm_base[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
+                                            ~static_cast<uintptr_t>(1023));
+  uint8_t *stage = sm;                // 128 rows x 128 B, swizzled
+  uint8_t *raw = sm + kTile * kRowBytes;  // 32 samples x 256 B
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  const int64_t tasks = (int64_t)n_chan * kb * n_tiles;  // tile fastest
+  const int n_rows = n_tiles * kTile;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
+  }
+  __syncthreads();
+  const uint32_t raw_u32 = (uint32_t)__cvta_generic_to_shared(raw);
+  auto issue = [&](int64_t k) {
+    const int tile = (int)(k % n_tiles);
+    const int64_t cb = k / n_tiles;
+    const int c = (int)(cb / kb), tb = (int)(cb % kb);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                 "r"((uint32_t)kTileRawBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(raw_u32),
+        "l"(reinterpret_cast<uint64_t>(&in_map)), "r"(tile * 256),
+        "r"((int)((chan0 + c) * (int64_t)T + (int64_t)tb * 32)), "r"(b)
+        : "memory");
+  };
+  int64_t k = blockIdx.x;
+  if (threadIdx.x == 0 && k < tasks) issue(k);
+  uint32_t phase = 0;
+  bool ok = true;
+  const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
+  const int i = threadIdx.x;  // operand row within the tile
+  for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
+    if (!u_wait(b, phase, tmo)) {
+      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    // the previous task's TMA store must have finished reading the staging tile
+    if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncthreads();
+    const int tile = (int)(k % n_tiles);
+    const int64_t cb = k / n_tiles;
+    const int c = (int)(cb / kb), tb = (int)(cb % kb);
+    const int rows = min(32, T - tb * 32);  // samples of this block (the box may run into the next channel)
+    uint32_t v[32];
+#pragma unroll
+    for (int s2 = 0; s2 < 32; ++s2)
+      v[s2] = s2 < rows ? (uint32_t) * reinterpret_cast<const uint16_t *>(raw + s2 * 256 + 2 * i) : 0u;
+    __syncthreads();  // raw is free: fetch the next task's box while this one is converted
+    if (threadIdx.x == 0 && k + gridDim.x < tasks) issue(k + gridDim.x);
+    uint8_t *row = stage + i * kRowBytes;
+    const int sw = i & 7;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // chunk q: samples 8q .. 8q+7 (re), chunk 4+q (im)
+      uint32_t re4[4], im4[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t x = v[8 * q + 2 * e], y = v[8 * q + 2 * e + 1];
+        re4[e] = s8pair_to_h2(__byte_perm(x, y, 0x0400));
+        im4[e] = s8pair_to_h2(__byte_perm(x, y, 0x0501));
+      }
+      *reinterpret_cast<uint4 *>(row + ((q ^ sw) << 4)) = make_uint4(re4[0], re4[1], re4[2], re4[3]);
+      *reinterpret_cast<uint4 *>(row + (((4 + q) ^ sw) << 4)) = make_uint4(im4[0], im4[1], im4[2], im4[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int y0 = (int)(((int64_t)c * kb + tb) * n_rows + tile * kTile);
+      asm volatile(
+          "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+              reinterpret_cast<uint64_t>(&out_map)),
+          "r"(0), "r"(y0), "r"(stage_u32)
+          : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (!ok) u_wait(b, phase, tmo);
+  }
+  __syncthreads();
+}
+
 }  // namespace
 
 cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
@@ -570,6 +676,61 @@ cudaError_t launch_unpack_tma2(const uint8_t *volt, int sample_bits, int n_input
   const int per_sm = std::max(1, std::min(4, (227 * 1024) / smem));
   unpack4_tma2_kernel<<<ctas * per_sm, threads, smem, s>>>(map, volt, n_inputs, n_time, n_rows, kb,
                                                            chan0, n_chan, status, timeout_ns);
+  return cudaGetLastError();
+}
+
+bool unpack_tile_supported(int sample_bits, int n_inputs) {
+  return sample_bits == 8 && n_inputs % 8 == 0;
+}
+
+int unpack_tile_smem_bytes() { return 1024 + kTile * kRowBytes + kTileRawBytes; }
+
+cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
+                               int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
+                               int ctas, int32_t *status, unsigned long long timeout_ns,
+                               cudaStream_t s) {
+  if (n_chan <= 0) return cudaSuccess;
+  if (ctas < 1 || !unpack_tile_supported(sample_bits, n_inputs)) return cudaErrorInvalidValue;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  // input: [ (chan0 + n_chan) * T rows ][ 2N bytes ], box 256 bytes x 32 rows, no swizzle
+  const cuuint64_t in_rows = (cuuint64_t)(chan0 + n_chan) * n_time;
+  const cuuint64_t out_rows = (cuuint64_t)n_chan * kb * n_tiles * kTile;
+  if (in_rows > 0x7FFFFFFFull || out_rows > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  CUtensorMap in_map, out_map;
+  cuuint64_t idims[2] = {(cuuint64_t)2 * n_inputs, in_rows};
+  cuuint64_t istr[1] = {(cuuint64_t)2 * n_inputs};
+  cuuint32_t ibox[2] = {256, 32};
+  cuuint32_t estr[2] = {1, 1};
+  if (encode(&in_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(volt), idims, istr, ibox,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  cuuint64_t odims[2] = {(cuuint64_t)kRowBytes, out_rows};
+  cuuint64_t ostr[1] = {(cuuint64_t)kRowBytes};
+  cuuint32_t obox[2] = {(cuuint32_t)kRowBytes, (cuuint32_t)kTile};
+  if (encode(&out_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, op, odims, ostr, obox, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const int smem = unpack_tile_smem_bytes();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(unpack8_tile_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  unpack8_tile_kernel<<<ctas, kTileThreads, smem, s>>>(in_map, out_map, n_inputs, n_time, n_tiles, kb,
+                                                       chan0, n_chan, status, timeout_ns);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ struct mwax_plan_s {
   int prefetch = 0;
   int wide = 0;
   int withhold_seg = -1;
-  int unpack_sms = 20;  // overlapped pipeline: SMs given to the persistent unpack
+  int unpack_sms = 0;  // overlapped pipeline: SMs given to the persistent unpack (0: co-resident)
   unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
   std::vector<mwax::JobState> jobs;
   uint8_t *scratch = nullptr;  // single-job plans: operand buffer for one channel group
@@ -230,7 +230,10 @@ mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt,
   TimedLaunch tu(p, 0, st);
   cudaError_t e;
   const int v = unpack_choice(s, volt);
-  if (v == 4)
+  if (p->overlap && p->unpack_sms == 0)
+    e = launch_unpack_tile(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb,
+                           c0, nc, op, p->sm_count, p->status, p->timeout_ns, st);
+  else if (v == 4)
     e = launch_unpack_tma2(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb,
                            c0, nc, op, ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
   else if (ctas > 0)
@@ -294,9 +297,10 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
     return MWAX_OK;
   }
   // Overlapped: the unpack of group g+1 runs on the aux stream into the other
-  // scratch buffer while group g correlates.  The unpack kernel (128 threads,
-  // no shared memory) fits beside the persistent correlate CTA on each SM and
-  // uses the DRAM bandwidth the correlate leaves idle.
+  // scratch buffer while group g correlates: either one small unpack CTA per
+  // SM beside the persistent correlate CTA (unpack_sms == 0; it uses the DRAM
+  // bandwidth the correlate leaves idle), or a persistent unpack on
+  // unpack_sms SMs with the correlate on the rest.
   uint8_t *buf[2] = {p->scratch, p->scratch2};
   cudaError_t e = cudaEventRecord(p->ev_start, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_start, 0);
@@ -428,7 +432,11 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
   if (p->engine == MWAX_ENGINE_TENSOR) {
     const int64_t one = s.op_chan_bytes * s.chan_group;
     const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : s.job.n_inputs % 4 == 0;
-    if (job->unpack_sms > 0) p->unpack_sms = job->unpack_sms;
+    // unpack_sms 0: the small unpack CTA runs beside the correlate on every SM
+    // where the shape allows it, else 20 SMs are set aside for the unpack
+    p->unpack_sms = job->unpack_sms > 0 ? job->unpack_sms
+                    : unpack_tile_supported(s.job.sample_bits, s.job.n_inputs) ? 0
+                                                                                : 20;
     p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan && even &&
                  p->unpack_sms < p->sm_count;
     p->scratch_bytes = one * (p->overlap ? 2 : 1);

@@ -92,6 +92,17 @@ def test_tensor_tma_unpack_shapes(mw, bits, N, T, C):
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tma {N},{T},{C}")
 
 
+@pytest.mark.parametrize("N,T,C,G", [(256, 1000, 12, 5), (200, 77, 7, 3), (1024, 100, 4, 1),
+                                     (136, 33, 5, 2)])
+def test_overlapped_coresident_unpack(mw, N, T, C, G):
+    """pipeline 2 with the small unpack CTA beside the correlate on every SM:
+    several channel groups (ragged last group), N not a multiple of 128 (the
+    raw box reads past N as zeros), ragged last time block."""
+    spec = synth.Spec("ov", N, C, T, 8, seed=N + T + C, sigma=40, tone_amp=0.3)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, pipeline=2, chan_group=G),
+                 oracle_for(spec, range(C)), f"overlap {N},{T},{C},{G}")
+
+
 def test_c0_both_engines(mw):
     spec = synth.spec_c0()
     ref = oracle_for(spec, range(spec.n_chan))
@@ -263,6 +274,11 @@ def _full_size(mw, spec, chans, **kw):
 def test_full_size_c1_sampled(mw, shape):
     spec = synth.spec_c1()
     _full_size(mw, spec, [0, 1, 383, 766, 767], mma_shape=shape)
+
+
+def test_full_size_c2_overlapped_sampled(mw):
+    spec = synth.spec_c2()
+    _full_size(mw, spec, [0, 208, 209, 1500, 3071], pipeline=2)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
