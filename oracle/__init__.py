@@ -23,7 +23,7 @@ OK, ERR_ARG, ERR_OOM, ERR_OVERFLOW = 0, 1, 2, 3
 def build_command():
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     return ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-Wall",
-            os.path.join(_HERE, "mwax_oracle.c"), "-o", LIB]
+            os.path.join(_HERE, "mwax_oracle.c"), "-o", LIB, "-lm"]
 
 
 def build() -> None:
@@ -57,6 +57,15 @@ def _load():
         lib.oracle_calib_grad.restype = ctypes.c_int
         lib.oracle_calib_grad.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int,
                                                                   ctypes.c_void_p, ctypes.c_int]
+        lib.oracle_grid.restype = ctypes.c_int
+        lib.oracle_grid.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_grid_cell.restype = ctypes.c_int
+        lib.oracle_grid_cell.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_void_p]
         lib.oracle_calib_als_target.restype = ctypes.c_int
         lib.oracle_calib_als_target.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int,
                                                                         ctypes.c_void_p, ctypes.c_int]
@@ -178,3 +187,32 @@ def calib_solve(V, M, g0, n_iter: int, n_threads: int | None = None):
         h = calib_als_target(V, M, g, n_threads)
         g = h if t % 2 == 1 else 0.5 * (g + h)
     return g, np.array(losses)
+
+
+def _grid_args(tile_xy, vis):
+    tile_xy = np.ascontiguousarray(tile_xy, np.float64)
+    vis = np.ascontiguousarray(vis, np.int32)
+    n_tiles = tile_xy.shape[0]
+    N = 2 * n_tiles
+    assert tile_xy.shape == (n_tiles, 2) and vis.ndim == 3 and vis.shape[1:] == (N * (N + 1) // 2, 2)
+    return tile_xy, vis, n_tiles, vis.shape[0]
+
+
+def grid(tile_xy, vis, f0, df, Ng, du, W, sigma) -> np.ndarray:
+    """FP64 gridding of correlator output onto four polarisation grids,
+    complex128 [4, Ng, Ng] (index 2p + q for product p, q; 0 = X, 1 = Y).
+    tile_xy: [n_tiles, 2] metres; vis: int32 [n_chan, N(N+1)/2, 2], N = 2 n_tiles."""
+    tile_xy, vis, n_tiles, n_chan = _grid_args(tile_xy, vis)
+    out = np.zeros((4, Ng, Ng, 2), np.float64)
+    _load().oracle_grid(tile_xy.ctypes.data, n_tiles, n_chan, f0, df, Ng, du, W, sigma,
+                        vis.ctypes.data, out.ctypes.data)
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def grid_cell(tile_xy, vis, f0, df, Ng, du, W, sigma, pol, r, s) -> complex:
+    """One cell of grid ``pol`` computed from every point directly."""
+    tile_xy, vis, n_tiles, n_chan = _grid_args(tile_xy, vis)
+    val = np.zeros(2, np.float64)
+    _load().oracle_grid_cell(tile_xy.ctypes.data, n_tiles, n_chan, f0, df, Ng, du, W, sigma,
+                             vis.ctypes.data, pol, r, s, val.ctypes.data)
+    return complex(val[0], val[1])

@@ -48,6 +48,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 
 /* ---- sample decoding ---------------------------------------------------- */
 
@@ -327,4 +328,113 @@ int oracle_calib_als_target(const double *V, const double *M, const double *g, i
   }
   for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
   return rc;
+}
+
+/* ---- gridding (FP64) ------------------------------------------------------
+ * Paper Sec. 2.1: the calibrated visibilities are convolved onto a regular
+ * grid so that an FFT can form the images.  Definition used here:
+ *   tiles a at (X_a, Y_a) metres; every tile baseline a > b and channel c
+ *   (frequency nu_c = f0 + c df) is a point at
+ *       u = (X_a - X_b) nu_c / c_light,  v = (Y_a - Y_b) nu_c / c_light
+ *   in wavelengths, i.e. at continuous cell coordinates
+ *       x = u / du + Ng / 2,  y = v / du + Ng / 2.
+ *   Polarisation product (p, q) (0 = X, 1 = Y) of that baseline is the
+ *   correlator output V[c][i(i+1)/2 + j] with i = 2a + p, j = 2b + q.  It is
+ *   added to grid G_pq at every cell (r, s) with |s - x| < W/2 and
+ *   |r - y| < W/2 with weight exp(-((s - x)^2 + (r - y)^2) / (2 sigma^2)).
+ *   The reversed baseline (b, a) is the point (-u, -v) carrying
+ *   conj(V of product (q, p) of (a, b)), gridded the same way.  Cells outside
+ *   [0, Ng) are dropped.  Grids out[pol = 2p + q][r][s][re, im].
+ */
+static const double kCLight = 299792458.0;
+
+typedef struct {
+  const double *tile_xy;
+  int n_tiles, n_chan;
+  double f0, df, du, sigma;
+  int Ng, W;
+  const int32_t *vis;
+} grid_geom;
+
+static cplx vis_pol(const grid_geom *G, int64_t c, int64_t a, int64_t b, int p, int q) {
+  const int64_t N = 2 * (int64_t)G->n_tiles, B = N * (N + 1) / 2;
+  const int64_t i = 2 * a + p, j = 2 * b + q;
+  const int32_t *v = G->vis + (c * B + i * (i + 1) / 2 + j) * 2;
+  return (cplx){(double)v[0], (double)v[1]};
+}
+
+/* add point (x, y) carrying V[4] (indexed 2p + q) to the grids */
+static void grid_point(const grid_geom *G, double x, double y, const cplx *V, double *out) {
+  const int Ng = G->Ng;
+  const double half = 0.5 * G->W, s2 = 2.0 * G->sigma * G->sigma;
+  for (int r = (int)floor(y - half); r <= (int)ceil(y + half); ++r) {
+    if (r < 0 || r >= Ng || !(fabs(r - y) < half)) continue;
+    for (int s = (int)floor(x - half); s <= (int)ceil(x + half); ++s) {
+      if (s < 0 || s >= Ng || !(fabs(s - x) < half)) continue;
+      const double w = exp(-((s - x) * (s - x) + (r - y) * (r - y)) / s2);
+      for (int pol = 0; pol < 4; ++pol) {
+        double *o = out + (((int64_t)pol * Ng + r) * Ng + s) * 2;
+        o[0] += w * V[pol].re;
+        o[1] += w * V[pol].im;
+      }
+    }
+  }
+}
+
+static void point_xy(const grid_geom *G, int64_t a, int64_t b, int64_t c, double *x, double *y) {
+  const double nu = G->f0 + (double)c * G->df;
+  const double u = (G->tile_xy[2 * a] - G->tile_xy[2 * b]) * nu / kCLight;
+  const double v = (G->tile_xy[2 * a + 1] - G->tile_xy[2 * b + 1]) * nu / kCLight;
+  *x = u / G->du + 0.5 * G->Ng;
+  *y = v / G->du + 0.5 * G->Ng;
+}
+
+/* All four polarisation grids, out [4][Ng][Ng][2] (zeroed here).  vis:
+ * [n_chan][N(N+1)/2][2] int32 with N = 2 n_tiles.  Returns 0. */
+int oracle_grid(const double *tile_xy, int n_tiles, int n_chan, double f0, double df, int Ng,
+                double du, int W, double sigma, const int32_t *vis, double *out) {
+  grid_geom G = {tile_xy, n_tiles, n_chan, f0, df, du, sigma, Ng, W, vis};
+  memset(out, 0, sizeof(double) * 2 * 4 * (size_t)Ng * Ng);
+  for (int64_t c = 0; c < n_chan; ++c)
+    for (int64_t a = 0; a < n_tiles; ++a)
+      for (int64_t b = 0; b < a; ++b) {
+        double x, y;
+        point_xy(&G, a, b, c, &x, &y);
+        cplx V[4], Vc[4];
+        for (int p = 0; p < 2; ++p)
+          for (int q = 0; q < 2; ++q) {
+            V[2 * p + q] = vis_pol(&G, c, a, b, p, q);
+            Vc[2 * p + q] = cconj(vis_pol(&G, c, a, b, q, p));  /* reversed baseline */
+          }
+        grid_point(&G, x, y, V, out);
+        grid_point(&G, (double)Ng - x, (double)Ng - y, Vc, out);
+      }
+  return 0;
+}
+
+/* One cell (r, s) of grid `pol`, from every point directly: val[re, im]. */
+int oracle_grid_cell(const double *tile_xy, int n_tiles, int n_chan, double f0, double df, int Ng,
+                     double du, int W, double sigma, const int32_t *vis, int pol, int r, int s,
+                     double *val) {
+  grid_geom G = {tile_xy, n_tiles, n_chan, f0, df, du, sigma, Ng, W, vis};
+  const int p = pol >> 1, q = pol & 1;
+  const double half = 0.5 * W, s2 = 2.0 * sigma * sigma;
+  double re = 0.0, im = 0.0;
+  for (int64_t c = 0; c < n_chan; ++c)
+    for (int64_t a = 0; a < n_tiles; ++a)
+      for (int64_t b = 0; b < a; ++b) {
+        double x, y;
+        point_xy(&G, a, b, c, &x, &y);
+        for (int side = 0; side < 2; ++side) {
+          const double px = side ? (double)Ng - x : x, py = side ? (double)Ng - y : y;
+          if (!(fabs(s - px) < half) || !(fabs(r - py) < half)) continue;
+          const double w = exp(-((s - px) * (s - px) + (r - py) * (r - py)) / s2);
+          const cplx v = side ? cconj(vis_pol(&G, c, a, b, q, p)) : vis_pol(&G, c, a, b, p, q);
+          re += w * v.re;
+          im += w * v.im;
+        }
+      }
+  val[0] = re;
+  val[1] = im;
+  return 0;
 }

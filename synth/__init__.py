@@ -191,6 +191,17 @@ def source_geometry(n_inputs: int, n_src: int, seed: int, chan_width_hz: float,
     return np.ascontiguousarray(rate), uv, lm
 
 
+def grid_geometry_c1():
+    """Inputs of the gridding workload that consumes the c1 correlation: the
+    c1 tile positions (metres, [128, 2]), the first channel's frequency and the
+    channel width (Hz): 768 channels of 40 kHz from 167.04 MHz (30.72 MHz, the
+    MWA's high band), and the grid: 2048 x 2048 cells of 1 wavelength (every
+    baseline of the 1.5 km array fits), support 7 cells, Gaussian width 1 cell."""
+    _, uv, _ = source_geometry(256, 5, 1, 40e3)
+    return {"tile_xy": np.ascontiguousarray(uv, np.float64), "f0": 167.04e6, "df": 40e3,
+            "Ng": 2048, "du": 1.0, "W": 7, "sigma": 1.0}
+
+
 # --------------------------------------------------------------------------
 # workloads (shapes of the MWA correlator, Sec. 2)
 # --------------------------------------------------------------------------

@@ -364,3 +364,112 @@ def test_solve_recovers_true_gains():
     assert np.abs(g_al - g_true).max() <= 1e-9 * np.abs(g_true).max()
     assert losses[-1] <= 1e-16 * losses[0]
     assert oracle.calib_loss(V, M, g) <= 1e-20 * losses[0]
+
+
+# ---------------------------------------------------------------------------
+# gridding
+# ---------------------------------------------------------------------------
+C_LIGHT = 299792458.0
+
+
+def grid_problem(rng, n_tiles, n_chan, Ng, du, f0=150e6, df=1e6, vmax=1000):
+    """Tile positions that keep every point inside the grid, random int32 visibilities."""
+    N = 2 * n_tiles
+    B = N * (N + 1) // 2
+    reach = (0.5 * Ng - 5) * du * C_LIGHT / (f0 + (n_chan - 1) * df) / 2
+    tile_xy = rng.uniform(-reach, reach, (n_tiles, 2)) * 0.7
+    vis = rng.integers(-vmax, vmax + 1, (n_chan, B, 2)).astype(np.int32)
+    return tile_xy, vis, f0, df
+
+
+def numpy_points(tile_xy, vis, f0, df, Ng, du):
+    """(x, y, V[4]) of every gridded point, both orientations, from the definition."""
+    n_tiles = tile_xy.shape[0]
+    n_chan = vis.shape[0]
+    Vc = vis[..., 0].astype(np.float64) + 1j * vis[..., 1]
+    pts = []
+    for c in range(n_chan):
+        nu = f0 + c * df
+        for a in range(n_tiles):
+            for b in range(a):
+                u = (tile_xy[a] - tile_xy[b]) * nu / C_LIGHT / du
+                V = np.array([Vc[c, oracle.baseline_index(2 * a + p, 2 * b + q)]
+                              for p in (0, 1) for q in (0, 1)])
+                Vr = np.array([np.conj(Vc[c, oracle.baseline_index(2 * a + q, 2 * b + p)])
+                               for p in (0, 1) for q in (0, 1)])
+                pts.append((u[0] + Ng / 2, u[1] + Ng / 2, V))
+                pts.append((Ng / 2 - u[0], Ng / 2 - u[1], Vr))
+    return pts
+
+
+def test_grid_brute_force_numpy():
+    rng = np.random.default_rng(31)
+    Ng, du, W, sigma = 40, 2.0, 7, 1.1
+    tile_xy, vis, f0, df = grid_problem(rng, 4, 3, Ng, du)
+    G = oracle.grid(tile_xy, vis, f0, df, Ng, du, W, sigma)
+    ref = np.zeros((4, Ng, Ng), complex)
+    cells = np.arange(Ng)
+    for x, y, V in numpy_points(tile_xy, vis, f0, df, Ng, du):
+        sx = cells[np.abs(cells - x) < W / 2]
+        sy = cells[np.abs(cells - y) < W / 2]
+        w = np.exp(-((sy[:, None] - y) ** 2 + (sx[None, :] - x) ** 2) / (2 * sigma ** 2))
+        for pol in range(4):
+            np.add.at(ref[pol], (sy[:, None], sx[None, :]), w * V[pol])
+    np.testing.assert_allclose(G, ref, rtol=1e-12, atol=1e-9)
+
+
+def test_grid_golden_single_baseline():
+    """Two tiles on the x axis, one channel, u = 5 cells exactly: the XX grid
+    holds V at (Ng/2, Ng/2 + 5), V e^{-1/(2 sigma^2)} one cell away, conj(V) at
+    (Ng/2, Ng/2 - 5), and nothing beyond three cells."""
+    Ng, du, W, sigma, nu = 32, 1.0, 7, 1.0, 200e6
+    tile_xy = np.array([[0.0, 0.0], [5 * du * C_LIGHT / nu, 0.0]])
+    vis = np.zeros((1, 10, 2), np.int32)
+    vis[0, oracle.baseline_index(2, 0)] = (3, -2)  # tile 1 X with tile 0 X
+    G = oracle.grid(tile_xy, vis, nu, 0.0, Ng, du, W, sigma)
+    c = Ng // 2
+    assert G[0, c, c + 5] == pytest.approx(3 - 2j, abs=1e-9)
+    assert G[0, c, c + 6] == pytest.approx((3 - 2j) * np.exp(-0.5), abs=1e-9)
+    assert G[0, c + 1, c + 4] == pytest.approx((3 - 2j) * np.exp(-1.0), abs=1e-9)
+    assert G[0, c, c - 5] == pytest.approx(3 + 2j, abs=1e-9)
+    assert G[0, c, c + 9] == 0 and G[0, c + 4, c + 5] == 0
+    assert np.abs(G[1:]).max() == 0  # only the XX product is non-zero
+
+
+def test_grid_hermitian():
+    """The reversed baseline makes G_pq(-u) = conj(G_qp(u)):
+    G[2p+q][Ng-r][Ng-s] = conj(G[2q+p][r][s]) for r, s >= 1."""
+    rng = np.random.default_rng(32)
+    Ng, du, W, sigma = 48, 1.5, 7, 1.3
+    tile_xy, vis, f0, df = grid_problem(rng, 5, 4, Ng, du)
+    G = oracle.grid(tile_xy, vis, f0, df, Ng, du, W, sigma)
+    flip = G[:, :0:-1, :0:-1]  # [pol][Ng - r][Ng - s] for r, s = 1 .. Ng-1
+    swap = G[[0, 2, 1, 3], 1:, 1:]
+    np.testing.assert_allclose(flip, np.conj(swap), rtol=1e-12, atol=1e-9)
+
+
+def test_grid_total_weight():
+    """Sum over the grid = sum over points of V Sx Sy, with Sx the sum of the
+    1D kernel over the cells in the point's support (the Gaussian factorises)."""
+    rng = np.random.default_rng(33)
+    Ng, du, W, sigma = 36, 2.5, 7, 0.9
+    tile_xy, vis, f0, df = grid_problem(rng, 4, 5, Ng, du)
+    G = oracle.grid(tile_xy, vis, f0, df, Ng, du, W, sigma)
+    cells = np.arange(Ng)
+    tot = np.zeros(4, complex)
+    for x, y, V in numpy_points(tile_xy, vis, f0, df, Ng, du):
+        Sx = np.exp(-((cells - x) ** 2) / (2 * sigma ** 2))[np.abs(cells - x) < W / 2].sum()
+        Sy = np.exp(-((cells - y) ** 2) / (2 * sigma ** 2))[np.abs(cells - y) < W / 2].sum()
+        tot += V * Sx * Sy
+    np.testing.assert_allclose(G.sum(axis=(1, 2)), tot, rtol=1e-11)
+
+
+def test_grid_cell_matches_grid():
+    rng = np.random.default_rng(34)
+    Ng, du, W, sigma = 44, 1.7, 7, 1.0
+    tile_xy, vis, f0, df = grid_problem(rng, 6, 3, Ng, du)
+    G = oracle.grid(tile_xy, vis, f0, df, Ng, du, W, sigma)
+    for _ in range(25):
+        pol, r, s = rng.integers(0, 4), rng.integers(0, Ng), rng.integers(0, Ng)
+        assert oracle.grid_cell(tile_xy, vis, f0, df, Ng, du, W, sigma, pol, r, s) == \
+            pytest.approx(G[pol, r, s], rel=1e-12, abs=1e-9)
