@@ -451,6 +451,91 @@ def model_visibilities(spec, chans, device):
     return out
 
 
+def run_grid(args):
+    """c5: gridding of the c1 correlation (128 tiles x 2 pol, 768 channels)
+    onto four 2048 x 2048 polarisation grids."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    import paper_0902_0915_gb300 as mw
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    spec = synth.spec_c1()
+    geo = synth.grid_geometry_c1()
+    N, C, T = spec.n_inputs, spec.n_chan, spec.n_time
+    n_tiles = N // 2
+    mw.ensure_built()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    vol = torch.empty(C * T * N, dtype=torch.uint8, device=dev)
+    synth.fill_device(spec, vol)
+    plan = mw.Plan(N, C, T, 4, stream=stream)
+    vis = plan.correlate(vol)
+    assert plan.status() == 0
+    plan.close()
+    del vol
+    t0 = time.perf_counter()
+    gp = mw.GridPlan(geo["tile_xy"], C, geo["f0"], geo["df"], geo["Ng"], geo["du"], geo["W"],
+                     geo["sigma"], stream=stream)
+    plan_s = time.perf_counter() - t0
+    grids = gp.empty_grids()
+    for _ in range(args.warmup):
+        gp.grid(vis, grids)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        gp.grid(vis, grids)
+    b.record(stream)
+    b.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    n_pts = gp.n_points
+    W = geo["W"]
+    # algorithmic work: every gridded point adds 4 complex values times a
+    # weight to the W x W cells of its support: 8 FMA (16 flops) per cell
+    flops = n_pts * W * W * 16.0
+    props = torch.cuda.get_device_properties(0)
+    sm_mhz = 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
+    achieved = flops / (ms / 1e3) / 1e12
+    desc = (f"gridding of the c1 correlation ({n_tiles} tiles x 2 pol, {C} ch from "
+            f"{geo['f0'] / 1e6:.2f} MHz) onto 4 x {geo['Ng']}^2 cells of {geo['du']} wavelength, "
+            f"Gaussian support {W}")
+    line = {"metric": "gridding throughput (visibility points x 4 polarisations / s), FP32",
+            "value": n_pts * 4 / (ms / 1e3) / 1e9, "unit": "G samples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (the c1 correlation of seeded voltages; seeded tile positions)",
+            "config": {"workload": f"c5: {desc}", "points": n_pts,
+                       "l2": f"points {n_pts * 48 / 1e9:.2f} GB + grids {4 * geo['Ng'] ** 2 * 8 / 1e9:.2f} GB"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "grid_values_kernel + grid_gather_kernel (one grid call)",
+                         "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flops x 2070 MHz (derived)"},
+            "plan_s": plan_s, "gpu_launches": 2 * args.steps, "clocks": clk}
+    gp.close()
+    if not args.no_cpu:
+        sub = 8
+        rng = np.random.default_rng(5)
+        vh = rng.integers(-2 ** 20, 2 ** 20, (sub, N * (N + 1) // 2, 2)).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.grid(geo["tile_xy"], vh, geo["f0"], geo["df"], geo["Ng"], geo["du"], W, geo["sigma"])
+        dt = time.perf_counter() - t0
+        pts = n_tiles * (n_tiles - 1) * sub
+        line["cpu_baseline"] = {"value": pts * 4 / dt / 1e9, "unit": "G samples/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{sub} of {C} channels (seeded values of the same shape), FP64"}
+    print(json.dumps(line), flush=True)
+
+
 def run_calib(args):
     """c4: calibration loss and adjoint (one pass) on correlator output."""
     import numpy as np
@@ -565,7 +650,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mwax", choices=["mwax", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0", "c3", "c4", "c5"])
     ap.add_argument("--engine", default="tensor", choices=["tensor", "plain"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -588,6 +673,8 @@ def main():
 
     if args.workload == "c3":
         return run_batch(args)
+    if args.workload == "c5":
+        return run_grid(args)
     if args.workload == "c4":
         return run_calib(args)
 

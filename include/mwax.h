@@ -273,6 +273,37 @@ int64_t mwax_calib_solve_workspace_bytes(int n_inputs, int n_chan);
 mwax_status mwax_calib_solve(const float *V, const float *M, float *g, int n_inputs, int n_chan,
                              int n_iter, void *workspace, float *loss_hist, cudaStream_t stream);
 
+/* ---- gridding (FP32) ------------------------------------------------------
+ * Paper Sec. 2.1: the visibilities are convolved onto a regular grid so an
+ * FFT can form the images; Sec. 3.2: each GPU thread gathers the values of
+ * its own output cell (no floating-point atomics).  Definition (the paper
+ * names no kernel or sizes): tiles a at tile_xy[a] = (X_a, Y_a) metres; every
+ * tile baseline a > b and channel c (nu = f0 + c df) is a point at cell
+ * coordinates x = (X_a - X_b) nu / c_light / du + Ng/2 (y likewise with Y),
+ * carrying the four polarisation products V_pq (correlator inputs 2a+p and
+ * 2b+q, p, q in {0 = X, 1 = Y}); the reversed baseline is the point
+ * (Ng - x, Ng - y) carrying conj(V_qp).  Each point adds
+ * V exp(-((s - x)^2 + (r - y)^2) / (2 sigma^2)) to cell (r, s) of grid 2p+q
+ * for |s - x| < W/2, |r - y| < W/2; cells outside [0, Ng) are dropped.
+ *
+ * mwax_grid_plan: geometry only (host tile_xy [n_tiles][2] doubles, copied);
+ *   bins the points by the first cell of their support on the GPU (counting
+ *   sort, each bin in ascending point order).  Blocks until done.  n_tiles in
+ *   [2, 4096], Ng even in [8, 16384], W in [1, 31]; INVALID_ARG otherwise,
+ *   OOM / CUDA on device failures.
+ * mwax_grid: vis = device correlator output [n_chan][N(N+1)/2][2] int32,
+ *   N = 2 n_tiles (the layout mwax_correlate writes); grids = device float
+ *   [4][Ng][Ng][2] (re, im), every cell written.  Both 8-byte aligned.
+ *   Asynchronous on the plan's stream; deterministic (fixed summation order).
+ * mwax_grid_plan_points: number of points that reach the grid. */
+typedef struct mwax_grid_plan_s *mwax_grid_plan_t;
+mwax_status mwax_grid_plan(mwax_grid_plan_t *plan, const double *tile_xy, int n_tiles, int n_chan,
+                           double f0, double df, int Ng, double du, int W, double sigma,
+                           cudaStream_t stream);
+mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids);
+int64_t mwax_grid_plan_points(mwax_grid_plan_t plan);
+mwax_status mwax_grid_destroy(mwax_grid_plan_t plan);
+
 /* ---- allocation-free calibration -------------------------------------------
  * No counterpart in the paper.  For callers that must not allocate device
  * memory when they evaluate the loss -- a real-time loop in which

@@ -94,6 +94,11 @@ SIGNATURES = {
     "mwax_calib_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "mwax_calib_solve_workspace_bytes": (_I64, [_I, _I]),
     "mwax_calib_solve": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "mwax_grid_plan": (_I, [_P, _P, _I, _I, ctypes.c_double, ctypes.c_double, _I, ctypes.c_double,
+                            _I, ctypes.c_double, _P]),
+    "mwax_grid": (_I, [_P, _P, _P]),
+    "mwax_grid_plan_points": (_I64, [_P]),
+    "mwax_grid_destroy": (_I, [_P]),
     "mwax_calib_static_workspace_bytes": (_I64, []),
     "mwax_calib_loss_grad_static": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
 }
@@ -251,6 +256,59 @@ class Plan:
         if self._h:
             lib().mwax_destroy(self._h)
             self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GridPlan:
+    """Gridding of correlator output onto four polarisation uv grids
+    (mwax_grid_plan / mwax_grid).  tile_xy: [n_tiles, 2] metres."""
+
+    def __init__(self, tile_xy, n_chan: int, f0: float, df: float, Ng: int, du: float, W: int = 7,
+                 sigma: float = 1.0, stream=None):
+        import numpy as np
+
+        torch = _torch()
+        xy = np.ascontiguousarray(tile_xy, np.float64)
+        if xy.ndim != 2 or xy.shape[1] != 2:
+            raise ValueError("tile_xy must be [n_tiles, 2]")
+        self.n_tiles, self.n_chan, self.Ng = xy.shape[0], n_chan, Ng
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib().mwax_grid_plan(ctypes.byref(h), xy.ctypes.data, self.n_tiles, n_chan, f0, df, Ng,
+                                    du, W, sigma, self._stream.cuda_stream), "mwax_grid_plan")
+        self._h = h.value
+
+    @property
+    def n_points(self) -> int:
+        return int(lib().mwax_grid_plan_points(self._h))
+
+    def empty_grids(self):
+        torch = _torch()
+        return torch.empty((4, self.Ng, self.Ng), dtype=torch.complex64, device="cuda")
+
+    def grid(self, vis, grids=None):
+        """vis: int32 CUDA tensor [n_chan, N(N+1)/2, 2] (N = 2 n_tiles), the
+        correlator's output; returns complex64 [4, Ng, Ng] (index 2p + q)."""
+        torch = _torch()
+        N = 2 * self.n_tiles
+        if not vis.is_cuda or vis.dtype != torch.int32 or vis.shape != (self.n_chan, N * (N + 1) // 2, 2):
+            raise ValueError("vis must be int32 CUDA [n_chan, N(N+1)/2, 2] with N = 2 n_tiles")
+        vis = vis.contiguous()
+        if grids is None:
+            grids = self.empty_grids()
+        _check(lib().mwax_grid(self._h, vis.data_ptr(), torch.view_as_real(grids).data_ptr()),
+               "mwax_grid")
+        return grids
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mwax_grid_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

@@ -66,3 +66,23 @@ def test_plan_rejects_bad_jobs_before_touching_the_device(mwax_lib):
     assert L.mwax_plan(None, None, None) == 1
     assert h.value is None
     assert L.mwax_destroy(None) == 0
+
+
+def test_grid_plan_rejects_bad_arguments_without_a_device(mwax_lib):
+    """Argument checks run before any CUDA call: odd or tiny grids, too few
+    tiles, non-positive cell size or width are INVALID_ARG (1)."""
+    import ctypes
+
+    import numpy as np
+
+    L = mwax_lib.lib()
+    xy = np.zeros((4, 2), np.float64)
+    h = ctypes.c_void_p()
+    cases = [(4, 8, 150e6, 1e6, 33, 1.0, 7, 1.0), (1, 8, 150e6, 1e6, 32, 1.0, 7, 1.0),
+             (4, 8, 150e6, 1e6, 32, 0.0, 7, 1.0), (4, 8, 150e6, 1e6, 32, 1.0, 7, 0.0),
+             (4, 0, 150e6, 1e6, 32, 1.0, 7, 1.0), (4, 8, 150e6, 1e6, 32, 1.0, 0, 1.0)]
+    for nt, nc, f0, df, Ng, du, W, sg in cases:
+        assert L.mwax_grid_plan(ctypes.byref(h), xy.ctypes.data, nt, nc, f0, df, Ng, du, W, sg,
+                                None) == 1
+    assert L.mwax_grid(None, None, None) == 1
+    assert L.mwax_grid_destroy(None) == 1
