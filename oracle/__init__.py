@@ -216,3 +216,45 @@ def grid_cell(tile_xy, vis, f0, df, Ng, du, W, sigma, pol, r, s) -> complex:
     _load().oracle_grid_cell(tile_xy.ctypes.data, n_tiles, n_chan, f0, df, Ng, du, W, sigma,
                              vis.ctypes.data, pol, r, s, val.ctypes.data)
     return complex(val[0], val[1])
+
+
+def stokes(inst, dl, chi):
+    """FP64 Stokes conversion of four instrumental-polarisation images.
+
+    Paper Sec. 2.1: the instrumental polarisation images are turned into
+    Stokes I, Q, U, V by a 4x4 matrix that depends on time and sky position
+    and is computed for every pixel.  Definition used (the paper gives no
+    beam model): pixel (r, c) of an n x n slant-orthographic image has
+    direction cosines l = (c - n/2) dl, m = (r - n/2) dl; with
+    rho = sqrt(l^2 + m^2) < 1, cos(theta) = sqrt(1 - rho^2) and
+    phi = atan2(m, l) + chi (chi: the parallactic rotation at the time), the
+    ideal crossed-dipole response is
+        J = [[cos(theta) cos(phi), -sin(phi)],
+             [cos(theta) sin(phi),  cos(phi)]]
+    (rows X, Y dipole; columns theta, phi sky components).  The instrumental
+    coherency C = [[XX, XY], [YX, YY]] gives the sky brightness
+    B = J^-1 C J^-H, and I = B00 + B11, Q = B00 - B11, U = B01 + B10,
+    V = -i (B01 - B10).  Pixels with rho >= 1 (horizon and below) are zero.
+
+    inst: complex [4, n, n] (XX, XY, YX, YY); returns complex [4, n, n]
+    (I, Q, U, V)."""
+    inst = np.asarray(inst, np.complex128)
+    n = inst.shape[-1]
+    assert inst.shape == (4, n, n)
+    idx = np.arange(n) - n / 2
+    l = idx[None, :] * dl
+    m = idx[:, None] * dl
+    l, m = np.broadcast_arrays(l, m)
+    rho = np.sqrt(l * l + m * m)
+    up = rho < 1.0
+    out = np.zeros_like(inst)
+    for r, c in zip(*np.nonzero(up)):
+        ct = np.sqrt(1.0 - rho[r, c] ** 2)
+        ph = np.arctan2(m[r, c], l[r, c]) + chi
+        J = np.array([[ct * np.cos(ph), -np.sin(ph)], [ct * np.sin(ph), np.cos(ph)]])
+        Ji = np.linalg.inv(J)
+        C = np.array([[inst[0, r, c], inst[1, r, c]], [inst[2, r, c], inst[3, r, c]]])
+        Bm = Ji @ C @ Ji.conj().T
+        out[:, r, c] = [Bm[0, 0] + Bm[1, 1], Bm[0, 0] - Bm[1, 1], Bm[0, 1] + Bm[1, 0],
+                        -1j * (Bm[0, 1] - Bm[1, 0])]
+    return out

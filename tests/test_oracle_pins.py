@@ -473,3 +473,70 @@ def test_grid_cell_matches_grid():
         pol, r, s = rng.integers(0, 4), rng.integers(0, Ng), rng.integers(0, Ng)
         assert oracle.grid_cell(tile_xy, vis, f0, df, Ng, du, W, sigma, pol, r, s) == \
             pytest.approx(G[pol, r, s], rel=1e-12, abs=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Stokes conversion
+# ---------------------------------------------------------------------------
+def test_stokes_zenith_is_plain_sum_and_difference():
+    """At the zenith J is the rotation by chi; with chi = 0 it is the identity
+    and I = XX + YY, Q = XX - YY, U = XY + YX, V = -i (XY - YX)."""
+    n = 8
+    rng = np.random.default_rng(41)
+    inst = rng.standard_normal((4, n, n)) + 1j * rng.standard_normal((4, n, n))
+    S = oracle.stokes(inst, 0.1, 0.0)
+    XX, XY, YX, YY = inst[:, n // 2, n // 2]
+    np.testing.assert_allclose(S[:, n // 2, n // 2],
+                               [XX + YY, XX - YY, XY + YX, -1j * (XY - YX)], rtol=1e-14)
+
+
+def test_stokes_round_trip_of_a_known_sky():
+    """Instrumental images made from known Stokes through J B J^H (written
+    here independently) convert back to those Stokes."""
+    n = 16
+    dl, chi = 0.11, 0.37
+    rng = np.random.default_rng(42)
+    I, Q, U, V = rng.standard_normal((4, n, n))
+    inst = np.zeros((4, n, n), complex)
+    idx = np.arange(n) - n / 2
+    for r in range(n):
+        for c in range(n):
+            l, m = idx[c] * dl, idx[r] * dl
+            rho = np.hypot(l, m)
+            if rho >= 1:
+                continue
+            th, ph = np.arcsin(rho), np.arctan2(m, l) + chi
+            J = np.array([[np.cos(th) * np.cos(ph), -np.sin(ph)], [np.cos(th) * np.sin(ph), np.cos(ph)]])
+            B = 0.5 * np.array([[I[r, c] + Q[r, c], U[r, c] + 1j * V[r, c]],
+                                [U[r, c] - 1j * V[r, c], I[r, c] - Q[r, c]]])
+            C = J @ B @ J.T
+            inst[:, r, c] = [C[0, 0], C[0, 1], C[1, 0], C[1, 1]]
+    S = oracle.stokes(inst, dl, chi)
+    up = np.hypot(*np.meshgrid(idx * dl, idx * dl)) < 1
+    for k, ref in enumerate((I, Q, U, V)):
+        np.testing.assert_allclose(S[k][up], ref[up], rtol=1e-10, atol=1e-12)
+    assert np.all(S[:, ~up] == 0)
+
+
+def test_stokes_unpolarised_source_stays_unpolarised():
+    """An unpolarised sky (B = I/2 1) seen anywhere above the horizon gives
+    Q = U = V = 0 after conversion, though the instrumental XY is not zero."""
+    n = 12
+    dl, chi = 0.15, -0.8
+    idx = np.arange(n) - n / 2
+    inst = np.zeros((4, n, n), complex)
+    for r in range(n):
+        for c in range(n):
+            l, m = idx[c] * dl, idx[r] * dl
+            rho = np.hypot(l, m)
+            if rho >= 1:
+                continue
+            ct, ph = np.sqrt(1 - rho ** 2), np.arctan2(m, l) + chi
+            # J J^T for the dipole response, times 1/2 (unit Stokes I)
+            a, b, cc, d = ct * np.cos(ph), -np.sin(ph), ct * np.sin(ph), np.cos(ph)
+            inst[:, r, c] = 0.5 * np.array([a * a + b * b, a * cc + b * d, cc * a + d * b, cc * cc + d * d])
+    S = oracle.stokes(inst, dl, chi)
+    up = np.hypot(*np.meshgrid(idx * dl, idx * dl)) < 1
+    np.testing.assert_allclose(S[0][up], 1.0, rtol=1e-12)
+    np.testing.assert_allclose(S[1:, up], 0.0, atol=1e-12)
+    assert np.abs(inst[1][up]).max() > 0.05
