@@ -536,6 +536,70 @@ def run_grid(args):
     print(json.dumps(line), flush=True)
 
 
+def run_stokes(args):
+    """c6: per-pixel Stokes conversion of four 4096 x 4096 instrumental
+    images covering the whole sky hemisphere (dl = 2/n)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_0902_0915_gb300 as mw
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    n, chi = 4096, 0.3
+    dl = 2.0 / n
+    mw.ensure_built()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(6)
+    inst = torch.randn((4, n, n), dtype=torch.complex64, device=dev, generator=gen)
+    out = torch.empty_like(inst)
+    for _ in range(args.warmup):
+        mw.stokes(inst, dl, chi, out)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        mw.stokes(inst, dl, chi, out)
+    b.record(stream)
+    b.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    # 4 complex64 written per pixel; 4 read only above the horizon
+    idx = (np.arange(n) - n / 2) * dl
+    up = int(((idx[:, None] ** 2 + idx[None, :] ** 2) < 1.0).sum())
+    bytes_step = 32.0 * n * n + 32.0 * up
+    peaks, src = load_peaks()
+    achieved = bytes_step / (ms / 1e3) / 1e9
+    line = {"metric": "Stokes conversion throughput (pixels/s), FP32", "value": n * n / (ms / 1e3) / 1e9,
+            "unit": "G pixels/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded complex Gaussian instrumental images)",
+            "config": {"workload": f"c6: Stokes conversion of 4 x {n}^2 instrumental images, whole hemisphere, chi = {chi}",
+                       "pixels_above_horizon": up,
+                       "l2": f"{bytes_step / 1e9:.2f} GB per call > L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "kernel": "stokes_kernel", "peak_source": src},
+            "gpu_launches": args.steps, "clocks": clk}
+    if not args.no_cpu:
+        rng = np.random.default_rng(6)
+        sub = 128
+        small = rng.standard_normal((4, sub, sub)) + 1j * rng.standard_normal((4, sub, sub))
+        t0 = time.perf_counter()
+        oracle.stokes(small, 2.0 / sub, chi)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sub * sub / dt / 1e9, "unit": "G pixels/s", "cores": 1,
+                                "kind": "oracle", "sample": f"one {sub} x {sub} image set (FP64)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_calib(args):
     """c4: calibration loss and adjoint (one pass) on correlator output."""
     import numpy as np
@@ -650,7 +714,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mwax", choices=["mwax", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0", "c3", "c4", "c5", "c6"])
     ap.add_argument("--engine", default="tensor", choices=["tensor", "plain"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -675,6 +739,8 @@ def main():
         return run_batch(args)
     if args.workload == "c5":
         return run_grid(args)
+    if args.workload == "c6":
+        return run_stokes(args)
     if args.workload == "c4":
         return run_calib(args)
 

@@ -304,6 +304,25 @@ mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids);
 int64_t mwax_grid_plan_points(mwax_grid_plan_t plan);
 mwax_status mwax_grid_destroy(mwax_grid_plan_t plan);
 
+/* ---- Stokes conversion (FP32) ----------------------------------------------
+ * Paper Sec. 2.1: the instrumental polarisation images become Stokes
+ * I, Q, U, V through a 4x4 matrix computed for every pixel from time and sky
+ * position.  Definition (the paper gives no beam model): pixel (r, c) of an
+ * n x n slant-orthographic image is at l = (c - n/2) dl, m = (r - n/2) dl;
+ * above the horizon (l^2 + m^2 < 1) the ideal crossed-dipole response at
+ * zenith angle theta = asin(sqrt(l^2 + m^2)) and azimuth
+ * phi = atan2(m, l) + chi (chi: parallactic rotation, radians) is
+ * J = [[cos th cos ph, -sin ph], [cos th sin ph, cos ph]], the sky brightness
+ * is B = J^-1 C J^-T for C = [[XX, XY], [YX, YY]], and
+ * (I, Q, U, V) = (B00 + B11, B00 - B11, B01 + B10, -i (B01 - B10)).
+ * Pixels on or below the horizon are zero.
+ *   inst:   device float [4][n][n][2] (XX, XY, YX, YY; re, im)
+ *   stokes: device float [4][n][n][2] (I, Q, U, V), a different buffer
+ * Both 8-byte aligned; n even in [2, 65536], dl > 0; INVALID_ARG otherwise.
+ * Asynchronous on `stream`. */
+mwax_status mwax_stokes(const float *inst, int n, double dl, double chi, float *stokes,
+                        cudaStream_t stream);
+
 /* ---- allocation-free calibration -------------------------------------------
  * No counterpart in the paper.  For callers that must not allocate device
  * memory when they evaluate the loss -- a real-time loop in which

@@ -218,7 +218,7 @@ def grid_cell(tile_xy, vis, f0, df, Ng, du, W, sigma, pol, r, s) -> complex:
     return complex(val[0], val[1])
 
 
-def stokes(inst, dl, chi):
+def stokes(inst, dl, chi, pixels=None):
     """FP64 Stokes conversion of four instrumental-polarisation images.
 
     Paper Sec. 2.1: the instrumental polarisation images are turned into
@@ -237,7 +237,8 @@ def stokes(inst, dl, chi):
     V = -i (B01 - B10).  Pixels with rho >= 1 (horizon and below) are zero.
 
     inst: complex [4, n, n] (XX, XY, YX, YY); returns complex [4, n, n]
-    (I, Q, U, V)."""
+    (I, Q, U, V).  With ``pixels`` (a list of (r, c)) only those pixels are
+    converted (the others stay zero)."""
     inst = np.asarray(inst, np.complex128)
     n = inst.shape[-1]
     assert inst.shape == (4, n, n)
@@ -248,7 +249,8 @@ def stokes(inst, dl, chi):
     rho = np.sqrt(l * l + m * m)
     up = rho < 1.0
     out = np.zeros_like(inst)
-    for r, c in zip(*np.nonzero(up)):
+    todo = zip(*np.nonzero(up)) if pixels is None else [(r, c) for r, c in pixels if up[r, c]]
+    for r, c in todo:
         ct = np.sqrt(1.0 - rho[r, c] ** 2)
         ph = np.arctan2(m[r, c], l[r, c]) + chi
         J = np.array([[ct * np.cos(ph), -np.sin(ph)], [ct * np.sin(ph), np.cos(ph)]])

@@ -99,6 +99,7 @@ SIGNATURES = {
     "mwax_grid": (_I, [_P, _P, _P]),
     "mwax_grid_plan_points": (_I64, [_P]),
     "mwax_grid_destroy": (_I, [_P]),
+    "mwax_stokes": (_I, [_P, _I, ctypes.c_double, ctypes.c_double, _P, _P]),
     "mwax_calib_static_workspace_bytes": (_I64, []),
     "mwax_calib_loss_grad_static": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
 }
@@ -315,6 +316,22 @@ class GridPlan:
             self.close()
         except Exception:
             pass
+
+
+def stokes(inst, dl: float, chi: float, out=None):
+    """Per-pixel Stokes conversion (mwax_stokes): inst complex64 CUDA
+    [4, n, n] (XX, XY, YX, YY) -> complex64 [4, n, n] (I, Q, U, V)."""
+    torch = _torch()
+    if not inst.is_cuda or inst.dtype != torch.complex64 or inst.ndim != 3 or inst.shape[0] != 4 \
+            or inst.shape[1] != inst.shape[2]:
+        raise ValueError("inst must be complex64 CUDA [4, n, n]")
+    inst = inst.contiguous()
+    n = inst.shape[1]
+    if out is None:
+        out = torch.empty_like(inst)
+    _check(lib().mwax_stokes(torch.view_as_real(inst).data_ptr(), n, dl, chi,
+                             torch.view_as_real(out).data_ptr(), _stream_handle()), "mwax_stokes")
+    return out
 
 
 class BatchPlan:
