@@ -478,6 +478,7 @@ def run_grid(args):
     assert plan.status() == 0
     plan.close()
     del vol
+    torch.cuda.empty_cache()
     t0 = time.perf_counter()
     gp = mw.GridPlan(geo["tile_xy"], C, geo["f0"], geo["df"], geo["Ng"], geo["du"], geo["W"],
                      geo["sigma"], stream=stream)

@@ -25,11 +25,10 @@
 //      support cell, last support cell (r_hi, s_hi), point id.
 // Grid call (per integration): a gather kernel reads each point's four
 // polarisation values from the int32 correlator output into the sorted
-// record; then one thread per output cell (r, s) sums over the points whose
-// support can contain it -- for each of the W bin rows r - dr, the W bins
-// s - W + 1 .. s, which are one contiguous range of the sorted points --
-// keeping those with r <= r_hi and s <= s_hi, in a fixed order.
-// Deterministic.
+// record; then every warp gathers a 4 x 8 patch of cells: it streams the
+// points whose support can reach the patch (per bin row, one contiguous range
+// of the sorted points) with broadcast loads, and each lane keeps the points
+// whose support contains its cell, in a fixed order.  Deterministic.
 #include <math.h>
 #include <string.h>
 
@@ -239,39 +238,70 @@ __global__ void grid_values_kernel(const GeomRec *__restrict__ rec, int n_kept, 
   pts[p] = o;
 }
 
-// grid call, step 2: one thread per output cell gathers from the W x W bins
-constexpr int kCellTileX = 16, kCellTileY = 16;
+// grid call, step 2: gather.  A warp owns a 4 x 8 patch of cells (lane =
+// row i = lane / 8, column j = lane % 8) and streams, once for the whole
+// warp, every point whose support can reach the patch: for each bin row
+// r0 - W + 1 .. r0 + 3 (shifted by W - 1), the bins of columns
+// s0 - W + 1 .. s0 + 7, one contiguous range of the sorted points.  All lanes
+// read the same point (a broadcast); each lane keeps it if its cell lies in
+// the point's support.  A 7 x 7 support covers up to 28 of the 32 cells.
+// Each cell's sum runs over bin rows, then bin columns, then point ids: a
+// fixed order.
+constexpr int kPatchR = 4, kPatchC = 8;
+constexpr int kGatherWarpsR = 4, kGatherWarpsC = 2;  // CTA = 16 x 16 cells
 
-__global__ void __launch_bounds__(kCellTileX *kCellTileY) grid_gather_kernel(
+__global__ void __launch_bounds__(32 * kGatherWarpsR * kGatherWarpsC) grid_gather_kernel(
     const PointRec *__restrict__ pts, const int *__restrict__ offsets, int Ng, int W, int nbw,
     float inv_2s2, float2 *__restrict__ grids) {
-  const int s = blockIdx.x * kCellTileX + threadIdx.x;
-  const int r = blockIdx.y * kCellTileY + threadIdx.y;
-  if (s >= Ng || r >= Ng) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = (blockIdx.y * kGatherWarpsR + warp / kGatherWarpsC) * kPatchR;
+  const int s0 = (blockIdx.x * kGatherWarpsC + warp % kGatherWarpsC) * kPatchC;
+  if (r0 >= Ng || s0 >= Ng) return;  // whole warp
+  const int r = r0 + lane / kPatchC, s = s0 + lane % kPatchC;
   float2 acc[4];
 #pragma unroll
   for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
-  for (int dr = 0; dr < W; ++dr) {
-    // points with r_lo = r - dr and s_lo in [s - W + 1, s]: bins (r - dr + W - 1,
-    // s .. s + W - 1), one contiguous range of the sorted points
-    const int row = (r - dr + W - 1) * nbw;
-    const int lo = offsets[row + s], hi = offsets[row + s + W];
-    for (int q = lo; q < hi; ++q) {
-      const PointRec &P = pts[q];
-      if (r > (P.hi >> 16) || s > (P.hi & 0xFFFF)) continue;
-      // s = s_lo + ds, r = r_lo + dr
-      const float dx = (float)(s + W - 1 - P.slo) - P.fx, dy = (float)dr - P.fy;
-      const float w = expf(-(dx * dx + dy * dy) * inv_2s2);
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        acc[p].x += w * P.v[p].x;
-        acc[p].y += w * P.v[p].y;
+  // bin row br holds points with r_lo = br - (W - 1); those reaching rows
+  // r0 .. r0 + 3 have br in [r0, r0 + 3 + W - 1]; likewise bin columns
+  const int br_end = min(r0 + kPatchR - 1 + W - 1, nbw - 1);
+  const int bc_end = min(s0 + kPatchC + W - 1, nbw);  // exclusive
+  for (int br = r0; br <= br_end; ++br) {
+    const int lo = __ldg(offsets + br * nbw + s0), hi = __ldg(offsets + br * nbw + bc_end);
+    const float dy0 = (float)(r - (br - (W - 1)));  // r - r_lo
+    // four points per step: their geometry loads are issued together
+    auto take = [&](const float4 g, int q) {
+      const int phi = __float_as_int(g.z), slo = __float_as_int(g.w);
+      const int ds = s - (slo - (W - 1));  // s - s_lo
+      if (dy0 >= 0.f && ds >= 0 && r <= (phi >> 16) && s <= (phi & 0xFFFF)) {
+        const float dx = (float)ds - g.x, dy = dy0 - g.y;
+        const float w = expf(-(dx * dx + dy * dy) * inv_2s2);
+        const float4 v01 = __ldg(reinterpret_cast<const float4 *>(pts + q) + 1);
+        const float4 v23 = __ldg(reinterpret_cast<const float4 *>(pts + q) + 2);
+        acc[0].x += w * v01.x;
+        acc[0].y += w * v01.y;
+        acc[1].x += w * v01.z;
+        acc[1].y += w * v01.w;
+        acc[2].x += w * v23.x;
+        acc[2].y += w * v23.y;
+        acc[3].x += w * v23.z;
+        acc[3].y += w * v23.w;
       }
-    }
-  }
-  const int64_t cell = (int64_t)r * Ng + s;
+    };
+    int q = lo;
+    for (; q + 4 <= hi; q += 4) {
+      float4 g[4];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) grids[(int64_t)p * Ng * Ng + cell] = acc[p];
+      for (int u = 0; u < 4; ++u) g[u] = __ldg(reinterpret_cast<const float4 *>(pts + q + u));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) take(g[u], q + u);
+    }
+    for (; q < hi; ++q) take(__ldg(reinterpret_cast<const float4 *>(pts + q)), q);
+  }
+  if (r < Ng && s < Ng) {
+    const int64_t cell = (int64_t)r * Ng + s;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) grids[(int64_t)p * Ng * Ng + cell] = acc[p];
+  }
 }
 
 }  // namespace
@@ -413,9 +443,9 @@ mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids) {
     grid_values_kernel<<<(plan->n_kept + T - 1) / T, T, 0, plan->stream>>>(
         plan->rec, plan->n_kept, plan->n_tbl, N * (N + 1) / 2, reinterpret_cast<const int2 *>(vis),
         plan->pts);
-  dim3 blk(kCellTileX, kCellTileY);
-  dim3 grd((plan->Ng + kCellTileX - 1) / kCellTileX, (plan->Ng + kCellTileY - 1) / kCellTileY);
-  grid_gather_kernel<<<grd, blk, 0, plan->stream>>>(plan->pts, plan->offsets, plan->Ng, plan->W,
+  const int tile_r = kPatchR * kGatherWarpsR, tile_c = kPatchC * kGatherWarpsC;
+  dim3 grd((plan->Ng + tile_c - 1) / tile_c, (plan->Ng + tile_r - 1) / tile_r);
+  grid_gather_kernel<<<grd, 32 * kGatherWarpsR * kGatherWarpsC, 0, plan->stream>>>(plan->pts, plan->offsets, plan->Ng, plan->W,
                                                     plan->nbw, plan->inv_2s2,
                                                     reinterpret_cast<float2 *>(grids));
   return cudaGetLastError() == cudaSuccess ? MWAX_OK : MWAX_ERR_CUDA;
