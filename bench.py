@@ -73,14 +73,14 @@ def unpack_bytes_per_channel(spec) -> float:
 
 
 def unpack_kernel_name(spec) -> str:
-    """The unpack kernel the plan picks for this shape (TMA both ways where the
-    raw rows are whole 16-byte units and the tile fits, else the fallbacks)."""
+    """The unpack kernel the plan picks for this shape (the TMA tile kernel
+    where the raw rows are whole 16-byte units, else the fallbacks)."""
     n = spec.n_inputs
-    if os.environ.get("MWAX_UNPACK") is None and n <= 1024:
+    if os.environ.get("MWAX_UNPACK") is None:
         if spec.sample_bits == 8 and n % 8 == 0:
-            return "unpack8_tma2_kernel"
+            return "unpack8_tile_kernel"
         if spec.sample_bits == 4 and n % 16 == 0:
-            return "unpack4_tma2_kernel"
+            return "unpack4_tile_kernel"
     return "unpack_kernel<8>" if spec.sample_bits == 8 else "unpack4_line_kernel"
 
 
@@ -92,7 +92,7 @@ def unpack_roofline(spec, info, tim, steps, peaks, peak_src):
     traffic = None
     if (spec.sample_bits == 8 and spec.n_inputs == 1024 and spec.n_time == 10000
             and os.environ.get("MWAX_UNPACK") is None):
-        traffic = measured_traffic("unpack8_tma2_kernel|N1024|T10000", info.chan_group)
+        traffic = measured_traffic("unpack8_tile_kernel|N1024|T10000", info.chan_group)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": per_ch * info.chan_group,

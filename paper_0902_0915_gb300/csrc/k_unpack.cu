@@ -235,9 +235,7 @@ __global__ void __launch_bounds__(512) unpack4_persist_kernel(const uint8_t *__r
 
 constexpr int kPersistSmem = 64 * 1024;  // > what a correlate CTA leaves free on an SM
 
-// ---- TMA path -----------------------------------------------------------------
-constexpr int kTmaThreads = 512;
-constexpr int kTmaBufBytes = 64 * 1024;
+// ---- TMA tile path --------------------------------------------------------------
 
 __device__ __forceinline__ uint64_t u_globaltimer() {
   uint64_t t;
@@ -258,224 +256,6 @@ __device__ __forceinline__ bool u_wait(uint32_t bar, uint32_t parity, unsigned l
     if (ok) return true;
     if (u_globaltimer() - t0 > tmo) return false;
   }
-}
-
-// 8-bit samples, TMA both ways: the raw time block comes in with one bulk
-// copy; each thread converts whole operand rows (input i: 32 two-byte loads,
-// conflict-free) into a 128-byte-swizzled staging tile (16-byte stores,
-// conflict-free), and TMA tensor stores write the tile out, un-swizzling it
-// into the linear [row][128 B] operand layout in full lines.
-constexpr int kStageOutBytes = 128 * 1024;  // up to 1024 operand rows
-constexpr int kStoreBox = 128;              // rows per TMA store (n_rows is a multiple of 128)
-
-__global__ void __launch_bounds__(kTmaThreads, 1)
-    unpack8_tma2_kernel(const __grid_constant__ CUtensorMap out_map, const uint8_t *__restrict__ volt,
-                        int N, int T, int n_rows, int kb, int64_t chan0, int n_chan, int32_t *status,
-                        unsigned long long tmo) {
-  extern __shared__ __align__(1024) uint8_t sm_base[];
-  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
-                                            ~static_cast<uintptr_t>(1023));
-  uint8_t *stage = sm;                    // swizzled operand tile, 1024-B aligned
-  uint8_t *raw = sm + kStageOutBytes;     // raw time block
-  __shared__ __align__(8) uint64_t bar;
-  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
-  const int64_t tasks = (int64_t)n_chan * kb;
-  const int64_t row_bytes = (int64_t)N * 2;
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
-  }
-  __syncthreads();
-  auto issue = [&](int64_t k) {
-    const int c = (int)(k / kb), tb = (int)(k % kb);
-    const int rows = min(32, T - tb * 32);
-    const uint32_t bytes = (uint32_t)(rows * row_bytes);
-    const uint8_t *src = volt + ((chan0 + c) * (int64_t)T + (int64_t)tb * 32) * row_bytes;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            (uint32_t)__cvta_generic_to_shared(raw)),
-        "l"(src), "r"(bytes), "r"(b)
-        : "memory");
-  };
-  int64_t k = blockIdx.x;
-  if (threadIdx.x == 0 && k < tasks) issue(k);
-  uint32_t phase = 0;
-  bool ok = true;
-  const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
-  for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
-    if (!u_wait(b, phase, tmo)) {
-      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
-      ok = false;
-      break;
-    }
-    phase ^= 1u;
-    // the previous task's TMA stores must have finished reading the staging tile
-    if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-    __syncthreads();
-    const int c = (int)(k / kb), tb = (int)(k % kb);
-    const int rows = min(32, T - tb * 32);
-    for (int i = threadIdx.x; i < n_rows; i += kTmaThreads) {
-      uint32_t v[32];  // (re, im) of input i at sample s, low 16 bits
-#pragma unroll
-      for (int s2 = 0; s2 < 32; ++s2)
-        v[s2] = (i < N && s2 < rows) ? (uint32_t) * reinterpret_cast<const uint16_t *>(raw + s2 * row_bytes + 2 * i)
-                                     : 0u;
-      uint8_t *row = stage + (int64_t)i * kRowBytes;
-      const int sw = i & 7;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {  // chunk q: samples 8q .. 8q+7 (re), chunk 4+q (im)
-        uint32_t re4[4], im4[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const uint32_t x = v[8 * q + 2 * e], y = v[8 * q + 2 * e + 1];
-          re4[e] = s8pair_to_h2(__byte_perm(x, y, 0x0400));
-          im4[e] = s8pair_to_h2(__byte_perm(x, y, 0x0501));
-        }
-        *reinterpret_cast<uint4 *>(row + ((q ^ sw) << 4)) = make_uint4(re4[0], re4[1], re4[2], re4[3]);
-        *reinterpret_cast<uint4 *>(row + (((4 + q) ^ sw) << 4)) = make_uint4(im4[0], im4[1], im4[2], im4[3]);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // the raw buffer is free: fetch the next block while this one is stored
-      if (k + gridDim.x < tasks) issue(k + gridDim.x);
-      const int y0 = (int)(((int64_t)c * kb + tb) * n_rows);
-      for (int r0 = 0; r0 < n_rows; r0 += kStoreBox)
-        asm volatile(
-            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                reinterpret_cast<uint64_t>(&out_map)),
-            "r"(0), "r"(y0 + r0), "r"(stage_u32 + r0 * kRowBytes)
-            : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    }
-  }
-  if (threadIdx.x == 0) {
-    // stores must complete before the CTA exits; after a timeout also let a
-    // fetch still in flight land
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    if (!ok) u_wait(b, phase, tmo);
-  }
-  __syncthreads();
-}
-
-// 4-bit samples, TMA both ways.  Same pipeline as the 8-bit kernel; a raw
-// time block is 64 samples x N inputs (one byte each).  Thread t converts
-// inputs 4q .. 4q+3 (q = t mod n_rows/4) for half h = t / (n_rows/4) of the
-// block (samples 32h .. 32h+31), in two quarters of 16 samples: 16 four-byte
-// loads (conflict-free across the warp), nibbles -> E4M3 by byte permutes, and
-// one 16-byte chunk of re and one of im for each of its four rows.  At step k lane q writes row 4q + ((k + q/2) mod 4), so
-// the 8 lanes of a store phase hit 8 different swizzle groups (no bank
-// conflicts).  Block size and shared memory follow N, so small N runs
-// several CTAs per SM.
-__global__ void __launch_bounds__(kTmaThreads)
-    unpack4_tma2_kernel(const __grid_constant__ CUtensorMap out_map, const uint8_t *__restrict__ volt,
-                        int N, int T, int n_rows, int kb, int64_t chan0, int n_chan, int32_t *status,
-                        unsigned long long tmo) {
-  extern __shared__ __align__(1024) uint8_t sm_base[];
-  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
-                                            ~static_cast<uintptr_t>(1023));
-  uint8_t *stage = sm;                                  // swizzled operand tile, 1024-B aligned
-  uint8_t *raw = sm + (int64_t)n_rows * kRowBytes;      // raw time block (64 x N bytes)
-  __shared__ __align__(8) uint64_t bar;
-  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
-  const int64_t tasks = (int64_t)n_chan * kb;
-  const int quads = n_rows / 4;
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
-  }
-  __syncthreads();
-  auto issue = [&](int64_t k) {
-    const int c = (int)(k / kb), tb = (int)(k % kb);
-    const int rows = min(64, T - tb * 64);
-    const uint32_t bytes = (uint32_t)(rows * N);
-    const uint8_t *src = volt + ((chan0 + c) * (int64_t)T + (int64_t)tb * 64) * N;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            (uint32_t)__cvta_generic_to_shared(raw)),
-        "l"(src), "r"(bytes), "r"(b)
-        : "memory");
-  };
-  int64_t k = blockIdx.x;
-  if (threadIdx.x == 0 && k < tasks) issue(k);
-  uint32_t phase = 0;
-  bool ok = true;
-  const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
-  const int q = (int)threadIdx.x % quads, h = (int)threadIdx.x / quads;
-  const int i0 = 4 * q;
-  for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
-    if (!u_wait(b, phase, tmo)) {
-      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
-      ok = false;
-      break;
-    }
-    phase ^= 1u;
-    // the previous task's TMA stores must have finished reading the staging tile
-    if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-    __syncthreads();
-    const int c = (int)(k / kb), tb = (int)(k % kb);
-    const int rows = min(64, T - tb * 64);
-    if (h < 2) {
-#pragma unroll
-      for (int qq = 0; qq < 2; ++qq) {  // 16-sample quarter: one 16-byte chunk per row for re, one for im
-        uint32_t re[16], im[16];        // byte m = E4M3 of input i0+m at sample 32h + 16qq + r
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int sidx = 32 * h + 16 * qq + r;
-          const uint32_t w = (i0 < N && sidx < rows)
-                                 ? *reinterpret_cast<const uint32_t *>(raw + sidx * N + i0)
-                                 : 0u;
-          re[r] = nib4_to_e4m3(w);
-          im[r] = nib4_to_e4m3(w >> 4);
-        }
-        const int cre = 2 * h + qq, cim = 4 + 2 * h + qq;  // chunk indices in the row
-#pragma unroll
-        for (int step = 0; step < 4; ++step) {
-          const int kk = (step + (q >> 1)) & 3;  // which of the four rows this lane writes now
-          const uint32_t sel = (uint32_t)(kk | ((kk + 4) << 4));
-          uint32_t vr[4], vi[4];
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            vr[g] = __byte_perm(__byte_perm(re[4 * g], re[4 * g + 1], sel),
-                                __byte_perm(re[4 * g + 2], re[4 * g + 3], sel), 0x5410);
-            vi[g] = __byte_perm(__byte_perm(im[4 * g], im[4 * g + 1], sel),
-                                __byte_perm(im[4 * g + 2], im[4 * g + 3], sel), 0x5410);
-          }
-          const int row = i0 + kk;
-          const int sw = row & 7;
-          uint8_t *dst = stage + (int64_t)row * kRowBytes;
-          *reinterpret_cast<uint4 *>(dst + ((cre ^ sw) << 4)) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
-          *reinterpret_cast<uint4 *>(dst + ((cim ^ sw) << 4)) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
-        }
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // the raw buffer is free: fetch the next block while this one is stored
-      if (k + gridDim.x < tasks) issue(k + gridDim.x);
-      const int y0 = (int)(((int64_t)c * kb + tb) * n_rows);
-      for (int r0 = 0; r0 < n_rows; r0 += kStoreBox)
-        asm volatile(
-            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                reinterpret_cast<uint64_t>(&out_map)),
-            "r"(0), "r"(y0 + r0), "r"(stage_u32 + r0 * kRowBytes)
-            : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    }
-  }
-  if (threadIdx.x == 0) {
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    if (!ok) u_wait(b, phase, tmo);
-  }
-  __syncthreads();
 }
 
 // 8-bit samples, small footprint: one task is one 128-input tile of one
@@ -584,6 +364,117 @@ __global__ void __launch_bounds__(kTileThreads, 6)
   __syncthreads();
 }
 
+// 4-bit samples, small footprint: one task is one 128-input tile of one
+// 64-sample time block.  A 2D TMA load brings the raw box (64 samples x 128
+// bytes, rows N bytes apart; inputs past N read as zeros) into shared memory;
+// warp w converts samples 16w .. 16w+15, lane q the inputs 4q .. 4q+3 (four-byte
+// loads, nibbles -> E4M3 by byte permutes), writing one re and one im chunk
+// of each of its four rows with the row rotation that keeps the stores free
+// of bank conflicts; one TMA tensor store writes the 16 KB tile.  About 25 KB
+// of shared memory and 128 threads, so several CTAs share an SM and hide each
+// other's load latency.
+__global__ void __launch_bounds__(kTileThreads)
+    unpack4_tile_kernel(const __grid_constant__ CUtensorMap in_map,
+                        const __grid_constant__ CUtensorMap out_map, int N, int T, int n_tiles,
+                        int kb, int64_t chan0, int n_chan, int32_t *status,
+                        unsigned long long tmo) {
+  extern __shared__ __align__(1024) uint8_t sm_base[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
+                                            ~static_cast<uintptr_t>(1023));
+  uint8_t *stage = sm;                    // 128 rows x 128 B, swizzled
+  uint8_t *raw = sm + kTile * kRowBytes;  // 64 samples x 128 B
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  const int64_t tasks = (int64_t)n_chan * kb * n_tiles;  // tile fastest
+  const int n_rows = n_tiles * kTile;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
+  }
+  __syncthreads();
+  const uint32_t raw_u32 = (uint32_t)__cvta_generic_to_shared(raw);
+  auto issue = [&](int64_t k) {
+    const int tile = (int)(k % n_tiles);
+    const int64_t cb = k / n_tiles;
+    const int c = (int)(cb / kb), tb = (int)(cb % kb);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                 "r"((uint32_t)kTileRawBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(raw_u32),
+        "l"(reinterpret_cast<uint64_t>(&in_map)), "r"(tile * kTile),
+        "r"((int)((chan0 + c) * (int64_t)T + (int64_t)tb * 64)), "r"(b)
+        : "memory");
+  };
+  int64_t k = blockIdx.x;
+  if (threadIdx.x == 0 && k < tasks) issue(k);
+  uint32_t phase = 0;
+  bool ok = true;
+  const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
+  const int q = threadIdx.x & 31, quarter = threadIdx.x >> 5;
+  for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
+    if (!u_wait(b, phase, tmo)) {
+      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+    if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncthreads();
+    const int tile = (int)(k % n_tiles);
+    const int64_t cb = k / n_tiles;
+    const int c = (int)(cb / kb), tb = (int)(cb % kb);
+    const int rows = min(64, T - tb * 64);  // the box may run into the next channel
+    uint32_t re[16], im[16];                // byte m = E4M3 of input 4q+m at sample 16 quarter + r
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int sidx = 16 * quarter + r;
+      const uint32_t w = sidx < rows ? *reinterpret_cast<const uint32_t *>(raw + sidx * kTile + 4 * q) : 0u;
+      re[r] = nib4_to_e4m3(w);
+      im[r] = nib4_to_e4m3(w >> 4);
+    }
+    __syncthreads();  // raw is free: fetch the next task's box while this one is converted
+    if (threadIdx.x == 0 && k + gridDim.x < tasks) issue(k + gridDim.x);
+#pragma unroll
+    for (int step = 0; step < 4; ++step) {
+      const int kk = (step + (q >> 1)) & 3;
+      const uint32_t sel = (uint32_t)(kk | ((kk + 4) << 4));
+      uint32_t vr[4], vi[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        vr[g] = __byte_perm(__byte_perm(re[4 * g], re[4 * g + 1], sel),
+                            __byte_perm(re[4 * g + 2], re[4 * g + 3], sel), 0x5410);
+        vi[g] = __byte_perm(__byte_perm(im[4 * g], im[4 * g + 1], sel),
+                            __byte_perm(im[4 * g + 2], im[4 * g + 3], sel), 0x5410);
+      }
+      const int row = 4 * q + kk;
+      const int sw = row & 7;
+      uint8_t *dst = stage + row * kRowBytes;
+      *reinterpret_cast<uint4 *>(dst + ((quarter ^ sw) << 4)) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
+      *reinterpret_cast<uint4 *>(dst + (((4 + quarter) ^ sw) << 4)) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int y0 = (int)(((int64_t)c * kb + tb) * n_rows + tile * kTile);
+      asm volatile(
+          "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+              reinterpret_cast<uint64_t>(&out_map)),
+          "r"(0), "r"(y0), "r"(stage_u32)
+          : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (!ok) u_wait(b, phase, tmo);
+  }
+  __syncthreads();
+}
+
 }  // namespace
 
 cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
@@ -612,75 +503,9 @@ cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n
   return cudaGetLastError();
 }
 
-bool unpack_tma2_supported(int sample_bits, int n_inputs) {
-  const int n_rows = (n_inputs + kTile - 1) / kTile * kTile;
-  if (n_inputs < 1 || n_rows * kRowBytes > kStageOutBytes) return false;
-  // raw rows must be whole 16-byte units for the bulk copy: 2N (8-bit) or N (4-bit) bytes
-  if (sample_bits == 8) return n_inputs % 8 == 0 && 64 * n_inputs <= kTmaBufBytes;
-  if (sample_bits == 4) return n_inputs % 16 == 0 && 64 * n_inputs <= kTmaBufBytes;
-  return false;
-}
-
-cudaError_t launch_unpack_tma2(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
-                               int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op, int ctas,
-                               int32_t *status, unsigned long long timeout_ns, cudaStream_t s) {
-  const int n_rows = n_tiles * kTile;
-  if (n_chan <= 0) return cudaSuccess;
-  if (ctas < 1 || !unpack_tma2_supported(sample_bits, n_inputs)) return cudaErrorInvalidValue;
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void *ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return cudaErrorNotSupported;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  }
-  CUtensorMap map;
-  const cuuint64_t rows = (cuuint64_t)n_chan * kb * n_rows;
-  if (rows > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-  cuuint64_t dims[2] = {(cuuint64_t)kRowBytes, rows};
-  cuuint64_t strides[1] = {(cuuint64_t)kRowBytes};
-  cuuint32_t box[2] = {(cuuint32_t)kRowBytes, (cuuint32_t)kStoreBox};
-  cuuint32_t estr[2] = {1, 1};
-  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, op, dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return cudaErrorInvalidValue;
-  if (sample_bits == 8) {
-    const int smem = 1024 + kStageOutBytes + kTmaBufBytes;
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(unpack8_tma2_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
-    unpack8_tma2_kernel<<<ctas, kTmaThreads, smem, s>>>(map, volt, n_inputs, n_time, n_rows, kb,
-                                                        chan0, n_chan, status, timeout_ns);
-    return cudaGetLastError();
-  }
-  // 4-bit: two threads per input quad, staging and raw buffers sized to N;
-  // `ctas` is per-SM-count scaled by how many such CTAs fit on an SM
-  const int threads = n_rows / 2;  // 2 halves x n_rows/4 quads; multiple of 64, <= 512
-  const int smem = 1024 + n_rows * kRowBytes + 64 * n_inputs;
-  static bool attr4_set = false;
-  if (!attr4_set) {
-    cudaError_t e = cudaFuncSetAttribute(unpack4_tma2_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         1024 + kStageOutBytes + kTmaBufBytes);
-    if (e != cudaSuccess) return e;
-    attr4_set = true;
-  }
-  const int per_sm = std::max(1, std::min(4, (227 * 1024) / smem));
-  unpack4_tma2_kernel<<<ctas * per_sm, threads, smem, s>>>(map, volt, n_inputs, n_time, n_rows, kb,
-                                                           chan0, n_chan, status, timeout_ns);
-  return cudaGetLastError();
-}
-
 bool unpack_tile_supported(int sample_bits, int n_inputs) {
-  return sample_bits == 8 && n_inputs % 8 == 0;
+  // raw rows must be whole 16-byte units for the 2D TMA box
+  return (sample_bits == 8 && n_inputs % 8 == 0) || (sample_bits == 4 && n_inputs % 16 == 0);
 }
 
 int unpack_tile_smem_bytes() { return 1024 + kTile * kRowBytes + kTileRawBytes; }
@@ -701,14 +526,17 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
       return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
   }
-  // input: [ (chan0 + n_chan) * T rows ][ 2N bytes ], box 256 bytes x 32 rows, no swizzle
+  // input: [ (chan0 + n_chan) * T rows ][ row bytes ], no swizzle; the box is
+  // one 128-input tile of one time block: 256 B x 32 rows (8-bit samples) or
+  // 128 B x 64 rows (4-bit samples)
   const cuuint64_t in_rows = (cuuint64_t)(chan0 + n_chan) * n_time;
   const cuuint64_t out_rows = (cuuint64_t)n_chan * kb * n_tiles * kTile;
   if (in_rows > 0x7FFFFFFFull || out_rows > 0x7FFFFFFFull) return cudaErrorInvalidValue;
   CUtensorMap in_map, out_map;
-  cuuint64_t idims[2] = {(cuuint64_t)2 * n_inputs, in_rows};
-  cuuint64_t istr[1] = {(cuuint64_t)2 * n_inputs};
-  cuuint32_t ibox[2] = {256, 32};
+  const cuuint64_t row_bytes = (cuuint64_t)n_inputs * (sample_bits == 8 ? 2 : 1);
+  cuuint64_t idims[2] = {row_bytes, in_rows};
+  cuuint64_t istr[1] = {row_bytes};
+  cuuint32_t ibox[2] = {sample_bits == 8 ? 256u : 128u, sample_bits == 8 ? 32u : 64u};
   cuuint32_t estr[2] = {1, 1};
   if (encode(&in_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(volt), idims, istr, ibox,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -726,11 +554,18 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(unpack8_tile_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(unpack4_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  unpack8_tile_kernel<<<ctas, kTileThreads, smem, s>>>(in_map, out_map, n_inputs, n_time, n_tiles, kb,
-                                                       chan0, n_chan, status, timeout_ns);
+  if (sample_bits == 8)
+    unpack8_tile_kernel<<<ctas, kTileThreads, smem, s>>>(in_map, out_map, n_inputs, n_time, n_tiles,
+                                                         kb, chan0, n_chan, status, timeout_ns);
+  else
+    unpack4_tile_kernel<<<ctas, kTileThreads, smem, s>>>(in_map, out_map, n_inputs, n_time, n_tiles,
+                                                         kb, chan0, n_chan, status, timeout_ns);
   return cudaGetLastError();
 }
 

@@ -206,11 +206,11 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
   return c;
 }
 
-// Unpack variant: MWAX_UNPACK overrides (1 shared-memory transpose, 2
-// full-line, 4 TMA both ways); automatic = TMA both ways for shapes that allow
-// it (and whose sample buffer starts on a 16-byte boundary, which the bulk
-// copy needs), else the full-line kernel (4-bit) or the shared-memory
-// transpose.
+// Unpack variant: automatic = the TMA tile kernel (5) for shapes that allow it
+// (and whose sample buffer starts on a 16-byte boundary, which TMA needs),
+// else the full-line kernel (4-bit) or the shared-memory transpose; the
+// environment variable MWAX_UNPACK = 1 (shared-memory transpose) or 2
+// (full-line) forces a fallback, for comparisons.
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int unpack_choice(const JobState &s, const void *volt) {
@@ -218,27 +218,29 @@ int unpack_choice(const JobState &s, const void *volt) {
     const char *e = getenv("MWAX_UNPACK");
     return e ? atoi(e) : 0;
   }();
-  const bool tma_ok = unpack_tma2_supported(s.job.sample_bits, s.job.n_inputs) &&
-                      (reinterpret_cast<uintptr_t>(volt) & 15u) == 0;
-  if (env == 4) return tma_ok ? 4 : 0;
+  const bool aligned = (reinterpret_cast<uintptr_t>(volt) & 15u) == 0;
+  const bool tile_ok = unpack_tile_supported(s.job.sample_bits, s.job.n_inputs) && aligned;
   if (env == 1 || env == 2) return env;
-  return tma_ok ? 4 : 0;
+  return tile_ok ? 5 : 0;
 }
+
+// small-footprint unpack: CTAs per SM when it runs alone
+constexpr int kTileCtasPerSm = 6;
 
 mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
                          uint8_t *op, int ctas, cudaStream_t st) {
   TimedLaunch tu(p, 0, st);
   cudaError_t e;
   const int v = unpack_choice(s, volt);
-  if (p->overlap && p->unpack_sms == 0)
+  if (p->overlap && p->unpack_sms == 0)  // one tile CTA beside the correlate on every SM
     e = launch_unpack_tile(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb,
                            c0, nc, op, p->sm_count, p->status, p->timeout_ns, st);
-  else if (v == 4)
-    e = launch_unpack_tma2(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb,
-                           c0, nc, op, ctas > 0 ? ctas : p->sm_count, p->status, p->timeout_ns, st);
-  else if (ctas > 0)
+  else if (ctas > 0)  // overlapped on `ctas` SMs set aside
     e = launch_unpack_persistent(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
                                  s.kb, c0, nc, op, ctas, st);
+  else if (v == 5)
+    e = launch_unpack_tile(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb,
+                           c0, nc, op, p->sm_count * kTileCtasPerSm, p->status, p->timeout_ns, st);
   else
     e = launch_unpack(volt, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, c0,
                       nc, op, v, st);
@@ -599,10 +601,11 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
         for (int k = 0; k < nj && e == cudaSuccess; ++k) {
           const JobState &s = plan->jobs[k];
           const uint8_t *v = reinterpret_cast<const uint8_t *>(voltages[k]);
-          if (unpack_choice(s, v) == 4)
-            e = launch_unpack_tma2(v, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
-                                   s.kb, 0, s.job.n_chan, s.op, plan->sm_count, plan->status,
-                                   plan->timeout_ns, cs);
+          const int uv = unpack_choice(s, v);
+          if (uv == 5)
+            e = launch_unpack_tile(v, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles,
+                                   s.kb, 0, s.job.n_chan, s.op, plan->sm_count * kTileCtasPerSm,
+                                   plan->status, plan->timeout_ns, cs);
           else
             e = launch_unpack(v, s.job.sample_bits, s.job.n_inputs, s.job.n_time, s.n_tiles, s.kb, 0,
                               s.job.n_chan, s.op, 0, cs);

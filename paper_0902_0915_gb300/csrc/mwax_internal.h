@@ -38,21 +38,15 @@ cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n
                                      int n_time, int n_tiles, int kb, int64_t chan0, int n_chan,
                                      uint8_t *op, int ctas, cudaStream_t s);
 
-// 8-bit samples with TMA both ways (bulk copy in, swizzled staging tile, TMA
-// tensor stores out).  Needs N % 8 == 0 and N <= 1024.  (For 4-bit samples
-// the nibble conversion is heavier and the full-line kernel is faster.)
-bool unpack_tma2_supported(int sample_bits, int n_inputs);
-// Small-footprint unpack (one 128-input tile x one time block per task) that
-// fits beside a resident correlate CTA; 8-bit samples, n_inputs % 8 == 0.
+// TMA tile unpack (one 128-input tile x one time block per task, ~25 KB of
+// shared memory: several CTAs per SM when it runs alone, one beside a
+// resident correlate CTA when it overlaps); 8-bit samples with n_inputs % 8
+// == 0, 4-bit samples with n_inputs % 16 == 0.
 bool unpack_tile_supported(int sample_bits, int n_inputs);
 cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
                                int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
                                int ctas, int32_t *status, unsigned long long timeout_ns,
                                cudaStream_t s);
-cudaError_t launch_unpack_tma2(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
-                               int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op, int ctas,
-                               int32_t *status, unsigned long long timeout_ns, cudaStream_t s);
-
 // ---- tensor-core correlator -------------------------------------------------
 #define MWAX_MAX_JOBS 8
 

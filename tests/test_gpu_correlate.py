@@ -84,9 +84,9 @@ def test_tensor_small(mw, bits, N, T, C, shape):
                                    (1024, 70, 1), (1000, 45, 2), (256, 130, 3), (128, 64, 2),
                                    (304, 200, 2)])
 def test_tensor_tma_unpack_shapes(mw, bits, N, T, C):
-    """Shapes the TMA both-ways unpack takes (N a multiple of 8 for 8-bit and
-    of 16 for 4-bit samples, up to 1024 inputs) and shapes that fall back to
-    the other kernels, with ragged last time blocks."""
+    """Shapes the TMA tile unpack takes (N a multiple of 8 for 8-bit and of 16
+    for 4-bit samples; inputs past N in the last tile read as zeros) and shapes
+    that fall back to the other kernels, with ragged last time blocks."""
     spec = synth.Spec("tma", N, C, T, bits, seed=N + T + bits, sigma=2 if bits == 4 else 40,
                       tone_amp=0.3)
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tma {N},{T},{C}")
