@@ -84,7 +84,8 @@ typedef struct {
   int32_t engine;      /* mwax_engine                                          */
   int32_t flush_blocks;    /* tuning: K-blocks per exact FP32 segment (0 = largest safe) */
   int32_t chan_group;      /* tuning: channels unpacked per pass (0 = auto)              */
-  int32_t stages;          /* tuning: shared-memory stages, 2..3 narrow, 2..4 wide (0=auto)*/
+  int32_t stages;          /* tuning: shared-memory stages: 2 narrow (3 K blocks each),
+                              2..4 wide (0 = auto)                                        */
   int32_t prefetch;        /* tuning: K-blocks of L2 prefetch ahead, 1..64 (0 = auto,
                               which is none; -1 = none)                                   */
   int32_t mma_shape;       /* tuning: 1 = M128xN128 MMAs (Re, Im separately), 2 = M128xN256

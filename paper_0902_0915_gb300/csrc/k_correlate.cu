@@ -24,7 +24,7 @@
 //
 // Roles (one persistent CTA per SM, 10 warps):
 //   warp 0      single-thread TMA producer: tiles A_I and A_J of the next
-//               K blocks into a ring of shared-memory stages (two blocks per
+//               K blocks into a ring of shared-memory stages (three blocks per
 //               stage for the narrow shape; A_J skipped on diagonal tiles)
 //   warp 1      tensor-memory allocator and single-thread MMA issuer (one
 //               full-barrier wait and one commit per stage)
@@ -55,17 +55,18 @@ constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
 // memory by two extra warps.
 // A shared-memory stage holds `kps` consecutive K blocks behind one pair of
 // full/empty barriers.  An mbarrier wait costs the single issuing thread
-// about as much as two MMA issues, so the narrow shape takes two blocks
-// (16 MMAs) per wait and per commit.
+// about as much as two MMA issues, and every stage boundary leaves a bubble
+// in the tensor pipe, so the narrow shape takes three blocks (24 MMAs) per
+// wait and per commit: two stages of 96 KB.
 template <bool WIDE>
 struct Shape {
   static constexpr int warps = WIDE ? 12 : 10;
   static constexpr int conv_warps = WIDE ? 2 : 0;   // warps 2 .. 2+conv_warps-1
   static constexpr int epi0 = 2 + conv_warps;       // 8 epilogue warps from here
-  static constexpr int kps = WIDE ? 1 : 2;          // K blocks per stage
+  static constexpr int kps = WIDE ? 1 : 3;          // K blocks per stage
   static constexpr int block_bytes = (WIDE ? 3 : 2) * kTileBytes;  // [A | B (| B')] of one block
   static constexpr int stage_bytes = kps * block_bytes;
-  static constexpr int max_stages = WIDE ? 4 : 3;
+  static constexpr int max_stages = WIDE ? 4 : 2;
 };
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;  // re 128 | im 128

@@ -46,7 +46,7 @@ struct mwax_plan_s {
   int engine = MWAX_ENGINE_TENSOR;
   int sample_bits = 4;
   int kind = MWAX_KIND_EXACT;
-  int stages = 3;
+  int stages = 2;
   int prefetch = 0;
   int wide = 0;
   int withhold_seg = -1;

@@ -179,7 +179,7 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
   apply(&base, Cand{0, 0, 0, 0, 0});
   const int reps = 2;
   const std::vector<Cand> cands = {
-      {1, 3, -1, 1, 0}, {1, 2, -1, 1, 0}, {1, 3, 8, 1, 0}, {1, 3, -1, 2, 0},
+      {1, 2, -1, 1, 0}, {1, 2, 8, 1, 0}, {1, 2, -1, 2, 0},
       {2, 4, -1, 1, 0}, {2, 3, -1, 1, 0}, {2, 4, 8, 1, 0}, {2, 4, -1, 2, 0},
   };
   best_ms = -1.0;
@@ -209,8 +209,8 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
   mwax_tune_report rep;
   memset(&rep, 0, sizeof(rep));
   std::vector<mwax_job> base(jobs, jobs + n_jobs);
-  const std::vector<Cand> cands = {{1, 3, -1, 0, 0}, {1, 2, -1, 0, 0}, {1, 3, 8, 0, 0},
-                                   {2, 4, -1, 0, 0}, {2, 3, -1, 0, 0}, {2, 4, 8, 0, 0}};
+  const std::vector<Cand> cands = {{1, 2, -1, 0, 0}, {1, 2, 8, 0, 0}, {2, 4, -1, 0, 0},
+                                   {2, 3, -1, 0, 0}, {2, 4, 8, 0, 0}};
   Cand best{0, 0, 0, 0, 0};
   double best_ms = -1.0;
   for (const Cand &c : cands) {
