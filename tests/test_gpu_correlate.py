@@ -287,3 +287,27 @@ def test_full_size_c2_sampled(mw, shape):
     rng = np.random.default_rng(2)
     chans = sorted(set([0, spec.n_chan - 1] + rng.choice(spec.n_chan, 6, replace=False).tolist()))
     _full_size(mw, spec, chans, mma_shape=shape)
+
+
+def test_full_size_c3_batched_sampled(mw):
+    """The batched workload as the benchmark runs it: all four jobs (48, 128,
+    300 and 1024 inputs; 256 .. 3072 channels; T up to 20000) in one batch
+    plan (one graph of unpacks, one persistent correlate launch), checked on
+    sampled channels of every job (first, last and one inside)."""
+    import torch
+
+    specs = [synth.spec_c3(j) for j in range(4)]
+    torch.cuda.empty_cache()
+    vs = [device_volt(s) for s in specs]
+    bp = mw.BatchPlan([(s.n_inputs, s.n_chan, s.n_time) for s in specs], sample_bits=4)
+    outs = bp.correlate(vs)
+    assert bp.status() == 0
+    picks = []
+    for s, o in zip(specs, outs):
+        chans = [0, s.n_chan // 3, s.n_chan - 1]
+        picks.append((s, chans, o[chans].cpu().numpy()))
+    bp.close()
+    del vs, outs
+    torch.cuda.empty_cache()
+    for s, chans, got in picks:
+        assert_exact(got, oracle_for(s, chans), s.name)
