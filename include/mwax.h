@@ -132,7 +132,11 @@ typedef struct mwax_plan_s *mwax_plan_t;
  * Checks the shape, the int32 bound (MWAX_ERR_OVERFLOW_BOUND when
  * n_time * 2 * max^2 > INT32_MAX, max = 7 or 127), the device
  * (MWAX_ERR_UNSUPPORTED unless compute capability 10.3), and allocates the
- * plan's scratch on the current device.  *plan is NULL on failure. */
+ * plan's scratch on the current device.  *plan is NULL on failure.
+ * Test hook: with the environment variable MWAX_TEST_FAIL_ALLOC set to a
+ * non-zero value, plan scratch allocations (here and in mwax_plan_batch)
+ * fail with MWAX_ERR_OOM without allocating.  Every entry point of the
+ * library opens an NVTX range named after itself. */
 mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t stream);
 
 /* Plan several jobs (uneven N, C, T) that are correlated together by one

@@ -328,6 +328,7 @@ int64_t mwax_calib_workspace_bytes(int n_inputs, int n_chan) {
 mwax_status mwax_calib_loss_grad(const float *V, const float *M, const float *g, int n_inputs,
                                  int n_chan, void *workspace, float *loss, float *grad,
                                  cudaStream_t stream) {
+  mwax::NvtxRange nvtx_("mwax_calib_loss_grad");
   if (n_inputs < 2 || n_chan < 1 || n_inputs > 65536) return MWAX_ERR_INVALID_ARG;
   if (!loss && !grad) return MWAX_ERR_INVALID_ARG;
   if (!dev_ptr(V) || !dev_ptr(M) || !dev_ptr(g) || !dev_ptr(workspace)) return MWAX_ERR_INVALID_ARG;
@@ -360,6 +361,7 @@ int64_t mwax_calib_solve_workspace_bytes(int n_inputs, int n_chan) {
 
 mwax_status mwax_calib_solve(const float *V, const float *M, float *g, int n_inputs, int n_chan,
                              int n_iter, void *workspace, float *loss_hist, cudaStream_t stream) {
+  mwax::NvtxRange nvtx_("mwax_calib_solve");
   if (n_inputs < 2 || n_chan < 1 || n_inputs > 65536 || n_iter < 0) return MWAX_ERR_INVALID_ARG;
   if (!dev_ptr(V) || !dev_ptr(M) || !dev_ptr(g) || !dev_ptr(workspace)) return MWAX_ERR_INVALID_ARG;
   if (loss_hist && !dev_ptr(loss_hist)) return MWAX_ERR_INVALID_ARG;

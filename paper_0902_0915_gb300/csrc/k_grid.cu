@@ -348,6 +348,7 @@ extern "C" {
 mwax_status mwax_grid_plan(mwax_grid_plan_t *out, const double *tile_xy, int n_tiles, int n_chan,
                            double f0, double df, int Ng, double du, int W, double sigma,
                            cudaStream_t stream) {
+  mwax::NvtxRange nvtx_("mwax_grid_plan");
   if (!out || !tile_xy) return MWAX_ERR_INVALID_ARG;
   *out = nullptr;
   if (n_tiles < 2 || n_tiles > 4096 || n_chan < 1 || Ng < 8 || Ng > 16384 || Ng % 2 || W < 1 ||
@@ -434,6 +435,7 @@ mwax_status mwax_grid_plan(mwax_grid_plan_t *out, const double *tile_xy, int n_t
 int64_t mwax_grid_plan_points(mwax_grid_plan_t plan) { return plan ? plan->n_kept : -1; }
 
 mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids) {
+  mwax::NvtxRange nvtx_("mwax_grid");
   if (!plan || !is_dev(vis) || !is_dev(grids)) return MWAX_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(vis) & 7u) || (reinterpret_cast<uintptr_t>(grids) & 7u))
     return MWAX_ERR_INVALID_ARG;

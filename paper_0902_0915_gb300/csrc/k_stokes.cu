@@ -92,6 +92,7 @@ bool dev_ptr8(const void *p) {
 extern "C" mwax_status mwax_stokes(const float *inst, int n, double dl, double chi, float *stokes,
                                    cudaStream_t stream) {
   using namespace mwax;
+  NvtxRange nvtx_("mwax_stokes");
   if (n < 2 || n % 2 || n > 65536 || !(dl > 0.0)) return MWAX_ERR_INVALID_ARG;
   if (!dev_ptr8(inst) || !dev_ptr8(stokes) || inst == stokes) return MWAX_ERR_INVALID_ARG;
   const int64_t npix = (int64_t)n * n;

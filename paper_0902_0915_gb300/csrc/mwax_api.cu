@@ -87,6 +87,19 @@ struct mwax_plan_s {
 namespace mwax {
 namespace {
 
+// Device allocation of plan buffers.  Test hook: with MWAX_TEST_FAIL_ALLOC set
+// to a non-zero value, plan allocations report cudaErrorMemoryAllocation
+// without allocating (read on every call), so the OOM paths can be tested
+// without exhausting a device.
+cudaError_t plan_alloc(void **ptr, size_t bytes) {
+  const char *f = getenv("MWAX_TEST_FAIL_ALLOC");
+  if (f && *f && strcmp(f, "0") != 0) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
 mwax_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return MWAX_OK;
   if (e == cudaErrorMemoryAllocation) return MWAX_ERR_OOM;
@@ -404,6 +417,7 @@ int64_t mwax_max_n_time(int sample_bits) {
 }
 
 mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t stream) {
+  NvtxRange nvtx_("mwax_plan");
   if (!plan) return MWAX_ERR_INVALID_ARG;
   *plan = nullptr;
   if (!job) return MWAX_ERR_INVALID_ARG;
@@ -442,10 +456,10 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
     p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan && even &&
                  p->unpack_sms < p->sm_count;
     p->scratch_bytes = one * (p->overlap ? 2 : 1);
-    cudaError_t e = cudaMalloc(&p->scratch, (size_t)one);
+    cudaError_t e = plan_alloc(reinterpret_cast<void **>(&p->scratch), (size_t)one);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)one, stream);
     if (e == cudaSuccess && p->overlap) {
-      e = cudaMalloc(&p->scratch2, (size_t)one);
+      e = plan_alloc(reinterpret_cast<void **>(&p->scratch2), (size_t)one);
       if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch2, 0, (size_t)one, stream);
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
@@ -466,6 +480,7 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
 
 mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
                             cudaStream_t stream) {
+  NvtxRange nvtx_("mwax_plan_batch");
   if (!plan) return MWAX_ERR_INVALID_ARG;
   *plan = nullptr;
   if (!jobs || n_jobs < 1 || n_jobs > MWAX_MAX_JOBS) return MWAX_ERR_INVALID_ARG;
@@ -493,7 +508,7 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
     JobState s;
     s.job = jobs[k];
     derive(s);
-    cudaError_t e = cudaMalloc(&s.op, (size_t)(s.op_chan_bytes * s.job.n_chan));
+    cudaError_t e = plan_alloc(reinterpret_cast<void **>(&s.op), (size_t)(s.op_chan_bytes * s.job.n_chan));
     if (e == cudaSuccess)
       e = cudaMemsetAsync(s.op, 0, (size_t)(s.op_chan_bytes * s.job.n_chan), stream);
     p->jobs.push_back(s);
@@ -552,6 +567,7 @@ mwax_status mwax_plan_status(mwax_plan_t plan) {
 
 mwax_status mwax_correlate(mwax_plan_t plan, const void *voltages, int n_inputs, int n_chan,
                            int n_time, void *out) {
+  NvtxRange nvtx_("mwax_correlate");
   if (!plan || plan->batch) return MWAX_ERR_INVALID_ARG;
   const JobState &s = plan->jobs[0];
   if (n_inputs != s.job.n_inputs || n_chan != s.job.n_chan || n_time != s.job.n_time)
@@ -562,6 +578,7 @@ mwax_status mwax_correlate(mwax_plan_t plan, const void *voltages, int n_inputs,
 }
 
 mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, void *const *out) {
+  NvtxRange nvtx_("mwax_correlate_batch");
   if (!plan || !plan->batch || !voltages || !out) return MWAX_ERR_INVALID_ARG;
   const int nj = (int)plan->jobs.size();
   for (int k = 0; k < nj; ++k)
@@ -669,6 +686,7 @@ mwax_status mwax_plan_get_timing(mwax_plan_t plan, mwax_timing *t) {
 
 mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int n_inputs,
                                 int n_chan, int n_time, void *out_host) {
+  NvtxRange nvtx_("mwax_correlate_host");
   if (!plan || plan->batch || !voltages_host || !out_host) return MWAX_ERR_INVALID_ARG;
   JobState &s = plan->jobs[0];
   if (n_inputs != s.job.n_inputs || n_chan != s.job.n_chan || n_time != s.job.n_time)

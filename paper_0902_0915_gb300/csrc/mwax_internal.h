@@ -6,6 +6,18 @@
 
 #include "mwax.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace mwax {
+// NVTX range over one library call (visible in profilers; a no-op otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace mwax
+
 namespace mwax {
 
 // Tensor-core tiling: a tile is 128 inputs (the MMA M and N extent); an

@@ -158,6 +158,7 @@ extern "C" {
 
 mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaStream_t stream,
                           mwax_tune_report *report) {
+  mwax::NvtxRange nvtx_("mwax_autotune");
   if (!job || !voltages || !out) return MWAX_ERR_INVALID_ARG;
   mwax_tune_report rep;
   memset(&rep, 0, sizeof(rep));
@@ -205,6 +206,7 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
 
 mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *voltages,
                                 void *const *out, cudaStream_t stream, mwax_tune_report *report) {
+  mwax::NvtxRange nvtx_("mwax_autotune_batch");
   if (!jobs || n_jobs < 1 || !voltages || !out) return MWAX_ERR_INVALID_ARG;
   mwax_tune_report rep;
   memset(&rep, 0, sizeof(rep));

@@ -56,3 +56,22 @@ def test_status_word_clears_after_read(mw):
     assert p.status() == mw.STATUS_BY_NAME["MWAX_ERR_TIMEOUT"]
     assert p.status() == 0  # read-and-clear
     p.close()
+
+
+def test_allocation_failure_is_reported(mw, monkeypatch):
+    """Host-side injected fault: with the allocation test hook set, plan
+    creation returns MWAX_ERR_OOM (no abort, nothing leaked), and the next
+    plan without it works."""
+    import torch
+
+    monkeypatch.setenv("MWAX_TEST_FAIL_ALLOC", "1")
+    for make in (lambda: mw.Plan(64, 4, 100, 4),
+                 lambda: mw.BatchPlan([(48, 2, 100), (64, 3, 200)], sample_bits=4)):
+        with pytest.raises(mw.MwaxError) as ei:
+            make()
+        assert ei.value.status == mw.STATUS_BY_NAME["MWAX_ERR_OOM"]
+    monkeypatch.delenv("MWAX_TEST_FAIL_ALLOC")
+    p = mw.Plan(64, 4, 100, 4)
+    out = p.correlate(torch.zeros(64 * 4 * 100, dtype=torch.uint8, device="cuda"))
+    assert p.status() == 0 and int(out.abs().sum().item()) == 0
+    p.close()

@@ -1,8 +1,10 @@
 """Multi-rank channel sharding on CPU (gloo, world size 2 and 3): every rank
 correlates its own contiguous channel range, rank 0 gathers the blocks, and
-the concatenation equals the single-process result bit for bit.  The
-correlation on each rank is the CPU oracle here; on GPUs it is the library,
-with the same partition (bench.py --scaling strong)."""
+the concatenation equals the single-process result bit for bit; for the
+calibration, each rank's loss and gradient over its channels summed by one
+all-reduce equal the single-process values.  The arithmetic on each rank is
+the CPU oracle here; on GPUs it is the library, with the same partition
+(bench.py --scaling strong)."""
 import os
 import socket
 
@@ -73,3 +75,60 @@ def test_sharded_equals_single(world):
     spec = synth.spec_c0().with_(n_chan=11, n_time=200)
     ref = oracle.correlate(synth.fill_host(spec), 4, spec.n_inputs, spec.n_chan, spec.n_time)
     np.testing.assert_array_equal(got, ref)
+
+
+def _calib_worker(rank, world, port, q):
+    """Each rank evaluates the calibration loss and gradient on its own
+    channel range; one all-reduce (sum) of the 2N gradient components and the
+    loss gives the full result (the design's only collective)."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    V, M, g = _calib_problem()
+    c0, c1 = channel_range(V.shape[0], rank, world)
+    loss = oracle.calib_loss(V[c0:c1], M[c0:c1], g) if c1 > c0 else 0.0
+    grad = oracle.calib_grad(V[c0:c1], M[c0:c1], g, n_threads=1) if c1 > c0 else np.zeros_like(g)
+    t = torch.tensor(np.concatenate([[loss], grad.real, grad.imag]), dtype=torch.float64)
+    dist.all_reduce(t)
+    if rank == 0:
+        q.put(t.numpy())
+    dist.destroy_process_group()
+
+
+def _calib_problem():
+    rng = np.random.default_rng(9)
+    N, C = 12, 7
+    B = N * (N + 1) // 2
+    V = rng.standard_normal((C, B)) + 1j * rng.standard_normal((C, B))
+    M = rng.standard_normal((C, B)) + 1j * rng.standard_normal((C, B))
+    g = rng.uniform(0.8, 1.2, N) * np.exp(1j * rng.uniform(0, 2 * np.pi, N))
+    return V, M, g
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_calibration_allreduce(world):
+    import torch.multiprocessing as mp
+
+    import oracle
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_calib_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    V, M, g = _calib_problem()
+    N = g.shape[0]
+    ref_loss = oracle.calib_loss(V, M, g)
+    ref_grad = oracle.calib_grad(V, M, g)
+    assert got[0] == pytest.approx(ref_loss, rel=1e-12)
+    np.testing.assert_allclose(got[1:1 + N] + 1j * got[1 + N:], ref_grad, rtol=1e-11, atol=1e-12)
