@@ -917,6 +917,21 @@ def main():
             del vol
             torch.cuda.empty_cache()
             plan.correlate_host(hin, hout)  # warm-up (allocates the staging ring)
+            # the host link's own rate in this run (pinned 1 GB copies after one
+            # warm-up copy), for context: the link is shared with other work on
+            # the machine and varies between runs
+            nb = min(1 << 30, in_b)
+            dbuf = torch.empty(nb, dtype=torch.uint8, device=dev)
+            dbuf.copy_(hin[:nb], non_blocking=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(4):
+                dbuf.copy_(hin[k * nb:(k + 1) * nb] if (k + 1) * nb <= in_b else hin[:nb], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            link_h2d_gbs = 4 * nb / (e0.elapsed_time(e1) / 1e3) / 1e9
+            del dbuf
+            torch.cuda.empty_cache()
             # each call is one step: H2D of every channel group, compute, D2H of
             # the visibilities.  The host link is shared with other tenants of
             # the machine, so the step time is the median of the timed calls.
@@ -931,7 +946,9 @@ def main():
             line["e2e"] = {"value": total_units / dt / 1e12, "unit": "TCMAC/s",
                            "h2d_bytes_per_step": in_b, "d2h_bytes_per_step": out_b,
                            "ms_per_step": dt * 1e3, "steps": n_e2e, "statistic": "median",
-                           "ms_min": min(times) * 1e3, "ms_max": max(times) * 1e3}
+                           "ms_min": min(times) * 1e3, "ms_max": max(times) * 1e3,
+                           "link_h2d_gbs": link_h2d_gbs,
+                           "link_bound_value": total_units / (in_b / (link_h2d_gbs * 1e9)) / 1e12}
 
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_budget)

@@ -339,7 +339,7 @@ mwax_status mwax_stokes(const float *inst, int n, double dl, double chi, float *
  * process exits; this call allocates nothing.
  *   - Shapes whose mwax_calib_workspace_bytes(n_inputs, n_chan) exceeds the
  *     array are rejected with MWAX_ERR_INVALID_ARG before any launch
- *     (1024 inputs need about 2.2 MB, for any n_chan).
+ *     (1024 inputs need about 3.3 MB, for any n_chan; up to about 1150 inputs fit).
  *   - The first call on each device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
  *   - All calls on a device share the array: calls that overlap on the GPU
