@@ -586,7 +586,8 @@ def run_stokes(args):
                        "pixels_above_horizon": up,
                        "l2": f"{bytes_step / 1e9:.2f} GB per call > L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
-                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
+                         "traffic": measured_traffic("stokes_kernel|4096", 1) if n == 4096 else None,
                          "kernel": "stokes_kernel", "peak_source": src},
             "gpu_launches": args.steps, "clocks": clk}
     if not args.no_cpu:
@@ -662,7 +663,8 @@ def run_calib(args):
             "data": "synthetic (V from correlating seeded c4-style voltages; point-source model)",
             "config": {"workload": f"c4: {desc}", "l2": f"V + M {2 * 8 * B * C / 1e9:.1f} GB > L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
-                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
+                         "traffic": measured_traffic("calib_step|N1024", C) if N == 1024 else None,
                          "kernel": "calib_tile_kernel + calib_gather_kernel (one step)",
                          "peak_source": src},
             "loss": float(loss), "gpu_launches": 2 * args.steps, "clocks": clk}
@@ -684,7 +686,8 @@ def run_calib(args):
                      "loss_start": float(hist[0]), "loss_after": float(loss_final),
                      "roofline": {"bound": "hbm", "achieved": achieved_s, "peak": float(peaks["hbm_gbs"]),
                                   "unit": "GB/s", "frac": achieved_s / float(peaks["hbm_gbs"]),
-                                  "traffic": None,
+                                  "traffic": (measured_traffic("calib_sweep|N1024", C)
+                                              if N == 1024 else None),
                                   "kernel": "calib_tile_kernel<den> + calib_gather_kernel<solve> (one sweep)",
                                   "peak_source": src},
                      "gpu_launches": 2 * n_sweeps}

@@ -92,13 +92,16 @@ def test_tensor_tma_unpack_shapes(mw, bits, N, T, C):
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tma {N},{T},{C}")
 
 
-@pytest.mark.parametrize("N,T,C,G", [(256, 1000, 12, 5), (200, 77, 7, 3), (1024, 100, 4, 1),
-                                     (136, 33, 5, 2)])
-def test_overlapped_coresident_unpack(mw, N, T, C, G):
+@pytest.mark.parametrize("bits,N,T,C,G", [(8, 256, 1000, 12, 5), (8, 200, 77, 7, 3),
+                                          (8, 1024, 100, 4, 1), (8, 136, 33, 5, 2),
+                                          (4, 256, 1000, 12, 5), (4, 208, 77, 7, 3),
+                                          (4, 144, 33, 5, 2)])
+def test_overlapped_coresident_unpack(mw, bits, N, T, C, G):
     """pipeline 2 with the small unpack CTA beside the correlate on every SM:
     several channel groups (ragged last group), N not a multiple of 128 (the
     raw box reads past N as zeros), ragged last time block."""
-    spec = synth.Spec("ov", N, C, T, 8, seed=N + T + C, sigma=40, tone_amp=0.3)
+    spec = synth.Spec("ov", N, C, T, bits, seed=N + T + C, sigma=40 if bits == 8 else 2,
+                      tone_amp=0.3)
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR, pipeline=2, chan_group=G),
                  oracle_for(spec, range(C)), f"overlap {N},{T},{C},{G}")
 
