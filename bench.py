@@ -49,16 +49,22 @@ def sky_seconds(spec) -> float:
     return spec.n_time / spec.chan_width_hz
 
 
-def measured_traffic(kernel_key: str, channels_per_launch: int):
-    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
-    scaled by channels (traffic grows in proportion), or None."""
+def traffic_entry(kernel_key: str):
+    """The committed ncu traffic record for a kernel and shape
+    (profiles/traffic.json), or None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    e = d.get(kernel_key)
+    return d.get(kernel_key)
+
+
+def measured_traffic(kernel_key: str, channels_per_launch: int):
+    """DRAM bytes per launch from the committed ncu capture, scaled by channels
+    (traffic grows in proportion), or None."""
+    e = traffic_entry(kernel_key)
     return None if e is None else e["bytes_per_channel"] * channels_per_launch
 
 
@@ -89,10 +95,8 @@ def unpack_roofline(spec, info, tim, steps, peaks, peak_src):
     per_ch = unpack_bytes_per_channel(spec)
     achieved = per_ch * spec.n_chan * steps / (tim.unpack_ms / 1e3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    traffic = None
-    if (spec.sample_bits == 8 and spec.n_inputs == 1024 and spec.n_time == 10000
-            and os.environ.get("MWAX_UNPACK") is None):
-        traffic = measured_traffic("unpack8_tile_kernel|N1024|T10000", info.chan_group)
+    traffic = measured_traffic(f"{unpack_kernel_name(spec)}|N{spec.n_inputs}|T{spec.n_time}",
+                               info.chan_group)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": per_ch * info.chan_group,
@@ -225,10 +229,17 @@ def cpu_baseline(spec, budget_s: float):
         chans.append(c)
         c += max(1, spec.n_chan // 16)
     units = cmacs(spec) / spec.n_chan * n_done
+    # the same oracle on one thread, one channel (the first of the sample)
+    v = synth.fill_host(spec, chans=[0])
+    t0 = time.perf_counter()
+    oracle.correlate(v, spec.sample_bits, spec.n_inputs, 1, spec.n_time, n_threads=1)
+    t1 = time.perf_counter() - t0
     return {"value": units / t_total / 1e12, "unit": "TCMAC/s", "cores": oracle.threads(),
             "kind": "oracle",
             "sample": f"{n_done} of {spec.n_chan} channels ({chans[0]}..{chans[-1]} step "
-                      f"{max(1, spec.n_chan // 16)}), full N and T; {units:.3g} CMAC in {t_total:.1f} s"}
+                      f"{max(1, spec.n_chan // 16)}), full N and T; {units:.3g} CMAC in {t_total:.1f} s",
+            "one_thread": {"value": cmacs(spec) / spec.n_chan / t1 / 1e12, "unit": "TCMAC/s",
+                           "cores": 1, "sample": f"channel 0, full N and T, {t1:.1f} s"}}
 
 
 def run_reference(args, spec, desc, world, rank):
@@ -840,17 +851,18 @@ def main():
     info = plan.info()
     if engine == mw.ENGINE_TENSOR and tim.correlate_ms > 0:
         achieved = 8.0 * units * args.steps / (tim.correlate_ms / 1e3) / 1e12
-        traffic = None
-        if (info.mma_shape == 1 and rspec.sample_bits == 8 and rspec.n_inputs == 1024
-                and rspec.n_time == 10000 and rspec.kind == synth.SYNTH_NOISE_TONE):
-            traffic = measured_traffic("correlate_tc_kernel<8,EXACT,narrow>|N1024|T10000",
-                                       info.chan_group)
+        tkey = (f"correlate_tc_kernel<{rspec.sample_bits},EXACT,"
+                f"{'narrow' if info.mma_shape == 1 else 'wide'}>|N{rspec.n_inputs}|T{rspec.n_time}")
+        tent = traffic_entry(tkey)
+        traffic = tent["bytes_per_channel"] * info.chan_group if tent else None
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": traffic,
-                    "traffic_note": "DRAM bytes per launch of chan_group channels, scaled from a "
-                                    "64-channel ncu capture (profiles/traffic.json); algorithmic "
-                                    "bytes per launch: operands + visibilities = "
-                                    f"{45223936.0 * info.chan_group:.4g}" if traffic else None,
+                    "traffic_note": (f"DRAM bytes per launch of chan_group channels, scaled from a "
+                                     f"{tent['capture_channels']}-channel ncu capture "
+                                     f"(profiles/traffic.json); algorithmic bytes per launch: "
+                                     f"operands + visibilities = "
+                                     f"{tent['algorithmic_bytes_per_channel'] * info.chan_group:.4g}"
+                                     if tent else None),
                     "kernel": "correlate_tc_kernel", "peak_source": peak_note,
                     "kernel_ms_per_launch": tim.correlate_ms / max(1, tim.correlate_launches),
                     "unpack_ms_per_step": tim.unpack_ms / args.steps,
