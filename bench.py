@@ -105,6 +105,17 @@ def unpack_roofline(spec, info, tim, steps, peaks, peak_src):
             "ms_per_launch": tim.unpack_ms / max(1, tim.unpack_launches)}
 
 
+def tensor_peak_at_clock(sample_bits: int, clk, sms: int):
+    """Context for the tensor roofline: the dense MMA rate at the SM clock
+    sampled during the timed region (8,192 FLOP per SM per cycle for
+    kind::f16, twice that for kind::f8f6f4 E4M3), beside the measured cuBLAS
+    figure, which was taken at a lower, power-capped clock."""
+    if not clk or not clk.get("sm_mhz"):
+        return None
+    per_sm = 8192 if sample_bits == 8 else 16384
+    return per_sm * sms * clk["sm_mhz"] * 1e6 / 1e12
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -406,6 +417,10 @@ def run_batch(args):
                 "kernel_ms_per_launch": tim.correlate_ms / max(1, tim.correlate_launches),
                 "unpack_ms_per_step": tim.unpack_ms / args.steps},
             "gpu_launches": int(5 * args.steps), "clocks": clk}
+    pk = tensor_peak_at_clock(4, clk, torch.cuda.get_device_properties(0).multi_processor_count)
+    if line["roofline"] is not None and pk:
+        line["roofline"]["peak_at_clock"] = {"tflops": pk, "frac": achieved / pk,
+                                             "note": "dense E4M3 MMA rate at the median SM clock sampled"}
     if rep is not None:
         line["config"]["autotune"] = {"candidates": rep.candidates, "best_ms": rep.best_ms,
                                       "default_ms": rep.default_ms}
@@ -852,7 +867,8 @@ def main():
     if engine == mw.ENGINE_TENSOR and tim.correlate_ms > 0:
         achieved = 8.0 * units * args.steps / (tim.correlate_ms / 1e3) / 1e12
         tkey = (f"correlate_tc_kernel<{rspec.sample_bits},EXACT,"
-                f"{'narrow' if info.mma_shape == 1 else 'wide'}>|N{rspec.n_inputs}|T{rspec.n_time}")
+                f"{ {1: 'narrow', 2: 'wide', 3: 'pair'}.get(info.mma_shape, 'narrow') }>"
+                f"|N{rspec.n_inputs}|T{rspec.n_time}")
         tent = traffic_entry(tkey)
         traffic = tent["bytes_per_channel"] * info.chan_group if tent else None
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -869,6 +885,11 @@ def main():
                     "correlate_ms_per_step": tim.correlate_ms / args.steps}
         if tim.unpack_ms > 0:
             roofline["unpack"] = unpack_roofline(rspec, info, tim, args.steps, peaks, peak_src)
+        pk = tensor_peak_at_clock(rspec.sample_bits, clk,
+                                  torch.cuda.get_device_properties(dev).multi_processor_count)
+        if pk:
+            roofline["peak_at_clock"] = {"tflops": pk, "frac": achieved / pk,
+                                         "note": "dense MMA rate at the median SM clock sampled"}
     else:
         roofline = None
 

@@ -85,11 +85,16 @@ typedef struct {
   int32_t flush_blocks;    /* tuning: K-blocks per exact FP32 segment (0 = largest safe) */
   int32_t chan_group;      /* tuning: channels unpacked per pass (0 = auto)              */
   int32_t stages;          /* tuning: shared-memory stages: 2 narrow (3 K blocks each),
-                              2..4 wide (0 = auto)                                        */
+                              2..4 wide, 2 pair (2 K blocks each) (0 = auto)               */
   int32_t prefetch;        /* tuning: K-blocks of L2 prefetch ahead, 1..64 (0 = auto,
                               which is none; -1 = none)                                   */
   int32_t mma_shape;       /* tuning: 1 = M128xN128 MMAs (Re, Im separately), 2 = M128xN256
-                              MMAs with [Re | Im] at once (0 = auto)                     */
+                              MMAs with [Re | Im] at once, 3 = two tile pairs (I, J),
+                              (I, J+1) per work item with M128xN256 MMAs against the
+                              tiles of J and J+1 (only when the whole integration is one
+                              exact FP32 segment: 4-bit samples with n_time <= 171,136,
+                              the FP16 kind, or flush_blocks >= the time blocks; else
+                              MWAX_ERR_UNSUPPORTED); 0 = auto: 3 where it applies, else 1 */
   int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
                               plan's stream, 2 = unpack the next group (second stream,
                               second scratch buffer) while the current group correlates,
@@ -118,10 +123,11 @@ typedef struct {
   int32_t grid;              /* persistent CTAs of the correlate kernel                */
   int32_t stages;            /* shared-memory pipeline stages                          */
   int32_t prefetch;          /* K-blocks of L2 prefetch ahead of the TMA loads         */
-  int32_t mma_shape;         /* 1 = N128, 2 = N256                                     */
+  int32_t mma_shape;         /* 1 = N128, 2 = N256 [Re | Im], 3 = two pairs per item   */
   int32_t pipeline;          /* 1 = sequential, 2 = overlapped unpack/correlate        */
   int64_t scratch_bytes;     /* device scratch owned by the plan                       */
-  int64_t work_items;        /* (job, channel, tile pair) items per call               */
+  int64_t work_items;        /* work items per call: (job, channel, tile pair), or the
+                                two-pair items of mma_shape 3                          */
 } mwax_plan_info;
 
 typedef struct mwax_plan_s *mwax_plan_t;

@@ -34,6 +34,17 @@
 // 512 tensor-memory columns so the epilogue of one segment overlaps the
 // MMAs of the next.
 //
+// Pair mode (jobs whose whole integration is one exact segment: 4-bit
+// samples up to 171,136 time samples, and the FP16 variant): a work item
+// holds two tile pairs, usually (I, J) and (I, J+1) of one channel, so one
+// M=128 N=256 MMA against the consecutive shared-memory tiles [A_J | A_J+1]
+// produces both; the A tile is loaded once for the two pairs and the tensor
+// pipe runs 136-cycle instructions, which hide the issuing thread's barrier
+// waits.  The 512 columns then hold one item (Re of both pairs in [0, 256),
+// Im in [256, 512)); the epilogue converts it once and stores it through a
+// per-warp shared-memory transpose, so every store instruction writes whole
+// 128-byte row segments.
+//
 // Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the
 // kernel records MWAX_ERR_TIMEOUT in the plan's status word, stops issuing,
 // waits (bounded) for its own copies and MMAs in flight, frees its tensor
@@ -49,24 +60,29 @@ namespace {
 
 constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
 
-// Two MMA shapes.  Narrow: eight M=128 N=128 MMAs per block (Re and Im
-// separately, negate-B bit for the minus sign).  Wide: four M=128 N=256 MMAs
-// per block against B = [A_J ; B'_J], B'_J = [-im_j | re_j] built in shared
-// memory by two extra warps.
+// Three MMA shapes (MODE).  0, narrow: eight M=128 N=128 MMAs per block (Re
+// and Im separately, negate-B bit for the minus sign).  1, wide: four M=128
+// N=256 MMAs per block against B = [A_J ; B'_J], B'_J = [-im_j | re_j] built
+// in shared memory by two extra warps.  2, pair: work items of two tile
+// pairs (see the header), up to three tiles per block.
 // A shared-memory stage holds `kps` consecutive K blocks behind one pair of
 // full/empty barriers.  An mbarrier wait costs the single issuing thread
-// about as much as two MMA issues, and every stage boundary leaves a bubble
-// in the tensor pipe, so the narrow shape takes three blocks (24 MMAs) per
-// wait and per commit: two stages of 96 KB.
-template <bool WIDE>
+// about as much as two N=128 MMA issues, and every stage boundary leaves a
+// bubble in the tensor pipe, so the narrow shape takes three blocks (24
+// MMAs) per wait and per commit: two stages of 96 KB.
+constexpr int kModeNarrow = 0, kModeWide = 1, kModePair = 2;
+constexpr int kEpiStageBytes = 32 * 128;  // pair mode: one warp's 32 rows x 16 (re, im) words
+
+template <int MODE>
 struct Shape {
-  static constexpr int warps = WIDE ? 12 : 10;
-  static constexpr int conv_warps = WIDE ? 2 : 0;   // warps 2 .. 2+conv_warps-1
-  static constexpr int epi0 = 2 + conv_warps;       // 8 epilogue warps from here
-  static constexpr int kps = WIDE ? 1 : 3;          // K blocks per stage
-  static constexpr int block_bytes = (WIDE ? 3 : 2) * kTileBytes;  // [A | B (| B')] of one block
+  static constexpr int warps = MODE == kModeWide ? 12 : 10;
+  static constexpr int conv_warps = MODE == kModeWide ? 2 : 0;  // warps 2 .. 2+conv_warps-1
+  static constexpr int epi0 = 2 + conv_warps;                   // 8 epilogue warps from here
+  static constexpr int kps = MODE == kModeWide ? 1 : MODE == kModePair ? 2 : 3;  // K blocks per stage
+  static constexpr int block_bytes = (MODE == kModeNarrow ? 2 : 3) * kTileBytes;  // tiles of one block
   static constexpr int stage_bytes = kps * block_bytes;
-  static constexpr int max_stages = WIDE ? 4 : 2;
+  static constexpr int max_stages = MODE == kModeWide ? 4 : 2;
+  static constexpr int epi_bytes = MODE == kModePair ? 8 * kEpiStageBytes : 0;
 };
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;  // re 128 | im 128
@@ -83,6 +99,7 @@ struct KJob {
 struct KParams {
   KJob job[kMaxJobs];
   int32_t *status;
+  const int4 *items;  // pair mode: the work list (n_items entries)
   int64_t n_items;
   unsigned long long timeout_ns;
   int32_t n_jobs, stages, prefetch;
@@ -266,16 +283,299 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-template <int BITS, int KIND, bool WIDE>
-__global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
+// ---- pair-mode work items -------------------------------------------------
+// One int4 per item: x = channel of the first pair, y = channel of the second
+// (both relative to the launch's first channel), z = job | type << 8 |
+// I0 << 16 | J0 << 24, w = I1 | J1 << 8.
+//   kItemShared:  (I0, J0) and (I0, J1 = J0 + 1 <= I0) of channel x; tiles
+//                 [A_J0 | A_J1 | A_I0] (two tiles, [A_J0 | A_I0], when J1 = I0)
+//   kItemTwoDiag: (I0, I0) of channel x and (I1, I1) of channel y; [A_I0 | A_I1]
+//   kItemOne:     (I0, J0) of channel x alone; [A_I0 | A_J0] ([A_I0] if diagonal)
+enum : uint32_t { kItemOne = 0, kItemShared = 1, kItemTwoDiag = 2 };
+
+struct PairItem {
+  int job, type, c0, c1, I0, J0, I1, J1;
+};
+
+__device__ __forceinline__ PairItem decode_pair_item(const int4 d) {
+  const uint32_t z = (uint32_t)d.z, w = (uint32_t)d.w;
+  PairItem it;
+  it.c0 = d.x;
+  it.c1 = d.y;
+  it.job = (int)(z & 0xFFu);
+  it.type = (int)((z >> 8) & 0xFFu);
+  it.I0 = (int)((z >> 16) & 0xFFu);
+  it.J0 = (int)(z >> 24);
+  it.I1 = (int)(w & 0xFFu);
+  it.J1 = (int)((w >> 8) & 0xFFu);
+  return it;
+}
+
+// The eight M=128 N=128 MMAs of one K block of one tile pair.
+template <int BITS>
+__device__ __forceinline__ void narrow_block(uint32_t d_re, uint32_t d_im, uint64_t da, uint64_t db,
+                                             uint32_t acc0) {
+  constexpr uint32_t id = make_idesc(false, kTile), idn = make_idesc(true, kTile);
+  tc_mma<BITS>(d_re, da + 0, db + 0, id, acc0);
+  tc_mma<BITS>(d_re, da + 2, db + 2, id, 1u);
+  tc_mma<BITS>(d_re, da + 4, db + 4, id, 1u);
+  tc_mma<BITS>(d_re, da + 6, db + 6, id, 1u);
+  tc_mma<BITS>(d_im, da + 4, db + 0, id, acc0);
+  tc_mma<BITS>(d_im, da + 6, db + 2, id, 1u);
+  tc_mma<BITS>(d_im, da + 0, db + 4, idn, 1u);
+  tc_mma<BITS>(d_im, da + 2, db + 6, idn, 1u);
+}
+
+// The three roles in pair mode (warp 0: producer, warp 1: MMA issuer, warps
+// 2..9: epilogue).  Barriers as in the kernel: full[0..S) empty[S..2S)
+// tfull[3S] tempty[3S+2] drain[3S+4] (one accumulator buffer: index 0 only).
+template <int BITS, int KIND>
+__device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, uint32_t smem_base,
+                                           uint8_t *epi_smem, uint32_t bar0, uint32_t tmem_base,
+                                           volatile int *abort_flag, volatile int *epi_flag,
+                                           int warp, int lane) {
+  using Sh = Shape<kModePair>;
+  constexpr int kStageBytes = Sh::stage_bytes;
+  const int S = p.stages;
+  const unsigned long long tmo = p.timeout_ns;
+  auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(S + s); };
+  const uint32_t tfull = bar0 + 8u * (uint32_t)(3 * S);
+  const uint32_t tempty = bar0 + 8u * (uint32_t)(3 * S + 2);
+  const uint32_t drain = bar0 + 8u * (uint32_t)(3 * S + 4);
+
+  if (warp == 0) {
+    // ---------------- TMA producer (one thread) ----------------
+    if (lane == 0) {
+      for (int j = 0; j < p.n_jobs; ++j)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[j]))
+                     : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t issued = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        const PairItem it = decode_pair_item(__ldg(p.items + item));
+        const KJob &jb = p.job[it.job];
+        const CUtensorMap *map = &maps.m[it.job];
+        const int n_rows = jb.n_tiles * kTile;
+        const int y0 = it.c0 * jb.kb * n_rows, y1 = it.c1 * jb.kb * n_rows;
+        // first row of each tile of the item at K block 0, in shared-memory order
+        int ys[3] = {0, 0, 0};
+        int nt;
+        if (it.type == kItemShared) {
+          ys[0] = y0 + it.J0 * kTile;
+          ys[1] = y0 + it.J1 * kTile;  // A_I itself when J1 == I0
+          ys[2] = y0 + it.I0 * kTile;
+          nt = it.J1 == it.I0 ? 2 : 3;
+        } else if (it.type == kItemTwoDiag) {
+          ys[0] = y0 + it.I0 * kTile;
+          ys[1] = y1 + it.I1 * kTile;
+          nt = 2;
+        } else {
+          ys[0] = y0 + it.I0 * kTile;
+          ys[1] = y0 + it.J0 * kTile;
+          nt = it.I0 == it.J0 ? 1 : 2;
+        }
+        const uint32_t blk_bytes = (uint32_t)nt * kTileBytes;
+        for (int kb = 0; kb < jb.kb; kb += Sh::kps) {
+          const int nb = min(Sh::kps, jb.kb - kb);
+          if (!mbar_wait(empty(stage), phase ^ 1u, abort_flag, tmo)) {
+            raise_timeout(abort_flag, p.status);
+            ok = false;
+            break;
+          }
+          const uint32_t a = smem_base + (uint32_t)stage * kStageBytes;
+          mbar_arrive_expect_tx(full(stage), (uint32_t)nb * blk_bytes);
+          for (int j = 0; j < nb; ++j)
+            for (int t = 0; t < nt; ++t)
+              tma_load_2d(a + (uint32_t)(j * Sh::block_bytes + t * kTileBytes), map, 0,
+                          ys[t] + (kb + j) * n_rows, full(stage));
+          ++issued;
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // wait (bounded) until every copy this thread issued has landed
+      int st = stage;
+      uint32_t ph = phase;
+      for (int64_t k = 0; k < issued && k < S; ++k) {
+        if (--st < 0) {
+          st = S - 1;
+          ph ^= 1u;
+        }
+        mbar_wait(full(st), ph, nullptr, tmo);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (one thread) ----------------
+    if (lane == 0) {
+      constexpr uint32_t id = make_idesc(false, 2 * kTile), idn = make_idesc(true, 2 * kTile);
+      const uint32_t d_re = tmem_base, d_im = tmem_base + 2 * kTile;
+      int stage = 0;
+      uint32_t phase = 0, n_it = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        const PairItem it = decode_pair_item(__ldg(p.items + item));
+        const int KB = p.job[it.job].kb;
+        // the accumulator is free once the epilogue has read the previous item
+        if (!mbar_wait(tempty, (n_it & 1u) ^ 1u, abort_flag, tmo)) {
+          raise_timeout(abort_flag, p.status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_off = it.J1 == it.I0 ? kTileBytes : 2 * kTileBytes;  // A_I of a shared item
+        for (int kb = 0; kb < KB; kb += Sh::kps) {
+          const int nb = min(Sh::kps, KB - kb);
+          if (!mbar_wait(full(stage), phase, abort_flag, tmo)) {
+            raise_timeout(abort_flag, p.status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int j = 0; j < nb; ++j) {
+            const uint32_t a = smem_base + (uint32_t)stage * kStageBytes + (uint32_t)(j * Sh::block_bytes);
+            const uint32_t acc0 = kb + j == 0 ? 0u : 1u;
+            if (it.type == kItemShared) {
+              // B = [A_J0 ; A_J1]: columns 0..127 give pair (I, J0), 128..255 pair (I, J1)
+              const uint64_t da = sw128_desc(a + a_off), db = sw128_desc(a);
+              tc_mma<BITS>(d_re, da + 0, db + 0, id, acc0);
+              tc_mma<BITS>(d_re, da + 2, db + 2, id, 1u);
+              tc_mma<BITS>(d_re, da + 4, db + 4, id, 1u);
+              tc_mma<BITS>(d_re, da + 6, db + 6, id, 1u);
+              tc_mma<BITS>(d_im, da + 4, db + 0, id, acc0);
+              tc_mma<BITS>(d_im, da + 6, db + 2, id, 1u);
+              tc_mma<BITS>(d_im, da + 0, db + 4, idn, 1u);
+              tc_mma<BITS>(d_im, da + 2, db + 6, idn, 1u);
+            } else if (it.type == kItemTwoDiag) {
+              const uint64_t d0 = sw128_desc(a), d1 = sw128_desc(a + kTileBytes);
+              narrow_block<BITS>(d_re, d_im, d0, d0, acc0);
+              narrow_block<BITS>(d_re + kTile, d_im + kTile, d1, d1, acc0);
+            } else {
+              const uint64_t da = sw128_desc(a);
+              const uint64_t db = it.I0 == it.J0 ? da : sw128_desc(a + kTileBytes);
+              narrow_block<BITS>(d_re, d_im, da, db, acc0);
+            }
+          }
+          if (kb + nb == KB) tc_commit(tfull);
+          tc_commit(empty(stage));
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        ++n_it;
+      }
+      // no MMA may be in flight when tensor memory is freed
+      tc_commit(drain);
+      mbar_wait(drain, 0, nullptr, tmo);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: convert + integration dump ----------------
+    // Warp (q, h): tensor-memory lanes 32q.. (rows of the tile) of pair h.
+    // Each 32-column chunk goes through this warp's shared-memory buffer, 16
+    // columns at a time: lane r writes row r (16 (re, im) words, XOR-swizzled
+    // so the 16 lanes of a phase hit distinct banks), then each store
+    // instruction writes rows r and r+1 as two contiguous 128-byte runs.
+    const int q = warp & 3;
+    const int h = (warp - Sh::epi0) >> 2;
+    uint8_t *stg = epi_smem + (warp - Sh::epi0) * kEpiStageBytes;
+    uint32_t n_it = 0;
+    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+      const PairItem it = decode_pair_item(__ldg(p.items + item));
+      const KJob &jb = p.job[it.job];
+      if (warp == Sh::epi0 && lane == 0) {
+        const bool got = mbar_wait(tfull, n_it & 1u, abort_flag, tmo);
+        if (!got) raise_timeout(abort_flag, p.status);
+        epi_flag[n_it & 1u] = got ? 1 : 0;
+      }
+      named_bar_sync(1, 8 * 32);
+      if (!epi_flag[n_it & 1u]) break;
+      tc_fence_after();
+      const bool has = h == 0 || it.type != kItemOne;
+      int c, I, J;
+      if (it.type == kItemShared) {
+        c = it.c0;
+        I = it.I0;
+        J = h ? it.J1 : it.J0;
+      } else if (it.type == kItemTwoDiag) {
+        c = h ? it.c1 : it.c0;
+        I = h ? it.I1 : it.I0;
+        J = I;
+      } else {
+        c = it.c0;
+        I = it.I0;
+        J = it.J0;
+      }
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kTile);
+      uint32_t *out = reinterpret_cast<uint32_t *>(jb.out) + (int64_t)c * jb.n_bl * 2;
+      const int n = jb.n_inputs;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t vre[32], vim[32];
+        if (has) {
+          tc_ld32(trow + 32 * cc, vre);
+          tc_ld32(trow + 2 * kTile + 32 * cc, vim);
+          tc_wait_ld();
+        }
+        if (cc == 3) {
+          // every column of this warp is in registers: release the accumulator
+          // (test hook: withholding one release makes the MMA warp's bounded
+          // wait run out -> MWAX_ERR_TIMEOUT, clean exit)
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0 && (int)n_it != p.withhold_seg) mbar_arrive(tempty);
+        }
+        if (!has) continue;
+        if constexpr (KIND == MWAX_KIND_EXACT) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            vre[k] = (uint32_t)__float2int_rn(__uint_as_float(vre[k]));
+            vim[k] = (uint32_t)__float2int_rn(__uint_as_float(vim[k]));
+          }
+        }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            *reinterpret_cast<uint2 *>(stg + lane * 128 + ((k ^ (lane & 15)) << 3)) =
+                make_uint2(vre[16 * half + k], vim[16 * half + k]);
+          __syncwarp();
+          const int col = lane & 15;
+          const int j = J * kTile + 32 * cc + 16 * half + col;
+#pragma unroll
+          for (int r2 = 0; r2 < 16; ++r2) {
+            const int r = 2 * r2 + (lane >> 4);
+            const uint2 val = *reinterpret_cast<const uint2 *>(stg + r * 128 + ((col ^ (r & 15)) << 3));
+            const int i = I * kTile + q * 32 + r;
+            if (i < n && j <= i)
+              *reinterpret_cast<uint2 *>(out + 2 * ((int64_t)i * (i + 1) / 2 + j)) = val;
+          }
+          __syncwarp();
+        }
+      }
+      ++n_it;
+    }
+  }
+}
+
+template <int BITS, int KIND, int MODE>
+__global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
     correlate_tc_kernel(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p) {
-  using Sh = Shape<WIDE>;
+  using Sh = Shape<MODE>;
+  constexpr bool WIDE = MODE == kModeWide;
+  constexpr bool PAIR = MODE == kModePair;
   constexpr int kStageBytes = Sh::stage_bytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                               ~static_cast<uintptr_t>(1023));
   const int S = p.stages;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * kStageBytes);
+  uint8_t *epi_smem = smem + (size_t)S * kStageBytes;  // pair mode: per-warp store staging
+  uint64_t *bars = reinterpret_cast<uint64_t *>(epi_smem + Sh::epi_bytes);
   // full[0..S) empty[S..2S) bfull[2S..3S) tfull[3S..3S+2) tempty[3S+2..3S+4) drain[3S+4]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * S + 5);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -317,7 +617,10 @@ __global__ void __launch_bounds__(Shape<WIDE>::warps * 32, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp == 0) {
+  if constexpr (PAIR) {
+    pair_roles<BITS, KIND>(maps, p, smem_base, epi_smem, smem_u32(bars), tmem_base, abort_flag,
+                           epi_flag, warp, lane);
+  } else if (warp == 0) {
     // ---------------- TMA producer (one thread) ----------------
     if (lane == 0) {
       for (int j = 0; j < p.n_jobs; ++j)
@@ -611,52 +914,104 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-template <int BITS, int KIND, bool WIDE>
+template <int BITS, int KIND, int MODE>
 cudaError_t set_smem_attr(int bytes) {
-  return cudaFuncSetAttribute(correlate_tc_kernel<BITS, KIND, WIDE>,
+  return cudaFuncSetAttribute(correlate_tc_kernel<BITS, KIND, MODE>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <bool WIDE>
+template <int MODE>
 cudaError_t prepare_shape(int sample_bits, int kind, int bytes) {
-  if (sample_bits == 4) return set_smem_attr<4, MWAX_KIND_EXACT, WIDE>(bytes);
-  if (kind == MWAX_KIND_FP16) return set_smem_attr<8, MWAX_KIND_FP16, WIDE>(bytes);
-  return set_smem_attr<8, MWAX_KIND_EXACT, WIDE>(bytes);
+  if (sample_bits == 4) return set_smem_attr<4, MWAX_KIND_EXACT, MODE>(bytes);
+  if (kind == MWAX_KIND_FP16) return set_smem_attr<8, MWAX_KIND_FP16, MODE>(bytes);
+  return set_smem_attr<8, MWAX_KIND_EXACT, MODE>(bytes);
 }
 
-template <bool WIDE>
+template <int MODE>
 void launch_shape(int sample_bits, int kind, int grid, int smem, cudaStream_t s, const KMaps &maps,
                   const KParams &kp) {
-  const int threads = Shape<WIDE>::warps * 32;
+  const int threads = Shape<MODE>::warps * 32;
   if (sample_bits == 4)
-    correlate_tc_kernel<4, MWAX_KIND_EXACT, WIDE><<<grid, threads, smem, s>>>(maps, kp);
+    correlate_tc_kernel<4, MWAX_KIND_EXACT, MODE><<<grid, threads, smem, s>>>(maps, kp);
   else if (kind == MWAX_KIND_FP16)
-    correlate_tc_kernel<8, MWAX_KIND_FP16, WIDE><<<grid, threads, smem, s>>>(maps, kp);
+    correlate_tc_kernel<8, MWAX_KIND_FP16, MODE><<<grid, threads, smem, s>>>(maps, kp);
   else
-    correlate_tc_kernel<8, MWAX_KIND_EXACT, WIDE><<<grid, threads, smem, s>>>(maps, kp);
+    correlate_tc_kernel<8, MWAX_KIND_EXACT, MODE><<<grid, threads, smem, s>>>(maps, kp);
+}
+
+int4 encode_item(int job, uint32_t type, int c0, int c1, int I0, int J0, int I1, int J1) {
+  const uint32_t z = (uint32_t)job | type << 8 | (uint32_t)I0 << 16 | (uint32_t)J0 << 24;
+  const uint32_t w = (uint32_t)I1 | (uint32_t)J1 << 8;
+  return make_int4(c0, c1, (int)z, (int)w);
 }
 
 }  // namespace
 
-int correlate_tc_max_stages(int wide) {
-  return wide ? Shape<true>::max_stages : Shape<false>::max_stages;
+int correlate_tc_max_stages(int mode) {
+  return mode == kModeWide ? Shape<kModeWide>::max_stages
+         : mode == kModePair ? Shape<kModePair>::max_stages
+                             : Shape<kModeNarrow>::max_stages;
 }
 
-int correlate_tc_smem_bytes(int stages, int wide) {
-  const int stage_bytes = wide ? Shape<true>::stage_bytes : Shape<false>::stage_bytes;
-  return 1024 + stages * stage_bytes + (3 * stages + 5) * 8 + 32;
+int correlate_tc_smem_bytes(int stages, int mode) {
+  const int stage_bytes = mode == kModeWide ? Shape<kModeWide>::stage_bytes
+                          : mode == kModePair ? Shape<kModePair>::stage_bytes
+                                              : Shape<kModeNarrow>::stage_bytes;
+  const int epi_bytes = mode == kModePair ? Shape<kModePair>::epi_bytes : 0;
+  return 1024 + stages * stage_bytes + epi_bytes + (3 * stages + 5) * 8 + 32;
 }
 
-cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int wide) {
-  const int bytes = correlate_tc_smem_bytes(stages, wide);
-  return wide ? prepare_shape<true>(sample_bits, kind, bytes)
-              : prepare_shape<false>(sample_bits, kind, bytes);
+cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode) {
+  const int bytes = correlate_tc_smem_bytes(stages, mode);
+  if (mode == kModeWide) return prepare_shape<kModeWide>(sample_bits, kind, bytes);
+  if (mode == kModePair) return prepare_shape<kModePair>(sample_bits, kind, bytes);
+  return prepare_shape<kModeNarrow>(sample_bits, kind, bytes);
+}
+
+bool pair_mode_supported(const TcJob *jobs, int n_jobs) {
+  for (int j = 0; j < n_jobs; ++j)
+    if (jobs[j].kb > jobs[j].flush_blocks || jobs[j].n_tiles > 255) return false;
+  return n_jobs >= 1 && n_jobs <= kMaxJobs;
+}
+
+// Channel by channel, row I of the tile triangle gives the shared items
+// (I; J, J+1) for J = 0, 2, ... while J+1 <= I, and, when I+1 is odd, its
+// diagonal pair (I, I) is left over; consecutive leftovers (in the same or the
+// next channel of the job) form a two-diagonal item, and a last unmatched one
+// a single item.  Items of one channel are adjacent, so the CTAs working on a
+// channel at the same time share its operand tiles in L2.
+void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items) {
+  items.clear();
+  for (int jn = 0; jn < n_jobs; ++jn) {
+    const TcJob &job = jobs[jn];
+    bool pending = false;
+    int pc = 0, pI = 0;
+    for (int c = 0; c < job.n_chan; ++c)
+      for (int I = 0; I < job.n_tiles; ++I) {
+        for (int J = 0; J + 1 <= I; J += 2)
+          items.push_back(encode_item(jn, kItemShared, c, c, I, J, I, J + 1));
+        if ((I + 1) % 2 == 1) {
+          if (pending) {
+            items.push_back(encode_item(jn, kItemTwoDiag, pc, c, pI, pI, I, I));
+            pending = false;
+          } else {
+            pending = true;
+            pc = c;
+            pI = I;
+          }
+        }
+      }
+    if (pending) items.push_back(encode_item(jn, kItemOne, pc, pc, pI, pI, 0, 0));
+  }
 }
 
 cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
                                 cudaStream_t s) {
   if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;
-  if (cfg.stages < 2 || cfg.stages > correlate_tc_max_stages(cfg.wide)) return cudaErrorInvalidValue;
+  if (cfg.mode < kModeNarrow || cfg.mode > kModePair) return cudaErrorInvalidValue;
+  if (cfg.stages < 2 || cfg.stages > correlate_tc_max_stages(cfg.mode)) return cudaErrorInvalidValue;
+  if (cfg.mode == kModePair && (!pair_mode_supported(jobs, n_jobs) || !cfg.items || cfg.n_items < 0))
+    return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
   if (!encode) return cudaErrorNotSupported;
   KMaps maps;
@@ -690,6 +1045,10 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
     kj.flush_blocks = job.flush_blocks;
     items += (int64_t)job.n_chan * job.n_pairs;
   }
+  if (cfg.mode == kModePair) {
+    kp.items = cfg.items;
+    items = cfg.n_items;
+  }
   kp.status = cfg.status;
   kp.n_items = items;
   kp.timeout_ns = cfg.timeout_ns;
@@ -699,11 +1058,13 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   kp.withhold_seg = cfg.withhold_seg;
   if (items <= 0) return cudaSuccess;
   const int grid = (int)(items < cfg.grid ? items : cfg.grid);
-  const int smem = correlate_tc_smem_bytes(cfg.stages, cfg.wide);
-  if (cfg.wide)
-    launch_shape<true>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
+  const int smem = correlate_tc_smem_bytes(cfg.stages, cfg.mode);
+  if (cfg.mode == kModeWide)
+    launch_shape<kModeWide>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
+  else if (cfg.mode == kModePair)
+    launch_shape<kModePair>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
   else
-    launch_shape<false>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
+    launch_shape<kModeNarrow>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
   return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ struct mwax_plan_s {
   int kind = MWAX_KIND_EXACT;
   int stages = 2;
   int prefetch = 0;
-  int wide = 0;
+  int mode = 0;  // correlate kernel: 0 narrow, 1 wide, 2 pair (mma_shape - 1)
   int withhold_seg = -1;
   int unpack_sms = 0;  // overlapped pipeline: SMs given to the persistent unpack (0: co-resident)
   unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
@@ -62,6 +62,11 @@ struct mwax_plan_s {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_start = nullptr, ev_unpacked[2] = {nullptr, nullptr}, ev_freed[2] = {nullptr, nullptr};
   int32_t *status = nullptr;
+  // pair mode: device work lists; single-job plans hold the list of a full
+  // channel group followed by that of the ragged last group, batch plans the
+  // list of their one launch
+  int4 *items = nullptr;
+  int64_t n_items_full = 0, n_items_last = 0;
   // batch graphs: every job's unpack, then the one persistent correlate launch
   cudaGraphExec_t graph = nullptr, graph2 = nullptr;
   std::vector<const void *> graph_in;
@@ -122,9 +127,10 @@ mwax_status check_job(const mwax_job &j) {
   if (j.kind != MWAX_KIND_EXACT && j.kind != MWAX_KIND_FP16) return MWAX_ERR_INVALID_ARG;
   if (j.engine != MWAX_ENGINE_TENSOR && j.engine != MWAX_ENGINE_PLAIN) return MWAX_ERR_INVALID_ARG;
   if (j.flush_blocks < 0 || j.chan_group < 0) return MWAX_ERR_INVALID_ARG;
-  if (j.mma_shape < 0 || j.mma_shape > 2) return MWAX_ERR_INVALID_ARG;
+  if (j.mma_shape < 0 || j.mma_shape > 3) return MWAX_ERR_INVALID_ARG;
   if (j.pipeline < 0 || j.pipeline > 2) return MWAX_ERR_INVALID_ARG;
-  if (j.stages < 0 || j.stages == 1 || j.stages > correlate_tc_max_stages(j.mma_shape == 2))
+  if (j.stages < 0 || j.stages == 1 ||
+      j.stages > correlate_tc_max_stages(j.mma_shape > 0 ? j.mma_shape - 1 : 0))
     return MWAX_ERR_INVALID_ARG;
   if (j.prefetch < -1 || j.prefetch > 64) return MWAX_ERR_INVALID_ARG;
   if (j.timeout_ms < 0 || j.test_fault < 0 || j.unpack_sms < 0) return MWAX_ERR_INVALID_ARG;
@@ -204,6 +210,46 @@ struct TimedLaunch {
   }
 };
 
+TcJob tc_job(const JobState &s, const uint8_t *op, void *out_c0, int nc) {
+  TcJob tj;
+  tj.op = op;
+  tj.out = out_c0;
+  tj.n_inputs = s.job.n_inputs;
+  tj.n_tiles = s.n_tiles;
+  tj.n_pairs = s.n_pairs;
+  tj.kb = s.kb;
+  tj.flush_blocks = s.flush_blocks;
+  tj.n_chan = nc;
+  tj.n_bl = s.n_bl;
+  return tj;
+}
+
+// Kernel mode for a job's mma_shape (0 = auto: pair mode where every job
+// integrates in one exact segment, else narrow); -1 when an explicit pair
+// request cannot be served.
+int choose_mode(int mma_shape, const std::vector<TcJob> &tj) {
+  const bool pair_ok = pair_mode_supported(tj.data(), (int)tj.size());
+  if (mma_shape == 3) return pair_ok ? 2 : -1;
+  if (mma_shape == 1 || mma_shape == 2) return mma_shape - 1;
+  return pair_ok ? 2 : 0;
+}
+
+// Build the pair-mode work lists (a and, if non-empty, b after it) and copy
+// them to a device buffer owned by the plan.
+cudaError_t upload_items(mwax_plan_s *p, const std::vector<TcJob> &a, const std::vector<TcJob> &b) {
+  std::vector<int4> la, lb;
+  build_pair_items(a.data(), (int)a.size(), la);
+  if (!b.empty()) build_pair_items(b.data(), (int)b.size(), lb);
+  p->n_items_full = (int64_t)la.size();
+  p->n_items_last = (int64_t)lb.size();
+  la.insert(la.end(), lb.begin(), lb.end());
+  if (la.empty()) return cudaSuccess;
+  cudaError_t e = plan_alloc(reinterpret_cast<void **>(&p->items), la.size() * sizeof(int4));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->items, la.data(), la.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  return e;
+}
+
 TcLaunch launch_cfg(const mwax_plan_s *p) {
   TcLaunch c;
   c.sample_bits = p->sample_bits;
@@ -212,7 +258,7 @@ TcLaunch launch_cfg(const mwax_plan_s *p) {
   c.grid = p->overlap ? p->sm_count - p->unpack_sms : p->sm_count;
   c.stages = p->stages;
   c.prefetch = p->prefetch;
-  c.wide = p->wide;
+  c.mode = p->mode;
   c.withhold_seg = p->withhold_seg;
   c.status = p->status;
   c.timeout_ns = p->timeout_ns;
@@ -263,18 +309,15 @@ mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt,
 
 mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op, int nc,
                             void *out_c0, cudaStream_t st) {
-  TcJob tj;
-  tj.op = op;
-  tj.out = out_c0;
-  tj.n_inputs = s.job.n_inputs;
-  tj.n_tiles = s.n_tiles;
-  tj.n_pairs = s.n_pairs;
-  tj.kb = s.kb;
-  tj.flush_blocks = s.flush_blocks;
-  tj.n_chan = nc;
-  tj.n_bl = s.n_bl;
+  TcJob tj = tc_job(s, op, out_c0, nc);
+  TcLaunch cfg = launch_cfg(p);
+  if (p->mode == 2) {
+    const bool full = nc == s.chan_group;
+    cfg.items = full ? p->items : p->items + p->n_items_full;
+    cfg.n_items = full ? p->n_items_full : p->n_items_last;
+  }
   TimedLaunch tc(p, 1, st);
-  cudaError_t e = launch_correlate_tc(&tj, 1, launch_cfg(p), st);
+  cudaError_t e = launch_correlate_tc(&tj, 1, cfg, st);
   tc.done();
   return cuda_status(e);
 }
@@ -346,6 +389,7 @@ void free_plan(mwax_plan_s *p) {
   if (p->scratch) cudaFree(p->scratch);
   if (p->scratch2) cudaFree(p->scratch2);
   if (p->status) cudaFree(p->status);
+  if (p->items) cudaFree(p->items);
   if (p->aux) cudaStreamDestroy(p->aux);
   if (p->ev_start) cudaEventDestroy(p->ev_start);
   for (int k = 0; k < 2; ++k) {
@@ -440,19 +484,30 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
   p->engine = job->engine;
   p->sample_bits = job->sample_bits;
   p->kind = job->kind;
-  p->wide = job->mma_shape == 2;
-  p->stages = job->stages > 0 ? job->stages : correlate_tc_max_stages(p->wide);
   if (job->prefetch != 0) p->prefetch = job->prefetch < 0 ? 0 : job->prefetch;
   if (job->timeout_ms > 0) p->timeout_ns = (unsigned long long)job->timeout_ms * 1000000ull;
   p->withhold_seg = job->test_fault - 1;
   if (p->engine == MWAX_ENGINE_TENSOR) {
+    const std::vector<TcJob> full = {tc_job(s, nullptr, nullptr, s.chan_group)};
+    p->mode = choose_mode(job->mma_shape, full);
+    if (p->mode < 0) {
+      free_plan(p);
+      return MWAX_ERR_UNSUPPORTED;
+    }
+    p->stages = job->stages > 0 ? job->stages : correlate_tc_max_stages(p->mode);
+    if (p->stages > correlate_tc_max_stages(p->mode)) {
+      free_plan(p);
+      return MWAX_ERR_INVALID_ARG;
+    }
     const int64_t one = s.op_chan_bytes * s.chan_group;
     const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : s.job.n_inputs % 4 == 0;
     // unpack_sms 0: the small unpack CTA runs beside the correlate on every SM
     // where the shape allows it, else 20 SMs are set aside for the unpack
+    // (pair mode fills the shared memory: no room for a co-resident unpack CTA)
     p->unpack_sms = job->unpack_sms > 0 ? job->unpack_sms
-                    : unpack_tile_supported(s.job.sample_bits, s.job.n_inputs) ? 0
-                                                                                : 20;
+                    : unpack_tile_supported(s.job.sample_bits, s.job.n_inputs) && p->mode != 2
+                        ? 0
+                        : 20;
     p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan && even &&
                  p->unpack_sms < p->sm_count;
     p->scratch_bytes = one * (p->overlap ? 2 : 1);
@@ -468,7 +523,13 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_freed[k], cudaEventDisableTiming);
       }
     }
-    if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->wide);
+    if (e == cudaSuccess && p->mode == 2) {
+      const int last = (int)(s.job.n_chan % s.chan_group);
+      std::vector<TcJob> tail;
+      if (last) tail.push_back(tc_job(s, nullptr, nullptr, last));
+      e = upload_items(p, full, tail);
+    }
+    if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->mode);
     if (e != cudaSuccess) {
       free_plan(p);
       return cuda_status(e);
@@ -501,8 +562,6 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
   p->batch = true;
   p->sample_bits = jobs[0].sample_bits;
   p->kind = jobs[0].kind;
-  p->wide = jobs[0].mma_shape == 2;
-  p->stages = jobs[0].stages > 0 ? jobs[0].stages : correlate_tc_max_stages(p->wide);
   if (jobs[0].prefetch != 0) p->prefetch = jobs[0].prefetch < 0 ? 0 : jobs[0].prefetch;
   for (int k = 0; k < n_jobs; ++k) {
     JobState s;
@@ -518,10 +577,20 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
       return cuda_status(e);
     }
   }
-  cudaError_t e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->wide);
+  std::vector<TcJob> tj;
+  for (const JobState &s : p->jobs) tj.push_back(tc_job(s, s.op, nullptr, s.job.n_chan));
+  p->mode = choose_mode(jobs[0].mma_shape, tj);
+  if (p->mode < 0) {
+    free_plan(p);
+    return MWAX_ERR_UNSUPPORTED;
+  }
+  p->stages = jobs[0].stages > 0 ? jobs[0].stages : correlate_tc_max_stages(p->mode);
+  cudaError_t e = p->stages <= correlate_tc_max_stages(p->mode) ? cudaSuccess : cudaErrorInvalidValue;
+  if (e == cudaSuccess && p->mode == 2) e = upload_items(p, tj, {});
+  if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->mode);
   if (e != cudaSuccess) {
     free_plan(p);
-    return cuda_status(e);
+    return e == cudaErrorInvalidValue ? MWAX_ERR_INVALID_ARG : cuda_status(e);
   }
   *plan = p;
   return MWAX_OK;
@@ -545,12 +614,18 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   info->chan_group = plan->batch ? s.job.n_chan : s.chan_group;
   info->grid = plan->sm_count;
   info->stages = plan->stages;
-  info->mma_shape = plan->wide ? 2 : 1;
+  info->mma_shape = plan->mode + 1;
   info->pipeline = plan->overlap ? 2 : 1;
   info->prefetch = plan->prefetch;
   info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
   int64_t items = 0;
-  for (const auto &j : plan->jobs) items += (int64_t)j.job.n_chan * j.n_pairs;
+  if (plan->mode == 2 && plan->batch) {
+    items = plan->n_items_full;
+  } else if (plan->mode == 2) {
+    items = (s.job.n_chan / s.chan_group) * plan->n_items_full + plan->n_items_last;
+  } else {
+    for (const auto &j : plan->jobs) items += (int64_t)j.job.n_chan * j.n_pairs;
+  }
   info->work_items = items;
   return MWAX_OK;
 }
@@ -595,18 +670,8 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
         *ge = nullptr;
       }
     std::vector<TcJob> tj(nj);
-    for (int k = 0; k < nj; ++k) {
-      const JobState &s = plan->jobs[k];
-      tj[k].op = s.op;
-      tj[k].out = out[k];
-      tj[k].n_inputs = s.job.n_inputs;
-      tj[k].n_tiles = s.n_tiles;
-      tj[k].n_pairs = s.n_pairs;
-      tj[k].kb = s.kb;
-      tj[k].flush_blocks = s.flush_blocks;
-      tj[k].n_chan = s.job.n_chan;
-      tj[k].n_bl = s.n_bl;
-    }
+    for (int k = 0; k < nj; ++k)
+      tj[k] = tc_job(plan->jobs[k], plan->jobs[k].op, out[k], plan->jobs[k].job.n_chan);
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_status(e);
@@ -628,7 +693,10 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
                               s.job.n_chan, s.op, 0, cs);
         }
       } else if (e == cudaSuccess) {
-        e = launch_correlate_tc(tj.data(), nj, launch_cfg(plan), cs);
+        TcLaunch cfg = launch_cfg(plan);
+        cfg.items = plan->items;
+        cfg.n_items = plan->n_items_full;
+        e = launch_correlate_tc(tj.data(), nj, cfg, cs);
       }
       cudaError_t e2 = cudaStreamEndCapture(cs, &g);
       if (e == cudaSuccess) e = e2;

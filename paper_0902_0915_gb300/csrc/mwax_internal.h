@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "mwax.h"
 
 #include <nvtx3/nvToolsExt.h>
@@ -74,20 +76,30 @@ struct TcLaunch {
   int kind;  // mwax_kind
   int grid;
   int stages;
-  int prefetch;  // K-blocks of L2 prefetch ahead of the TMA loads (0 = none)
-  int wide;      // 1: N=256 MMAs with B' built in shared memory; 0: N=128 MMAs
+  int prefetch;  // K-blocks of L2 prefetch ahead of the TMA loads (0 = none; narrow only)
+  int mode;      // 0: narrow (N=128 MMAs), 1: wide (N=256 with B' built in shared
+                 // memory), 2: pair (two tile pairs per work item, see items)
   int withhold_seg;  // test hook (-1: off): see mwax_job.test_fault
   int32_t *status;
   unsigned long long timeout_ns;
+  const int4 *items = nullptr;  // mode 2: device work list from build_pair_items
+  int64_t n_items = 0;
 };
 
 // Encodes one TMA descriptor per job and launches the persistent kernel over
-// the concatenated work items (job by job, channel-major, tile pairs inside).
+// the work items: in modes 0 and 1 the concatenated (job, channel, tile pair)
+// items, job by job, channel-major; in mode 2 the given work list.
 cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
                                 cudaStream_t s);
-int correlate_tc_smem_bytes(int stages, int wide);
-int correlate_tc_max_stages(int wide);
-cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int wide);
+int correlate_tc_smem_bytes(int stages, int mode);
+int correlate_tc_max_stages(int mode);
+cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode);
+
+// Pair mode needs every job's integration in one exact segment (kb <=
+// flush_blocks) and at most 255 tiles.
+bool pair_mode_supported(const TcJob *jobs, int n_jobs);
+// The pair-mode work list of one launch over `jobs` (16 bytes per item).
+void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items);
 
 // Fill the tuning fields of an all-auto job from the MWAX_TUNE_CACHE file.
 void apply_tune_cache(mwax_job *job);

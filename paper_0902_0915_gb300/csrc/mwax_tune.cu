@@ -128,8 +128,8 @@ double time_batch(const std::vector<mwax_job> &jobs, const void *const *volt, vo
 }
 
 bool valid(const Cand &c) {
-  const bool shape_ok = c.mma_shape == 0 || c.mma_shape == 1 || c.mma_shape == 2;
-  const int max_st = correlate_tc_max_stages(c.mma_shape == 2);
+  const bool shape_ok = c.mma_shape >= 0 && c.mma_shape <= 3;
+  const int max_st = correlate_tc_max_stages(c.mma_shape > 0 ? c.mma_shape - 1 : 0);
   return shape_ok && (c.stages == 0 || (c.stages >= 2 && c.stages <= max_st));
 }
 
@@ -179,9 +179,11 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
   mwax_job base = *job;
   apply(&base, Cand{0, 0, 0, 0, 0});
   const int reps = 2;
+  // (pair-mode candidates fail to plan, and are skipped, where a job needs
+  // more than one exact segment)
   const std::vector<Cand> cands = {
-      {1, 2, -1, 1, 0}, {1, 2, 8, 1, 0}, {1, 2, -1, 2, 0},
-      {2, 4, -1, 1, 0}, {2, 3, -1, 1, 0}, {2, 4, 8, 1, 0}, {2, 4, -1, 2, 0},
+      {1, 2, -1, 1, 0}, {1, 2, 8, 1, 0}, {1, 2, -1, 2, 0}, {2, 4, -1, 1, 0},
+      {2, 3, -1, 1, 0}, {2, 4, 8, 1, 0},  {2, 4, -1, 2, 0}, {3, 2, -1, 1, 0},
   };
   best_ms = -1.0;
   for (const Cand &c : cands) {
@@ -212,7 +214,7 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
   memset(&rep, 0, sizeof(rep));
   std::vector<mwax_job> base(jobs, jobs + n_jobs);
   const std::vector<Cand> cands = {{1, 2, -1, 0, 0}, {1, 2, 8, 0, 0}, {2, 4, -1, 0, 0},
-                                   {2, 3, -1, 0, 0}, {2, 4, 8, 0, 0}};
+                                   {2, 3, -1, 0, 0}, {2, 4, 8, 0, 0}, {3, 2, -1, 0, 0}};
   Cand best{0, 0, 0, 0, 0};
   double best_ms = -1.0;
   for (const Cand &c : cands) {

@@ -67,9 +67,11 @@ def test_plain_small(mw, bits, N, T, C):
 
 
 SHAPES = [1, 2]  # M128xN128 (Re, Im separately) and M128xN256 ([Re | Im] per MMA)
+# plus 3: two tile pairs per work item, for integrations that are one exact segment
+SHAPES_ONE_SEGMENT = [1, 2, 3]
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES_ONE_SEGMENT)
 @pytest.mark.parametrize("bits", [4, 8])
 @pytest.mark.parametrize("N,T,C", SMALL)
 def test_tensor_small(mw, bits, N, T, C, shape):
@@ -127,11 +129,58 @@ def test_tensor_multiple_channel_groups(mw):
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR, chan_group=3), oracle_for(spec, range(7)), "groups")
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("bits,N,T,C,G", [
+    (4, 48, 100, 5, 0), (4, 136, 333, 4, 0), (4, 256, 2000, 5, 2), (4, 300, 1000, 3, 0),
+    (4, 520, 130, 3, 2), (4, 640, 64, 3, 0), (4, 1024, 64, 2, 0), (4, 1100, 70, 1, 0),
+    (4, 256, 65, 1, 0), (8, 200, 512, 3, 0), (8, 384, 100, 4, 3), (8, 1000, 33, 2, 0)])
+def test_pair_mode_shapes(mw, bits, N, T, C, G):
+    """Two tile pairs per work item: 1 to 9 tiles (shared items (I; J, J+1)
+    with and without the diagonal tile, diagonal leftovers paired across
+    channels, a last single item), odd and even channel counts, channel
+    groups with a ragged last group (its own work list), ragged N and T."""
+    spec = synth.Spec("pm", N, C, T, bits, seed=N + 3 * T + C, sigma=2 if bits == 4 else 40,
+                      tone_amp=0.3)
+    kw = {"chan_group": G} if G else {}
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, mma_shape=3, **kw), oracle_for(spec, range(C)),
+                 f"pair {bits},{N},{T},{C},{G}")
+
+
+def test_pair_mode_choice(mw):
+    """Auto takes the pair mode exactly where the integration is one exact
+    segment; an explicit request elsewhere is refused."""
+    p = mw.Plan(256, 2, 20000, 4)
+    assert p.info().mma_shape == 3
+    p.close()
+    p = mw.Plan(256, 2, 20000, 8)  # 8-bit: 16 blocks per segment
+    assert p.info().mma_shape == 1
+    p.close()
+    p = mw.Plan(256, 2, 512, 8)  # exactly one segment
+    assert p.info().mma_shape == 3
+    p.close()
+    with pytest.raises(mw.MwaxError):
+        mw.Plan(256, 2, 513, 8, mma_shape=3)
+    with pytest.raises(mw.MwaxError):
+        mw.Plan(256, 2, 2000, 4, mma_shape=3, flush_blocks=4)
+
+
+def test_pair_mode_largest_single_segment(mw):
+    """4-bit samples all (7, 7) over the longest integration that is still one
+    exact segment (2674 blocks of 64 samples): V_ii = 98 T = 16,771,328, just
+    below 2^24, accumulated in FP32 tensor memory without any flush."""
+    T = 2674 * 64
+    spec = synth.Spec("pmax", 130, 1, T, 4, seed=0, kind=synth.SYNTH_CONST, c_re=7, c_im=7)
+    out = run(mw, spec, mw.ENGINE_TENSOR, mma_shape=3)
+    assert out[0, 0, 0] == 98 * T == 16_771_328 and out[0, 0, 1] == 0
+    assert_exact(out, oracle_for(spec, [0]), "pair max")
+
+
+@pytest.mark.parametrize("shape", SHAPES_ONE_SEGMENT)
 @pytest.mark.parametrize("bits", [4, 8])
 def test_exact_window_big_then_small(mw, bits, shape):
     """Accumulator near the top of its segment window, then +-1 addends: any
     loss of low-order bits in the tensor-core accumulation shows up."""
+    if shape == 3 and bits == 8:
+        pytest.skip("8-bit integrations of several segments have no pair mode")
     T = 20000 if bits == 4 else 2000
     split = 19000 if bits == 4 else 500
     spec = synth.Spec("bs", 130, 2, T, bits, seed=11, kind=synth.SYNTH_BIGSMALL, t_split=split)
@@ -170,19 +219,22 @@ def test_quarter_tone_closed_form(mw):
     np.testing.assert_array_equal(out[:, 1], e.imag.astype(np.int64))
 
 
-def test_fp16_variant_error(mw):
+@pytest.mark.parametrize("shape", [0, 1, 3])
+def test_fp16_variant_error(mw, shape):
     """FP16 inputs, FP32 accumulation without integer flushes: error against
     the exact (int64 = FP64-exact) oracle stays within the FP32 summation
-    bound 2T * 2^-24 (autos-normalised)."""
+    bound 2T * 2^-24 (autos-normalised).  Auto picks the pair mode (one
+    segment); 1 forces the narrow shape."""
     import torch
 
-    spec = synth.Spec("h", 128, 2, 10000, 8, seed=21, sigma=20)
+    spec = synth.Spec("h", 300, 3, 10000, 8, seed=21, sigma=20)
     v = device_volt(spec)
-    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, kind=mw.KIND_FP16)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, kind=mw.KIND_FP16, mma_shape=shape)
+    assert p.info().mma_shape == (3 if shape == 0 else shape)
     out = p.correlate(v)
     assert p.status() == 0
     got = out.cpu().numpy().astype(np.float64)
-    _, ref = oracle_for(spec, range(2), want64=True)
+    _, ref = oracle_for(spec, range(spec.n_chan), want64=True)
     N = spec.n_inputs
     ii, jj = np.tril_indices(N)
     auto = ref[:, [oracle.baseline_index(i, i) for i in range(N)], 0].astype(np.float64)
@@ -273,7 +325,7 @@ def _full_size(mw, spec, chans, **kw):
     assert_exact(got, oracle_for(spec, chans), spec.name)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES_ONE_SEGMENT)
 def test_full_size_c1_sampled(mw, shape):
     spec = synth.spec_c1()
     _full_size(mw, spec, [0, 1, 383, 766, 767], mma_shape=shape)

@@ -47,6 +47,32 @@ def test_withheld_release_times_out_and_device_recovers(mw, shape):
     torch.cuda.synchronize()
 
 
+def test_withheld_release_times_out_pair_mode(mw):
+    """The same in pair mode (one accumulator buffer per CTA, released per work
+    item): CTA 0 withholds the release of its first item, so the MMA warp's
+    wait before its second item runs out."""
+    import torch
+
+    spec = synth.Spec("ffp", 256, 400, 600, 4, seed=5, sigma=2)
+    v = device_volt(spec)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, timeout_ms=150, test_fault=1,
+                mma_shape=3)
+    assert p.info().work_items > 2 * 152
+    t0 = time.time()
+    p.correlate(v)
+    st = p.status()
+    assert st == mw.STATUS_BY_NAME["MWAX_ERR_TIMEOUT"]
+    assert time.time() - t0 < 30.0
+    p.close()
+    q = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, mma_shape=3)
+    out = q.correlate(v)
+    assert q.status() == 0
+    chans = [0, 1, 199, 398, 399]
+    assert_exact(out[chans].cpu().numpy(), oracle_for(spec, chans), "after timeout (pair)")
+    q.close()
+    torch.cuda.synchronize()
+
+
 def test_status_word_clears_after_read(mw):
     spec = synth.Spec("ff2", 64, 2, 200, 8, seed=4, sigma=30)
     v = device_volt(spec)
