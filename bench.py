@@ -864,6 +864,7 @@ def main():
         peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_note = f"2 x bf16 sustained ({peak_src}; nominal fp8/bf16 ratio 4.5/2.25)"
     info = plan.info()
+    recomputed = plan.recomputed_channels() if engine == mw.ENGINE_TENSOR else 0
     if engine == mw.ENGINE_TENSOR and tim.correlate_ms > 0:
         achieved = 8.0 * units * args.steps / (tim.correlate_ms / 1e3) / 1e12
         tkey = (f"correlate_tc_kernel<{rspec.sample_bits},EXACT,"
@@ -906,13 +907,21 @@ def main():
                    "chan_group": info.chan_group, "flush_blocks": info.flush_blocks,
                    "mma_shape": info.mma_shape, "stages": info.stages, "prefetch": info.prefetch,
                    "pipeline": info.pipeline,
+                   "checked_segment": None if not info.checked_segment else {
+                       "recomputed_channels": recomputed,
+                       "of": rspec.n_chan * (args.warmup + args.steps),
+                       "note": "one FP32 segment per item; channels whose largest auto "
+                               "reached 2^24 recomputed with exact segments"},
                    "autotune": None if tune_rep is None else {
                        "candidates": tune_rep.candidates, "from_cache": bool(tune_rep.from_cache),
                        "best_ms": tune_rep.best_ms, "default_ms": tune_rep.default_ms},
                    "parallelism": f"channels, {world} GPU(s), no collective"},
         "rtf": rtf,
         "roofline": roofline,
-        "gpu_launches": int(tim.unpack_launches + tim.correlate_launches),
+        # a checked-segment correlate launch is followed by the check kernel and
+        # the (usually empty) recompute launch inside the same timed record
+        "gpu_launches": int(tim.unpack_launches
+                            + tim.correlate_launches * (3 if info.checked_segment else 1)),
         "clocks": clk,
     }
 

@@ -93,8 +93,11 @@ typedef struct {
                               (I, J+1) per work item with M128xN256 MMAs against the
                               tiles of J and J+1 (only when the whole integration is one
                               exact FP32 segment: 4-bit samples with n_time <= 171,136,
-                              the FP16 kind, or flush_blocks >= the time blocks; else
-                              MWAX_ERR_UNSUPPORTED); 0 = auto: 3 where it applies, else 1 */
+                              the FP16 kind, or flush_blocks >= the time blocks; or,
+                              for longer exact single-job plans with flush_blocks 0,
+                              one checked segment, see mwax_plan_info.checked_segment;
+                              else MWAX_ERR_UNSUPPORTED); 0 = auto: 3 where it applies,
+                              else 1                                                      */
   int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
                               plan's stream, 2 = unpack the next group (second stream,
                               second scratch buffer) while the current group correlates,
@@ -128,6 +131,18 @@ typedef struct {
   int64_t scratch_bytes;     /* device scratch owned by the plan                       */
   int64_t work_items;        /* work items per call: (job, channel, tile pair), or the
                                 two-pair items of mma_shape 3                          */
+  int32_t checked_segment;   /* 1: 8-bit exact job longer than one exact segment, run
+                                in pair mode with each item accumulated in ONE FP32
+                                segment; a check after each channel group finds every
+                                channel whose largest auto-correlation Re V_ii reached
+                                2^24 (by Cauchy-Schwarz no partial sum of any pair of a
+                                channel exceeds that channel's largest V_ii, so all
+                                other channels are exact) and a narrow launch
+                                recomputes those channels with flush_blocks segments;
+                                the output is exact either way.  Chosen when kind is
+                                exact and mma_shape and flush_blocks are auto (0) or
+                                mma_shape is 3.  0 otherwise.                           */
+  int32_t reserved_info;
 } mwax_plan_info;
 
 typedef struct mwax_plan_s *mwax_plan_t;
@@ -178,6 +193,12 @@ mwax_status mwax_plan_get_timing(mwax_plan_t plan, mwax_timing *timing);
  * if a bounded device wait gave up (the output is then invalid).  Reading it
  * synchronises the plan's stream; the word is cleared afterwards. */
 mwax_status mwax_plan_status(mwax_plan_t plan);
+
+/* Plans with checked_segment: the number of channels recomputed with exact
+ * segments since the previous call (a measure of how often the input left
+ * the one-segment window; 0 for other plans).  Synchronises the plan's
+ * stream, then resets the count. */
+mwax_status mwax_plan_recomputed_channels(mwax_plan_t plan, int64_t *n_channels);
 
 /* ---- autotuning ------------------------------------------------------------ */
 

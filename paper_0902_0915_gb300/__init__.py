@@ -50,7 +50,8 @@ class PlanInfo(ctypes.Structure):
                 ("chan_group", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("mma_shape", ctypes.c_int32), ("pipeline", ctypes.c_int32),
-                ("scratch_bytes", ctypes.c_int64), ("work_items", ctypes.c_int64)]
+                ("scratch_bytes", ctypes.c_int64), ("work_items", ctypes.c_int64),
+                ("checked_segment", ctypes.c_int32), ("reserved_info", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -75,6 +76,7 @@ SIGNATURES = {
     "mwax_destroy": (_I, [_P]),
     "mwax_plan_get_info": (_I, [_P, ctypes.POINTER(PlanInfo)]),
     "mwax_plan_status": (_I, [_P]),
+    "mwax_plan_recomputed_channels": (_I, [_P, ctypes.POINTER(_I64)]),
     "mwax_plan_set_timing": (_I, [_P, _I]),
     "mwax_plan_get_timing": (_I, [_P, ctypes.POINTER(Timing)]),
     "mwax_autotune": (_I, [ctypes.POINTER(Job), _P, _P, _P, ctypes.POINTER(TuneReport)]),
@@ -244,6 +246,14 @@ class Plan:
     def status(self) -> int:
         """Device status word of the last calls (synchronises the stream)."""
         return int(lib().mwax_plan_status(self._h))
+
+    def recomputed_channels(self) -> int:
+        """Channels recomputed with exact segments since the last read (plans
+        with a checked single segment; synchronises the stream)."""
+        n = ctypes.c_int64(0)
+        _check(lib().mwax_plan_recomputed_channels(self._h, ctypes.byref(n)),
+               "mwax_plan_recomputed_channels")
+        return int(n.value)
 
     def set_timing(self, on: bool = True) -> None:
         _check(lib().mwax_plan_set_timing(self._h, 1 if on else 0), "mwax_plan_set_timing")

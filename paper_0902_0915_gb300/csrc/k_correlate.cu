@@ -100,6 +100,10 @@ struct KParams {
   KJob job[kMaxJobs];
   int32_t *status;
   const int4 *items;  // pair mode: the work list (n_items entries)
+  // narrow mode, one job: when n_chan_dev is set, the launch covers the
+  // *n_chan_dev channels chan_map[0..) (count and list written on the device)
+  const int32_t *chan_map;
+  const int32_t *n_chan_dev;
   int64_t n_items;
   unsigned long long timeout_ns;
   int32_t n_jobs, stages, prefetch;
@@ -260,9 +264,17 @@ __device__ __forceinline__ Item decode_item(const KParams &p, int64_t item) {
   const int64_t local = item - p.job[j].item_begin;
   Item it;
   it.job = j;
-  it.c = (int)(local / p.job[j].n_pairs);
+  const int cl = (int)(local / p.job[j].n_pairs);
+  it.c = p.chan_map ? __ldg(p.chan_map + cl) : cl;
   pair_of((int)(local % p.job[j].n_pairs), it.I, it.J);
   return it;
+}
+
+// Items of a narrow/wide launch (read once per thread; with a device-side
+// channel count the launch was sized for the largest count).
+__device__ __forceinline__ int64_t launch_items(const KParams &p) {
+  if (!p.n_chan_dev) return p.n_items;
+  return (int64_t)*reinterpret_cast<const volatile int32_t *>(p.n_chan_dev) * p.job[0].n_pairs;
 }
 
 // Named barrier `id` over `threads` threads (whole warps); waiting warps sleep.
@@ -616,6 +628,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const int64_t n_items = launch_items(p);
 
   if constexpr (PAIR) {
     pair_roles<BITS, KIND>(maps, p, smem_base, epi_smem, smem_u32(bars), tmem_base, abort_flag,
@@ -631,7 +644,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
       uint32_t phase = 0;
       int64_t issued = 0;
       bool ok = true;
-      for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      for (int64_t item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
         const Item it = decode_item(p, item);
         const KJob &jb = p.job[it.job];
         const CUtensorMap *map = &maps.m[it.job];
@@ -696,7 +709,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
       uint32_t phase = 0;
       uint32_t seg = 0;
       bool ok = true;
-      for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      for (int64_t item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
         const Item it = decode_item(p, item);
         const KJob &jb = p.job[it.job];
         const int F = jb.flush_blocks, KB = jb.kb;
@@ -780,7 +793,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
-    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+    for (int64_t item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
       const Item it = decode_item(p, item);
       const KJob &jb = p.job[it.job];
       const bool diag = it.I == it.J;
@@ -821,7 +834,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
     const int h = (warp - Sh::epi0) >> 2;  // column half: local columns [64h, 64h + 64)
     uint32_t seg = 0;
     bool ok = true;
-    for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+    for (int64_t item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
       const Item it = decode_item(p, item);
       const KJob &jb = p.job[it.job];
       const int F = jb.flush_blocks;
@@ -899,6 +912,37 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
   }
 }
 
+// ---- exactness check of a one-segment pass ---------------------------------
+// Every product term of a pair (i, j) is bounded by |x_i(t)| |x_j(t)|, so by
+// Cauchy-Schwarz every partial sum the tensor core forms for that pair, in any
+// order, is at most sqrt(E_i E_j) <= max(E_i, E_j) with E_i = sum_t |x_i(t)|^2
+// = Re V_ii.  A channel whose largest auto-correlation stayed below 2^24 was
+// therefore accumulated exactly in FP32.  Otherwise the FP32 auto sum, a sum
+// of non-negative terms, cannot have ended below 2^24 either (rounding is
+// monotonic and 2^24 is representable), so the test below catches every
+// channel that left the exact window.  One CTA per channel; flagged channels
+// are appended to bad[1..] (count in bad[0]).
+__global__ void __launch_bounds__(256) exact_check_kernel(const int32_t *out, int64_t n_bl,
+                                                          int n_inputs, int32_t *bad,
+                                                          unsigned long long *recomputed) {
+  const int c = blockIdx.x;
+  const int32_t *o = out + (int64_t)c * n_bl * 2;
+  uint32_t m = 0;
+  for (int i = threadIdx.x; i < n_inputs; i += blockDim.x)
+    m = max(m, (uint32_t)__ldg(o + 2 * ((int64_t)i * (i + 1) / 2 + i)));  // negative -> huge
+  m = __reduce_max_sync(0xffffffffu, m);
+  __shared__ uint32_t wmax[8];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, wmax[w]);
+    if (m >= (1u << 24)) {
+      bad[1 + atomicAdd(bad, 1)] = c;
+      atomicAdd(recomputed, 1ull);
+    }
+  }
+}
+
 // ---- host side ------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -968,6 +1012,14 @@ cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode
   return prepare_shape<kModeNarrow>(sample_bits, kind, bytes);
 }
 
+cudaError_t launch_exact_check(const int32_t *out, int64_t n_bl, int n_inputs, int n_chan,
+                               int32_t *bad, unsigned long long *recomputed, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess || n_chan <= 0) return e;
+  exact_check_kernel<<<n_chan, 256, 0, s>>>(out, n_bl, n_inputs, bad, recomputed);
+  return cudaGetLastError();
+}
+
 bool pair_mode_supported(const TcJob *jobs, int n_jobs) {
   for (int j = 0; j < n_jobs; ++j)
     if (jobs[j].kb > jobs[j].flush_blocks || jobs[j].n_tiles > 255) return false;
@@ -1012,6 +1064,9 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   if (cfg.stages < 2 || cfg.stages > correlate_tc_max_stages(cfg.mode)) return cudaErrorInvalidValue;
   if (cfg.mode == kModePair && (!pair_mode_supported(jobs, n_jobs) || !cfg.items || cfg.n_items < 0))
     return cudaErrorInvalidValue;
+  if ((cfg.chan_map || cfg.n_chan_dev) &&
+      (cfg.mode == kModePair || n_jobs != 1 || !cfg.chan_map || !cfg.n_chan_dev))
+    return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
   if (!encode) return cudaErrorNotSupported;
   KMaps maps;
@@ -1049,6 +1104,8 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
     kp.items = cfg.items;
     items = cfg.n_items;
   }
+  kp.chan_map = cfg.chan_map;  // (items stays the bound for all n_chan channels)
+  kp.n_chan_dev = cfg.n_chan_dev;
   kp.status = cfg.status;
   kp.n_items = items;
   kp.timeout_ns = cfg.timeout_ns;

@@ -67,6 +67,14 @@ struct mwax_plan_s {
   // list of their one launch
   int4 *items = nullptr;
   int64_t n_items_full = 0, n_items_last = 0;
+  // checked single segment (8-bit exact jobs longer than one exact segment):
+  // the pair-mode pass accumulates each item in one FP32 segment, a check
+  // lists the channels whose largest auto-correlation reached 2^24 (bad[0] =
+  // count, bad[1..] = channels) and a narrow launch recomputes just those with
+  // flush_blocks segments
+  bool checked = false;
+  int32_t *bad = nullptr;
+  unsigned long long *recomputed = nullptr;  // channels recomputed since the last read
   // batch graphs: every job's unpack, then the one persistent correlate launch
   cudaGraphExec_t graph = nullptr, graph2 = nullptr;
   std::vector<const void *> graph_in;
@@ -315,9 +323,26 @@ mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op
     const bool full = nc == s.chan_group;
     cfg.items = full ? p->items : p->items + p->n_items_full;
     cfg.n_items = full ? p->n_items_full : p->n_items_last;
+    if (p->checked) tj.flush_blocks = s.kb;  // one optimistic segment per item
   }
   TimedLaunch tc(p, 1, st);
   cudaError_t e = launch_correlate_tc(&tj, 1, cfg, st);
+  if (e == cudaSuccess && p->checked) {
+    e = launch_exact_check(reinterpret_cast<const int32_t *>(out_c0), s.n_bl, s.job.n_inputs, nc,
+                           p->bad, p->recomputed, st);
+    if (e == cudaSuccess) {
+      // the flagged channels again, narrow shape, exact segments (an empty
+      // list makes every CTA return at once)
+      TcJob fj = tc_job(s, op, out_c0, nc);
+      TcLaunch fc = launch_cfg(p);
+      fc.mode = 0;
+      fc.stages = correlate_tc_max_stages(0);
+      fc.withhold_seg = -1;
+      fc.chan_map = p->bad + 1;
+      fc.n_chan_dev = p->bad;
+      e = launch_correlate_tc(&fj, 1, fc, st);
+    }
+  }
   tc.done();
   return cuda_status(e);
 }
@@ -390,6 +415,8 @@ void free_plan(mwax_plan_s *p) {
   if (p->scratch2) cudaFree(p->scratch2);
   if (p->status) cudaFree(p->status);
   if (p->items) cudaFree(p->items);
+  if (p->bad) cudaFree(p->bad);
+  if (p->recomputed) cudaFree(p->recomputed);
   if (p->aux) cudaStreamDestroy(p->aux);
   if (p->ev_start) cudaEventDestroy(p->ev_start);
   for (int k = 0; k < 2; ++k) {
@@ -488,7 +515,13 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
   if (job->timeout_ms > 0) p->timeout_ns = (unsigned long long)job->timeout_ms * 1000000ull;
   p->withhold_seg = job->test_fault - 1;
   if (p->engine == MWAX_ENGINE_TENSOR) {
-    const std::vector<TcJob> full = {tc_job(s, nullptr, nullptr, s.chan_group)};
+    std::vector<TcJob> full = {tc_job(s, nullptr, nullptr, s.chan_group)};
+    // exact jobs longer than one exact segment, shape and segments left to the
+    // plan: one checked optimistic segment per pair-mode item
+    p->checked = job->kind == MWAX_KIND_EXACT && job->flush_blocks == 0 &&
+                 (job->mma_shape == 0 || job->mma_shape == 3) && s.flush_blocks < s.kb &&
+                 s.n_tiles <= 255;
+    if (p->checked) full[0].flush_blocks = s.kb;
     p->mode = choose_mode(job->mma_shape, full);
     if (p->mode < 0) {
       free_plan(p);
@@ -526,8 +559,18 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
     if (e == cudaSuccess && p->mode == 2) {
       const int last = (int)(s.job.n_chan % s.chan_group);
       std::vector<TcJob> tail;
-      if (last) tail.push_back(tc_job(s, nullptr, nullptr, last));
+      if (last) {
+        tail.push_back(tc_job(s, nullptr, nullptr, last));
+        tail[0].flush_blocks = full[0].flush_blocks;
+      }
       e = upload_items(p, full, tail);
+    }
+    if (e == cudaSuccess && p->checked) {
+      e = plan_alloc(reinterpret_cast<void **>(&p->bad), (size_t)(s.chan_group + 1) * sizeof(int32_t));
+      if (e == cudaSuccess)
+        e = plan_alloc(reinterpret_cast<void **>(&p->recomputed), sizeof(unsigned long long));
+      if (e == cudaSuccess) e = cudaMemsetAsync(p->recomputed, 0, sizeof(unsigned long long), stream);
+      if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, correlate_tc_max_stages(0), 0);
     }
     if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->mode);
     if (e != cudaSuccess) {
@@ -615,6 +658,7 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   info->grid = plan->sm_count;
   info->stages = plan->stages;
   info->mma_shape = plan->mode + 1;
+  info->checked_segment = plan->checked ? 1 : 0;
   info->pipeline = plan->overlap ? 2 : 1;
   info->prefetch = plan->prefetch;
   info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
@@ -638,6 +682,19 @@ mwax_status mwax_plan_status(mwax_plan_t plan) {
   if (e == cudaSuccess) e = cudaMemsetAsync(plan->status, 0, sizeof(int32_t), plan->stream);
   if (e != cudaSuccess) return cuda_status(e);
   return (mwax_status)v;
+}
+
+mwax_status mwax_plan_recomputed_channels(mwax_plan_t plan, int64_t *n_channels) {
+  if (!plan || !n_channels) return MWAX_ERR_INVALID_ARG;
+  *n_channels = 0;
+  if (!plan->recomputed) return MWAX_OK;
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, plan->recomputed, sizeof(v), cudaMemcpyDeviceToHost, plan->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->recomputed, 0, sizeof(v), plan->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  *n_channels = (int64_t)v;
+  return MWAX_OK;
 }
 
 mwax_status mwax_correlate(mwax_plan_t plan, const void *voltages, int n_inputs, int n_chan,

@@ -84,6 +84,10 @@ struct TcLaunch {
   unsigned long long timeout_ns;
   const int4 *items = nullptr;  // mode 2: device work list from build_pair_items
   int64_t n_items = 0;
+  // modes 0/1, one job: correlate only the channels chan_map[0 .. *n_chan_dev)
+  // (device memory, written by an earlier launch on the stream)
+  const int32_t *chan_map = nullptr;
+  const int32_t *n_chan_dev = nullptr;
 };
 
 // Encodes one TMA descriptor per job and launches the persistent kernel over
@@ -100,6 +104,13 @@ cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode
 bool pair_mode_supported(const TcJob *jobs, int n_jobs);
 // The pair-mode work list of one launch over `jobs` (16 bytes per item).
 void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items);
+
+// After a pass that accumulated each item in one FP32 segment: append to
+// bad[1..] (count in bad[0], reset here) every channel of out[0 .. n_chan)
+// whose largest auto-correlation reached 2^24, so its result may be inexact,
+// and add their number to *recomputed.
+cudaError_t launch_exact_check(const int32_t *out, int64_t n_bl, int n_inputs, int n_chan,
+                               int32_t *bad, unsigned long long *recomputed, cudaStream_t s);
 
 // Fill the tuning fields of an all-auto job from the MWAX_TUNE_CACHE file.
 void apply_tune_cache(mwax_job *job);

@@ -146,21 +146,67 @@ def test_pair_mode_shapes(mw, bits, N, T, C, G):
 
 
 def test_pair_mode_choice(mw):
-    """Auto takes the pair mode exactly where the integration is one exact
-    segment; an explicit request elsewhere is refused."""
-    p = mw.Plan(256, 2, 20000, 4)
-    assert p.info().mma_shape == 3
-    p.close()
-    p = mw.Plan(256, 2, 20000, 8)  # 8-bit: 16 blocks per segment
-    assert p.info().mma_shape == 1
-    p.close()
-    p = mw.Plan(256, 2, 512, 8)  # exactly one segment
-    assert p.info().mma_shape == 3
-    p.close()
-    with pytest.raises(mw.MwaxError):
-        mw.Plan(256, 2, 513, 8, mma_shape=3)
+    """Auto takes the pair mode where the integration is one exact segment,
+    and the checked single segment for longer 8-bit exact jobs; explicit
+    segments or shapes are kept; a pair request that cannot be served is
+    refused."""
+    def info(*a, **kw):
+        p = mw.Plan(*a, **kw)
+        i = p.info()
+        p.close()
+        return i.mma_shape, i.checked_segment
+
+    assert info(256, 2, 20000, 4) == (3, 0)
+    assert info(256, 2, 512, 8) == (3, 0)  # exactly one segment (16 blocks)
+    assert info(256, 2, 20000, 8) == (3, 1)  # 8-bit, 16 blocks per exact segment
+    assert info(256, 2, 513, 8, mma_shape=3) == (3, 1)
+    assert info(256, 2, 20000, 8, mma_shape=1) == (1, 0)
+    assert info(256, 2, 20000, 8, flush_blocks=16) == (1, 0)
+    assert info(256, 2, 20000, 8, kind=mw.KIND_FP16) == (3, 0)
     with pytest.raises(mw.MwaxError):
         mw.Plan(256, 2, 2000, 4, mma_shape=3, flush_blocks=4)
+    with pytest.raises(mw.MwaxError):
+        mw.BatchPlan([(256, 2, 2000), (128, 2, 2000)], sample_bits=8, mma_shape=3)
+
+
+def _volt8(arr):
+    """[chan][time][input] complex integers -> packed 8+8-bit bytes (host)
+    and a device copy of them."""
+    import torch
+
+    raw = np.empty(arr.shape + (2,), np.int8)
+    raw[..., 0] = arr.real
+    raw[..., 1] = arr.imag
+    host = raw.view(np.uint8).ravel().copy()
+    return host, torch.from_numpy(host.copy()).cuda()
+
+
+@pytest.mark.parametrize("group", [0, 2])
+def test_checked_segment_recomputes_only_flagged_channels(mw, group):
+    """8-bit, T = 2000 (125 blocks, 8 exact segments): channels 1 and 4 carry
+    full-scale samples (Re V_ii = 2000 * 2 * 127^2 > 2^24), the others sigma
+    20 noise.  The one-segment pass is inexact on channels 1 and 4 only; the
+    check flags exactly those two and the narrow recompute makes the whole
+    output bit-exact, also across channel groups."""
+    import torch
+
+    N, C, T = 200, 6, 2000
+    rng = np.random.default_rng(9)
+    x = np.clip(np.rint(rng.normal(0, 20, (C, T, N, 2))), -127, 127)
+    x = x[..., 0] + 1j * x[..., 1]
+    for c in (1, 4):
+        x[c] = rng.choice([-127, 127], (T, N)) + 1j * rng.choice([-127, 127], (T, N))
+    host, v = _volt8(x)
+    kw = {"chan_group": group} if group else {}
+    p = mw.Plan(N, C, T, 8, **kw)
+    assert p.info().checked_segment == 1
+    out = p.correlate(v)
+    assert p.status() == 0
+    assert p.recomputed_channels() == 2
+    assert p.recomputed_channels() == 0  # read-and-clear
+    assert_exact(out.cpu().numpy(), oracle.correlate(host, 8, N, C, T), "checked")
+    p.close()
+    torch.cuda.synchronize()
 
 
 def test_pair_mode_largest_single_segment(mw):
@@ -179,8 +225,6 @@ def test_pair_mode_largest_single_segment(mw):
 def test_exact_window_big_then_small(mw, bits, shape):
     """Accumulator near the top of its segment window, then +-1 addends: any
     loss of low-order bits in the tensor-core accumulation shows up."""
-    if shape == 3 and bits == 8:
-        pytest.skip("8-bit integrations of several segments have no pair mode")
     T = 20000 if bits == 4 else 2000
     split = 19000 if bits == 4 else 500
     spec = synth.Spec("bs", 130, 2, T, bits, seed=11, kind=synth.SYNTH_BIGSMALL, t_split=split)
@@ -188,7 +232,7 @@ def test_exact_window_big_then_small(mw, bits, shape):
                  "big-small")
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES_ONE_SEGMENT)
 def test_exact_random_max_magnitude(mw, shape):
     spec = synth.Spec("rm", 256, 2, 3000, 8, seed=12, kind=synth.SYNTH_RANDMAX)
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR, mma_shape=shape), oracle_for(spec, range(2)),
@@ -336,7 +380,7 @@ def test_full_size_c2_overlapped_sampled(mw):
     _full_size(mw, spec, [0, 208, 209, 1500, 3071], pipeline=2)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", [0] + SHAPES)
 def test_full_size_c2_sampled(mw, shape):
     spec = synth.spec_c2()
     rng = np.random.default_rng(2)
