@@ -925,6 +925,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
 __global__ void __launch_bounds__(256) exact_check_kernel(const int32_t *out, int64_t n_bl,
                                                           int n_inputs, int32_t *bad,
                                                           unsigned long long *recomputed) {
+  // recomputed[0]: running total for the caller, recomputed[1]: this call
   const int c = blockIdx.x;
   const int32_t *o = out + (int64_t)c * n_bl * 2;
   uint32_t m = 0;
@@ -939,6 +940,7 @@ __global__ void __launch_bounds__(256) exact_check_kernel(const int32_t *out, in
     if (m >= (1u << 24)) {
       bad[1 + atomicAdd(bad, 1)] = c;
       atomicAdd(recomputed, 1ull);
+      atomicAdd(recomputed + 1, 1ull);
     }
   }
 }

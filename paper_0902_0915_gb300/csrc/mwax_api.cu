@@ -74,7 +74,16 @@ struct mwax_plan_s {
   // flush_blocks segments
   bool checked = false;
   int32_t *bad = nullptr;
-  unsigned long long *recomputed = nullptr;  // channels recomputed since the last read
+  // [0]: channels recomputed since the caller last read the count; [1]: in
+  // the current call (copied to recomp_host at the end of each call)
+  unsigned long long *recomputed = nullptr;
+  // adaptivity: after a call in which more than a quarter of the channels
+  // had to be recomputed, the next kNarrowCalls calls run the narrow shape
+  // directly, then the pair pass is tried again
+  unsigned long long *recomp_host = nullptr;  // pinned
+  cudaEvent_t ev_recomp = nullptr;
+  bool recomp_pending = false;
+  int narrow_calls_left = 0;
   // batch graphs: every job's unpack, then the one persistent correlate launch
   cudaGraphExec_t graph = nullptr, graph2 = nullptr;
   std::vector<const void *> graph_in;
@@ -315,10 +324,46 @@ mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt,
   return cuda_status(e);
 }
 
+constexpr int kNarrowCalls = 8;
+
+// Start of a call of a checked plan: true = pair pass + check, false = this
+// call runs the narrow shape (see mwax_plan_s::narrow_calls_left).
+bool checked_call_uses_pair(mwax_plan_s *p) {
+  if (p->recomp_pending && cudaEventQuery(p->ev_recomp) == cudaSuccess) {
+    p->recomp_pending = false;
+    if (*p->recomp_host * 4 > (unsigned long long)p->jobs[0].job.n_chan)
+      p->narrow_calls_left = kNarrowCalls;
+  }
+  if (p->narrow_calls_left > 0) {
+    --p->narrow_calls_left;
+    return false;
+  }
+  return true;
+}
+
+// End of a call of a checked plan that ran the pair pass: publish this
+// call's recompute count to the host without blocking.
+cudaError_t checked_call_done(mwax_plan_s *p, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(p->recomp_host, p->recomputed + 1, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->recomputed + 1, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_recomp, st);
+  if (e == cudaSuccess) p->recomp_pending = true;
+  return e;
+}
+
 mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op, int nc,
-                            void *out_c0, cudaStream_t st) {
+                            void *out_c0, cudaStream_t st, bool use_pair = true) {
   TcJob tj = tc_job(s, op, out_c0, nc);
   TcLaunch cfg = launch_cfg(p);
+  if (p->mode == 2 && !use_pair) {  // a checked plan's narrow call
+    cfg.mode = 0;
+    cfg.stages = correlate_tc_max_stages(0);
+    TimedLaunch tn(p, 1, st);
+    cudaError_t e = launch_correlate_tc(&tj, 1, cfg, st);
+    tn.done();
+    return cuda_status(e);
+  }
   if (p->mode == 2) {
     const bool full = nc == s.chan_group;
     cfg.items = full ? p->items : p->items + p->n_items_full;
@@ -350,10 +395,10 @@ mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op
 // Channels [c0, c0+nc) of a single-job tensor plan, one after the other on
 // `st`: unpack into the scratch, then one persistent correlate launch.
 mwax_status run_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
-                      void *out_c0, cudaStream_t st) {
+                      void *out_c0, cudaStream_t st, bool use_pair = true) {
   mwax_status r = unpack_group(p, s, volt, c0, nc, p->scratch, 0, st);
   if (r != MWAX_OK) return r;
-  return correlate_group(p, s, p->scratch, nc, out_c0, st);
+  return correlate_group(p, s, p->scratch, nc, out_c0, st, use_pair);
 }
 
 mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cudaStream_t st) {
@@ -371,13 +416,14 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
     return MWAX_OK;
   }
   uint8_t *out8 = reinterpret_cast<uint8_t *>(out);
+  const bool use_pair = !p->checked || checked_call_uses_pair(p);
   if (!p->overlap) {
     for (int64_t c0 = 0; c0 < s.job.n_chan; c0 += s.chan_group) {
       const int nc = (int)std::min<int64_t>(s.chan_group, s.job.n_chan - c0);
-      mwax_status r = run_group(p, s, volt, c0, nc, out8 + c0 * s.out_chan_bytes, st);
+      mwax_status r = run_group(p, s, volt, c0, nc, out8 + c0 * s.out_chan_bytes, st, use_pair);
       if (r != MWAX_OK) return r;
     }
-    return MWAX_OK;
+    return p->checked && use_pair ? cuda_status(checked_call_done(p, st)) : MWAX_OK;
   }
   // Overlapped: the unpack of group g+1 runs on the aux stream into the other
   // scratch buffer while group g correlates: either one small unpack CTA per
@@ -398,11 +444,11 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
     if (r != MWAX_OK) return r;
     if ((e = cudaEventRecord(p->ev_unpacked[k], p->aux)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaStreamWaitEvent(st, p->ev_unpacked[k], 0)) != cudaSuccess) return cuda_status(e);
-    r = correlate_group(p, s, buf[k], nc, out8 + c0 * s.out_chan_bytes, st);
+    r = correlate_group(p, s, buf[k], nc, out8 + c0 * s.out_chan_bytes, st, use_pair);
     if (r != MWAX_OK) return r;
     if ((e = cudaEventRecord(p->ev_freed[k], st)) != cudaSuccess) return cuda_status(e);
   }
-  return MWAX_OK;
+  return p->checked && use_pair ? cuda_status(checked_call_done(p, st)) : MWAX_OK;
 }
 
 void free_plan(mwax_plan_s *p) {
@@ -417,6 +463,8 @@ void free_plan(mwax_plan_s *p) {
   if (p->items) cudaFree(p->items);
   if (p->bad) cudaFree(p->bad);
   if (p->recomputed) cudaFree(p->recomputed);
+  if (p->recomp_host) cudaFreeHost(p->recomp_host);
+  if (p->ev_recomp) cudaEventDestroy(p->ev_recomp);
   if (p->aux) cudaStreamDestroy(p->aux);
   if (p->ev_start) cudaEventDestroy(p->ev_start);
   for (int k = 0; k < 2; ++k) {
@@ -568,8 +616,13 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
     if (e == cudaSuccess && p->checked) {
       e = plan_alloc(reinterpret_cast<void **>(&p->bad), (size_t)(s.chan_group + 1) * sizeof(int32_t));
       if (e == cudaSuccess)
-        e = plan_alloc(reinterpret_cast<void **>(&p->recomputed), sizeof(unsigned long long));
-      if (e == cudaSuccess) e = cudaMemsetAsync(p->recomputed, 0, sizeof(unsigned long long), stream);
+        e = plan_alloc(reinterpret_cast<void **>(&p->recomputed), 2 * sizeof(unsigned long long));
+      if (e == cudaSuccess)
+        e = cudaMemsetAsync(p->recomputed, 0, 2 * sizeof(unsigned long long), stream);
+      if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&p->recomp_host), sizeof(unsigned long long),
+                          cudaHostAllocDefault);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_recomp, cudaEventDisableTiming);
       if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, correlate_tc_max_stages(0), 0);
     }
     if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->mode);
@@ -834,6 +887,7 @@ mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int
   }
   const uint8_t *hin = reinterpret_cast<const uint8_t *>(voltages_host);
   uint8_t *hout = reinterpret_cast<uint8_t *>(out_host);
+  const bool use_pair = !plan->checked || checked_call_uses_pair(plan);
   // the copy streams must not start before earlier work on the plan's stream
   e = cudaEventRecord(plan->ev_comp[0], plan->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->h2d, plan->ev_comp[0], 0);
@@ -860,7 +914,7 @@ mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int
             s.job.n_time, reinterpret_cast<int32_t *>(plan->stage_out[k]) + (int64_t)c * s.n_bl * 2,
             plan->stream));
     } else {
-      r = run_group(plan, s, plan->stage_in[k], 0, nc, plan->stage_out[k], plan->stream);
+      r = run_group(plan, s, plan->stage_in[k], 0, nc, plan->stage_out[k], plan->stream, use_pair);
     }
     if (r != MWAX_OK) return r;
     e = cudaEventRecord(plan->ev_comp[k], plan->stream);
@@ -870,6 +924,7 @@ mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int
                           cudaMemcpyDeviceToHost, plan->d2h);
     if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[k], plan->d2h);
   }
+  if (e == cudaSuccess && plan->checked && use_pair) e = checked_call_done(plan, plan->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(plan->d2h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
   return cuda_status(e);

@@ -108,7 +108,7 @@ void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items);
 // After a pass that accumulated each item in one FP32 segment: append to
 // bad[1..] (count in bad[0], reset here) every channel of out[0 .. n_chan)
 // whose largest auto-correlation reached 2^24, so its result may be inexact,
-// and add their number to *recomputed.
+// and add their number to recomputed[0] and recomputed[1].
 cudaError_t launch_exact_check(const int32_t *out, int64_t n_bl, int n_inputs, int n_chan,
                                int32_t *bad, unsigned long long *recomputed, cudaStream_t s);
 

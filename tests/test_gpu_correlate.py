@@ -181,6 +181,30 @@ def _volt8(arr):
     return host, torch.from_numpy(host.copy()).cuda()
 
 
+def test_checked_segment_adapts_to_full_scale_input(mw):
+    """Every channel at full scale: the first call recomputes them all; the
+    plan then runs the narrow shape for the next 8 calls (nothing recomputed)
+    and tries the one-segment pass again on the 10th.  Exact every time."""
+    import torch
+
+    N, C, T = 200, 8, 2000
+    rng = np.random.default_rng(10)
+    x = rng.choice([-127, 127], (C, T, N)) + 1j * rng.choice([-127, 127], (C, T, N))
+    host, v = _volt8(x)
+    ref = oracle.correlate(host, 8, N, C, T)
+    p = mw.Plan(N, C, T, 8)
+    counts = []
+    for call in range(10):
+        out = p.correlate(v)
+        assert p.status() == 0  # (synchronises: the next call sees this one's count)
+        counts.append(p.recomputed_channels())
+        if call in (0, 1, 9):
+            assert_exact(out.cpu().numpy(), ref, f"adaptive call {call}")
+    assert counts == [C] + [0] * 8 + [C]
+    p.close()
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("group", [0, 2])
 def test_checked_segment_recomputes_only_flagged_channels(mw, group):
     """8-bit, T = 2000 (125 blocks, 8 exact segments): channels 1 and 4 carry
