@@ -139,9 +139,11 @@ typedef struct {
                                 channel exceeds that channel's largest V_ii, so all
                                 other channels are exact) and a narrow launch
                                 recomputes those channels with flush_blocks segments;
-                                the output is exact either way.  Chosen when kind is
-                                exact and mma_shape and flush_blocks are auto (0) or
-                                mma_shape is 3.  0 otherwise.                           */
+                                the output is exact either way.  After a call that
+                                recomputed more than a quarter of its channels, the
+                                next 8 calls run the narrow shape directly.  Chosen
+                                when kind is exact and mma_shape and flush_blocks are
+                                auto (0) or mma_shape is 3.  0 otherwise.               */
   int32_t reserved_info;
 } mwax_plan_info;
 
