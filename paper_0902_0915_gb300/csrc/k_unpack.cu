@@ -162,11 +162,10 @@ __global__ void __launch_bounds__(512) unpack8_persist_kernel(const uint8_t *__r
 
 // Four nibbles (the low nibble of each byte of x) -> four E4M3 codes, one per
 // byte.  The low three bits index an 8-entry byte table held in two registers
-// (byte_perm); the sign bit picks the table of negative values.  The four
-// 3-bit indices are packed into the selector with one shift-or and one byte
-// permute (l | l >> 4 holds index k | index k+1 << 4 in byte k), and the sign
-// mask comes from byte_perm's sign-replicate selectors on x << 4 (bit 3 of
-// each nibble moved to bit 7 of its byte).
+// (byte_perm, whose selectors use three bits per byte); the sign bit picks
+// the table of negative values.  The four 3-bit indices are packed into the
+// selector with one shift-or and one byte permute (l | l >> 4 holds index k
+// | index k+1 << 4 in byte k).
 __device__ __forceinline__ uint32_t nib4_to_e4m3(uint32_t x) {
   const uint32_t pos_lo = 0x44403800u, pos_hi = 0x4E4C4A48u;  // 0..7
   const uint32_t neg_lo = 0xCACCCED0u, neg_hi = 0xB8C0C4C8u;  // -8..-1
@@ -174,7 +173,7 @@ __device__ __forceinline__ uint32_t nib4_to_e4m3(uint32_t x) {
   const uint32_t sel = __byte_perm(l | (l >> 4), 0u, 0x0020u);
   const uint32_t p = __byte_perm(pos_lo, pos_hi, sel);
   const uint32_t n = __byte_perm(neg_lo, neg_hi, sel);
-  const uint32_t m = __byte_perm(x << 4, 0u, 0xBA98u);  // 0xFF where the nibble is negative
+  const uint32_t m = ((x >> 3) & 0x01010101u) * 0xFFu;  // 0xFF where the nibble is negative
   return (p & ~m) | (n & m);
 }
 
