@@ -101,13 +101,7 @@ typedef struct {
   int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
                               plan's stream, 2 = unpack the next group (second stream,
                               second scratch buffer) while the current group correlates,
-                              see unpack_sms; 3 = the correlate launch of each group
-                              also unpacks the next group into a second scratch buffer
-                              with four of its warps (pair mode, mma_shape 3, only; N
-                              even for 8-bit samples, a multiple of 4 for 4-bit; with
-                              chan_group 0 the channels are split into about 8 groups,
-                              so only the first group's unpack is not hidden); 0 = auto:
-                              3 where it applies, else 1                                 */
+                              see unpack_sms; 0 = auto (1)                               */
   int32_t timeout_ms;      /* limit of every device-side wait, ms (0 = 2000)              */
   int32_t test_fault;      /* failure-detection tests only, 0 = off: with k > 0 the
                               epilogue of the tensor correlator withholds the release of
@@ -133,8 +127,7 @@ typedef struct {
   int32_t stages;            /* shared-memory pipeline stages                          */
   int32_t prefetch;          /* K-blocks of L2 prefetch ahead of the TMA loads         */
   int32_t mma_shape;         /* 1 = N128, 2 = N256 [Re | Im], 3 = two pairs per item   */
-  int32_t pipeline;          /* 1 = sequential, 2 = overlapped unpack/correlate, 3 = next
-                                group unpacked inside the correlate launch             */
+  int32_t pipeline;          /* 1 = sequential, 2 = overlapped unpack/correlate        */
   int64_t scratch_bytes;     /* device scratch owned by the plan                       */
   int64_t work_items;        /* work items per call: (job, channel, tile pair), or the
                                 two-pair items of mma_shape 3                          */

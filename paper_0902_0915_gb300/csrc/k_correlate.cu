@@ -54,7 +54,6 @@
 #include <string.h>
 
 #include "mwax_internal.h"
-#include "unpack_rows.cuh"
 
 namespace mwax {
 namespace {
@@ -83,10 +82,7 @@ struct Shape {
   static constexpr int block_bytes = (MODE == kModeNarrow ? 2 : 3) * kTileBytes;  // tiles of one block
   static constexpr int stage_bytes = kps * block_bytes;
   static constexpr int max_stages = MODE == kModeWide ? 4 : 2;
-  // pair mode: warps epi0 .. epi0+3 drain the accumulator, the other four
-  // unpack the next channel group; the other shapes drain with all eight
-  static constexpr int drain_warps = MODE == kModePair ? 4 : 8;
-  static constexpr int epi_bytes = MODE == kModePair ? drain_warps * kEpiStageBytes : 0;
+  static constexpr int epi_bytes = MODE == kModePair ? 8 * kEpiStageBytes : 0;
 };
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;  // re 128 | im 128
@@ -112,13 +108,6 @@ struct KParams {
   unsigned long long timeout_ns;
   int32_t n_jobs, stages, prefetch;
   int32_t withhold_seg;  // test hook: segment whose accumulator release the epilogue withholds (-1: none)
-  // pair mode: the next channel group [un_chan0, un_chan0 + un_n_chan) of
-  // the samples un_volt, converted into the operand rows un_op by the spare
-  // epilogue warps during this launch (un_n_chan 0: nothing to do)
-  const uint8_t *un_volt;
-  uint8_t *un_op;
-  int64_t un_chan0;
-  int32_t un_n_chan, un_N, un_T, un_n_rows, un_kb;
 };
 
 struct KMaps {
@@ -497,26 +486,15 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
       mbar_wait(drain, 0, nullptr, tmo);
     }
     __syncwarp();
-  } else if (warp >= Sh::epi0 + Sh::drain_warps) {
-    // ---------------- unpack of the next channel group ----------------
-    // Global loads and stores only (no shared memory, no waits): these warps
-    // convert a share of the next group's samples into the other operand
-    // buffer while the tensor cores work on this group.
-    if (p.un_n_chan > 0) {
-      const int64_t first = (int64_t)blockIdx.x * (4 * 32) +
-                            (threadIdx.x - (Sh::epi0 + Sh::drain_warps) * 32);
-      unpack_rows<BITS>(p.un_volt, p.un_op, p.un_N, p.un_T, p.un_n_rows, p.un_kb, p.un_chan0,
-                        p.un_n_chan, first, (int64_t)gridDim.x * (4 * 32));
-    }
   } else {
     // ---------------- epilogue: convert + integration dump ----------------
-    // Warp q (tensor-memory lanes 32q.., the rows of the tile) drains both
-    // pairs of the item.  Each 32-column chunk goes through this warp's
-    // shared-memory buffer, 16 columns at a time: lane r writes row r (16 (re,
-    // im) words, XOR-swizzled so the 16 lanes of a phase hit distinct banks),
-    // then each store instruction writes rows r and r+1 as two contiguous
-    // 128-byte runs.
+    // Warp (q, h): tensor-memory lanes 32q.. (rows of the tile) of pair h.
+    // Each 32-column chunk goes through this warp's shared-memory buffer, 16
+    // columns at a time: lane r writes row r (16 (re, im) words, XOR-swizzled
+    // so the 16 lanes of a phase hit distinct banks), then each store
+    // instruction writes rows r and r+1 as two contiguous 128-byte runs.
     const int q = warp & 3;
+    const int h = (warp - Sh::epi0) >> 2;
     uint8_t *stg = epi_smem + (warp - Sh::epi0) * kEpiStageBytes;
     uint32_t n_it = 0;
     for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
@@ -527,68 +505,69 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
         if (!got) raise_timeout(abort_flag, p.status);
         epi_flag[n_it & 1u] = got ? 1 : 0;
       }
-      named_bar_sync(1, Sh::drain_warps * 32);
+      named_bar_sync(1, 8 * 32);
       if (!epi_flag[n_it & 1u]) break;
       tc_fence_after();
-      const int n_pairs_item = it.type == kItemOne ? 1 : 2;
+      const bool has = h == 0 || it.type != kItemOne;
+      int c, I, J;
+      if (it.type == kItemShared) {
+        c = it.c0;
+        I = it.I0;
+        J = h ? it.J1 : it.J0;
+      } else if (it.type == kItemTwoDiag) {
+        c = h ? it.c1 : it.c0;
+        I = h ? it.I1 : it.I0;
+        J = I;
+      } else {
+        c = it.c0;
+        I = it.I0;
+        J = it.J0;
+      }
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kTile);
+      uint32_t *out = reinterpret_cast<uint32_t *>(jb.out) + (int64_t)c * jb.n_bl * 2;
       const int n = jb.n_inputs;
-      for (int h = 0; h < n_pairs_item; ++h) {
-        int c, I, J;
-        if (it.type == kItemShared) {
-          c = it.c0;
-          I = it.I0;
-          J = h ? it.J1 : it.J0;
-        } else if (it.type == kItemTwoDiag) {
-          c = h ? it.c1 : it.c0;
-          I = h ? it.I1 : it.I0;
-          J = I;
-        } else {
-          c = it.c0;
-          I = it.I0;
-          J = it.J0;
-        }
-        const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kTile);
-        uint32_t *out = reinterpret_cast<uint32_t *>(jb.out) + (int64_t)c * jb.n_bl * 2;
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          uint32_t vre[32], vim[32];
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t vre[32], vim[32];
+        if (has) {
           tc_ld32(trow + 32 * cc, vre);
           tc_ld32(trow + 2 * kTile + 32 * cc, vim);
           tc_wait_ld();
-          if (cc == 3 && h == n_pairs_item - 1) {
-            // every column of this warp is in registers: release the
-            // accumulator (test hook: withholding one release makes the MMA
-            // warp's bounded wait run out -> MWAX_ERR_TIMEOUT, clean exit)
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0 && (int)n_it != p.withhold_seg) mbar_arrive(tempty);
+        }
+        if (cc == 3) {
+          // every column of this warp is in registers: release the accumulator
+          // (test hook: withholding one release makes the MMA warp's bounded
+          // wait run out -> MWAX_ERR_TIMEOUT, clean exit)
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0 && (int)n_it != p.withhold_seg) mbar_arrive(tempty);
+        }
+        if (!has) continue;
+        if constexpr (KIND == MWAX_KIND_EXACT) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            vre[k] = (uint32_t)__float2int_rn(__uint_as_float(vre[k]));
+            vim[k] = (uint32_t)__float2int_rn(__uint_as_float(vim[k]));
           }
-          if constexpr (KIND == MWAX_KIND_EXACT) {
+        }
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              vre[k] = (uint32_t)__float2int_rn(__uint_as_float(vre[k]));
-              vim[k] = (uint32_t)__float2int_rn(__uint_as_float(vim[k]));
-            }
+        for (int half = 0; half < 2; ++half) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            *reinterpret_cast<uint2 *>(stg + lane * 128 + ((k ^ (lane & 15)) << 3)) =
+                make_uint2(vre[16 * half + k], vim[16 * half + k]);
+          __syncwarp();
+          const int col = lane & 15;
+          const int j = J * kTile + 32 * cc + 16 * half + col;
+#pragma unroll
+          for (int r2 = 0; r2 < 16; ++r2) {
+            const int r = 2 * r2 + (lane >> 4);
+            const uint2 val = *reinterpret_cast<const uint2 *>(stg + r * 128 + ((col ^ (r & 15)) << 3));
+            const int i = I * kTile + q * 32 + r;
+            if (i < n && j <= i)
+              *reinterpret_cast<uint2 *>(out + 2 * ((int64_t)i * (i + 1) / 2 + j)) = val;
           }
-#pragma unroll
-          for (int half = 0; half < 2; ++half) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-              *reinterpret_cast<uint2 *>(stg + lane * 128 + ((k ^ (lane & 15)) << 3)) =
-                  make_uint2(vre[16 * half + k], vim[16 * half + k]);
-            __syncwarp();
-            const int col = lane & 15;
-            const int j = J * kTile + 32 * cc + 16 * half + col;
-#pragma unroll
-            for (int r2 = 0; r2 < 16; ++r2) {
-              const int r = 2 * r2 + (lane >> 4);
-              const uint2 val = *reinterpret_cast<const uint2 *>(stg + r * 128 + ((col ^ (r & 15)) << 3));
-              const int i = I * kTile + q * 32 + r;
-              if (i < n && j <= i)
-                *reinterpret_cast<uint2 *>(out + 2 * ((int64_t)i * (i + 1) / 2 + j)) = val;
-            }
-            __syncwarp();
-          }
+          __syncwarp();
         }
       }
       ++n_it;
@@ -632,7 +611,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), Sh::drain_warps);
+      mbar_init(tempty(b), 8);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -1129,22 +1108,6 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   }
   kp.chan_map = cfg.chan_map;  // (items stays the bound for all n_chan channels)
   kp.n_chan_dev = cfg.n_chan_dev;
-  if (cfg.un_n_chan > 0) {
-    // spare-warp unpack of the next group: pair mode only, whole 4-byte
-    // sample words (N even for 8-bit, N % 4 == 0 for 4-bit samples)
-    if (cfg.mode != kModePair || !cfg.un_volt || !cfg.un_op || cfg.un_kb < 1 ||
-        cfg.un_n_rows < cfg.un_N || cfg.un_n_rows % kTile ||
-        (cfg.sample_bits == 8 ? cfg.un_N % 2 : cfg.un_N % 4) != 0)
-      return cudaErrorInvalidValue;
-    kp.un_volt = cfg.un_volt;
-    kp.un_op = cfg.un_op;
-    kp.un_chan0 = cfg.un_chan0;
-    kp.un_n_chan = cfg.un_n_chan;
-    kp.un_N = cfg.un_N;
-    kp.un_T = cfg.un_T;
-    kp.un_n_rows = cfg.un_n_rows;
-    kp.un_kb = cfg.un_kb;
-  }
   kp.status = cfg.status;
   kp.n_items = items;
   kp.timeout_ns = cfg.timeout_ns;

@@ -59,9 +59,6 @@ struct mwax_plan_s {
   // overlapped pipeline: unpack of group g+1 (aux stream) runs beside the
   // persistent correlate of group g (plan stream)
   bool overlap = false;
-  // fused pipeline (pair mode): the correlate launch of group g also unpacks
-  // group g+1 into the other scratch buffer with its spare epilogue warps
-  bool fused = false;
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_start = nullptr, ev_unpacked[2] = {nullptr, nullptr}, ev_freed[2] = {nullptr, nullptr};
   int32_t *status = nullptr;
@@ -148,7 +145,7 @@ mwax_status check_job(const mwax_job &j) {
   if (j.engine != MWAX_ENGINE_TENSOR && j.engine != MWAX_ENGINE_PLAIN) return MWAX_ERR_INVALID_ARG;
   if (j.flush_blocks < 0 || j.chan_group < 0) return MWAX_ERR_INVALID_ARG;
   if (j.mma_shape < 0 || j.mma_shape > 3) return MWAX_ERR_INVALID_ARG;
-  if (j.pipeline < 0 || j.pipeline > 3) return MWAX_ERR_INVALID_ARG;
+  if (j.pipeline < 0 || j.pipeline > 2) return MWAX_ERR_INVALID_ARG;
   if (j.stages < 0 || j.stages == 1 ||
       j.stages > correlate_tc_max_stages(j.mma_shape > 0 ? j.mma_shape - 1 : 0))
     return MWAX_ERR_INVALID_ARG;
@@ -328,7 +325,6 @@ mwax_status unpack_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt,
 }
 
 constexpr int kNarrowCalls = 8;
-constexpr int kFusedGroups = 8;
 
 // Start of a call of a checked plan: true = pair pass + check, false = this
 // call runs the narrow shape (see mwax_plan_s::narrow_calls_left).
@@ -357,21 +353,9 @@ cudaError_t checked_call_done(mwax_plan_s *p, cudaStream_t st) {
 }
 
 mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op, int nc,
-                            void *out_c0, cudaStream_t st, bool use_pair = true,
-                            const uint8_t *next_volt = nullptr, int64_t next_c0 = 0,
-                            int next_nc = 0, uint8_t *next_op = nullptr) {
+                            void *out_c0, cudaStream_t st, bool use_pair = true) {
   TcJob tj = tc_job(s, op, out_c0, nc);
   TcLaunch cfg = launch_cfg(p);
-  if (next_nc > 0) {  // fused pipeline: the next group's unpack rides along
-    cfg.un_volt = next_volt;
-    cfg.un_op = next_op;
-    cfg.un_chan0 = next_c0;
-    cfg.un_n_chan = next_nc;
-    cfg.un_N = s.job.n_inputs;
-    cfg.un_T = s.job.n_time;
-    cfg.un_n_rows = s.n_tiles * kTile;
-    cfg.un_kb = s.kb;
-  }
   if (p->mode == 2 && !use_pair) {  // a checked plan's narrow call
     cfg.mode = 0;
     cfg.stages = correlate_tc_max_stages(0);
@@ -433,25 +417,6 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
   }
   uint8_t *out8 = reinterpret_cast<uint8_t *>(out);
   const bool use_pair = !p->checked || checked_call_uses_pair(p);
-  if (p->fused && use_pair) {
-    // group 0 unpacked alone; every correlate launch then unpacks the next
-    // group into the other buffer with its spare warps
-    uint8_t *buf[2] = {p->scratch, p->scratch2};
-    const int G = s.chan_group;
-    const int64_t C = s.job.n_chan;
-    mwax_status r = unpack_group(p, s, volt, 0, (int)std::min<int64_t>(G, C), buf[0], 0, st);
-    if (r != MWAX_OK) return r;
-    int64_t g = 0;
-    for (int64_t c0 = 0; c0 < C; c0 += G, ++g) {
-      const int nc = (int)std::min<int64_t>(G, C - c0);
-      const int64_t c1 = c0 + G;
-      const int nn = c1 < C ? (int)std::min<int64_t>(G, C - c1) : 0;
-      r = correlate_group(p, s, buf[g & 1], nc, out8 + c0 * s.out_chan_bytes, st, true, volt, c1,
-                          nn, buf[(g + 1) & 1]);
-      if (r != MWAX_OK) return r;
-    }
-    return p->checked ? cuda_status(checked_call_done(p, st)) : MWAX_OK;
-  }
   if (!p->overlap) {
     for (int64_t c0 = 0; c0 < s.job.n_chan; c0 += s.chan_group) {
       const int nc = (int)std::min<int64_t>(s.chan_group, s.job.n_chan - c0);
@@ -615,25 +580,8 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
       free_plan(p);
       return MWAX_ERR_INVALID_ARG;
     }
-    const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : s.job.n_inputs % 4 == 0;
-    // fused pipeline (pipeline 3, and the default where it applies): pair
-    // mode, whole 4-byte sample words, more than one channel; the channels
-    // are then split into about kFusedGroups groups so that only the first
-    // group's unpack is not hidden
-    const bool fused_ok = p->mode == 2 && even && s.job.n_chan > 1;
-    if (job->pipeline == 3 && !fused_ok) {
-      free_plan(p);
-      return MWAX_ERR_UNSUPPORTED;
-    }
-    p->fused = fused_ok && (job->pipeline == 3 || job->pipeline == 0);
-    if (p->fused && job->chan_group == 0) {
-      const int64_t g =
-          std::min<int64_t>(s.chan_group, (s.job.n_chan + kFusedGroups - 1) / kFusedGroups);
-      s.chan_group = (int)std::max<int64_t>(1, g);
-      p->jobs[0].chan_group = s.chan_group;
-      full[0].n_chan = s.chan_group;
-    }
     const int64_t one = s.op_chan_bytes * s.chan_group;
+    const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : s.job.n_inputs % 4 == 0;
     // unpack_sms 0: the small unpack CTA runs beside the correlate on every SM
     // where the shape allows it, else 20 SMs are set aside for the unpack
     // (pair mode fills the shared memory: no room for a co-resident unpack CTA)
@@ -643,13 +591,9 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
                         : 20;
     p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan && even &&
                  p->unpack_sms < p->sm_count;
-    p->scratch_bytes = one * (p->overlap || p->fused ? 2 : 1);
+    p->scratch_bytes = one * (p->overlap ? 2 : 1);
     cudaError_t e = plan_alloc(reinterpret_cast<void **>(&p->scratch), (size_t)one);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)one, stream);
-    if (e == cudaSuccess && p->fused) {
-      e = plan_alloc(reinterpret_cast<void **>(&p->scratch2), (size_t)one);
-      if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch2, 0, (size_t)one, stream);
-    }
     if (e == cudaSuccess && p->overlap) {
       e = plan_alloc(reinterpret_cast<void **>(&p->scratch2), (size_t)one);
       if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch2, 0, (size_t)one, stream);
@@ -768,7 +712,7 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   info->stages = plan->stages;
   info->mma_shape = plan->mode + 1;
   info->checked_segment = plan->checked ? 1 : 0;
-  info->pipeline = plan->fused ? 3 : plan->overlap ? 2 : 1;
+  info->pipeline = plan->overlap ? 2 : 1;
   info->prefetch = plan->prefetch;
   info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
   int64_t items = 0;

@@ -88,13 +88,6 @@ struct TcLaunch {
   // (device memory, written by an earlier launch on the stream)
   const int32_t *chan_map = nullptr;
   const int32_t *n_chan_dev = nullptr;
-  // mode 2, one job: the spare epilogue warps convert channels [un_chan0,
-  // un_chan0 + un_n_chan) of un_volt into the operand rows un_op (the next
-  // channel group) during the launch; un_n_chan 0: nothing
-  const uint8_t *un_volt = nullptr;
-  uint8_t *un_op = nullptr;
-  int64_t un_chan0 = 0;
-  int un_n_chan = 0, un_N = 0, un_T = 0, un_n_rows = 0, un_kb = 0;
 };
 
 // Encodes one TMA descriptor per job and launches the persistent kernel over

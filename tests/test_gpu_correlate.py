@@ -145,48 +145,6 @@ def test_pair_mode_shapes(mw, bits, N, T, C, G):
                  f"pair {bits},{N},{T},{C},{G}")
 
 
-@pytest.mark.parametrize("bits,N,T,C,G", [
-    (4, 256, 2000, 9, 2), (4, 300, 130, 7, 3), (4, 1024, 64, 5, 2), (4, 52, 1000, 6, 0),
-    (8, 200, 1000, 7, 3), (8, 1024, 100, 5, 2), (8, 130, 33, 9, 4), (8, 386, 700, 4, 0)])
-def test_fused_pipeline(mw, bits, N, T, C, G):
-    """pipeline 3: each pair-mode correlate launch also converts the next
-    channel group's samples (four spare warps, plain loads and stores) into
-    the second operand buffer.  Several groups with a ragged last one, N not
-    a multiple of 128 (padding rows written as zeros), ragged T; 8-bit cases
-    longer than one exact segment also run the checked single segment."""
-    spec = synth.Spec("fu", N, C, T, bits, seed=N + T + 7 * C, sigma=2 if bits == 4 else 40,
-                      tone_amp=0.3)
-    kw = {"chan_group": G} if G else {}
-    import torch
-
-    v = device_volt(spec)
-    p = mw.Plan(N, C, T, bits, pipeline=3, **kw)
-    assert p.info().pipeline == 3
-    out = p.correlate(v)
-    out = p.correlate(v, out)  # second call: both buffers reused
-    assert p.status() == 0
-    assert_exact(out.cpu().numpy(), oracle_for(spec, range(C)), f"fused {bits},{N},{T},{C},{G}")
-    p.close()
-    torch.cuda.synchronize()
-
-
-def test_fused_pipeline_choice(mw):
-    def pipe(*a, **kw):
-        p = mw.Plan(*a, **kw)
-        i = p.info()
-        p.close()
-        return i.pipeline, i.chan_group
-
-    assert pipe(256, 768, 20000, 4) == (3, 96)  # split into 8 groups
-    assert pipe(1024, 3072, 100, 8)[0] == 3
-    assert pipe(130, 4, 100, 4)[0] == 1  # 4-bit needs N % 4 == 0
-    assert pipe(256, 1, 100, 4)[0] == 1  # one channel: nothing to overlap
-    assert pipe(256, 8, 100, 4, mma_shape=1)[0] == 1  # narrow shape: no spare warps
-    assert pipe(256, 8, 100, 4, pipeline=1)[0] == 1
-    with pytest.raises(mw.MwaxError):
-        mw.Plan(130, 4, 100, 4, pipeline=3)
-
-
 def test_pair_mode_choice(mw):
     """Auto takes the pair mode where the integration is one exact segment,
     and the checked single segment for longer 8-bit exact jobs; explicit
