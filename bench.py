@@ -525,14 +525,19 @@ def run_grid(args):
     clk = clocks.stop()
     ms = a.elapsed_time(b) / args.steps
     n_pts = gp.n_points
+    n_entries = gp.n_entries
     W = geo["W"]
-    # algorithmic work: every gridded point adds 4 complex values times a
-    # weight to the W x W cells of its support: 8 FMA (16 flops) per cell
-    flops = n_pts * W * W * 16.0
-    props = torch.cuda.get_device_properties(0)
-    sm_mhz = 2070.0
-    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 x clock
-    achieved = flops / (ms / 1e3) / 1e12
+    Ng = geo["Ng"]
+    # one grid call streams the stored weight factors (12 x 4 B per patch
+    # candidate), gathers 4 int32 pairs per point (32 B), writes
+    # and reads back the points' FP32 values (2 x 32 B), and writes the 4
+    # grids (8 B per cell)
+    bytes_call = 4.0 * n_entries + 96.0 * n_pts + 32.0 * Ng * Ng
+    peaks, src = load_peaks()
+    achieved = bytes_call / (ms / 1e3) / 1e9
+    # context: every gridded point adds 4 complex values times a weight to the
+    # W x W cells of its support, 8 FMA (16 flops) per cell
+    tflops = n_pts * W * W * 16.0 / (ms / 1e3) / 1e12
     desc = (f"gridding of the c1 correlation ({n_tiles} tiles x 2 pol, {C} ch from "
             f"{geo['f0'] / 1e6:.2f} MHz) onto 4 x {geo['Ng']}^2 cells of {geo['du']} wavelength, "
             f"Gaussian support {W}")
@@ -541,13 +546,14 @@ def run_grid(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (the c1 correlation of seeded voltages; seeded tile positions)",
-            "config": {"workload": f"c5: {desc}", "points": n_pts,
-                       "l2": f"points {n_pts * 48 / 1e9:.2f} GB + grids {4 * geo['Ng'] ** 2 * 8 / 1e9:.2f} GB"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "grid_values_kernel + grid_gather_kernel (one grid call)",
-                         "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flops x 2070 MHz (derived)"},
-            "plan_s": plan_s, "gpu_launches": 2 * args.steps, "clocks": clk}
+            "config": {"workload": f"c5: {desc}", "points": n_pts, "operator_entries": n_entries,
+                       "l2": f"weight factors {4 * n_entries / 1e9:.2f} GB + grids {32 * Ng * Ng / 1e9:.2f} GB > L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "kernel": "grid_values_kernel + grid_apply_heavy_kernel + grid_apply_kernel (one grid call)",
+                         "algorithmic_bytes": bytes_call, "fp32_tflops": tflops,
+                         "peak_source": src},
+            "plan_s": plan_s, "gpu_launches": 3 * args.steps, "clocks": clk}
     gp.close()
     if not args.no_cpu:
         sub = 8

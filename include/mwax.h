@@ -322,20 +322,27 @@ mwax_status mwax_calib_solve(const float *V, const float *M, float *g, int n_inp
  *
  * mwax_grid_plan: geometry only (host tile_xy [n_tiles][2] doubles, copied);
  *   bins the points by the first cell of their support on the GPU (counting
- *   sort, each bin in ascending point order).  Blocks until done.  n_tiles in
- *   [2, 4096], Ng even in [8, 16384], W in [1, 31]; INVALID_ARG otherwise,
- *   OOM / CUDA on device failures.
+ *   sort, each bin in ascending point order), then stores the weights: the
+ *   cells are cut into 4 x 8 patches, and for every point whose support can
+ *   reach a patch (its candidates) the separable Gaussian's 8 column and 4
+ *   row factors, computed in FP64 and kept in FP32 (0 outside the support):
+ *   48 bytes per patch candidate, at most 12 patches per point at W = 7.  Blocks
+ *   until done.  n_tiles in [2, 4096], Ng even in [8, 16384], W in [1, 31];
+ *   INVALID_ARG otherwise; UNSUPPORTED when the candidates exceed 2^31; OOM /
+ *   CUDA on device failures.
  * mwax_grid: vis = device correlator output [n_chan][N(N+1)/2][2] int32,
  *   N = 2 n_tiles (the layout mwax_correlate writes); grids = device float
  *   [4][Ng][Ng][2] (re, im), every cell written.  Both 8-byte aligned.
  *   Asynchronous on the plan's stream; deterministic (fixed summation order).
- * mwax_grid_plan_points: number of points that reach the grid. */
+ * mwax_grid_plan_points: number of points that reach the grid.
+ * mwax_grid_plan_entries: stored weight factors (12 per patch candidate). */
 typedef struct mwax_grid_plan_s *mwax_grid_plan_t;
 mwax_status mwax_grid_plan(mwax_grid_plan_t *plan, const double *tile_xy, int n_tiles, int n_chan,
                            double f0, double df, int Ng, double du, int W, double sigma,
                            cudaStream_t stream);
 mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids);
 int64_t mwax_grid_plan_points(mwax_grid_plan_t plan);
+int64_t mwax_grid_plan_entries(mwax_grid_plan_t plan);
 mwax_status mwax_grid_destroy(mwax_grid_plan_t plan);
 
 /* ---- Stokes conversion (FP32) ----------------------------------------------

@@ -100,6 +100,7 @@ SIGNATURES = {
                             _I, ctypes.c_double, _P]),
     "mwax_grid": (_I, [_P, _P, _P]),
     "mwax_grid_plan_points": (_I64, [_P]),
+    "mwax_grid_plan_entries": (_I64, [_P]),
     "mwax_grid_destroy": (_I, [_P]),
     "mwax_stokes": (_I, [_P, _I, ctypes.c_double, ctypes.c_double, _P, _P]),
     "mwax_calib_static_workspace_bytes": (_I64, []),
@@ -297,6 +298,11 @@ class GridPlan:
     @property
     def n_points(self) -> int:
         return int(lib().mwax_grid_plan_points(self._h))
+
+    @property
+    def n_entries(self) -> int:
+        """Stored weight factors (4 bytes each: 12 per patch candidate)."""
+        return int(lib().mwax_grid_plan_entries(self._h))
 
     def empty_grids(self):
         torch = _torch()

@@ -21,14 +21,23 @@
 //   2. counting sort by bin (integer atomics for counts and slots, an
 //      exclusive prefix sum for bin offsets), then every bin's ids sorted
 //      ascending so the order of each gathered sum is fixed;
-//   3. per sorted point: float offset of the position from the first
-//      support cell, last support cell (r_hi, s_hi), point id.
-// Grid call (per integration): a gather kernel reads each point's four
-// polarisation values from the int32 correlator output into the sorted
-// record; then every warp gathers a 4 x 8 patch of cells: it streams the
-// points whose support can reach the patch (per bin row, one contiguous range
-// of the sorted points) with broadcast loads, and each lane keeps the points
-// whose support contains its cell, in a fixed order.  Deterministic.
+//   3. per sorted point: last support cell (r_hi, s_hi), first support
+//      column, point id;
+//   4. the weights: the cells are cut into patches of 4 x 8 (one warp each);
+//      the candidates of a patch are the points whose support can reach it,
+//      in a fixed order (bin rows, then bin columns, then point id: per bin
+//      row one contiguous range of the sorted points).  The Gaussian is
+//      separable, w = wx(s - x) wy(r - y), and the support is a rectangle, so
+//      for every candidate the plan stores its 8 column factors and 4 row
+//      factors (12 floats, computed in FP64, 0 outside the support), and the
+//      patches in order of decreasing candidate count (the dense centre of
+//      the uv plane first, so the longest warps do not start last).
+// Grid call (per integration): one kernel gathers each sorted point's four
+// polarisation values from the int32 correlator output; then each warp walks
+// its patch's candidates in the plan's order, reads the candidate's values
+// once for the whole warp (a broadcast) and its 12 factors, and every lane
+// adds wx[col] wy[row] x values (four complex multiply-adds).  No support
+// tests and no exponentials per call; deterministic.
 #include <math.h>
 #include <string.h>
 
@@ -43,21 +52,12 @@ namespace {
 constexpr double kCLight = 299792458.0;
 constexpr int kScanBlock = 1024;
 
-// Positions are kept as offsets from the first support cell (x - s_lo,
-// y - r_lo, in [W/2 - 1, W/2]): a float holds those to ~1e-7 cells, where the
-// absolute coordinate (up to Ng) would lose ~1e-4.
-struct GeomRec {  // sorted point, geometry part (20 B)
-  float fx, fy;  // x - s_lo, y - r_lo
+// Weights are formed at plan time from the FP64 position, recomputed from the
+// point id (an absolute float coordinate up to Ng would lose ~1e-4 cells).
+struct GeomRec {  // sorted point (12 B)
   int hi;        // r_hi << 16 | s_hi (both in [0, Ng))
   int id;        // point id: ((c * n_tbl) + tbl) * 2 + side
   int slo;       // s_lo + W - 1
-};
-
-struct __align__(16) PointRec {  // sorted point with its values (48 B)
-  float fx, fy;
-  int hi;
-  int slo;  // s_lo + W - 1 (the bin column, >= 0)
-  float2 v[4];
 };
 
 __device__ __forceinline__ void tbl_pair(int tbl, int &a, int &b) {
@@ -78,7 +78,7 @@ struct GridGeom {
 
 // 1. positions, support bounds and bins (bin -1: no cell of the grid reached)
 __global__ void grid_points_kernel(GridGeom g, int64_t n_pts, int *__restrict__ bin,
-                                   float2 *__restrict__ xy, int *__restrict__ hi) {
+                                   int *__restrict__ hi) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n_pts) return;
   const int side = (int)(k & 1);
@@ -98,7 +98,6 @@ __global__ void grid_points_kernel(GridGeom g, int64_t n_pts, int *__restrict__ 
   // and the largest below x + W/2
   const int s_lo = (int)floor(x - half) + 1, s_hi = (int)ceil(x + half) - 1;
   const int r_lo = (int)floor(y - half) + 1, r_hi = (int)ceil(y + half) - 1;
-  xy[k] = make_float2((float)(x - s_lo), (float)(y - r_lo));
   const bool reach = s_hi >= 0 && s_lo <= g.Ng - 1 && r_hi >= 0 && r_lo <= g.Ng - 1 &&
                      s_lo >= -(g.W - 1) && r_lo >= -(g.W - 1);
   if (!reach) {
@@ -193,38 +192,124 @@ __global__ void grid_sort_bins_kernel(const int *__restrict__ offsets, int n_bin
 }
 
 __global__ void grid_records_kernel(const int *__restrict__ ids, int n_kept,
-                                    const float2 *__restrict__ xy, const int *__restrict__ hi,
+                                    const int *__restrict__ hi,
                                     const int *__restrict__ bin, int nbw, GeomRec *__restrict__ rec) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_kept) return;
   const int k = ids[p];
   GeomRec r;
-  r.fx = xy[k].x;
-  r.fy = xy[k].y;
   r.hi = hi[k];
   r.id = k;
   r.slo = bin[k] % nbw;
   rec[p] = r;
 }
 
+// Cell position of a point in FP64, from its id ((c * n_tbl + tbl) * 2 + side).
+__device__ __forceinline__ void point_xy(const GridGeom &g, int id, double &x, double &y) {
+  const int side = id & 1;
+  const int ct = id >> 1;
+  const int c = ct / g.n_tbl, tbl = ct % g.n_tbl;
+  int a, b;
+  tbl_pair(tbl, a, b);
+  const double nu = g.f0 + (double)c * g.df;
+  x = (g.tile_xy[2 * a] - g.tile_xy[2 * b]) * nu / kCLight / g.du + 0.5 * g.Ng;
+  y = (g.tile_xy[2 * a + 1] - g.tile_xy[2 * b + 1]) * nu / kCLight / g.du + 0.5 * g.Ng;
+  if (side) {
+    x = (double)g.Ng - x;
+    y = (double)g.Ng - y;
+  }
+}
+
+// Patches: a warp owns rows r0 .. r0+3, columns s0 .. s0+7 (lane = row
+// lane / 8, column lane % 8); a CTA runs 8 patches.
+constexpr int kPatchR = 4, kPatchC = 8;
+constexpr int kPatchThreads = 32 * 8;
+
+constexpr int kFactors = kPatchC + kPatchR;  // per candidate: 8 column, 4 row factors
+
+struct Patch {
+  int r0, s0, br_end, bc_end;
+};
+
+// Patch `idx` (row-major over patch rows and columns).
+__device__ __forceinline__ Patch patch_at(int idx, int n_patch_c, int W, int nbw) {
+  Patch pt;
+  pt.r0 = (idx / n_patch_c) * kPatchR;
+  pt.s0 = (idx % n_patch_c) * kPatchC;
+  // bin row br holds points with r_lo = br - (W - 1); those reaching rows
+  // r0 .. r0+3 have br in [r0, r0 + 3 + W - 1]; likewise bin columns
+  pt.br_end = min(pt.r0 + kPatchR - 1 + W - 1, nbw - 1);
+  pt.bc_end = min(pt.s0 + kPatchC + W - 1, nbw);  // exclusive
+  return pt;
+}
+
+// 4a. candidates per patch (into cnt[patch])
+__global__ void __launch_bounds__(kPatchThreads) grid_patch_count_kernel(
+    const int *__restrict__ offsets, int n_patches, int W, int nbw, int n_patch_c,
+    int *__restrict__ cnt) {
+  const int idx = blockIdx.x * (kPatchThreads / 32) + (threadIdx.x >> 5);
+  if (idx >= n_patches) return;
+  const Patch pt = patch_at(idx, n_patch_c, W, nbw);
+  const int lane = threadIdx.x & 31;
+  int n = 0;
+  for (int br = pt.r0 + lane; br <= pt.br_end; br += 32)
+    n += offsets[br * nbw + pt.bc_end] - offsets[br * nbw + pt.s0];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if (lane == 0) cnt[idx] = n;
+}
+
+// 4b. the factors of every candidate of a patch, from w_off[patch] * 12:
+// lanes 0..7 the column factors wx(s0 + l - x), lanes 8..11 the row factors
+// wy(r0 + l - 8 - y), each 0 outside the support or the grid.
+__global__ void __launch_bounds__(kPatchThreads) grid_patch_weights_kernel(
+    GridGeom g, const GeomRec *__restrict__ rec, const int *__restrict__ offsets, double inv_2s2d,
+    int n_patches, int n_patch_c, const int *__restrict__ w_off, float *__restrict__ wts) {
+  const int idx = blockIdx.x * (kPatchThreads / 32) + (threadIdx.x >> 5);
+  if (idx >= n_patches) return;
+  const int W = g.W, nbw = g.nbw;
+  const Patch pt = patch_at(idx, n_patch_c, W, nbw);
+  const int lane = threadIdx.x & 31;
+  const bool col = lane < kPatchC, row = lane >= kPatchC && lane < kFactors;
+  const int s = pt.s0 + lane, r = pt.r0 + lane - kPatchC;
+  int64_t k = (int64_t)w_off[idx] * kFactors + lane;
+  for (int br = pt.r0; br <= pt.br_end; ++br) {
+    const int r_lo = br - (W - 1);
+    const int lo = offsets[br * nbw + pt.s0], hi = offsets[br * nbw + pt.bc_end];
+    for (int q = lo; q < hi; ++q, k += kFactors) {
+      if (!col && !row) continue;
+      const GeomRec p = rec[q];
+      const int s_lo = p.slo - (W - 1);
+      float f = 0.f;
+      double x, y;
+      if (col && s >= s_lo && s <= (p.hi & 0xFFFF) && s < g.Ng) {
+        point_xy(g, p.id, x, y);
+        const double d = (double)s - x;
+        f = (float)exp(-d * d * inv_2s2d);
+      } else if (row && r >= r_lo && r <= (p.hi >> 16) && r < g.Ng) {
+        point_xy(g, p.id, x, y);
+        const double d = (double)r - y;
+        f = (float)exp(-d * d * inv_2s2d);
+      }
+      wts[k] = f;
+    }
+  }
+}
+
 // grid call, step 1: the four polarisation values of every sorted point
 __global__ void grid_values_kernel(const GeomRec *__restrict__ rec, int n_kept, int n_tbl,
                                    int64_t n_bl, const int2 *__restrict__ vis,
-                                   PointRec *__restrict__ pts) {
+                                   float4 *__restrict__ vals) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_kept) return;
-  const GeomRec g = rec[p];
-  const int side = g.id & 1;
-  const int ct = g.id >> 1;
+  const int id = rec[p].id;
+  const int side = id & 1;
+  const int ct = id >> 1;
   const int c = ct / n_tbl, tbl = ct % n_tbl;
   int a, b;
   tbl_pair(tbl, a, b);
   const int2 *vc = vis + (int64_t)c * n_bl;
-  PointRec o;
-  o.fx = g.fx;
-  o.fy = g.fy;
-  o.hi = g.hi;
-  o.slo = g.slo;
+  float v[8];
 #pragma unroll
   for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
@@ -232,76 +317,171 @@ __global__ void grid_values_kernel(const GeomRec *__restrict__ rec, int n_kept, 
       // forward point: product (pp, qq) of (a, b); reversed: conj of (qq, pp)
       const int ip = side ? qq : pp, jq = side ? pp : qq;
       const int64_t i = 2 * a + ip, j = 2 * b + jq;
-      const int2 v = vc[i * (i + 1) / 2 + j];
-      o.v[2 * pp + qq] = make_float2((float)v.x, side ? -(float)v.y : (float)v.y);
+      const int2 x = vc[i * (i + 1) / 2 + j];
+      v[2 * (2 * pp + qq)] = (float)x.x;
+      v[2 * (2 * pp + qq) + 1] = side ? -(float)x.y : (float)x.y;
     }
-  pts[p] = o;
+  vals[2 * (int64_t)p] = make_float4(v[0], v[1], v[2], v[3]);
+  vals[2 * (int64_t)p + 1] = make_float4(v[4], v[5], v[6], v[7]);
 }
 
-// grid call, step 2: gather.  A warp owns a 4 x 8 patch of cells (lane =
-// row i = lane / 8, column j = lane % 8) and streams, once for the whole
-// warp, every point whose support can reach the patch: for each bin row
-// r0 - W + 1 .. r0 + 3 (shifted by W - 1), the bins of columns
-// s0 - W + 1 .. s0 + 7, one contiguous range of the sorted points.  All lanes
-// read the same point (a broadcast); each lane keeps it if its cell lies in
-// the point's support.  A 7 x 7 support covers up to 28 of the 32 cells.
-// Each cell's sum runs over bin rows, then bin columns, then point ids: a
-// fixed order.
-constexpr int kPatchR = 4, kPatchC = 8;
-constexpr int kGatherWarpsR = 4, kGatherWarpsC = 2;  // CTA = 16 x 16 cells
+// grid call, step 2: every cell of a patch sums, in the plan's candidate order,
+// wx[col] wy[row] x values.  apply_range adds candidates [k0, k1) of a patch
+// for this lane's cell.
+constexpr int kHeavy = 1024;  // patches with more candidates get a whole CTA
 
-__global__ void __launch_bounds__(32 * kGatherWarpsR * kGatherWarpsC) grid_gather_kernel(
-    const PointRec *__restrict__ pts, const int *__restrict__ offsets, int Ng, int W, int nbw,
-    float inv_2s2, float2 *__restrict__ grids) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r0 = (blockIdx.y * kGatherWarpsR + warp / kGatherWarpsC) * kPatchR;
-  const int s0 = (blockIdx.x * kGatherWarpsC + warp % kGatherWarpsC) * kPatchC;
-  if (r0 >= Ng || s0 >= Ng) return;  // whole warp
-  const int r = r0 + lane / kPatchC, s = s0 + lane % kPatchC;
-  float2 acc[4];
-#pragma unroll
-  for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.f, 0.f);
-  // bin row br holds points with r_lo = br - (W - 1); those reaching rows
-  // r0 .. r0 + 3 have br in [r0, r0 + 3 + W - 1]; likewise bin columns
-  const int br_end = min(r0 + kPatchR - 1 + W - 1, nbw - 1);
-  const int bc_end = min(s0 + kPatchC + W - 1, nbw);  // exclusive
-  for (int br = r0; br <= br_end; ++br) {
-    const int lo = __ldg(offsets + br * nbw + s0), hi = __ldg(offsets + br * nbw + bc_end);
-    const float dy0 = (float)(r - (br - (W - 1)));  // r - r_lo
-    // four points per step: their geometry loads are issued together
-    auto take = [&](const float4 g, int q) {
-      const int phi = __float_as_int(g.z), slo = __float_as_int(g.w);
-      const int ds = s - (slo - (W - 1));  // s - s_lo
-      if (dy0 >= 0.f && ds >= 0 && r <= (phi >> 16) && s <= (phi & 0xFFFF)) {
-        const float dx = (float)ds - g.x, dy = dy0 - g.y;
-        const float w = expf(-(dx * dx + dy * dy) * inv_2s2);
-        const float4 v01 = __ldg(reinterpret_cast<const float4 *>(pts + q) + 1);
-        const float4 v23 = __ldg(reinterpret_cast<const float4 *>(pts + q) + 2);
-        acc[0].x += w * v01.x;
-        acc[0].y += w * v01.y;
-        acc[1].x += w * v01.z;
-        acc[1].y += w * v01.w;
-        acc[2].x += w * v23.x;
-        acc[2].y += w * v23.y;
-        acc[3].x += w * v23.z;
-        acc[3].y += w * v23.w;
-      }
-    };
-    int q = lo;
-    for (; q + 4 <= hi; q += 4) {
-      float4 g[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) g[u] = __ldg(reinterpret_cast<const float4 *>(pts + q + u));
-#pragma unroll
-      for (int u = 0; u < 4; ++u) take(g[u], q + u);
+struct Acc {
+  float2 v[4];
+};
+
+// Per-warp staging of 32 candidates: their values (8 floats) and factors
+// (12 floats), double-buffered; plus the patch's bin rows (first candidate
+// index and first sorted point of each).
+constexpr int kMaxRows = 40;  // >= kPatchR - 1 + W for W <= 31
+struct WarpStage {
+  float4 v[2][32][2];
+  float f[2][32][kFactors];
+  int row_k[kMaxRows + 1], row_q[kMaxRows];
+};
+
+__device__ __forceinline__ void cp16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
+// Adds candidates [k0, k1) of the patch to this lane's cell: 32 candidates at
+// a time are copied (one per lane) into the warp's staging buffer while the
+// previous 32 are applied, in candidate order.
+__device__ __forceinline__ void apply_range(const Patch &pt, int nbw, const int *__restrict__ offsets,
+                                            const float *__restrict__ wf0,
+                                            const float4 *__restrict__ vals, int k0, int k1,
+                                            int lane, WarpStage &st, Acc &acc) {
+  const int fx = lane % kPatchC, fy = kPatchC + lane / kPatchC;  // this cell's two factors
+  // bin rows of the patch: candidate index of each row's first point
+  const int n_rows = pt.br_end - pt.r0 + 1;
+  if (lane == 0) {
+    int k = 0;
+    for (int i = 0; i < n_rows; ++i) {
+      const int br = pt.r0 + i;
+      const int lo = __ldg(offsets + br * nbw + pt.s0), hi = __ldg(offsets + br * nbw + pt.bc_end);
+      st.row_k[i] = k;
+      st.row_q[i] = lo;
+      k += hi - lo;
     }
-    for (; q < hi; ++q) take(__ldg(reinterpret_cast<const float4 *>(pts + q)), q);
+    st.row_k[n_rows] = k;
   }
+  __syncwarp();
+  auto issue = [&](int base, int buf) {  // candidates base .. base+31 (those < k1)
+    const int kk = base + lane;
+    if (kk < k1) {
+      int i = 0;
+      while (st.row_k[i + 1] <= kk) ++i;
+      const int q = st.row_q[i] + (kk - st.row_k[i]);
+      cp16(&st.v[buf][lane][0], vals + 2 * (int64_t)q);
+      cp16(&st.v[buf][lane][1], vals + 2 * (int64_t)q + 1);
+      const float *f = wf0 + (int64_t)kk * kFactors;
+      cp16(&st.f[buf][lane][0], f);
+      cp16(&st.f[buf][lane][4], f + 4);
+      cp16(&st.f[buf][lane][8], f + 8);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int buf = 0;
+  if (k0 < k1) issue(k0, 0);
+  for (int base = k0; base < k1; base += 32, buf ^= 1) {
+    if (base + 32 < k1) {
+      issue(base + 32, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncwarp();
+    const int n = min(32, k1 - base);
+    for (int j = 0; j < n; ++j) {
+      const float w = st.f[buf][j][fx] * st.f[buf][j][fy];
+      const float4 a = st.v[buf][j][0], b = st.v[buf][j][1];
+      acc.v[0].x += w * a.x;
+      acc.v[0].y += w * a.y;
+      acc.v[1].x += w * a.z;
+      acc.v[1].y += w * a.w;
+      acc.v[2].x += w * b.x;
+      acc.v[2].y += w * b.y;
+      acc.v[3].x += w * b.z;
+      acc.v[3].y += w * b.w;
+    }
+    __syncwarp();  // this buffer is refilled two steps on
+  }
+}
+
+__device__ __forceinline__ void store_cell(const Patch &pt, int lane, int Ng, const Acc &acc,
+                                           float2 *__restrict__ grids) {
+  const int r = pt.r0 + lane / kPatchC, s = pt.s0 + lane % kPatchC;
   if (r < Ng && s < Ng) {
     const int64_t cell = (int64_t)r * Ng + s;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) grids[(int64_t)p * Ng * Ng + cell] = acc[p];
+    for (int p = 0; p < 4; ++p) grids[(int64_t)p * Ng * Ng + cell] = acc.v[p];
   }
+}
+
+// Heavy patches (order[0 .. n_heavy)): one CTA each; warp w takes the w-th
+// eighth of the candidates, and warp 0 adds the eight partial sums in warp
+// order.
+__global__ void __launch_bounds__(kPatchThreads) grid_apply_heavy_kernel(
+    const int *__restrict__ offsets, const int *__restrict__ order, const int *__restrict__ w_off,
+    const float *__restrict__ wts, const float4 *__restrict__ vals, int Ng, int W, int nbw,
+    int n_patch_c, float2 *__restrict__ grids) {
+  __shared__ WarpStage stage[kPatchThreads / 32];
+  const int idx = __ldg(order + blockIdx.x);
+  const Patch pt = patch_at(idx, n_patch_c, W, nbw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int first = __ldg(w_off + idx), count = __ldg(w_off + idx + 1) - first;
+  const int nw = kPatchThreads / 32;
+  Acc acc;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) acc.v[p] = make_float2(0.f, 0.f);
+  apply_range(pt, nbw, offsets, wts + (int64_t)first * kFactors, vals,
+              (int)((int64_t)count * warp / nw), (int)((int64_t)count * (warp + 1) / nw), lane,
+              stage[warp], acc);
+  // the partial sums reuse the staging memory once every warp is done with it
+  __syncthreads();
+  float2(*part)[4][32] = reinterpret_cast<float2(*)[4][32]>(stage);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) part[warp][p][lane] = acc.v[p];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float2 t = part[0][p][lane];
+      for (int w = 1; w < nw; ++w) {
+        t.x += part[w][p][lane].x;
+        t.y += part[w][p][lane].y;
+      }
+      acc.v[p] = t;
+    }
+    store_cell(pt, lane, Ng, acc, grids);
+  }
+}
+
+// The other patches (order[n_heavy .. n_patches)): one warp each.
+__global__ void __launch_bounds__(kPatchThreads) grid_apply_kernel(
+    const int *__restrict__ offsets, const int *__restrict__ order, const int *__restrict__ w_off,
+    const float *__restrict__ wts, const float4 *__restrict__ vals, int Ng, int W, int nbw,
+    int slot0, int n_patches, int n_patch_c, float2 *__restrict__ grids) {
+  __shared__ WarpStage stage[kPatchThreads / 32];
+  const int slot = slot0 + blockIdx.x * (kPatchThreads / 32) + (threadIdx.x >> 5);
+  if (slot >= n_patches) return;
+  const int idx = __ldg(order + slot);
+  const Patch pt = patch_at(idx, n_patch_c, W, nbw);
+  const int lane = threadIdx.x & 31;
+  const int first = __ldg(w_off + idx), count = __ldg(w_off + idx + 1) - first;
+  Acc acc;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) acc.v[p] = make_float2(0.f, 0.f);
+  apply_range(pt, nbw, offsets, wts + (int64_t)first * kFactors, vals, 0, count, lane,
+              stage[threadIdx.x >> 5], acc);
+  store_cell(pt, lane, Ng, acc, grids);
 }
 
 }  // namespace
@@ -313,21 +493,24 @@ struct mwax_grid_plan_s {
   cudaStream_t stream = nullptr;
   int device = 0;
   int n_tiles = 0, n_chan = 0, n_tbl = 0, Ng = 0, W = 0, nbw = 0;
-  float inv_2s2 = 0.f;
   int64_t n_pts = 0;
-  int n_kept = 0, max_bin = 0;
-  int *offsets = nullptr;   // [n_bins + 1]
-  GeomRec *rec = nullptr;   // [n_kept]
-  PointRec *pts = nullptr;  // [n_kept], filled per call
+  int n_kept = 0, n_patches = 0, n_patch_c = 0, n_heavy = 0;
+  int64_t n_entries = 0;     // stored factors (12 per patch candidate)
+  int *offsets = nullptr;    // [n_bins + 1]
+  GeomRec *rec = nullptr;    // [n_kept]
+  int *w_off = nullptr;      // [n_patches + 1]: first candidate of each patch
+  int *order = nullptr;      // [n_patches]: patches by decreasing candidate count
+  float *wts = nullptr;      // [n_entries]: [candidate][8 column | 4 row factors] per patch
+  float4 *vals = nullptr;    // [n_kept][2], filled per call
 };
 
 namespace {
 
 void free_grid_plan(mwax_grid_plan_s *p) {
   if (!p) return;
-  if (p->offsets) cudaFree(p->offsets);
-  if (p->rec) cudaFree(p->rec);
-  if (p->pts) cudaFree(p->pts);
+  for (void *q : {(void *)p->offsets, (void *)p->rec, (void *)p->w_off, (void *)p->order,
+                  (void *)p->wts, (void *)p->vals})
+    if (q) cudaFree(q);
   delete p;
 }
 
@@ -368,19 +551,16 @@ mwax_status mwax_grid_plan(mwax_grid_plan_t *out, const double *tile_xy, int n_t
   p->Ng = Ng;
   p->W = W;
   p->nbw = (int)nbw;
-  p->inv_2s2 = (float)(1.0 / (2.0 * sigma * sigma));
   p->n_pts = n_pts;
   // plan-time scratch
   double *d_xy = nullptr;
   int *bin = nullptr, *hi = nullptr, *count = nullptr, *fill = nullptr, *ids = nullptr,
       *totals = nullptr;
-  float2 *xy = nullptr;
   const int n_scan = (int)(n_bins + 1);
   const int scan_blocks = (n_scan + kScanBlock - 1) / kScanBlock;
   cudaError_t e = cudaMalloc(&d_xy, sizeof(double) * 2 * n_tiles);
   if (e == cudaSuccess) e = cudaMalloc(&bin, sizeof(int) * n_pts);
   if (e == cudaSuccess) e = cudaMalloc(&hi, sizeof(int) * n_pts);
-  if (e == cudaSuccess) e = cudaMalloc(&xy, sizeof(float2) * n_pts);
   if (e == cudaSuccess) e = cudaMalloc(&count, sizeof(int) * n_scan);
   if (e == cudaSuccess) e = cudaMalloc(&fill, sizeof(int) * n_bins);
   if (e == cudaSuccess) e = cudaMalloc(&totals, sizeof(int) * scan_blocks);
@@ -393,7 +573,7 @@ mwax_status mwax_grid_plan(mwax_grid_plan_t *out, const double *tile_xy, int n_t
   const int T = 256;
   const unsigned nblk = (unsigned)((n_pts + T - 1) / T);
   if (e == cudaSuccess) {
-    grid_points_kernel<<<nblk, T, 0, stream>>>(g, n_pts, bin, xy, hi);
+    grid_points_kernel<<<nblk, T, 0, stream>>>(g, n_pts, bin, hi);
     grid_count_kernel<<<nblk, T, 0, stream>>>(bin, n_pts, count);
     scan_blocks_kernel<<<scan_blocks, kScanBlock, 0, stream>>>(count, n_scan, p->offsets, totals);
     scan_totals_kernel<<<1, kScanBlock, 0, stream>>>(totals, scan_blocks);
@@ -410,19 +590,77 @@ mwax_status mwax_grid_plan(mwax_grid_plan_t *out, const double *tile_xy, int n_t
     e = cudaMalloc(&ids, sizeof(int) * std::max(kept, 1));
   }
   if (e == cudaSuccess) e = cudaMalloc(&p->rec, sizeof(GeomRec) * std::max(kept, 1));
-  if (e == cudaSuccess) e = cudaMalloc(&p->pts, sizeof(PointRec) * std::max(kept, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->vals, 2 * sizeof(float4) * std::max(kept, 1));
   if (e == cudaSuccess) {
     grid_fill_kernel<<<nblk, T, 0, stream>>>(bin, n_pts, p->offsets, fill, ids);
     grid_sort_bins_kernel<<<(unsigned)((n_bins + T - 1) / T), T, 0, stream>>>(p->offsets,
                                                                              (int)n_bins, ids);
     if (kept > 0)
-      grid_records_kernel<<<(kept + T - 1) / T, T, 0, stream>>>(ids, kept, xy, hi, bin, (int)nbw,
+      grid_records_kernel<<<(kept + T - 1) / T, T, 0, stream>>>(ids, kept, hi, bin, (int)nbw,
                                                                 p->rec);
     e = cudaGetLastError();
   }
+  // the weights: candidates per patch, their prefix sum, then [candidate][cell]
+  // (a point is a candidate of at most this many patches; the int32 prefix
+  // sum must hold the total)
+  const int64_t per_point = (int64_t)((W + kPatchR - 1) / kPatchR + 1) * ((W + kPatchC - 1) / kPatchC + 1);
+  if (e == cudaSuccess && (int64_t)kept * per_point > 0x7FFFFFFFll) {
+    for (void *q : {(void *)d_xy, (void *)bin, (void *)hi, (void *)count, (void *)fill, (void *)ids,
+                    (void *)totals})
+      if (q) cudaFree(q);
+    free_grid_plan(p);
+    return MWAX_ERR_UNSUPPORTED;
+  }
+  const int npr = (Ng + kPatchR - 1) / kPatchR, npc = (Ng + kPatchC - 1) / kPatchC;
+  const int n_patches = npr * npc;
+  const int n_pscan = n_patches + 1;  // one extra zero: the last offset is the total
+  const int pscan_blocks = (n_pscan + kScanBlock - 1) / kScanBlock;
+  int *pcnt = nullptr, *ptot = nullptr;
+  p->n_patches = n_patches;
+  p->n_patch_c = npc;
+  const double inv_2s2d = 1.0 / (2.0 * sigma * sigma);
+  const unsigned pgrid = (unsigned)((n_patches + kPatchThreads / 32 - 1) / (kPatchThreads / 32));
+  if (e == cudaSuccess) e = cudaMalloc(&pcnt, sizeof(int) * n_pscan);
+  if (e == cudaSuccess) e = cudaMalloc(&ptot, sizeof(int) * pscan_blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&p->w_off, sizeof(int) * n_pscan);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pcnt, 0, sizeof(int) * n_pscan, stream);
+  if (e == cudaSuccess) {
+    grid_patch_count_kernel<<<pgrid, kPatchThreads, 0, stream>>>(p->offsets, n_patches, W,
+                                                                   (int)nbw, npc, pcnt);
+    scan_blocks_kernel<<<pscan_blocks, kScanBlock, 0, stream>>>(pcnt, n_pscan, p->w_off, ptot);
+    scan_totals_kernel<<<1, kScanBlock, 0, stream>>>(ptot, pscan_blocks);
+    scan_add_kernel<<<pscan_blocks, kScanBlock, 0, stream>>>(p->w_off, n_pscan, ptot);
+    e = cudaGetLastError();
+  }
+  int total = 0;
+  std::vector<int> hcnt(n_patches), horder(n_patches);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&total, p->w_off + n_patches, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hcnt.data(), pcnt, sizeof(int) * n_patches, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  for (void *q : {(void *)d_xy, (void *)bin, (void *)hi, (void *)xy, (void *)count, (void *)fill,
-                  (void *)ids, (void *)totals})
+  if (e == cudaSuccess) {
+    // heaviest patches first (ties in patch order)
+    for (int i = 0; i < n_patches; ++i) horder[i] = i;
+    std::stable_sort(horder.begin(), horder.end(),
+                     [&](int a, int b) { return hcnt[a] > hcnt[b]; });
+    while (p->n_heavy < n_patches && hcnt[horder[p->n_heavy]] > kHeavy) ++p->n_heavy;
+    e = cudaMalloc(&p->order, sizeof(int) * n_patches);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->order, horder.data(), sizeof(int) * n_patches, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    p->n_entries = (int64_t)total * kFactors;
+    e = cudaMalloc(&p->wts, sizeof(float) * std::max<int64_t>(p->n_entries, 1));
+  }
+  if (e == cudaSuccess) {
+    grid_patch_weights_kernel<<<pgrid, kPatchThreads, 0, stream>>>(
+        g, p->rec, p->offsets, inv_2s2d, n_patches, npc, p->w_off, p->wts);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  for (void *q : {(void *)d_xy, (void *)bin, (void *)hi, (void *)count, (void *)fill,
+                  (void *)ids, (void *)totals, (void *)pcnt, (void *)ptot})
     if (q) cudaFree(q);
   if (e != cudaSuccess) {
     free_grid_plan(p);
@@ -434,6 +672,8 @@ mwax_status mwax_grid_plan(mwax_grid_plan_t *out, const double *tile_xy, int n_t
 
 int64_t mwax_grid_plan_points(mwax_grid_plan_t plan) { return plan ? plan->n_kept : -1; }
 
+int64_t mwax_grid_plan_entries(mwax_grid_plan_t plan) { return plan ? plan->n_entries : -1; }
+
 mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids) {
   mwax::NvtxRange nvtx_("mwax_grid");
   if (!plan || !is_dev(vis) || !is_dev(grids)) return MWAX_ERR_INVALID_ARG;
@@ -444,12 +684,18 @@ mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids) {
   if (plan->n_kept > 0)
     grid_values_kernel<<<(plan->n_kept + T - 1) / T, T, 0, plan->stream>>>(
         plan->rec, plan->n_kept, plan->n_tbl, N * (N + 1) / 2, reinterpret_cast<const int2 *>(vis),
-        plan->pts);
-  const int tile_r = kPatchR * kGatherWarpsR, tile_c = kPatchC * kGatherWarpsC;
-  dim3 grd((plan->Ng + tile_c - 1) / tile_c, (plan->Ng + tile_r - 1) / tile_r);
-  grid_gather_kernel<<<grd, 32 * kGatherWarpsR * kGatherWarpsC, 0, plan->stream>>>(plan->pts, plan->offsets, plan->Ng, plan->W,
-                                                    plan->nbw, plan->inv_2s2,
-                                                    reinterpret_cast<float2 *>(grids));
+        plan->vals);
+  float2 *g2 = reinterpret_cast<float2 *>(grids);
+  if (plan->n_heavy > 0)
+    grid_apply_heavy_kernel<<<plan->n_heavy, kPatchThreads, 0, plan->stream>>>(
+        plan->offsets, plan->order, plan->w_off, plan->wts, plan->vals, plan->Ng, plan->W,
+        plan->nbw, plan->n_patch_c, g2);
+  const int n_light = plan->n_patches - plan->n_heavy;
+  if (n_light > 0)
+    grid_apply_kernel<<<(unsigned)((n_light + kPatchThreads / 32 - 1) / (kPatchThreads / 32)),
+                        kPatchThreads, 0, plan->stream>>>(
+        plan->offsets, plan->order, plan->w_off, plan->wts, plan->vals, plan->Ng, plan->W,
+        plan->nbw, plan->n_heavy, plan->n_patches, plan->n_patch_c, g2);
   return cudaGetLastError() == cudaSuccess ? MWAX_OK : MWAX_ERR_CUDA;
 }
 

@@ -1,9 +1,9 @@
 """GPU gridding against the FP64 CPU oracle.
 
-Tolerance: the weights carry ~1e-7 relative error (expf of an argument
-formed from offsets held in float relative to the support origin) and each
-cell is an FP32 sum of up to a few hundred terms (~K x 6e-8 relative to the
-largest term), so every cell is compared within 1e-5 of the largest |G|.
+Tolerance: the weights are computed in FP64 and rounded to FP32 (6e-8
+relative) and each cell is an FP32 sum of up to a few hundred terms (~K x
+6e-8 relative to the largest term), so every cell is compared within 1e-5 of
+the largest |G|.
 Inputs are seeded int32 visibilities generated on the host (the gridding
 does not care whether they came from the correlator) and seeded tile
 positions."""
