@@ -296,13 +296,22 @@ __global__ void __launch_bounds__(kPatchThreads) grid_patch_weights_kernel(
   }
 }
 
-// grid call, step 1: the four polarisation values of every sorted point
-__global__ void grid_values_kernel(const GeomRec *__restrict__ rec, int n_kept, int n_tbl,
+// sorted position of every point id (-1: the point reaches no cell)
+__global__ void grid_slot_kernel(const GeomRec *__restrict__ rec, int n_kept, int *__restrict__ slot) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_kept) slot[rec[p].id] = p;
+}
+
+// grid call, step 1: the four polarisation values of every point, read in
+// point-id order (channel, then baseline: nearly sequential in the
+// correlator output) and written to the point's sorted position
+__global__ void grid_values_kernel(const int *__restrict__ slot, int n_pts, int n_tbl,
                                    int64_t n_bl, const int2 *__restrict__ vis,
                                    float4 *__restrict__ vals) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_kept) return;
-  const int id = rec[p].id;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n_pts) return;
+  const int p = slot[id];
+  if (p < 0) return;
   const int side = id & 1;
   const int ct = id >> 1;
   const int c = ct / n_tbl, tbl = ct % n_tbl;
@@ -498,6 +507,7 @@ struct mwax_grid_plan_s {
   int64_t n_entries = 0;     // stored factors (12 per patch candidate)
   int *offsets = nullptr;    // [n_bins + 1]
   GeomRec *rec = nullptr;    // [n_kept]
+  int *slot = nullptr;       // [n_pts]: sorted position of each point id, or -1
   int *w_off = nullptr;      // [n_patches + 1]: first candidate of each patch
   int *order = nullptr;      // [n_patches]: patches by decreasing candidate count
   float *wts = nullptr;      // [n_entries]: [candidate][8 column | 4 row factors] per patch
@@ -508,8 +518,8 @@ namespace {
 
 void free_grid_plan(mwax_grid_plan_s *p) {
   if (!p) return;
-  for (void *q : {(void *)p->offsets, (void *)p->rec, (void *)p->w_off, (void *)p->order,
-                  (void *)p->wts, (void *)p->vals})
+  for (void *q : {(void *)p->offsets, (void *)p->rec, (void *)p->slot, (void *)p->w_off,
+                  (void *)p->order, (void *)p->wts, (void *)p->vals})
     if (q) cudaFree(q);
   delete p;
 }
@@ -600,6 +610,13 @@ mwax_status mwax_grid_plan(mwax_grid_plan_t *out, const double *tile_xy, int n_t
                                                                 p->rec);
     e = cudaGetLastError();
   }
+  // sorted position of every point id
+  if (e == cudaSuccess) e = cudaMalloc(&p->slot, sizeof(int) * n_pts);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->slot, 0xFF, sizeof(int) * n_pts, stream);
+  if (e == cudaSuccess && kept > 0) {
+    grid_slot_kernel<<<(kept + T - 1) / T, T, 0, stream>>>(p->rec, kept, p->slot);
+    e = cudaGetLastError();
+  }
   // the weights: candidates per patch, their prefix sum, then [candidate][cell]
   // (a point is a candidate of at most this many patches; the int32 prefix
   // sum must hold the total)
@@ -682,9 +699,9 @@ mwax_status mwax_grid(mwax_grid_plan_t plan, const int32_t *vis, float *grids) {
   const int64_t N = 2 * (int64_t)plan->n_tiles;
   const int T = 256;
   if (plan->n_kept > 0)
-    grid_values_kernel<<<(plan->n_kept + T - 1) / T, T, 0, plan->stream>>>(
-        plan->rec, plan->n_kept, plan->n_tbl, N * (N + 1) / 2, reinterpret_cast<const int2 *>(vis),
-        plan->vals);
+    grid_values_kernel<<<(unsigned)((plan->n_pts + T - 1) / T), T, 0, plan->stream>>>(
+        plan->slot, (int)plan->n_pts, plan->n_tbl, N * (N + 1) / 2,
+        reinterpret_cast<const int2 *>(vis), plan->vals);
   float2 *g2 = reinterpret_cast<float2 *>(grids);
   if (plan->n_heavy > 0)
     grid_apply_heavy_kernel<<<plan->n_heavy, kPatchThreads, 0, plan->stream>>>(
