@@ -83,9 +83,9 @@ def unpack_kernel_name(spec) -> str:
     where the raw rows are whole 16-byte units, else the fallbacks)."""
     n = spec.n_inputs
     if os.environ.get("MWAX_UNPACK") is None:
-        if spec.sample_bits == 8 and n % 8 == 0:
+        if spec.sample_bits == 8 and n % 2 == 0:
             return "unpack8_tile_kernel"
-        if spec.sample_bits == 4 and n % 16 == 0:
+        if spec.sample_bits == 4 and n % 4 == 0:
             return "unpack4_tile_kernel"
     return "unpack_kernel<8>" if spec.sample_bits == 8 else "unpack4_line_kernel"
 

@@ -22,6 +22,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -272,10 +273,40 @@ __device__ __forceinline__ bool u_wait(uint32_t bar, uint32_t parity, unsigned l
 constexpr int kTileThreads = 128;
 constexpr int kTileRawBytes = 32 * 256;
 
+// The raw box of one task loaded by the threads (for rows that are not whole
+// 16-byte units, which TMA needs): rows grow0 .. grow0 + rows_valid - 1 of the
+// [rows][row_bytes] sample array, bytes x0 .. x0 + 255 (8-bit) or 127 (4-bit)
+// of each, bytes past the row read as zero; consecutive threads take
+// consecutive 4-byte words of a row (row_bytes % 4 == 0).  The words of the
+// next task are fetched into registers while the current one is converted.
+constexpr int kRawWords = kTileRawBytes / 4 / kTileThreads;  // per thread
+
+template <int BITS>
+__device__ __forceinline__ void fetch_raw_box(const uint8_t *__restrict__ volt,
+                                              uint32_t (&v)[kRawWords], int64_t row_bytes,
+                                              int64_t grow0, int rows_valid, int x0) {
+  constexpr int row_w = BITS == 8 ? 64 : 32;  // 4-byte words per box row
+#pragma unroll
+  for (int j = 0; j < kRawWords; ++j) {
+    const int idx = j * kTileThreads + threadIdx.x;
+    const int r = idx / row_w, x = x0 + 4 * (idx % row_w);
+    v[j] = r < rows_valid && x < row_bytes
+               ? __ldg(reinterpret_cast<const uint32_t *>(volt + (grow0 + r) * row_bytes + x))
+               : 0u;
+  }
+}
+
+__device__ __forceinline__ void put_raw_box(uint8_t *raw, const uint32_t (&v)[kRawWords]) {
+#pragma unroll
+  for (int j = 0; j < kRawWords; ++j) reinterpret_cast<uint32_t *>(raw)[j * kTileThreads + threadIdx.x] = v[j];
+}
+
+// TMA_IN = false: the raw box is loaded by the threads (load_raw_box).
+template <bool TMA_IN>
 __global__ void __launch_bounds__(kTileThreads, 6)
     unpack8_tile_kernel(const __grid_constant__ CUtensorMap in_map,
-                        const __grid_constant__ CUtensorMap out_map, int N, int T, int n_tiles,
-                        int kb, int64_t chan0, int n_chan, int32_t *status,
+                        const __grid_constant__ CUtensorMap out_map, const uint8_t *volt, int N,
+                        int T, int n_tiles, int kb, int64_t chan0, int n_chan, int32_t *status,
                         unsigned long long tmo) {
   extern __shared__ __align__(1024) uint8_t sm_base[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
@@ -289,7 +320,8 @@ __global__ void __launch_bounds__(kTileThreads, 6)
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+    if (TMA_IN)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
   }
   __syncthreads();
@@ -309,18 +341,32 @@ __global__ void __launch_bounds__(kTileThreads, 6)
         : "memory");
   };
   int64_t k = blockIdx.x;
-  if (threadIdx.x == 0 && k < tasks) issue(k);
+  if (TMA_IN && threadIdx.x == 0 && k < tasks) issue(k);
+  uint32_t rv[kRawWords];  // thread-loaded form: the raw words of the task in hand
+  auto fetch = [&](int64_t kk) {
+    const int tile_l = (int)(kk % n_tiles);
+    const int64_t cb_l = kk / n_tiles;
+    const int c_l = (int)(cb_l / kb), tb_l = (int)(cb_l % kb);
+    fetch_raw_box<8>(volt, rv, 2 * (int64_t)N, (chan0 + c_l) * (int64_t)T + (int64_t)tb_l * 32,
+                       min(32, T - tb_l * 32), tile_l * 256);
+  };
+  if (!TMA_IN && k < tasks) fetch(k);
   uint32_t phase = 0;
   bool ok = true;
   const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
   const int i = threadIdx.x;  // operand row within the tile
   for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
-    if (!u_wait(b, phase, tmo)) {
-      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
-      ok = false;
-      break;
+    if constexpr (TMA_IN) {
+      if (!u_wait(b, phase, tmo)) {
+        if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
+        ok = false;
+        break;
+      }
+      phase ^= 1u;
+    } else {
+      // (raw was last read before the barrier that follows the conversion)
+      put_raw_box(raw, rv);
     }
-    phase ^= 1u;
     // the previous task's TMA store must have finished reading the staging tile
     if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncthreads();
@@ -333,7 +379,8 @@ __global__ void __launch_bounds__(kTileThreads, 6)
     for (int s2 = 0; s2 < 32; ++s2)
       v[s2] = s2 < rows ? (uint32_t) * reinterpret_cast<const uint16_t *>(raw + s2 * 256 + 2 * i) : 0u;
     __syncthreads();  // raw is free: fetch the next task's box while this one is converted
-    if (threadIdx.x == 0 && k + gridDim.x < tasks) issue(k + gridDim.x);
+    if (TMA_IN && threadIdx.x == 0 && k + gridDim.x < tasks) issue(k + gridDim.x);
+    if (!TMA_IN && k + gridDim.x < tasks) fetch(k + gridDim.x);
     uint8_t *row = stage + i * kRowBytes;
     const int sw = i & 7;
 #pragma unroll
@@ -362,7 +409,7 @@ __global__ void __launch_bounds__(kTileThreads, 6)
   }
   if (threadIdx.x == 0) {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    if (!ok) u_wait(b, phase, tmo);
+    if (TMA_IN && !ok) u_wait(b, phase, tmo);
   }
   __syncthreads();
 }
@@ -376,10 +423,11 @@ __global__ void __launch_bounds__(kTileThreads, 6)
 // of bank conflicts; one TMA tensor store writes the 16 KB tile.  About 25 KB
 // of shared memory and 128 threads, so several CTAs share an SM and hide each
 // other's load latency.
+template <bool TMA_IN>
 __global__ void __launch_bounds__(kTileThreads)
     unpack4_tile_kernel(const __grid_constant__ CUtensorMap in_map,
-                        const __grid_constant__ CUtensorMap out_map, int N, int T, int n_tiles,
-                        int kb, int64_t chan0, int n_chan, int32_t *status,
+                        const __grid_constant__ CUtensorMap out_map, const uint8_t *volt, int N,
+                        int T, int n_tiles, int kb, int64_t chan0, int n_chan, int32_t *status,
                         unsigned long long tmo) {
   extern __shared__ __align__(1024) uint8_t sm_base[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
@@ -393,7 +441,8 @@ __global__ void __launch_bounds__(kTileThreads)
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+    if (TMA_IN)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
   }
   __syncthreads();
@@ -413,18 +462,32 @@ __global__ void __launch_bounds__(kTileThreads)
         : "memory");
   };
   int64_t k = blockIdx.x;
-  if (threadIdx.x == 0 && k < tasks) issue(k);
+  if (TMA_IN && threadIdx.x == 0 && k < tasks) issue(k);
+  uint32_t rv[kRawWords];  // thread-loaded form: the raw words of the task in hand
+  auto fetch = [&](int64_t kk) {
+    const int tile_l = (int)(kk % n_tiles);
+    const int64_t cb_l = kk / n_tiles;
+    const int c_l = (int)(cb_l / kb), tb_l = (int)(cb_l % kb);
+    fetch_raw_box<4>(volt, rv, (int64_t)N, (chan0 + c_l) * (int64_t)T + (int64_t)tb_l * 64,
+                       min(64, T - tb_l * 64), tile_l * 128);
+  };
+  if (!TMA_IN && k < tasks) fetch(k);
   uint32_t phase = 0;
   bool ok = true;
   const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
   const int q = threadIdx.x & 31, quarter = threadIdx.x >> 5;
   for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
-    if (!u_wait(b, phase, tmo)) {
-      if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
-      ok = false;
-      break;
+    if constexpr (TMA_IN) {
+      if (!u_wait(b, phase, tmo)) {
+        if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
+        ok = false;
+        break;
+      }
+      phase ^= 1u;
+    } else {
+      // (raw was last read before the barrier that follows the conversion)
+      put_raw_box(raw, rv);
     }
-    phase ^= 1u;
     if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncthreads();
     const int tile = (int)(k % n_tiles);
@@ -440,7 +503,8 @@ __global__ void __launch_bounds__(kTileThreads)
       im[r] = nib4_to_e4m3(w >> 4);
     }
     __syncthreads();  // raw is free: fetch the next task's box while this one is converted
-    if (threadIdx.x == 0 && k + gridDim.x < tasks) issue(k + gridDim.x);
+    if (TMA_IN && threadIdx.x == 0 && k + gridDim.x < tasks) issue(k + gridDim.x);
+    if (!TMA_IN && k + gridDim.x < tasks) fetch(k + gridDim.x);
 #pragma unroll
     for (int step = 0; step < 4; ++step) {
       const int kk = (step + (q >> 1)) & 3;
@@ -473,7 +537,7 @@ __global__ void __launch_bounds__(kTileThreads)
   }
   if (threadIdx.x == 0) {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    if (!ok) u_wait(b, phase, tmo);
+    if (TMA_IN && !ok) u_wait(b, phase, tmo);
   }
   __syncthreads();
 }
@@ -506,9 +570,14 @@ cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n
   return cudaGetLastError();
 }
 
-bool unpack_tile_supported(int sample_bits, int n_inputs) {
-  // raw rows must be whole 16-byte units for the 2D TMA box
+// Raw rows that are whole 16-byte units: the box comes by 2D TMA; rows that
+// are whole 4-byte units: the threads load it.
+bool unpack_tile_tma_in(int sample_bits, int n_inputs) {
   return (sample_bits == 8 && n_inputs % 8 == 0) || (sample_bits == 4 && n_inputs % 16 == 0);
+}
+
+bool unpack_tile_supported(int sample_bits, int n_inputs) {
+  return (sample_bits == 8 && n_inputs % 2 == 0) || (sample_bits == 4 && n_inputs % 4 == 0);
 }
 
 int unpack_tile_smem_bytes() { return 1024 + kTile * kRowBytes + kTileRawBytes; }
@@ -536,12 +605,15 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
   const cuuint64_t out_rows = (cuuint64_t)n_chan * kb * n_tiles * kTile;
   if (in_rows > 0x7FFFFFFFull || out_rows > 0x7FFFFFFFull) return cudaErrorInvalidValue;
   CUtensorMap in_map, out_map;
+  memset(&in_map, 0, sizeof(in_map));
+  const bool tma_in = unpack_tile_tma_in(sample_bits, n_inputs);
   const cuuint64_t row_bytes = (cuuint64_t)n_inputs * (sample_bits == 8 ? 2 : 1);
   cuuint64_t idims[2] = {row_bytes, in_rows};
   cuuint64_t istr[1] = {row_bytes};
   cuuint32_t ibox[2] = {sample_bits == 8 ? 256u : 128u, sample_bits == 8 ? 32u : 64u};
   cuuint32_t estr[2] = {1, 1};
-  if (encode(&in_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(volt), idims, istr, ibox,
+  if (tma_in &&
+      encode(&in_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(volt), idims, istr, ibox,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
@@ -555,20 +627,26 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
   const int smem = unpack_tile_smem_bytes();
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(unpack8_tile_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(unpack4_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem);
+    const auto set = [&](const void *f) {
+      return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    };
+    cudaError_t e = set(reinterpret_cast<const void *>(unpack8_tile_kernel<true>));
+    if (e == cudaSuccess) e = set(reinterpret_cast<const void *>(unpack8_tile_kernel<false>));
+    if (e == cudaSuccess) e = set(reinterpret_cast<const void *>(unpack4_tile_kernel<true>));
+    if (e == cudaSuccess) e = set(reinterpret_cast<const void *>(unpack4_tile_kernel<false>));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  if (sample_bits == 8)
-    unpack8_tile_kernel<<<ctas, kTileThreads, smem, s>>>(in_map, out_map, n_inputs, n_time, n_tiles,
-                                                         kb, chan0, n_chan, status, timeout_ns);
+#define MWAX_TILE_ARGS in_map, out_map, volt, n_inputs, n_time, n_tiles, kb, chan0, n_chan, status, timeout_ns
+  if (sample_bits == 8 && tma_in)
+    unpack8_tile_kernel<true><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
+  else if (sample_bits == 8)
+    unpack8_tile_kernel<false><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
+  else if (tma_in)
+    unpack4_tile_kernel<true><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
   else
-    unpack4_tile_kernel<<<ctas, kTileThreads, smem, s>>>(in_map, out_map, n_inputs, n_time, n_tiles,
-                                                         kb, chan0, n_chan, status, timeout_ns);
+    unpack4_tile_kernel<false><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
+#undef MWAX_TILE_ARGS
   return cudaGetLastError();
 }
 

@@ -52,10 +52,12 @@ cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n
                                      int n_time, int n_tiles, int kb, int64_t chan0, int n_chan,
                                      uint8_t *op, int ctas, cudaStream_t s);
 
-// TMA tile unpack (one 128-input tile x one time block per task, ~25 KB of
+// Tile unpack (one 128-input tile x one time block per task, ~25 KB of
 // shared memory: several CTAs per SM when it runs alone, one beside a
-// resident correlate CTA when it overlaps); 8-bit samples with n_inputs % 8
-// == 0, 4-bit samples with n_inputs % 16 == 0.
+// resident correlate CTA when it overlaps; TMA store of the operand tile; the
+// raw box by 2D TMA where the sample rows are whole 16-byte units, else loaded
+// by the threads); 8-bit samples with n_inputs even, 4-bit samples with
+// n_inputs % 4 == 0.
 bool unpack_tile_supported(int sample_bits, int n_inputs);
 cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
                                int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,

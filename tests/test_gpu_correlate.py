@@ -94,6 +94,18 @@ def test_tensor_tma_unpack_shapes(mw, bits, N, T, C):
     assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tma {N},{T},{C}")
 
 
+@pytest.mark.parametrize("bits,N,T,C", [(8, 130, 1000, 3), (8, 202, 77, 4), (8, 1002, 45, 2),
+                                        (4, 300, 1000, 3), (4, 52, 130, 5), (4, 1004, 65, 2),
+                                        (4, 132, 20000, 1)])
+def test_tile_unpack_thread_loaded_rows(mw, bits, N, T, C):
+    """Sample rows that are whole 4-byte but not 16-byte units (2N bytes for
+    8-bit, N for 4-bit samples): the tile unpack loads its raw box with the
+    threads instead of TMA; inputs past N and samples past T read as zero."""
+    spec = synth.Spec("tl", N, C, T, bits, seed=N + T, sigma=2 if bits == 4 else 40,
+                      tone_amp=0.3)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR), oracle_for(spec, range(C)), f"tile {bits},{N},{T}")
+
+
 @pytest.mark.parametrize("bits,N,T,C,G", [(8, 256, 1000, 12, 5), (8, 200, 77, 7, 3),
                                           (8, 1024, 100, 4, 1), (8, 136, 33, 5, 2),
                                           (4, 256, 1000, 12, 5), (4, 208, 77, 7, 3),
