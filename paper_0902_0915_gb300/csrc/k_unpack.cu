@@ -25,6 +25,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "mwax_internal.h"
 
@@ -542,6 +543,24 @@ __global__ void __launch_bounds__(kTileThreads)
   __syncthreads();
 }
 
+// Function attributes apply to the current device: set them once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_attr_mu;
+bool g_attr_tile[kMaxDevices], g_attr_persist[kMaxDevices];
+
+template <class F>
+cudaError_t once_per_device(bool (&done)[kMaxDevices], F &&set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  if (done[dev]) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
 }  // namespace
 
 cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
@@ -551,16 +570,15 @@ cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n
   if (n_chan <= 0) return cudaSuccess;
   if (ctas < 1 || (sample_bits == 8 && n_inputs % 2) || (sample_bits == 4 && n_inputs % 4))
     return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(unpack8_persist_kernel,
+  cudaError_t e = once_per_device(g_attr_persist, [] {
+    cudaError_t r = cudaFuncSetAttribute(unpack8_persist_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(unpack4_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(unpack4_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kPersistSmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   if (sample_bits == 8)
     unpack8_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
                                                            chan0, n_chan);
@@ -625,18 +643,17 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int smem = unpack_tile_smem_bytes();
-  static bool attr_set = false;
-  if (!attr_set) {
+  cudaError_t ea = once_per_device(g_attr_tile, [smem] {
     const auto set = [&](const void *f) {
       return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     };
-    cudaError_t e = set(reinterpret_cast<const void *>(unpack8_tile_kernel<true>));
-    if (e == cudaSuccess) e = set(reinterpret_cast<const void *>(unpack8_tile_kernel<false>));
-    if (e == cudaSuccess) e = set(reinterpret_cast<const void *>(unpack4_tile_kernel<true>));
-    if (e == cudaSuccess) e = set(reinterpret_cast<const void *>(unpack4_tile_kernel<false>));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+    cudaError_t r = set(reinterpret_cast<const void *>(unpack8_tile_kernel<true>));
+    if (r == cudaSuccess) r = set(reinterpret_cast<const void *>(unpack8_tile_kernel<false>));
+    if (r == cudaSuccess) r = set(reinterpret_cast<const void *>(unpack4_tile_kernel<true>));
+    if (r == cudaSuccess) r = set(reinterpret_cast<const void *>(unpack4_tile_kernel<false>));
+    return r;
+  });
+  if (ea != cudaSuccess) return ea;
 #define MWAX_TILE_ARGS in_map, out_map, volt, n_inputs, n_time, n_tiles, kb, chan0, n_chan, status, timeout_ns
   if (sample_bits == 8 && tma_in)
     unpack8_tile_kernel<true><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
