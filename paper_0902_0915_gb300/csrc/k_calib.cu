@@ -113,10 +113,15 @@ __global__ void __launch_bounds__(kCalThreads, 3) calib_tile_kernel(
       mv[m] = valid[m] ? __ldcs(Mn + boff[m]) : make_float2(0.f, 0.f);
     }
   };
+  // channels in flight: the current one and the next (the solve's extra
+  // accumulators leave no registers for more), or also the one after
+  constexpr int ahead = DEN ? 1 : 2;
+  float2 v1[4] = {}, m1[4] = {};
   if (cg < C) load(cg, v, mm);
+  if (ahead == 2 && cg + n_cg < C) load(cg + n_cg, v1, m1);
   for (int nu = cg; nu < C; nu += n_cg) {
     float2 vn[4] = {}, mn[4] = {};
-    if (nu + n_cg < C) load(nu + n_cg, vn, mn);
+    if (nu + ahead * n_cg < C) load(nu + ahead * n_cg, vn, mn);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       if (!valid[m]) continue;
@@ -144,8 +149,15 @@ __global__ void __launch_bounds__(kCalThreads, 3) calib_tile_kernel(
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      v[m] = vn[m];
-      mm[m] = mn[m];
+      if constexpr (ahead == 2) {
+        v[m] = v1[m];
+        mm[m] = m1[m];
+        v1[m] = vn[m];
+        m1[m] = mn[m];
+      } else {
+        v[m] = vn[m];
+        mm[m] = mn[m];
+      }
     }
   }
   const int out_idx = tile * n_cg + cg;
