@@ -87,7 +87,7 @@ typedef struct {
   int32_t stages;          /* tuning: shared-memory stages: 2 narrow (3 K blocks each),
                               2..4 wide, 2 pair (2 K blocks each) (0 = auto)               */
   int32_t prefetch;        /* tuning: K-blocks of L2 prefetch ahead, 1..64 (0 = auto,
-                              which is none; -1 = none)                                   */
+                              which is none; -1 = none); narrow and wide shapes only      */
   int32_t mma_shape;       /* tuning: 1 = M128xN128 MMAs (Re, Im separately), 2 = M128xN256
                               MMAs with [Re | Im] at once, 3 = two tile pairs (I, J),
                               (I, J+1) per work item with M128xN256 MMAs against the
