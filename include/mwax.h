@@ -202,6 +202,15 @@ mwax_status mwax_plan_status(mwax_plan_t plan);
  * stream, then resets the count. */
 mwax_status mwax_plan_recomputed_channels(mwax_plan_t plan, int64_t *n_channels);
 
+/* The pair-mode work list (mma_shape 3) of one job of n_tiles x n_tiles tile
+ * pairs and n_chan channels, for inspection (host only, no device use):
+ * writes min(count, capacity) items of 7 int32 each, (type, c0, I0, J0, c1,
+ * I1, J1) -- type 1: tile pairs (I0, J0) and (I0, J1 = J0 + 1) of channel c0;
+ * type 2: the diagonal pairs (I0, I0) of channel c0 and (I1, I1) of channel
+ * c1; type 0: the single pair (I0, J0) of channel c0 -- and returns the
+ * count; -1 for bad arguments (n_tiles in [1, 255], n_chan >= 1). */
+int64_t mwax_pair_work_list(int n_tiles, int n_chan, int32_t *items, int64_t capacity);
+
 /* ---- autotuning ------------------------------------------------------------ */
 
 typedef struct {

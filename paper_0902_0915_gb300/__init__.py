@@ -77,6 +77,7 @@ SIGNATURES = {
     "mwax_plan_get_info": (_I, [_P, ctypes.POINTER(PlanInfo)]),
     "mwax_plan_status": (_I, [_P]),
     "mwax_plan_recomputed_channels": (_I, [_P, ctypes.POINTER(_I64)]),
+    "mwax_pair_work_list": (_I64, [_I, _I, _P, _I64]),
     "mwax_plan_set_timing": (_I, [_P, _I]),
     "mwax_plan_get_timing": (_I, [_P, ctypes.POINTER(Timing)]),
     "mwax_autotune": (_I, [ctypes.POINTER(Job), _P, _P, _P, ctypes.POINTER(TuneReport)]),
@@ -158,6 +159,19 @@ def baseline_pair(b: int):
 
 def max_n_time(sample_bits: int) -> int:
     return int(lib().mwax_max_n_time(sample_bits))
+
+
+def pair_work_list(n_tiles: int, n_chan: int):
+    """The pair-mode work list of one job (host only): rows (type, c0, I0, J0,
+    c1, I1, J1), see mwax_pair_work_list."""
+    import numpy as np
+
+    n = int(lib().mwax_pair_work_list(n_tiles, n_chan, None, 0))
+    if n < 0:
+        raise ValueError("bad work-list shape")
+    out = np.zeros((max(n, 1), 7), np.int32)
+    lib().mwax_pair_work_list(n_tiles, n_chan, out.ctypes.data, n)
+    return out[:n]
 
 
 # ---- torch plumbing ---------------------------------------------------------------

@@ -1059,6 +1059,33 @@ void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items) {
   }
 }
 
+}  // namespace mwax
+
+extern "C" int64_t mwax_pair_work_list(int n_tiles, int n_chan, int32_t *items, int64_t capacity) {
+  if (n_tiles < 1 || n_tiles > 255 || n_chan < 1 || capacity < 0 || (capacity > 0 && !items))
+    return -1;
+  mwax::TcJob job{};
+  job.n_tiles = n_tiles;
+  job.n_chan = n_chan;
+  std::vector<int4> list;
+  mwax::build_pair_items(&job, 1, list);
+  const int64_t n = (int64_t)list.size();
+  for (int64_t k = 0; k < n && k < capacity; ++k) {
+    const uint32_t z = (uint32_t)list[k].z, w = (uint32_t)list[k].w;
+    int32_t *o = items + 7 * k;
+    o[0] = (int32_t)((z >> 8) & 0xFFu);  // type
+    o[1] = list[k].x;                    // c0
+    o[2] = (int32_t)((z >> 16) & 0xFFu);  // I0
+    o[3] = (int32_t)(z >> 24);           // J0
+    o[4] = list[k].y;                    // c1
+    o[5] = (int32_t)(w & 0xFFu);          // I1
+    o[6] = (int32_t)((w >> 8) & 0xFFu);   // J1
+  }
+  return n;
+}
+
+namespace mwax {
+
 cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
                                 cudaStream_t s) {
   if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;

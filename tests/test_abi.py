@@ -86,3 +86,36 @@ def test_grid_plan_rejects_bad_arguments_without_a_device(mwax_lib):
                                 None) == 1
     assert L.mwax_grid(None, None, None) == 1
     assert L.mwax_grid_destroy(None) == 1
+
+
+@pytest.mark.parametrize("n_tiles,n_chan", [(1, 1), (1, 5), (2, 1), (2, 768), (3, 7), (5, 4),
+                                            (8, 3), (9, 2), (17, 2)])
+def test_pair_work_list_covers_every_tile_pair_once(mwax_lib, n_tiles, n_chan):
+    """The pair mode's host-built work list: every tile pair I >= J of every
+    channel appears exactly once; shared items are (I, J), (I, J+1) with
+    J+1 <= I in one channel; two-diagonal items pair diagonals of the same or
+    the next channel; single items are diagonals; channels appear in order."""
+    mw = mwax_lib
+    items = mw.pair_work_list(n_tiles, n_chan)
+    seen = {}
+    last_c = -1
+    for typ, c0, I0, J0, c1, I1, J1 in items.tolist():
+        assert c0 >= last_c
+        last_c = c0
+        if typ == 1:
+            assert c1 == c0 and I1 == I0 and J1 == J0 + 1 and J1 <= I0
+            pairs = [(c0, I0, J0), (c0, I0, J1)]
+        elif typ == 2:
+            assert I0 == J0 and I1 == J1 and c1 in (c0, c0 + 1)
+            pairs = [(c0, I0, I0), (c1, I1, I1)]
+        else:
+            assert typ == 0 and I0 == J0
+            pairs = [(c0, I0, J0)]
+        for q in pairs:
+            seen[q] = seen.get(q, 0) + 1
+    want = {(c, I, J) for c in range(n_chan) for I in range(n_tiles) for J in range(I + 1)}
+    assert set(seen) == want and all(v == 1 for v in seen.values())
+    # work balance: every item but at most one holds two tile pairs
+    assert (items[:, 0] == 0).sum() <= 1
+    assert mw.lib().mwax_pair_work_list(0, 1, None, 0) == -1
+    assert mw.lib().mwax_pair_work_list(256, 1, None, 0) == -1
