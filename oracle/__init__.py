@@ -189,6 +189,56 @@ def calib_solve(V, M, g0, n_iter: int, n_threads: int | None = None):
     return g, np.array(losses)
 
 
+# ---- per-channel gains ----------------------------------------------------
+# The same fit with one complex gain per input AND channel: g_k(nu).  The
+# channels then decouple, so the definition is the single-channel problem
+# above applied to every channel with that channel's gains:
+#     L(G) = sum_nu L_nu(G[nu]),  L_nu the loss above over channel nu alone,
+# and the gradient and the alternating least-squares target of channel nu
+# are those of L_nu.  G, gradients and targets are complex [n_chan, N].
+def _chan_args(V, M, G):
+    V = np.ascontiguousarray(V, np.complex128)
+    M = np.ascontiguousarray(M, np.complex128)
+    G = np.ascontiguousarray(G, np.complex128)
+    C, B = V.shape
+    N = G.shape[1]
+    assert G.shape == (C, N) and B == N * (N + 1) // 2 and M.shape == V.shape
+    return V, M, G, C
+
+
+def calib_chan_loss(V, M, G) -> float:
+    """FP64 loss with per-channel gains G [n_chan, N]."""
+    V, M, G, C = _chan_args(V, M, G)
+    return float(sum(calib_loss(V[c:c + 1], M[c:c + 1], G[c]) for c in range(C)))
+
+
+def calib_chan_grad(V, M, G, n_threads: int | None = None) -> np.ndarray:
+    """FP64 gradient 2 dL/d conj(G), complex [n_chan, N]."""
+    V, M, G, C = _chan_args(V, M, G)
+    return np.stack([calib_grad(V[c:c + 1], M[c:c + 1], G[c], n_threads) for c in range(C)])
+
+
+def calib_chan_als_target(V, M, G, n_threads: int | None = None) -> np.ndarray:
+    """FP64 alternating least-squares target per channel, complex [n_chan, N]."""
+    V, M, G, C = _chan_args(V, M, G)
+    return np.stack([calib_als_target(V[c:c + 1], M[c:c + 1], G[c], n_threads)
+                     for c in range(C)])
+
+
+def calib_chan_solve(V, M, G0, n_iter: int, n_threads: int | None = None):
+    """FP64 per-channel gain solve: the sweeps of ``calib_solve`` (plain
+    target on odd sweeps, average with the previous gains on even ones) with
+    the per-channel target.  Returns (G, losses), losses[t] the total loss of
+    the gains entering sweep t + 1."""
+    G = np.array(G0, np.complex128)
+    losses = []
+    for t in range(1, n_iter + 1):
+        losses.append(calib_chan_loss(V, M, G))
+        H = calib_chan_als_target(V, M, G, n_threads)
+        G = H if t % 2 == 1 else 0.5 * (G + H)
+    return G, np.array(losses)
+
+
 def _grid_args(tile_xy, vis):
     tile_xy = np.ascontiguousarray(tile_xy, np.float64)
     vis = np.ascontiguousarray(vis, np.int32)

@@ -367,6 +367,98 @@ def test_solve_recovers_true_gains():
 
 
 # ---------------------------------------------------------------------------
+# per-channel gains
+# ---------------------------------------------------------------------------
+def test_calib_chan_golden_two_inputs():
+    """N = 2, two channels, by hand.  Channel 0: g = (1, i), M_10 = 1, V_10 = 0:
+    R = i, L_0 = 1, grad = (2, 2i).  Channel 1: g = (2, 1), M_10 = 1, V_10 = 1:
+    R = g_1 conj(g_0) M - V = 1, L_1 = 1, grad_1 = 2 R g_0 conj(M) = 4,
+    grad_0 = 2 conj(R) g_1 M = 2."""
+    V = np.zeros((2, 3), complex)
+    M = np.zeros((2, 3), complex)
+    M[:, 1] = 1.0
+    V[1, 1] = 1.0
+    G = np.array([[1.0, 1j], [2.0, 1.0]])
+    assert oracle.calib_chan_loss(V, M, G) == pytest.approx(2.0, abs=1e-15)
+    np.testing.assert_allclose(oracle.calib_chan_grad(V, M, G), [[2.0, 2j], [2.0, 4.0]],
+                               atol=1e-14)
+
+
+def test_calib_chan_against_autograd():
+    """Per-channel loss and gradient pinned by torch autograd on a complex128
+    loss over the full matrices, G_c g_i(c) conj(g_j(c)) per channel."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(31)
+    N, C = 6, 4
+    V, M, _ = rand_cal(rng, N, C)
+    G = rng.uniform(0.8, 1.2, (C, N)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (C, N)))
+    Vf = np.zeros((C, N, N), complex)
+    Mf = np.zeros((C, N, N), complex)
+    ii, jj = np.tril_indices(N)
+    Vf[:, ii, jj] = V
+    Mf[:, ii, jj] = M
+    gt = torch.tensor(G, dtype=torch.complex128, requires_grad=True)
+    Gm = gt[:, :, None] * torch.conj(gt)[:, None, :]
+    R = Gm * torch.tensor(Mf) - torch.tensor(Vf)
+    mask = torch.tril(torch.ones(N, N, dtype=torch.bool), diagonal=-1)
+    L = (R.abs() ** 2)[:, mask].sum()
+    L.backward()
+    assert oracle.calib_chan_loss(V, M, G) == pytest.approx(L.item(), rel=1e-12)
+    np.testing.assert_allclose(oracle.calib_chan_grad(V, M, G), gt.grad.numpy(), rtol=1e-10,
+                               atol=1e-12)
+
+
+def test_calib_chan_reduces_to_shared_gains():
+    """With the same gains in every channel the per-channel loss is the
+    frequency-independent loss, the channel sum of the per-channel gradients
+    is its gradient, and the per-channel target differs from it only through
+    the per-channel normal equations (equal when there is one channel)."""
+    rng = np.random.default_rng(32)
+    N, C = 8, 5
+    V, M, g = rand_cal(rng, N, C)
+    G = np.tile(g, (C, 1))
+    assert oracle.calib_chan_loss(V, M, G) == pytest.approx(oracle.calib_loss(V, M, g), rel=1e-13)
+    np.testing.assert_allclose(oracle.calib_chan_grad(V, M, G).sum(0), oracle.calib_grad(V, M, g),
+                               rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.calib_chan_als_target(V[:1], M[:1], G[:1])[0],
+                               oracle.calib_als_target(V[:1], M[:1], g), rtol=1e-13)
+
+
+def test_calib_chan_target_zeroes_its_gradient_component():
+    rng = np.random.default_rng(33)
+    N, C = 7, 3
+    V, M, _ = rand_cal(rng, N, C)
+    G = rng.uniform(0.8, 1.2, (C, N)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (C, N)))
+    H = oracle.calib_chan_als_target(V, M, G)
+    scale = np.abs(oracle.calib_chan_grad(V, M, G)).max()
+    for c in range(C):
+        for k in range(N):
+            Gk = G.copy()
+            Gk[c, k] = H[c, k]
+            assert abs(oracle.calib_chan_grad(V, M, Gk)[c, k]) <= 1e-11 * scale
+
+
+def test_calib_chan_solve_recovers_channel_dependent_gains():
+    """Noise-free data whose gains change across the band: the per-channel
+    solve recovers every channel's gains up to that channel's global phase,
+    which a single frequency-independent gain per input cannot fit."""
+    rng = np.random.default_rng(34)
+    N, C = 12, 4
+    _, M, _ = rand_cal(rng, N, C)
+    G_true = rng.uniform(0.8, 1.2, (C, N)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (C, N)))
+    ii, jj = np.tril_indices(N)
+    V = G_true[:, ii] * np.conj(G_true[:, jj]) * M
+    G0 = G_true * (1 + 0.2 * (rng.standard_normal((C, N)) + 1j * rng.standard_normal((C, N))))
+    G, losses = oracle.calib_chan_solve(V, M, G0, 60)
+    for c in range(C):
+        ph = np.vdot(G[c], G_true[c])
+        assert np.abs(G[c] * ph / abs(ph) - G_true[c]).max() <= 1e-9 * np.abs(G_true).max()
+    assert losses[-1] <= 1e-16 * losses[0]
+    g_shared, l_shared = oracle.calib_solve(V, M, G0.mean(0), 60)
+    assert l_shared[-1] > 1e3 * losses[-1]
+
+
+# ---------------------------------------------------------------------------
 # gridding
 # ---------------------------------------------------------------------------
 C_LIGHT = 299792458.0
