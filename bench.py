@@ -723,6 +723,43 @@ def run_calib(args):
                                   "kernel": "calib_tile_kernel<den> + calib_gather_kernel<solve> (one sweep)",
                                   "peak_source": src},
                      "gpu_launches": 2 * n_sweeps}
+    # per-channel gains g_k(nu): the same pass with one gain per input and channel
+    G = (g[None, :] * torch.from_numpy(
+        (1 + 0.02 * (rng.standard_normal((C, N)) + 1j * rng.standard_normal((C, N))))
+        .astype(np.complex64)).to(dev)).contiguous()
+    ws_c = torch.empty(int(mw.lib().mwax_calib_chan_solve_workspace_bytes(N, C)), dtype=torch.uint8,
+                       device=dev)
+    for _ in range(args.warmup):
+        mw.calib_chan_loss_grad(V, M, G, ws_c)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        loss_c, _ = mw.calib_chan_loss_grad(V, M, G, ws_c)
+    b.record(stream)
+    b.synchronize()
+    ms_c = a.elapsed_time(b) / args.steps
+    bytes_c = 2 * 8 * B * C + 2 * 8 * N * C  # V, M; G in, gradient out
+    ach_c = bytes_c / (ms_c / 1e3) / 1e9
+    mw.calib_chan_solve(V, M, G, 1, ws_c)  # warm-up
+    torch.cuda.synchronize()
+    a.record(stream)
+    G_sol, hist_c = mw.calib_chan_solve(V, M, G, n_sweeps, ws_c)
+    b.record(stream)
+    b.synchronize()
+    ms_cs = a.elapsed_time(b) / n_sweeps
+    loss_c_final, _ = mw.calib_chan_loss_grad(V, M, G_sol, ws_c, want_grad=False)
+    line["per_channel_gains"] = {
+        "ms_per_step": ms_c, "value": terms / (ms_c / 1e3) / 1e9, "unit": "Gterms/s",
+        "loss": float(loss_c),
+        "roofline": {"bound": "hbm", "achieved": ach_c, "peak": float(peaks["hbm_gbs"]),
+                     "unit": "GB/s", "frac": ach_c / float(peaks["hbm_gbs"]), "traffic": None,
+                     "kernel": "calib_chan_tile_kernel + calib_chan_gather_kernel (one step)",
+                     "peak_source": src},
+        "solve": {"sweeps": n_sweeps, "ms_per_sweep": ms_cs,
+                  "value": terms / (ms_cs / 1e3) / 1e9, "unit": "Gterms/s per sweep",
+                  "loss_start": float(hist_c[0]), "loss_after": float(loss_c_final),
+                  "hbm_frac": bytes_c / (ms_cs / 1e3) / 1e9 / float(peaks["hbm_gbs"])},
+        "gpu_launches": 2 * args.steps + 2 * n_sweeps}
     if not args.no_cpu:
         sub = list(range(0, C, C // 8))[:8]
         V64 = V[sub].cpu().numpy().astype(np.complex128)
@@ -740,6 +777,14 @@ def run_calib(args):
         line["solve"]["cpu_baseline"] = {"value": B * len(sub) / dt / 1e9, "unit": "Gterms/s per sweep",
                                          "cores": oracle.threads(), "kind": "oracle",
                                          "sample": f"1 sweep on {len(sub)} of {C} channels (FP64)"}
+        G64 = G[sub].cpu().numpy().astype(np.complex128)
+        t0 = time.perf_counter()
+        oracle.calib_chan_loss(V64, M64, G64)
+        oracle.calib_chan_grad(V64, M64, G64)
+        dt = time.perf_counter() - t0
+        line["per_channel_gains"]["cpu_baseline"] = {
+            "value": B * len(sub) / dt / 1e9, "unit": "Gterms/s", "cores": oracle.threads(),
+            "kind": "oracle", "sample": f"{len(sub)} of {C} channels (FP64 loss + gradient)"}
     print(json.dumps(line), flush=True)
 
 

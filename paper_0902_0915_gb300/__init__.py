@@ -97,6 +97,10 @@ SIGNATURES = {
     "mwax_calib_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "mwax_calib_solve_workspace_bytes": (_I64, [_I, _I]),
     "mwax_calib_solve": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "mwax_calib_chan_workspace_bytes": (_I64, [_I, _I]),
+    "mwax_calib_chan_solve_workspace_bytes": (_I64, [_I, _I]),
+    "mwax_calib_chan_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "mwax_calib_chan_solve": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "mwax_grid_plan": (_I, [_P, _P, _I, _I, ctypes.c_double, ctypes.c_double, _I, ctypes.c_double,
                             _I, ctypes.c_double, _P]),
     "mwax_grid": (_I, [_P, _P, _P]),
@@ -525,6 +529,61 @@ def calib_solve(V, M, g0, n_iter: int, workspace=None, loss_history: bool = True
     return torch.view_as_complex(g), (hist[:n_iter] if hist is not None else None)
 
 
+def _chan_shapes(Vr, Mr, Gr):
+    if Gr.dim() != 3:
+        raise ValueError("per-channel gains must be [n_chan, N]")
+    c, n = Gr.shape[0], Gr.shape[1]
+    if Vr.shape != (c, n * (n + 1) // 2, 2) or Mr.shape != Vr.shape:
+        raise ValueError("V, M must be [n_chan, N(N+1)/2] for G of shape [n_chan, N]")
+    return n, c
+
+
+def calib_chan_loss_grad(V, M, G, workspace=None, want_loss=True, want_grad=True):
+    """Per-channel gains: (loss float32 scalar tensor or None, grad complex64
+    [n_chan, N] or None).  V, M: complex64 [n_chan, N(N+1)/2]; G: complex64
+    [n_chan, N]."""
+    torch = _torch()
+    Vr, Mr, Gr = _f32_pairs(V), _f32_pairs(M), _f32_pairs(G)
+    n, c = _chan_shapes(Vr, Mr, Gr)
+    if workspace is None:
+        nb = int(lib().mwax_calib_chan_workspace_bytes(n, c))
+        if nb < 0:
+            raise ValueError("invalid calibration shape")
+        workspace = torch.empty(nb, dtype=torch.uint8, device=V.device)
+    loss = torch.empty((), dtype=torch.float32, device=V.device) if want_loss else None
+    grad = torch.empty((c, n, 2), dtype=torch.float32, device=V.device) if want_grad else None
+    _check(lib().mwax_calib_chan_loss_grad(Vr.data_ptr(), Mr.data_ptr(), Gr.data_ptr(), n, c,
+                                           workspace.data_ptr(),
+                                           loss.data_ptr() if want_loss else None,
+                                           grad.data_ptr() if want_grad else None,
+                                           _stream_handle()), "mwax_calib_chan_loss_grad")
+    return loss, (torch.view_as_complex(grad) if want_grad else None)
+
+
+def calib_chan_solve(V, M, G0, n_iter: int, workspace=None, loss_history: bool = True):
+    """Per-channel gain solve: ``n_iter`` sweeps from ``G0`` (complex64
+    [n_chan, N], not modified).  Returns (G complex64 [n_chan, N], losses
+    float32 [n_iter] or None)."""
+    torch = _torch()
+    Vr, Mr = _f32_pairs(V), _f32_pairs(M)
+    G = _f32_pairs(G0).clone()
+    n, c = _chan_shapes(Vr, Mr, G)
+    if n_iter < 0:
+        raise ValueError("n_iter must be >= 0")
+    if workspace is None:
+        nb = int(lib().mwax_calib_chan_solve_workspace_bytes(n, c))
+        if nb < 0:
+            raise ValueError("invalid calibration shape")
+        workspace = torch.empty(nb, dtype=torch.uint8, device=V.device)
+    hist = (torch.empty(max(n_iter, 1), dtype=torch.float32, device=V.device)
+            if loss_history else None)
+    _check(lib().mwax_calib_chan_solve(Vr.data_ptr(), Mr.data_ptr(), G.data_ptr(), n, c, n_iter,
+                                       workspace.data_ptr(),
+                                       hist.data_ptr() if hist is not None else None,
+                                       _stream_handle()), "mwax_calib_chan_solve")
+    return torch.view_as_complex(G), (hist[:n_iter] if hist is not None else None)
+
+
 def _make_calib_function():
     torch = _torch()
 
@@ -536,7 +595,9 @@ def _make_calib_function():
 
         @staticmethod
         def forward(ctx, g, V, M):
-            loss, grad = calib_loss_grad(V, M, g.detach().contiguous(), want_grad=g.requires_grad)
+            # g [N]: one gain per input; g [n_chan, N]: per-channel gains
+            fn = calib_chan_loss_grad if g.dim() == 2 else calib_loss_grad
+            loss, grad = fn(V, M, g.detach().contiguous(), want_grad=g.requires_grad)
             ctx.save_for_backward(grad if grad is not None else torch.empty(0, device=g.device))
             return loss
 
@@ -552,7 +613,8 @@ _calib_cls = None
 
 
 def calib_loss(g, V, M):
-    """Differentiable calibration loss (torch.autograd.Function)."""
+    """Differentiable calibration loss (torch.autograd.Function); g complex64
+    [N] (one gain per input) or [n_chan, N] (per-channel gains)."""
     global _calib_cls
     if _calib_cls is None:
         _calib_cls = _make_calib_function()

@@ -291,6 +291,193 @@ __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
   }
 }
 
+// ---- per-channel gains ----------------------------------------------------------
+// g_k(nu), stored [C][N]: the channels decouple, so every (tile, channel) is a
+// reduction of its own and nothing is carried across channels.  One warp owns
+// one 32x32 tile of one channel: lane = column j = J*32 + lane, rows
+// i = I*32 + r taken in four groups of eight.  Column sums (to input j) stay in
+// the lane.  The eight row values of a group (to inputs i) are reduce-scattered
+// across the warp -- a butterfly over lane bits 4, 3, 2 that halves the values
+// each lane carries, then a sum over bits 1, 0 -- after which lanes 4s..4s+3
+// all hold the sum of row s of the group; lane 4s + t keeps group t's value,
+// so at the end lane 4s + t holds row 8t + s.  Eight warps of a CTA take eight
+// consecutive channels of the same tile.  Entries outside the stored triangle
+// load V = M = 0, whose residual and contributions are exactly 0.
+
+// a[0..7] (one value per row of the group) -> the full-warp sum of value
+// (lane >> 2) & 7, fixed order.
+__device__ __forceinline__ float reduce_scatter8(float (&a)[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = b4 ? a[k] : a[k + 4];
+    const float keep = b4 ? a[k + 4] : a[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = b3 ? a[k] : a[k + 2];
+    const float keep = b3 ? a[k + 2] : a[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send = b2 ? a[0] : a[1];
+  float x = (b2 ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  return x;
+}
+
+// grid: (tiles, ceil(C / 8)).  Partial sums per (tile, channel):
+// part_row / part_col [tile][C][32], DEN: part_rden / part_cden likewise;
+// part_loss [tile][gridDim.y] (the CTA's eight channels).
+template <bool DEN>
+__global__ void __launch_bounds__(kCalThreads, 3) calib_chan_tile_kernel(
+    const float2 *__restrict__ V, const float2 *__restrict__ M, const float2 *__restrict__ g,
+    int N, int C, float *__restrict__ part_loss, float2 *__restrict__ part_row,
+    float2 *__restrict__ part_col, float *__restrict__ part_rden, float *__restrict__ part_cden) {
+  __shared__ float2 sgi[kCalThreads / 32][kCT];
+  __shared__ float sloss[kCalThreads / 32];
+  const int tile = blockIdx.x;
+  int I, J;
+  tile_of(tile, I, J);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nu = blockIdx.y * (kCalThreads / 32) + w;
+  float lsum = 0.f;
+  if (nu < C) {
+    const int64_t B = (int64_t)N * (N + 1) / 2;
+    const float2 *gn = g + (int64_t)nu * N;
+    const float2 zero = make_float2(0.f, 0.f);
+    const int j = J * kCT + lane, il = I * kCT + lane;
+    const float2 gj = j < N ? gn[j] : zero;
+    sgi[w][lane] = il < N ? gn[il] : zero;
+    __syncwarp();
+    const float gj2 = gj.x * gj.x + gj.y * gj.y;
+    const float2 *Vn = V + (int64_t)nu * B, *Mn = M + (int64_t)nu * B;
+    float cre = 0.f, cim = 0.f, cden = 0.f, rre = 0.f, rim = 0.f, rden = 0.f;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      float2 v[8], m[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int i = I * kCT + 8 * q + s;
+        const bool ok = i < N && j < i;
+        const int64_t b = (int64_t)i * (i + 1) / 2 + j;
+        v[s] = ok ? __ldcs(Vn + b) : zero;
+        m[s] = ok ? __ldcs(Mn + b) : zero;
+      }
+      float ar[8], ai[8], ad[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const float2 gi = sgi[w][8 * q + s];
+        const float Gr = gi.x * gj.x + gi.y * gj.y;  // g_i conj(g_j)
+        const float Gi = gi.y * gj.x - gi.x * gj.y;
+        const float Rr = Gr * m[s].x - Gi * m[s].y - v[s].x;  // R = G M - V
+        const float Ri = Gr * m[s].y + Gi * m[s].x - v[s].y;
+        lsum += Rr * Rr + Ri * Ri;
+        const float Pr = Rr * gj.x - Ri * gj.y, Pi = Rr * gj.y + Ri * gj.x;  // R g_j
+        ar[s] = Pr * m[s].x + Pi * m[s].y;                                     // to row i
+        ai[s] = Pi * m[s].x - Pr * m[s].y;
+        const float Qr = Rr * gi.x + Ri * gi.y, Qi = Rr * gi.y - Ri * gi.x;  // conj(R) g_i
+        cre += Qr * m[s].x - Qi * m[s].y;                                      // to column j
+        cim += Qr * m[s].y + Qi * m[s].x;
+        if constexpr (DEN) {
+          const float m2 = m[s].x * m[s].x + m[s].y * m[s].y;
+          ad[s] = gj2 * m2;
+          cden += (gi.x * gi.x + gi.y * gi.y) * m2;
+        }
+      }
+      const float xr = reduce_scatter8(ar, lane);
+      const float xi = reduce_scatter8(ai, lane);
+      if ((lane & 3) == q) {
+        rre = xr;
+        rim = xi;
+      }
+      if constexpr (DEN) {
+        const float xd = reduce_scatter8(ad, lane);
+        if ((lane & 3) == q) rden = xd;
+      }
+    }
+    const int64_t base = ((int64_t)tile * C + nu) * kCT;
+    const int row = 8 * (lane & 3) + ((lane >> 2) & 7);
+    part_row[base + row] = make_float2(rre, rim);
+    part_col[base + lane] = make_float2(cre, cim);
+    if constexpr (DEN) {
+      part_rden[base + row] = rden;
+      part_cden[base + lane] = cden;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  }
+  if (lane == 0) sloss[w] = lsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < kCalThreads / 32; ++k) t += sloss[k];
+    part_loss[(int64_t)tile * gridDim.y + blockIdx.y] = t;
+  }
+}
+
+// grid: (n_blocks + 1, ceil(C / 8)).  Block (K, y), warp w: channel
+// nu = 8y + w, lane r: input k = 32K + r, summing its row partials over tiles
+// (K, J <= K) and its column partials over tiles (I >= K, K) in that order.
+// Block (n_blocks, 0) sums the loss partials.  SOLVE: one sweep's update of
+// g[nu][k] in place, as in calib_gather_kernel.
+template <bool SOLVE>
+__global__ void __launch_bounds__(kCalThreads) calib_chan_gather_kernel(
+    int N, int C, int n_blocks, const float *__restrict__ part_loss,
+    const float2 *__restrict__ part_row, const float2 *__restrict__ part_col,
+    const float *__restrict__ part_rden, const float *__restrict__ part_cden,
+    float *__restrict__ loss, float2 *__restrict__ grad, float2 *__restrict__ g_io, int avg) {
+  const int K = blockIdx.x;
+  if (K == n_blocks) {
+    if (blockIdx.y != 0 || !loss) return;
+    __shared__ float sred[kCalThreads];
+    const int64_t n_part = (int64_t)n_blocks * (n_blocks + 1) / 2 * gridDim.y;
+    Kahan acc;
+    for (int64_t k = threadIdx.x; k < n_part; k += kCalThreads) acc.add(part_loss[k]);
+    sred[threadIdx.x] = acc.s;
+    __syncthreads();
+    for (int h = kCalThreads / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) sred[threadIdx.x] += sred[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = sred[0];
+    return;
+  }
+  if (!SOLVE && !grad) return;
+  const int lane = threadIdx.x & 31;
+  const int nu = blockIdx.y * (kCalThreads / 32) + (threadIdx.x >> 5);
+  const int k = K * kCT + lane;
+  if (nu >= C || k >= N) return;
+  float ar = 0.f, ai = 0.f, ad = 0.f;
+  for (int Jt = 0; Jt <= K; ++Jt) {
+    const int64_t idx = ((int64_t)(K * (K + 1) / 2 + Jt) * C + nu) * kCT + lane;
+    const float2 v = part_row[idx];
+    ar += v.x;
+    ai += v.y;
+    if constexpr (SOLVE) ad += part_rden[idx];
+  }
+  for (int It = K; It < n_blocks; ++It) {
+    const int64_t idx = ((int64_t)(It * (It + 1) / 2 + K) * C + nu) * kCT + lane;
+    const float2 v = part_col[idx];
+    ar += v.x;
+    ai += v.y;
+    if constexpr (SOLVE) ad += part_cden[idx];
+  }
+  const int64_t o = (int64_t)nu * N + k;
+  if constexpr (SOLVE) {
+    if (ad > 0.f) {
+      const float2 gk = g_io[o];
+      const float inv = 1.f / ad;
+      float2 h = make_float2(gk.x - ar * inv, gk.y - ai * inv);  // (ar, ai) = grad / 2
+      if (avg) h = make_float2(0.5f * (gk.x + h.x), 0.5f * (gk.y + h.y));
+      g_io[o] = h;
+    }
+  } else {
+    grad[o] = make_float2(2.f * ar, 2.f * ai);
+  }
+}
+
 bool dev_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -321,6 +508,46 @@ Ws carve(void *ws, int n_blocks, int n_cg, bool solve) {
   p += (tiles * n_cg * (int64_t)sizeof(float) + 255) / 256 * 256;
   w.rden = solve ? reinterpret_cast<float *>(p) : nullptr;
   p += tiles * n_cg * kCT * sizeof(float);
+  w.cden = solve ? reinterpret_cast<float *>(p) : nullptr;
+  return w;
+}
+
+constexpr int kChanPerCta = kCalThreads / 32;
+constexpr int kMaxCalibChan = 65535 * kChanPerCta;  // grid.y limit
+
+struct ChanWs {
+  float *loss;
+  float2 *row, *col;
+  float *rden, *cden;  // gain solve only
+};
+
+int64_t chan_ws_bytes(int n_inputs, int n_chan, bool solve) {
+  if (n_inputs < 2 || n_chan < 1 || n_inputs > 65536 || n_chan > kMaxCalibChan) return -1;
+  const int64_t nb = (n_inputs + kCT - 1) / kCT;
+  const int64_t tiles = nb * (nb + 1) / 2;
+  const int64_t n_cy = (n_chan + kChanPerCta - 1) / kChanPerCta;
+  const int64_t slots = tiles * n_chan * kCT;
+  int64_t b = slots * (int64_t)sizeof(float2) * 2 +
+              (tiles * n_cy * (int64_t)sizeof(float) + 255) / 256 * 256;
+  if (solve) b += slots * (int64_t)sizeof(float) * 2;
+  return b;
+}
+
+// Layout: row and column partials, loss partials (256-byte padded), then (gain
+// solve) the row and column den partials.
+ChanWs chan_carve(void *ws, int nb, int n_chan, int n_cy, bool solve) {
+  const int64_t tiles = (int64_t)nb * (nb + 1) / 2;
+  const int64_t slots = tiles * n_chan * kCT;
+  uint8_t *p = reinterpret_cast<uint8_t *>(ws);
+  ChanWs w;
+  w.row = reinterpret_cast<float2 *>(p);
+  p += slots * sizeof(float2);
+  w.col = reinterpret_cast<float2 *>(p);
+  p += slots * sizeof(float2);
+  w.loss = reinterpret_cast<float *>(p);
+  p += (tiles * n_cy * (int64_t)sizeof(float) + 255) / 256 * 256;
+  w.rden = solve ? reinterpret_cast<float *>(p) : nullptr;
+  p += slots * sizeof(float);
   w.cden = solve ? reinterpret_cast<float *>(p) : nullptr;
   return w;
 }
@@ -392,6 +619,62 @@ mwax_status mwax_calib_solve(const float *V, const float *M, float *g, int n_inp
     if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
     calib_gather_kernel<true><<<nb + 1, kCalThreads, 0, stream>>>(
         n_inputs, nb, n_cg, w.loss, w.row, w.col, w.rden, w.cden,
+        loss_hist ? loss_hist + (t - 1) : nullptr, nullptr, g2, (t % 2 == 0) ? 1 : 0);
+    if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
+  }
+  return MWAX_OK;
+}
+
+int64_t mwax_calib_chan_workspace_bytes(int n_inputs, int n_chan) {
+  return chan_ws_bytes(n_inputs, n_chan, false);
+}
+
+int64_t mwax_calib_chan_solve_workspace_bytes(int n_inputs, int n_chan) {
+  return chan_ws_bytes(n_inputs, n_chan, true);
+}
+
+mwax_status mwax_calib_chan_loss_grad(const float *V, const float *M, const float *g,
+                                      int n_inputs, int n_chan, void *workspace, float *loss,
+                                      float *grad, cudaStream_t stream) {
+  mwax::NvtxRange nvtx_("mwax_calib_chan_loss_grad");
+  if (chan_ws_bytes(n_inputs, n_chan, false) < 0) return MWAX_ERR_INVALID_ARG;
+  if (!loss && !grad) return MWAX_ERR_INVALID_ARG;
+  if (!dev_ptr(V) || !dev_ptr(M) || !dev_ptr(g) || !dev_ptr(workspace)) return MWAX_ERR_INVALID_ARG;
+  if ((loss && !dev_ptr(loss)) || (grad && !dev_ptr(grad))) return MWAX_ERR_INVALID_ARG;
+  const int nb = (n_inputs + kCT - 1) / kCT;
+  const int tiles = nb * (nb + 1) / 2;
+  const int n_cy = (n_chan + kChanPerCta - 1) / kChanPerCta;
+  ChanWs w = chan_carve(workspace, nb, n_chan, n_cy, false);
+  calib_chan_tile_kernel<false><<<dim3(tiles, n_cy), kCalThreads, 0, stream>>>(
+      reinterpret_cast<const float2 *>(V), reinterpret_cast<const float2 *>(M),
+      reinterpret_cast<const float2 *>(g), n_inputs, n_chan, w.loss, w.row, w.col, nullptr,
+      nullptr);
+  if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
+  calib_chan_gather_kernel<false><<<dim3(nb + 1, n_cy), kCalThreads, 0, stream>>>(
+      n_inputs, n_chan, nb, w.loss, w.row, w.col, nullptr, nullptr, loss,
+      reinterpret_cast<float2 *>(grad), nullptr, 0);
+  return cudaGetLastError() == cudaSuccess ? MWAX_OK : MWAX_ERR_CUDA;
+}
+
+mwax_status mwax_calib_chan_solve(const float *V, const float *M, float *g, int n_inputs,
+                                  int n_chan, int n_iter, void *workspace, float *loss_hist,
+                                  cudaStream_t stream) {
+  mwax::NvtxRange nvtx_("mwax_calib_chan_solve");
+  if (chan_ws_bytes(n_inputs, n_chan, true) < 0 || n_iter < 0) return MWAX_ERR_INVALID_ARG;
+  if (!dev_ptr(V) || !dev_ptr(M) || !dev_ptr(g) || !dev_ptr(workspace)) return MWAX_ERR_INVALID_ARG;
+  if (loss_hist && !dev_ptr(loss_hist)) return MWAX_ERR_INVALID_ARG;
+  const int nb = (n_inputs + kCT - 1) / kCT;
+  const int tiles = nb * (nb + 1) / 2;
+  const int n_cy = (n_chan + kChanPerCta - 1) / kChanPerCta;
+  ChanWs w = chan_carve(workspace, nb, n_chan, n_cy, true);
+  float2 *g2 = reinterpret_cast<float2 *>(g);
+  for (int t = 1; t <= n_iter; ++t) {
+    calib_chan_tile_kernel<true><<<dim3(tiles, n_cy), kCalThreads, 0, stream>>>(
+        reinterpret_cast<const float2 *>(V), reinterpret_cast<const float2 *>(M), g2, n_inputs,
+        n_chan, w.loss, w.row, w.col, w.rden, w.cden);
+    if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
+    calib_chan_gather_kernel<true><<<dim3(nb + 1, n_cy), kCalThreads, 0, stream>>>(
+        n_inputs, n_chan, nb, w.loss, w.row, w.col, w.rden, w.cden,
         loss_hist ? loss_hist + (t - 1) : nullptr, nullptr, g2, (t % 2 == 0) ? 1 : 0);
     if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
   }

@@ -119,3 +119,22 @@ def test_pair_work_list_covers_every_tile_pair_once(mwax_lib, n_tiles, n_chan):
     assert (items[:, 0] == 0).sum() <= 1
     assert mw.lib().mwax_pair_work_list(0, 1, None, 0) == -1
     assert mw.lib().mwax_pair_work_list(256, 1, None, 0) == -1
+
+
+def test_calib_workspace_sizes(mwax_lib):
+    """Workspace sizes from the partial-sum layout: per (32 x 32 input tile,
+    channel group or channel) a row and a column complex partial per input,
+    loss partials, and for the solves a real den partial per row and column;
+    -1 for shapes out of range."""
+    L = mwax_lib.lib()
+    N, C = 1024, 768
+    tiles = 32 * 33 // 2
+    slots = tiles * C * 32
+    loss_bytes = -(-tiles * (C // 8) * 4 // 256) * 256
+    assert L.mwax_calib_chan_workspace_bytes(N, C) == slots * 16 + loss_bytes
+    assert L.mwax_calib_chan_solve_workspace_bytes(N, C) == slots * 24 + loss_bytes
+    assert L.mwax_calib_workspace_bytes(N, C) > 0
+    for n, c in ((1, 4), (2, 0), (65537, 1), (4, 65535 * 8 + 1)):
+        assert L.mwax_calib_chan_workspace_bytes(n, c) == -1
+        assert L.mwax_calib_chan_solve_workspace_bytes(n, c) == -1
+    assert L.mwax_calib_chan_workspace_bytes(2, 65535 * 8) > 0

@@ -213,3 +213,145 @@ def test_solve_full_size(mw):
     V, M, g0 = big_problem(1024, 768, seed=12)
     g, hist = gpu_solve(mw, V, M, g0, 2)
     check_solve(V, M, g0, 2, g, hist, tol_g=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# per-channel gains g_k(nu)
+# ---------------------------------------------------------------------------
+def problem_chan(N, C, seed, noise=0.05, gain_err=0.05):
+    """Point-source-like model, gains that change across the band, and a
+    perturbed per-channel estimate G [C, N]."""
+    V, M, _ = problem(N, C, seed, noise=0.0)
+    rng = np.random.default_rng(seed + 1000)
+    ii, jj = np.tril_indices(N)
+    G_true = rng.uniform(0.8, 1.2, (C, N)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (C, N)))
+    Vc = G_true[:, ii] * np.conj(G_true[:, jj]) * M.astype(np.complex128)
+    Vc = Vc + noise * np.abs(M).mean() * (rng.standard_normal(Vc.shape) + 1j * rng.standard_normal(Vc.shape))
+    G = G_true * (1 + gain_err * (rng.standard_normal((C, N)) + 1j * rng.standard_normal((C, N))))
+    return (np.ascontiguousarray(Vc, np.complex64), M,
+            np.ascontiguousarray(G, np.complex64), G_true)
+
+
+def gpu_chan_loss_grad(mw, V, M, G):
+    import torch
+
+    loss, grad = mw.calib_chan_loss_grad(torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda(),
+                                         torch.from_numpy(G).cuda())
+    torch.cuda.synchronize()
+    return float(loss.item()), grad.cpu().numpy()
+
+
+def check_chan(V, M, G, loss, grad, chans=None):
+    """Loss within 1e-5 relative of the FP64 oracle (all channels); gradient
+    within 1e-4 (max-norm, relative) on the channels checked."""
+    chans = range(V.shape[0]) if chans is None else chans
+    L64 = sum(oracle.calib_chan_loss(V[c:c + 1].astype(np.complex128), M[c:c + 1].astype(np.complex128),
+                                     G[c:c + 1].astype(np.complex128)) for c in range(V.shape[0]))
+    assert abs(loss - L64) / L64 <= 1e-5, (loss, L64)
+    for c in chans:
+        G64 = oracle.calib_chan_grad(V[c:c + 1].astype(np.complex128),
+                                     M[c:c + 1].astype(np.complex128),
+                                     G[c:c + 1].astype(np.complex128))[0]
+        assert np.abs(grad[c] - G64).max() / np.abs(G64).max() <= 1e-4, c
+
+
+@pytest.mark.parametrize("N,C", [(2, 1), (33, 3), (70, 9), (130, 17), (257, 8)])
+def test_calib_chan_small(mw, N, C):
+    """Ragged tiles (N not a multiple of 32) and channel counts that leave
+    warps of the last CTA without a channel."""
+    V, M, G, _ = problem_chan(N, C, seed=200 + N + C)
+    loss, grad = gpu_chan_loss_grad(mw, V, M, G)
+    check_chan(V, M, G, loss, grad)
+
+
+def test_calib_chan_deterministic(mw):
+    V, M, G, _ = problem_chan(100, 12, seed=6)
+    a = gpu_chan_loss_grad(mw, V, M, G)
+    b = gpu_chan_loss_grad(mw, V, M, G)
+    assert a[0] == b[0]
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_calib_chan_autograd_function(mw):
+    """calib_loss with [n_chan, N] gains takes the per-channel path."""
+    import torch
+
+    V, M, G, _ = problem_chan(48, 5, seed=7)
+    gt = torch.from_numpy(G).cuda().requires_grad_(True)
+    L = mw.calib_loss(gt, torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda())
+    (2.0 * L).backward()
+    G64 = oracle.calib_chan_grad(V.astype(np.complex128), M.astype(np.complex128), G.astype(np.complex128))
+    got = gt.grad.cpu().numpy()
+    assert got.shape == G.shape
+    assert np.abs(got - 2.0 * G64).max() / np.abs(2.0 * G64).max() <= 1e-4
+
+
+def test_calib_chan_shared_gains_match_the_per_input_kernel(mw):
+    """The same gains in every channel: the per-channel loss equals the
+    frequency-independent kernel's, and the channel sum of the per-channel
+    gradient equals its gradient (two different kernels, same mathematics)."""
+    V, M, g = problem(90, 7, seed=12)
+    G = np.ascontiguousarray(np.tile(g, (7, 1)))
+    lc, gc = gpu_chan_loss_grad(mw, V, M, G)
+    l1, g1 = gpu_loss_grad(mw, V, M, g)
+    assert abs(lc - l1) <= 1e-5 * l1
+    assert np.abs(gc.sum(0) - g1).max() <= 1e-4 * np.abs(g1).max()
+
+
+def test_calib_chan_full_size(mw):
+    """1024 inputs x 768 channels: the loss over every channel, the gradient
+    on 12 seeded channels including the first and last."""
+    V, M, g = big_problem(1024, 768, seed=14)
+    rng = np.random.default_rng(15)
+    G = (g[None, :] * (1 + 0.02 * (rng.standard_normal((768, 1024)) + 1j * rng.standard_normal((768, 1024))))).astype(np.complex64)
+    loss, grad = gpu_chan_loss_grad(mw, V, M, G)
+    chans = sorted({0, 767, *rng.choice(768, 10, replace=False).tolist()})
+    check_chan(V, M, G, loss, grad, chans)
+
+
+def gpu_chan_solve(mw, V, M, G0, n_iter):
+    import torch
+
+    G, hist = mw.calib_chan_solve(torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda(),
+                                  torch.from_numpy(G0).cuda(), n_iter)
+    torch.cuda.synchronize()
+    return G.cpu().numpy(), hist.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,C,n_iter", [(2, 1, 1), (33, 3, 2), (70, 9, 5), (130, 5, 4)])
+def test_calib_chan_solve_small(mw, N, C, n_iter):
+    V, M, G0, _ = problem_chan(N, C, seed=300 + N + C)
+    G, hist = gpu_chan_solve(mw, V, M, G0, n_iter)
+    G64, l64 = oracle.calib_chan_solve(V.astype(np.complex128), M.astype(np.complex128),
+                                       G0.astype(np.complex128), n_iter)
+    assert np.abs(G - G64).max() <= 1e-4 * np.abs(G64).max()
+    assert hist.shape == (n_iter,)
+    assert abs(hist[0] - l64[0]) <= 1e-5 * l64[0]
+    np.testing.assert_allclose(hist, l64, rtol=1e-4)
+
+
+def test_calib_chan_solve_recovers_band_dependent_gains(mw):
+    """Noise-free data with gains that change across the band: every channel
+    comes back to FP32 accuracy up to its own global phase."""
+    V, M, G0, G_true = problem_chan(64, 6, seed=21, noise=0.0, gain_err=0.2)
+    G, hist = gpu_chan_solve(mw, V, M, G0, 40)
+    for c in range(6):
+        ph = np.vdot(G[c], G_true[c])
+        err = np.abs(G[c] * ph / abs(ph) - G_true[c]).max() / np.abs(G_true).max()
+        assert err <= 2e-5, (c, err)
+    assert hist[-1] <= 1e-8 * hist[0]
+
+
+def test_calib_chan_rejects_bad_shapes(mw):
+    import torch
+
+    V, M, G, _ = problem_chan(20, 3, seed=2)
+    Vd, Md = torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda()
+    with pytest.raises(ValueError):
+        mw.calib_chan_loss_grad(Vd, Md, torch.from_numpy(G[:2]).cuda())
+    with pytest.raises(ValueError):
+        mw.calib_chan_loss_grad(Vd, Md, torch.from_numpy(G[0]).cuda())
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    # host pointers are refused before any launch
+    assert mw.lib().mwax_calib_chan_loss_grad(V.ctypes.data, M.ctypes.data, G.ctypes.data, 20, 3,
+                                              ws.data_ptr(), ws.data_ptr(), None, None) != 0
