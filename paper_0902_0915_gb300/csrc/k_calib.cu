@@ -17,8 +17,8 @@
 // CTA owns a 32x32 tile of input pairs for a fixed group of channels and
 // writes its row / column / loss partial sums to a workspace, and a second
 // kernel gathers them per input in a fixed order.  No atomics, FP32 only
-// (Kahan-compensated accumulation inside a thread, fixed trees across
-// threads).  One pass reads V and M once.
+// (plain 32-term sums inside a channel, Kahan-compensated accumulation across
+// channels, fixed trees across lanes and warps).  One pass reads V and M once.
 //
 // Gain solve (alternating least squares): with every gain but g_k fixed, L
 // is a linear least-squares problem in g_k whose minimiser is
@@ -62,149 +62,185 @@ __device__ __forceinline__ void tile_of(int p, int &I, int &J) {
   J = p - i * (i + 1) / 2;
 }
 
-// grid: (tiles, channel groups).  Thread (ty, tx): column j = J*32 + tx,
-// rows i = I*32 + ty + 8m, m = 0..3.  DEN: also the per-row and per-column
-// sums of |g_other|^2 |M|^2 (the gain solve's normal-equation weight).
+// Reduce-scatter of eight values across a warp (used by both tile kernels):
+// a[0..7] (one value per row of a group of eight rows) -> the full-warp sum
+// of value (lane >> 2) & 7, in a fixed order.  A butterfly over lane bits 4,
+// 3, 2 halves the values each lane carries, then a sum over bits 1, 0 leaves
+// lanes 4s..4s+3 all holding the sum of value s.
+__device__ __forceinline__ float reduce_scatter8(float (&a)[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = b4 ? a[k] : a[k + 4];
+    const float keep = b4 ? a[k + 4] : a[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = b3 ? a[k] : a[k + 2];
+    const float keep = b3 ? a[k + 2] : a[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send = b2 ? a[0] : a[1];
+  float x = (b2 ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  return x;
+}
+
+// One channel of one 32x32 tile, processed by one warp: lane = column
+// j = J*32 + lane, rows i = I*32 + r in four groups of eight.  Returns, per
+// lane, this channel's column sums (to input j), its row sums for row
+// 8 (lane & 3) + ((lane >> 2) & 7) (to input i; the eight rows of a group are
+// reduce-scattered across the warp, lane 4s + t keeping group t's value) and
+// its part of the loss.  sgi: g of the tile's 32 rows.  Entries outside the
+// stored triangle load V = M = 0, whose residual and contributions are 0.
+struct TileSums {
+  float loss, rre, rim, rden, cre, cim, cden;
+};
+
+template <bool DEN>
+__device__ __forceinline__ TileSums tile_channel(const float2 *__restrict__ Vn,
+                                                 const float2 *__restrict__ Mn,
+                                                 const float2 *sgi, float2 gj, int I, int j,
+                                                 int N, int lane) {
+  const float2 zero = make_float2(0.f, 0.f);
+  const float gj2 = gj.x * gj.x + gj.y * gj.y;
+  TileSums t = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int q = 0; q < 4; ++q) {
+    float2 v[8], m[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int i = I * kCT + 8 * q + s;
+      const bool ok = i < N && j < i;
+      const int64_t b = (int64_t)i * (i + 1) / 2 + j;
+      v[s] = ok ? __ldcs(Vn + b) : zero;
+      m[s] = ok ? __ldcs(Mn + b) : zero;
+    }
+    float ar[8], ai[8], ad[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const float2 gi = sgi[8 * q + s];
+      const float Gr = gi.x * gj.x + gi.y * gj.y;  // g_i conj(g_j)
+      const float Gi = gi.y * gj.x - gi.x * gj.y;
+      const float Rr = Gr * m[s].x - Gi * m[s].y - v[s].x;  // R = G M - V
+      const float Ri = Gr * m[s].y + Gi * m[s].x - v[s].y;
+      t.loss += Rr * Rr + Ri * Ri;
+      const float Pr = Rr * gj.x - Ri * gj.y, Pi = Rr * gj.y + Ri * gj.x;  // R g_j
+      ar[s] = Pr * m[s].x + Pi * m[s].y;                                     // to row i
+      ai[s] = Pi * m[s].x - Pr * m[s].y;
+      const float Qr = Rr * gi.x + Ri * gi.y, Qi = Rr * gi.y - Ri * gi.x;  // conj(R) g_i
+      t.cre += Qr * m[s].x - Qi * m[s].y;                                    // to column j
+      t.cim += Qr * m[s].y + Qi * m[s].x;
+      if constexpr (DEN) {
+        const float m2 = m[s].x * m[s].x + m[s].y * m[s].y;
+        ad[s] = gj2 * m2;                              // row i: |g_j|^2 |M_ij|^2
+        t.cden += (gi.x * gi.x + gi.y * gi.y) * m2;    // column j: |g_i|^2 |M_ij|^2
+      }
+    }
+    const float xr = reduce_scatter8(ar, lane);
+    const float xi = reduce_scatter8(ai, lane);
+    if ((lane & 3) == q) {
+      t.rre = xr;
+      t.rim = xi;
+    }
+    if constexpr (DEN) {
+      const float xd = reduce_scatter8(ad, lane);
+      if ((lane & 3) == q) t.rden = xd;
+    }
+  }
+  return t;
+}
+
+__device__ __forceinline__ int tile_row_of_lane(int lane) {
+  return 8 * (lane & 3) + ((lane >> 2) & 7);
+}
+
+// grid: (tiles, channel groups).  CTA (tile, cg) covers channels cg,
+// cg + n_cg, ...; its warp w takes every eighth of them
+// (nu = cg + n_cg (w + 8k)), each channel with tile_channel, and adds the
+// channel's sums into Kahan accumulators (one compensated add per channel;
+// the 32-term sums inside a channel are plain FP32).  The eight warps' totals
+// are then summed in a fixed order.  DEN: also the per-row and per-column
+// sums of |g_other|^2 |M|^2 (the gain solve's normal-equation weight; sums of
+// positive terms, plain FP32).
 template <bool DEN>
 __global__ void __launch_bounds__(kCalThreads, 3) calib_tile_kernel(
     const float2 *__restrict__ V, const float2 *__restrict__ M, const float2 *__restrict__ g,
     int N, int C, int n_cg, float *__restrict__ part_loss, float2 *__restrict__ part_row,
     float2 *__restrict__ part_col, float *__restrict__ part_rden, float *__restrict__ part_cden) {
-  __shared__ float2 sg_i[kCT], sg_j[kCT];
-  __shared__ float2 scol[8][kCT];
-  __shared__ float scden[8][kCT];
-  __shared__ float sloss[kCalThreads / 32];
+  constexpr int kWarps = kCalThreads / 32;
+  __shared__ float2 sgi[kCT];
+  __shared__ float2 srow[kWarps][kCT], scol[kWarps][kCT];
+  __shared__ float srden[kWarps][kCT], scden[kWarps][kCT];
+  __shared__ float sloss[kWarps];
   const int tile = blockIdx.x, cg = blockIdx.y;
   int I, J;
   tile_of(tile, I, J);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = J * kCT + lane;
   if (threadIdx.x < kCT) {
-    const int i = I * kCT + threadIdx.x, j = J * kCT + threadIdx.x;
-    sg_i[threadIdx.x] = i < N ? g[i] : make_float2(0.f, 0.f);
-    sg_j[threadIdx.x] = j < N ? g[j] : make_float2(0.f, 0.f);
+    const int il = I * kCT + threadIdx.x;
+    sgi[threadIdx.x] = il < N ? g[il] : make_float2(0.f, 0.f);
   }
+  const float2 gj = j < N ? g[j] : make_float2(0.f, 0.f);
   __syncthreads();
   const int64_t B = (int64_t)N * (N + 1) / 2;
-  const int j = J * kCT + tx;
-  const float2 gj = sg_j[tx];
-  // rows of this thread that hold a stored off-diagonal pair (fixed over channels)
-  bool valid[4];
-  int64_t boff[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int i = I * kCT + ty + 8 * m;
-    valid[m] = i < N && j < N && j < i;
-    boff[m] = valid[m] ? (int64_t)i * (i + 1) / 2 + j : 0;
-  }
-  // channels of this group: cg, cg + n_cg, ...  The next channel's V and M
-  // are loaded while the current one is processed (two channels in flight).
-  Kahan loss, rre[4], rim[4], cre, cim;
-  // the solve's weights are sums of positive terms (~C / n_cg per thread):
-  // plain FP32 sums are accurate enough and keep registers free
-  float rden[4] = {0.f, 0.f, 0.f, 0.f}, cden = 0.f;
-  const float gj2 = gj.x * gj.x + gj.y * gj.y;
-  float2 v[4], mm[4];
-  auto load = [&](int nu, float2 (&vv)[4], float2 (&mv)[4]) {
-    const float2 *Vn = V + (int64_t)nu * B;
-    const float2 *Mn = M + (int64_t)nu * B;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      vv[m] = valid[m] ? __ldcs(Vn + boff[m]) : make_float2(0.f, 0.f);
-      mv[m] = valid[m] ? __ldcs(Mn + boff[m]) : make_float2(0.f, 0.f);
-    }
-  };
-  // channels in flight: the current one and the next (the solve's extra
-  // accumulators leave no registers for more), or also the one after
-  constexpr int ahead = DEN ? 1 : 2;
-  float2 v1[4] = {}, m1[4] = {};
-  if (cg < C) load(cg, v, mm);
-  if (ahead == 2 && cg + n_cg < C) load(cg + n_cg, v1, m1);
-  for (int nu = cg; nu < C; nu += n_cg) {
-    float2 vn[4] = {}, mn[4] = {};
-    if (nu + ahead * n_cg < C) load(nu + ahead * n_cg, vn, mn);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      if (!valid[m]) continue;
-      const float2 gi = sg_i[ty + 8 * m];
-      // G = g_i conj(g_j)
-      const float Gr = gi.x * gj.x + gi.y * gj.y;
-      const float Gi = gi.y * gj.x - gi.x * gj.y;
-      // R = G M - V
-      const float Rr = Gr * mm[m].x - Gi * mm[m].y - v[m].x;
-      const float Ri = Gr * mm[m].y + Gi * mm[m].x - v[m].y;
-      loss.add(Rr * Rr + Ri * Ri);
-      // to row i: R g_j conj(M)
-      const float Pr = Rr * gj.x - Ri * gj.y, Pi = Rr * gj.y + Ri * gj.x;  // R g_j
-      rre[m].add(Pr * mm[m].x + Pi * mm[m].y);
-      rim[m].add(Pi * mm[m].x - Pr * mm[m].y);
-      // to column j: conj(R) g_i M
-      const float Qr = Rr * gi.x + Ri * gi.y, Qi = Rr * gi.y - Ri * gi.x;  // conj(R) g_i
-      cre.add(Qr * mm[m].x - Qi * mm[m].y);
-      cim.add(Qr * mm[m].y + Qi * mm[m].x);
-      if constexpr (DEN) {
-        const float m2 = mm[m].x * mm[m].x + mm[m].y * mm[m].y;
-        rden[m] += gj2 * m2;                           // row i: |g_j|^2 |M_ij|^2
-        cden += (gi.x * gi.x + gi.y * gi.y) * m2;      // column j: |g_i|^2 |M_ij|^2
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      if constexpr (ahead == 2) {
-        v[m] = v1[m];
-        mm[m] = m1[m];
-        v1[m] = vn[m];
-        m1[m] = mn[m];
-      } else {
-        v[m] = vn[m];
-        mm[m] = mn[m];
-      }
-    }
-  }
-  const int out_idx = tile * n_cg + cg;
-  // rows: sum over the 32 columns (lanes) of the warp, fixed butterfly
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    float xr = rre[m].s, xi = rim[m].s;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      xr += __shfl_xor_sync(0xffffffffu, xr, o);
-      xi += __shfl_xor_sync(0xffffffffu, xi, o);
-    }
-    if (tx == 0) part_row[(int64_t)out_idx * kCT + ty + 8 * m] = make_float2(xr, xi);
+  Kahan loss, rre, rim, cre, cim;
+  float rden = 0.f, cden = 0.f;
+  for (int nu = cg + n_cg * w; nu < C; nu += n_cg * kWarps) {
+    const TileSums t = tile_channel<DEN>(V + (int64_t)nu * B, M + (int64_t)nu * B, sgi, gj, I, j,
+                                         N, lane);
+    loss.add(t.loss);
+    rre.add(t.rre);
+    rim.add(t.rim);
+    cre.add(t.cre);
+    cim.add(t.cim);
     if constexpr (DEN) {
-      float d = rden[m];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (tx == 0) part_rden[(int64_t)out_idx * kCT + ty + 8 * m] = d;
+      rden += t.rden;
+      cden += t.cden;
     }
   }
-  // columns: sum over the 8 warps in a fixed order
-  scol[ty][tx] = make_float2(cre.s, cim.s);
-  if constexpr (DEN) scden[ty][tx] = cden;
+  const int row = tile_row_of_lane(lane);
+  srow[w][row] = make_float2(rre.s, rim.s);
+  scol[w][lane] = make_float2(cre.s, cim.s);
+  if constexpr (DEN) {
+    srden[w][row] = rden;
+    scden[w][lane] = cden;
+  }
   float l = loss.s;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if (tx == 0) sloss[ty] = l;
+  if (lane == 0) sloss[w] = l;
   __syncthreads();
-  if (ty == 0) {
-    float2 acc = scol[0][tx];
+  const int out_idx = tile * n_cg + cg;
+  if (w == 0) {
+    float2 ar = srow[0][lane], ac = scol[0][lane];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) {
-      acc.x += scol[w][tx].x;
-      acc.y += scol[w][tx].y;
+    for (int k = 1; k < kWarps; ++k) {
+      ar.x += srow[k][lane].x;
+      ar.y += srow[k][lane].y;
+      ac.x += scol[k][lane].x;
+      ac.y += scol[k][lane].y;
     }
-    part_col[(int64_t)out_idx * kCT + tx] = acc;
+    part_row[(int64_t)out_idx * kCT + lane] = ar;
+    part_col[(int64_t)out_idx * kCT + lane] = ac;
     if constexpr (DEN) {
-      float d = scden[0][tx];
+      float dr = srden[0][lane], dc = scden[0][lane];
 #pragma unroll
-      for (int w = 1; w < 8; ++w) d += scden[w][tx];
-      part_cden[(int64_t)out_idx * kCT + tx] = d;
+      for (int k = 1; k < kWarps; ++k) {
+        dr += srden[k][lane];
+        dc += scden[k][lane];
+      }
+      part_rden[(int64_t)out_idx * kCT + lane] = dr;
+      part_cden[(int64_t)out_idx * kCT + lane] = dc;
     }
-  }
-  if (threadIdx.x == 0) {
-    float s = 0.f;
-    for (int w = 0; w < kCalThreads / 32; ++w) s += sloss[w];
-    part_loss[out_idx] = s;
+    if (lane == 0) {
+      float t = 0.f;
+      for (int k = 0; k < kWarps; ++k) t += sloss[k];
+      part_loss[out_idx] = t;
+    }
   }
 }
 
@@ -294,38 +330,9 @@ __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
 // ---- per-channel gains ----------------------------------------------------------
 // g_k(nu), stored [C][N]: the channels decouple, so every (tile, channel) is a
 // reduction of its own and nothing is carried across channels.  One warp owns
-// one 32x32 tile of one channel: lane = column j = J*32 + lane, rows
-// i = I*32 + r taken in four groups of eight.  Column sums (to input j) stay in
-// the lane.  The eight row values of a group (to inputs i) are reduce-scattered
-// across the warp -- a butterfly over lane bits 4, 3, 2 that halves the values
-// each lane carries, then a sum over bits 1, 0 -- after which lanes 4s..4s+3
-// all hold the sum of row s of the group; lane 4s + t keeps group t's value,
-// so at the end lane 4s + t holds row 8t + s.  Eight warps of a CTA take eight
-// consecutive channels of the same tile.  Entries outside the stored triangle
-// load V = M = 0, whose residual and contributions are exactly 0.
-
-// a[0..7] (one value per row of the group) -> the full-warp sum of value
-// (lane >> 2) & 7, fixed order.
-__device__ __forceinline__ float reduce_scatter8(float (&a)[8], int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float send = b4 ? a[k] : a[k + 4];
-    const float keep = b4 ? a[k + 4] : a[k];
-    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float send = b3 ? a[k] : a[k + 2];
-    const float keep = b3 ? a[k + 2] : a[k];
-    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  const float send = b2 ? a[0] : a[1];
-  float x = (b2 ? a[1] : a[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
-  x += __shfl_xor_sync(0xffffffffu, x, 2);
-  x += __shfl_xor_sync(0xffffffffu, x, 1);
-  return x;
-}
+// one 32x32 tile of one channel (tile_channel) and writes that channel's row
+// and column sums; the eight warps of a CTA take eight consecutive channels of
+// the same tile.
 
 // grid: (tiles, ceil(C / 8)).  Partial sums per (tile, channel):
 // part_row / part_col [tile][C][32], DEN: part_rden / part_cden likewise;
@@ -346,65 +353,21 @@ __global__ void __launch_bounds__(kCalThreads, 3) calib_chan_tile_kernel(
   if (nu < C) {
     const int64_t B = (int64_t)N * (N + 1) / 2;
     const float2 *gn = g + (int64_t)nu * N;
-    const float2 zero = make_float2(0.f, 0.f);
     const int j = J * kCT + lane, il = I * kCT + lane;
-    const float2 gj = j < N ? gn[j] : zero;
-    sgi[w][lane] = il < N ? gn[il] : zero;
+    const float2 gj = j < N ? gn[j] : make_float2(0.f, 0.f);
+    sgi[w][lane] = il < N ? gn[il] : make_float2(0.f, 0.f);
     __syncwarp();
-    const float gj2 = gj.x * gj.x + gj.y * gj.y;
-    const float2 *Vn = V + (int64_t)nu * B, *Mn = M + (int64_t)nu * B;
-    float cre = 0.f, cim = 0.f, cden = 0.f, rre = 0.f, rim = 0.f, rden = 0.f;
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      float2 v[8], m[8];
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const int i = I * kCT + 8 * q + s;
-        const bool ok = i < N && j < i;
-        const int64_t b = (int64_t)i * (i + 1) / 2 + j;
-        v[s] = ok ? __ldcs(Vn + b) : zero;
-        m[s] = ok ? __ldcs(Mn + b) : zero;
-      }
-      float ar[8], ai[8], ad[8];
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const float2 gi = sgi[w][8 * q + s];
-        const float Gr = gi.x * gj.x + gi.y * gj.y;  // g_i conj(g_j)
-        const float Gi = gi.y * gj.x - gi.x * gj.y;
-        const float Rr = Gr * m[s].x - Gi * m[s].y - v[s].x;  // R = G M - V
-        const float Ri = Gr * m[s].y + Gi * m[s].x - v[s].y;
-        lsum += Rr * Rr + Ri * Ri;
-        const float Pr = Rr * gj.x - Ri * gj.y, Pi = Rr * gj.y + Ri * gj.x;  // R g_j
-        ar[s] = Pr * m[s].x + Pi * m[s].y;                                     // to row i
-        ai[s] = Pi * m[s].x - Pr * m[s].y;
-        const float Qr = Rr * gi.x + Ri * gi.y, Qi = Rr * gi.y - Ri * gi.x;  // conj(R) g_i
-        cre += Qr * m[s].x - Qi * m[s].y;                                      // to column j
-        cim += Qr * m[s].y + Qi * m[s].x;
-        if constexpr (DEN) {
-          const float m2 = m[s].x * m[s].x + m[s].y * m[s].y;
-          ad[s] = gj2 * m2;
-          cden += (gi.x * gi.x + gi.y * gi.y) * m2;
-        }
-      }
-      const float xr = reduce_scatter8(ar, lane);
-      const float xi = reduce_scatter8(ai, lane);
-      if ((lane & 3) == q) {
-        rre = xr;
-        rim = xi;
-      }
-      if constexpr (DEN) {
-        const float xd = reduce_scatter8(ad, lane);
-        if ((lane & 3) == q) rden = xd;
-      }
-    }
+    const TileSums t = tile_channel<DEN>(V + (int64_t)nu * B, M + (int64_t)nu * B, sgi[w], gj, I,
+                                         j, N, lane);
     const int64_t base = ((int64_t)tile * C + nu) * kCT;
-    const int row = 8 * (lane & 3) + ((lane >> 2) & 7);
-    part_row[base + row] = make_float2(rre, rim);
-    part_col[base + lane] = make_float2(cre, cim);
+    const int row = tile_row_of_lane(lane);
+    part_row[base + row] = make_float2(t.rre, t.rim);
+    part_col[base + lane] = make_float2(t.cre, t.cim);
     if constexpr (DEN) {
-      part_rden[base + row] = rden;
-      part_cden[base + lane] = cden;
+      part_rden[base + row] = t.rden;
+      part_cden[base + lane] = t.cden;
     }
+    lsum = t.loss;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
   }
