@@ -239,6 +239,100 @@ def calib_chan_solve(V, M, G0, n_iter: int, n_threads: int | None = None):
     return G, np.array(losses)
 
 
+# ---- full 2x2 Jones matrices per tile ---------------------------------------
+# Inputs 2a and 2a + 1 are the two polarisations of tile a.  With one 2x2
+# complex Jones matrix J_a per tile (frequency independent), the measurement
+# of tile pair a > b is the 2x2 block V_ab[p][q] = V_{2a+p, 2b+q} (all four
+# entries in the stored lower triangle), modelled as J_a M_ab J_b^H:
+#     R_ab = J_a M_ab J_b^H - V_ab,   L = sum_nu sum_{a>b} ||R_ab||_F^2
+# (blocks of a tile with itself, which hold the autocorrelations, are left
+# out).  Gradient (2 dL/d conj(J_a), the PyTorch convention):
+#     grad_a = 2 [ sum_{b<a} R_ab J_b M_ab^H + sum_{c>a} R_ca^H J_c M_ca ].
+# Alternating least squares: with the other matrices fixed, L is a linear
+# least-squares problem in J_a, sum_k ||J_a B_k - W_k||^2 with
+# (B, W) = (M_ab J_b^H, V_ab) for b < a and (M_ca^H J_c^H, V_ca^H) for c > a,
+# minimised by H_a = (sum W B^H)(sum B B^H)^-1 (H_a = J_a where sum B B^H is
+# singular).  J, gradients and targets are complex [n_tiles, 2, 2].
+def _jones_blocks(n_tiles):
+    """(a, b, idx): tile pairs a > b and the baseline index of block entry (p, q)."""
+    a, b = np.tril_indices(n_tiles, -1)
+    i = 2 * a[:, None, None] + np.arange(2)[None, :, None]
+    j = 2 * b[:, None, None] + np.arange(2)[None, None, :]
+    return a, b, i * (i + 1) // 2 + j
+
+
+def _jones_args(V, M, J):
+    V = np.asarray(V, np.complex128)
+    M = np.asarray(M, np.complex128)
+    J = np.ascontiguousarray(J, np.complex128)
+    n_tiles = J.shape[0]
+    N = 2 * n_tiles
+    assert J.shape == (n_tiles, 2, 2) and V.shape[1] == N * (N + 1) // 2 and M.shape == V.shape
+    return V, M, J
+
+
+def _herm(X):
+    return np.conj(np.swapaxes(X, -1, -2))
+
+
+def calib_jones_loss(V, M, J) -> float:
+    """FP64 loss of per-tile Jones matrices J [n_tiles, 2, 2]."""
+    V, M, J = _jones_args(V, M, J)
+    a, b, idx = _jones_blocks(J.shape[0])
+    L = 0.0
+    for c in range(V.shape[0]):
+        R = J[a] @ M[c][idx] @ _herm(J[b]) - V[c][idx]
+        L += float(np.sum(np.abs(R) ** 2))
+    return L
+
+
+def calib_jones_grad(V, M, J) -> np.ndarray:
+    """FP64 gradient 2 dL/d conj(J), complex [n_tiles, 2, 2]."""
+    V, M, J = _jones_args(V, M, J)
+    a, b, idx = _jones_blocks(J.shape[0])
+    G = np.zeros_like(J)
+    for c in range(V.shape[0]):
+        Mb = M[c][idx]
+        R = J[a] @ Mb @ _herm(J[b]) - V[c][idx]
+        np.add.at(G, a, R @ J[b] @ _herm(Mb))
+        np.add.at(G, b, _herm(R) @ J[a] @ Mb)
+    return 2.0 * G
+
+
+def calib_jones_als_target(V, M, J) -> np.ndarray:
+    """FP64 alternating least-squares target H, complex [n_tiles, 2, 2]."""
+    V, M, J = _jones_args(V, M, J)
+    a, b, idx = _jones_blocks(J.shape[0])
+    num = np.zeros_like(J)
+    den = np.zeros_like(J)
+    for c in range(V.shape[0]):
+        Mb, Vb = M[c][idx], V[c][idx]
+        Bl = Mb @ _herm(J[b])            # J_a B - V_ab, for tile a
+        Bh = _herm(Mb) @ _herm(J[a])     # J_b B - V_ab^H, for tile b
+        np.add.at(num, a, Vb @ _herm(Bl))
+        np.add.at(den, a, Bl @ _herm(Bl))
+        np.add.at(num, b, _herm(Vb) @ _herm(Bh))
+        np.add.at(den, b, Bh @ _herm(Bh))
+    H = J.copy()
+    for t in range(J.shape[0]):
+        if abs(np.linalg.det(den[t])) > 0.0:
+            H[t] = num[t] @ np.linalg.inv(den[t])
+    return H
+
+
+def calib_jones_solve(V, M, J0, n_iter: int):
+    """FP64 Jones solve: the sweeps of ``calib_solve`` (plain target on odd
+    sweeps, average with the previous matrices on even ones) with the Jones
+    target.  Returns (J, losses), losses[t] the loss entering sweep t + 1."""
+    J = np.array(J0, np.complex128)
+    losses = []
+    for t in range(1, n_iter + 1):
+        losses.append(calib_jones_loss(V, M, J))
+        H = calib_jones_als_target(V, M, J)
+        J = H if t % 2 == 1 else 0.5 * (J + H)
+    return J, np.array(losses)
+
+
 def _grid_args(tile_xy, vis):
     tile_xy = np.ascontiguousarray(tile_xy, np.float64)
     vis = np.ascontiguousarray(vis, np.int32)

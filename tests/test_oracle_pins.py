@@ -459,6 +459,137 @@ def test_calib_chan_solve_recovers_channel_dependent_gains():
 
 
 # ---------------------------------------------------------------------------
+# full 2x2 Jones matrices per tile
+# ---------------------------------------------------------------------------
+def rand_jones(rng, n_tiles, leak=0.2):
+    d = rng.uniform(0.8, 1.2, (n_tiles, 2)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (n_tiles, 2)))
+    J = np.zeros((n_tiles, 2, 2), complex)
+    J[:, 0, 0], J[:, 1, 1] = d[:, 0], d[:, 1]
+    J[:, 0, 1] = leak * (rng.standard_normal(n_tiles) + 1j * rng.standard_normal(n_tiles))
+    J[:, 1, 0] = leak * (rng.standard_normal(n_tiles) + 1j * rng.standard_normal(n_tiles))
+    return J
+
+
+def test_jones_golden_two_tiles():
+    """Two tiles, one channel, M_10 = I, V = 0, J_0 = I, J_1 = [[1, 1], [0, 1]]
+    (leakage), by hand: R = J_1, L = ||J_1||^2 = 3, grad_1 = 2 R J_0 M^H =
+    2 J_1, grad_0 = 2 R^H J_1 M = 2 J_1^H J_1 = [[2, 2], [2, 4]]."""
+    B = 4 * 5 // 2
+    V = np.zeros((1, B), complex)
+    M = np.zeros((1, B), complex)
+    M[0, oracle.baseline_index(2, 0)] = 1.0
+    M[0, oracle.baseline_index(3, 1)] = 1.0
+    J = np.array([np.eye(2), [[1.0, 1.0], [0.0, 1.0]]], complex)
+    assert oracle.calib_jones_loss(V, M, J) == pytest.approx(3.0, abs=1e-15)
+    np.testing.assert_allclose(oracle.calib_jones_grad(V, M, J),
+                               [[[2, 2], [2, 4]], [[2, 2], [0, 2]]], atol=1e-14)
+
+
+def test_jones_against_autograd():
+    """Loss and gradient pinned by torch autograd on a complex128 loss over
+    the full N x N matrices cut into 2x2 tile blocks."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(41)
+    n_tiles, C = 5, 3
+    N = 2 * n_tiles
+    V, M, _ = rand_cal(rng, N, C)
+    J = rand_jones(rng, n_tiles)
+    Vf, Mf = np.zeros((C, N, N), complex), np.zeros((C, N, N), complex)
+    ii, jj = np.tril_indices(N)
+    Vf[:, ii, jj] = V
+    Mf[:, ii, jj] = M
+    Jt = torch.tensor(J, requires_grad=True)
+    # block-diagonal N x N Jones: Jfull[2a+p, 2a+r] = J_a[p, r]
+    Jfull = torch.block_diag(*[Jt[t] for t in range(n_tiles)])
+    R = Jfull[None] @ torch.tensor(Mf) @ torch.conj(Jfull).T[None] - torch.tensor(Vf)
+    tile = np.arange(N) // 2
+    mask = torch.tensor(tile[:, None] > tile[None, :])
+    L = (R.abs() ** 2)[:, mask].sum()
+    L.backward()
+    assert oracle.calib_jones_loss(V, M, J) == pytest.approx(L.item(), rel=1e-12)
+    np.testing.assert_allclose(oracle.calib_jones_grad(V, M, J), Jt.grad.numpy(), rtol=1e-10,
+                               atol=1e-12)
+
+
+def test_jones_diagonal_is_per_input_gains():
+    """Diagonal J_a = diag(g_2a, g_2a+1) with the intra-tile pair zeroed in V
+    and M: the Jones loss is the per-input loss and the diagonal of the Jones
+    gradient is the per-input gradient."""
+    rng = np.random.default_rng(42)
+    n_tiles, C = 6, 4
+    N = 2 * n_tiles
+    V, M, g = rand_cal(rng, N, C)
+    for a in range(n_tiles):
+        V[:, oracle.baseline_index(2 * a + 1, 2 * a)] = 0
+        M[:, oracle.baseline_index(2 * a + 1, 2 * a)] = 0
+    J = np.zeros((n_tiles, 2, 2), complex)
+    J[:, 0, 0], J[:, 1, 1] = g[0::2], g[1::2]
+    assert oracle.calib_jones_loss(V, M, J) == pytest.approx(oracle.calib_loss(V, M, g), rel=1e-12)
+    Gj = oracle.calib_jones_grad(V, M, J)
+    Gi = oracle.calib_grad(V, M, g)
+    np.testing.assert_allclose(Gj[:, 0, 0], Gi[0::2], rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(Gj[:, 1, 1], Gi[1::2], rtol=1e-11, atol=1e-12)
+
+
+def test_jones_target_is_least_squares():
+    """H_a equals numpy's least-squares solution of X [B_1 B_2 ...] = [W_1 W_2 ...]
+    built from the full Hermitian matrices: B = M_ab J_b^H, W = V_ab over every
+    other tile b and channel (the full matrix holds both orientations)."""
+    rng = np.random.default_rng(43)
+    n_tiles, C = 5, 2
+    N = 2 * n_tiles
+    V, M, _ = rand_cal(rng, N, C)
+    J = rand_jones(rng, n_tiles)
+    H = oracle.calib_jones_als_target(V, M, J)
+    Vf, Mf = full_hermitian(V, N), full_hermitian(M, N)
+    for a in range(n_tiles):
+        Bs, Ws = [], []
+        for c in range(C):
+            for b in range(n_tiles):
+                if b == a:
+                    continue
+                Mab = Mf[c, 2 * a:2 * a + 2, 2 * b:2 * b + 2]
+                Bs.append(Mab @ np.conj(J[b]).T)
+                Ws.append(Vf[c, 2 * a:2 * a + 2, 2 * b:2 * b + 2])
+        Bc, Wc = np.hstack(Bs), np.hstack(Ws)
+        X = np.linalg.lstsq(Bc.T, Wc.T, rcond=None)[0].T
+        np.testing.assert_allclose(H[a], X, rtol=1e-11, atol=1e-12)
+
+
+def test_jones_target_zeroes_its_gradient_block():
+    rng = np.random.default_rng(44)
+    n_tiles, C = 6, 3
+    V, M, _ = rand_cal(rng, 2 * n_tiles, C)
+    J = rand_jones(rng, n_tiles)
+    H = oracle.calib_jones_als_target(V, M, J)
+    scale = np.abs(oracle.calib_jones_grad(V, M, J)).max()
+    for a in range(n_tiles):
+        Ja = J.copy()
+        Ja[a] = H[a]
+        assert np.abs(oracle.calib_jones_grad(V, M, Ja)[a]).max() <= 1e-11 * scale
+
+
+def test_jones_solve_recovers_leaky_jones():
+    """Noise-free data from Jones matrices with leakage: the solve recovers
+    them up to one global phase (the only freedom the loss leaves for a
+    generic model), which per-input gains cannot fit."""
+    rng = np.random.default_rng(45)
+    n_tiles, C = 7, 3
+    N = 2 * n_tiles
+    _, M, g = rand_cal(rng, N, C)
+    J_true = rand_jones(rng, n_tiles)
+    a, b, idx = oracle._jones_blocks(n_tiles)
+    V = np.zeros_like(M)
+    for c in range(C):
+        V[c][idx] = J_true[a] @ M[c][idx] @ np.conj(np.swapaxes(J_true[b], -1, -2))
+    J0 = J_true + 0.1 * (rng.standard_normal(J_true.shape) + 1j * rng.standard_normal(J_true.shape))
+    J, losses = oracle.calib_jones_solve(V, M, J0, 80)
+    ph = np.vdot(J.ravel(), J_true.ravel())
+    assert np.abs(J * ph / abs(ph) - J_true).max() <= 1e-8 * np.abs(J_true).max()
+    assert losses[-1] <= 1e-14 * losses[0]
+
+
+# ---------------------------------------------------------------------------
 # gridding
 # ---------------------------------------------------------------------------
 C_LIGHT = 299792458.0
