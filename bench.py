@@ -760,6 +760,45 @@ def run_calib(args):
                   "loss_start": float(hist_c[0]), "loss_after": float(loss_c_final),
                   "hbm_frac": bytes_c / (ms_cs / 1e3) / 1e9 / float(peaks["hbm_gbs"])},
         "gpu_launches": 2 * args.steps + 2 * n_sweeps}
+    # full 2x2 Jones matrices per tile (leakage terms), from diagonal gains plus 5 % leakage
+    n_t = N // 2
+    Jm = torch.zeros((n_t, 2, 2), dtype=torch.complex64, device=dev)
+    Jm[:, 0, 0], Jm[:, 1, 1] = g[0::2], g[1::2]
+    Jm[:, 0, 1] = torch.from_numpy((0.05 * (rng.standard_normal(n_t) + 1j * rng.standard_normal(n_t))).astype(np.complex64)).to(dev)
+    Jm[:, 1, 0] = torch.from_numpy((0.05 * (rng.standard_normal(n_t) + 1j * rng.standard_normal(n_t))).astype(np.complex64)).to(dev)
+    ws_j = torch.empty(int(mw.lib().mwax_calib_jones_workspace_bytes(N, C)), dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        mw.calib_jones_loss_grad(V, M, Jm, ws_j)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        loss_j, _ = mw.calib_jones_loss_grad(V, M, Jm, ws_j)
+    b.record(stream)
+    b.synchronize()
+    ms_j = a.elapsed_time(b) / args.steps
+    terms_j = 4 * (n_t * (n_t - 1) // 2) * C  # baseline-channel terms inside cross-tile blocks
+    bytes_j = 16 * terms_j + 2 * 32 * n_t
+    ach_j = bytes_j / (ms_j / 1e3) / 1e9
+    mw.calib_jones_solve(V, M, Jm, 1, ws_j)  # warm-up
+    torch.cuda.synchronize()
+    a.record(stream)
+    J_sol, hist_j = mw.calib_jones_solve(V, M, Jm, n_sweeps, ws_j)
+    b.record(stream)
+    b.synchronize()
+    ms_js = a.elapsed_time(b) / n_sweeps
+    loss_j_final, _ = mw.calib_jones_loss_grad(V, M, J_sol, ws_j, want_grad=False)
+    line["jones"] = {
+        "ms_per_step": ms_j, "value": terms_j / (ms_j / 1e3) / 1e9, "unit": "Gterms/s",
+        "loss": float(loss_j),
+        "roofline": {"bound": "hbm", "achieved": ach_j, "peak": float(peaks["hbm_gbs"]),
+                     "unit": "GB/s", "frac": ach_j / float(peaks["hbm_gbs"]), "traffic": None,
+                     "kernel": "calib_jones_tile_kernel + calib_jones_gather_kernel (one step)",
+                     "peak_source": src},
+        "solve": {"sweeps": n_sweeps, "ms_per_sweep": ms_js,
+                  "value": terms_j / (ms_js / 1e3) / 1e9, "unit": "Gterms/s per sweep",
+                  "loss_start": float(hist_j[0]), "loss_after": float(loss_j_final),
+                  "hbm_frac": bytes_j / (ms_js / 1e3) / 1e9 / float(peaks["hbm_gbs"])},
+        "gpu_launches": 2 * args.steps + 2 * n_sweeps}
     if not args.no_cpu:
         sub = list(range(0, C, C // 8))[:8]
         V64 = V[sub].cpu().numpy().astype(np.complex128)
@@ -782,6 +821,14 @@ def run_calib(args):
         oracle.calib_chan_loss(V64, M64, G64)
         oracle.calib_chan_grad(V64, M64, G64)
         dt = time.perf_counter() - t0
+        J64 = Jm.cpu().numpy().astype(np.complex128)
+        t0 = time.perf_counter()
+        oracle.calib_jones_loss(V64, M64, J64)
+        oracle.calib_jones_grad(V64, M64, J64)
+        dt = time.perf_counter() - t0
+        line["jones"]["cpu_baseline"] = {
+            "value": 4 * (n_t * (n_t - 1) // 2) * len(sub) / dt / 1e9, "unit": "Gterms/s",
+            "cores": 1, "kind": "oracle", "sample": f"{len(sub)} of {C} channels (FP64 numpy loss + gradient)"}
         line["per_channel_gains"]["cpu_baseline"] = {
             "value": B * len(sub) / dt / 1e9, "unit": "Gterms/s", "cores": oracle.threads(),
             "kind": "oracle", "sample": f"{len(sub)} of {C} channels (FP64 loss + gradient)"}

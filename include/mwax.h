@@ -347,6 +347,37 @@ mwax_status mwax_calib_chan_solve(const float *V, const float *M, float *G, int 
                                   int n_chan, int n_iter, void *workspace, float *loss_hist,
                                   cudaStream_t stream);
 
+/* ---- full 2x2 Jones matrices per tile (FP32) -------------------------------
+ * Inputs 2a and 2a + 1 are the two polarisations of tile a.  With one 2x2
+ * complex Jones matrix J_a per tile (frequency independent) the tile pair
+ * a > b is the block V_ab[p][q] = V_{2a+p, 2b+q}, modelled as J_a M_ab J_b^H:
+ *     L(J) = sum_nu sum_{a>b} ||J_a M_ab J_b^H - V_ab||_F^2
+ * (a tile's block with itself, which holds autocorrelations, is left out).
+ * Per-input gains are the diagonal case; the off-diagonal terms model
+ * polarisation leakage.
+ *   J:         device float [n_inputs / 2][2][2][2] (row-major 2x2, re/im).
+ *   grad:      same layout, grad_a = 2 dL/d conj(J_a).
+ *   workspace: device, >= mwax_calib_jones_workspace_bytes (10 MB at 1024
+ *              inputs; the same for the solve).
+ * mwax_calib_jones_loss_grad: loss and/or grad (one may be NULL), one pass.
+ * mwax_calib_jones_solve: n_iter alternating least-squares sweeps: with the
+ *   other matrices fixed, J_a's minimiser is H_a = (sum W B^H)(sum B B^H)^-1
+ *   over (B, W) = (M_ab J_b^H, V_ab), b < a, and (M_ca^H J_c^H, V_ca^H),
+ *   c > a, all channels; computed as H_a = J_a - (grad_a / 2) D_a^-1 with
+ *   D_a = sum B B^H, J_a kept where det D_a <= 0.  J = H on odd sweeps,
+ *   (J + H) / 2 on even ones; J updated in place; loss_hist as in
+ *   mwax_calib_solve.
+ * V, M as in mwax_calib_loss.  Asynchronous on `stream`; deterministic.
+ * n_inputs even in [2, 65536], n_chan >= 1; INVALID_ARG otherwise or for
+ * host/null pointers; the workspace-size call returns -1 for such shapes. */
+int64_t mwax_calib_jones_workspace_bytes(int n_inputs, int n_chan);
+mwax_status mwax_calib_jones_loss_grad(const float *V, const float *M, const float *J,
+                                       int n_inputs, int n_chan, void *workspace, float *loss,
+                                       float *grad, cudaStream_t stream);
+mwax_status mwax_calib_jones_solve(const float *V, const float *M, float *J, int n_inputs,
+                                   int n_chan, int n_iter, void *workspace, float *loss_hist,
+                                   cudaStream_t stream);
+
 /* ---- gridding (FP32) ------------------------------------------------------
  * Paper Sec. 2.1: the visibilities are convolved onto a regular grid so an
  * FFT can form the images; Sec. 3.2: each GPU thread gathers the values of

@@ -101,6 +101,9 @@ SIGNATURES = {
     "mwax_calib_chan_solve_workspace_bytes": (_I64, [_I, _I]),
     "mwax_calib_chan_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "mwax_calib_chan_solve": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
+    "mwax_calib_jones_workspace_bytes": (_I64, [_I, _I]),
+    "mwax_calib_jones_loss_grad": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "mwax_calib_jones_solve": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P]),
     "mwax_grid_plan": (_I, [_P, _P, _I, _I, ctypes.c_double, ctypes.c_double, _I, ctypes.c_double,
                             _I, ctypes.c_double, _P]),
     "mwax_grid": (_I, [_P, _P, _P]),
@@ -582,6 +585,60 @@ def calib_chan_solve(V, M, G0, n_iter: int, workspace=None, loss_history: bool =
                                        hist.data_ptr() if hist is not None else None,
                                        _stream_handle()), "mwax_calib_chan_solve")
     return torch.view_as_complex(G), (hist[:n_iter] if hist is not None else None)
+
+
+def _jones_shapes(Vr, Mr, Jr):
+    if Jr.dim() != 4 or Jr.shape[1:3] != (2, 2):
+        raise ValueError("Jones matrices must be [n_tiles, 2, 2]")
+    n = 2 * Jr.shape[0]
+    c = Vr.shape[0]
+    if Vr.shape != (c, n * (n + 1) // 2, 2) or Mr.shape != Vr.shape:
+        raise ValueError("V, M must be [n_chan, N(N+1)/2] for N = 2 n_tiles")
+    return n, c
+
+
+def _jones_workspace(n, c, device):
+    torch = _torch()
+    nb = int(lib().mwax_calib_jones_workspace_bytes(n, c))
+    if nb < 0:
+        raise ValueError("invalid calibration shape")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def calib_jones_loss_grad(V, M, J, workspace=None, want_loss=True, want_grad=True):
+    """Per-tile 2x2 Jones matrices: (loss float32 scalar tensor or None, grad
+    complex64 [n_tiles, 2, 2] or None).  V, M: complex64 [n_chan, N(N+1)/2]
+    with N = 2 n_tiles; J: complex64 [n_tiles, 2, 2]."""
+    torch = _torch()
+    Vr, Mr, Jr = _f32_pairs(V), _f32_pairs(M), _f32_pairs(J)
+    n, c = _jones_shapes(Vr, Mr, Jr)
+    ws = workspace if workspace is not None else _jones_workspace(n, c, V.device)
+    loss = torch.empty((), dtype=torch.float32, device=V.device) if want_loss else None
+    grad = torch.empty(Jr.shape, dtype=torch.float32, device=V.device) if want_grad else None
+    _check(lib().mwax_calib_jones_loss_grad(Vr.data_ptr(), Mr.data_ptr(), Jr.data_ptr(), n, c,
+                                            ws.data_ptr(), loss.data_ptr() if want_loss else None,
+                                            grad.data_ptr() if want_grad else None,
+                                            _stream_handle()), "mwax_calib_jones_loss_grad")
+    return loss, (torch.view_as_complex(grad) if want_grad else None)
+
+
+def calib_jones_solve(V, M, J0, n_iter: int, workspace=None, loss_history: bool = True):
+    """Jones solve: ``n_iter`` alternating least-squares sweeps from ``J0``
+    (complex64 [n_tiles, 2, 2], not modified).  Returns (J, losses float32
+    [n_iter] or None)."""
+    torch = _torch()
+    Vr, Mr = _f32_pairs(V), _f32_pairs(M)
+    Jr = _f32_pairs(J0).clone()
+    n, c = _jones_shapes(Vr, Mr, Jr)
+    if n_iter < 0:
+        raise ValueError("n_iter must be >= 0")
+    ws = workspace if workspace is not None else _jones_workspace(n, c, V.device)
+    hist = (torch.empty(max(n_iter, 1), dtype=torch.float32, device=V.device)
+            if loss_history else None)
+    _check(lib().mwax_calib_jones_solve(Vr.data_ptr(), Mr.data_ptr(), Jr.data_ptr(), n, c, n_iter,
+                                        ws.data_ptr(), hist.data_ptr() if hist is not None else None,
+                                        _stream_handle()), "mwax_calib_jones_solve")
+    return torch.view_as_complex(Jr), (hist[:n_iter] if hist is not None else None)
 
 
 def _make_calib_function():

@@ -355,3 +355,138 @@ def test_calib_chan_rejects_bad_shapes(mw):
     # host pointers are refused before any launch
     assert mw.lib().mwax_calib_chan_loss_grad(V.ctypes.data, M.ctypes.data, G.ctypes.data, 20, 3,
                                               ws.data_ptr(), ws.data_ptr(), None, None) != 0
+
+
+# ---------------------------------------------------------------------------
+# full 2x2 Jones matrices per tile
+# ---------------------------------------------------------------------------
+def rand_jones(rng, n_tiles, leak=0.2):
+    d = rng.uniform(0.8, 1.2, (n_tiles, 2)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (n_tiles, 2)))
+    J = np.zeros((n_tiles, 2, 2), complex)
+    J[:, 0, 0], J[:, 1, 1] = d[:, 0], d[:, 1]
+    J[:, 0, 1] = leak * (rng.standard_normal(n_tiles) + 1j * rng.standard_normal(n_tiles))
+    J[:, 1, 0] = leak * (rng.standard_normal(n_tiles) + 1j * rng.standard_normal(n_tiles))
+    return J
+
+
+def problem_jones(n_tiles, C, seed, noise=0.05, err=0.05):
+    """Point-source-like model, data from leaky Jones matrices plus noise, and
+    a perturbed estimate."""
+    N = 2 * n_tiles
+    _, M, _ = problem(N, C, seed, noise=0.0)
+    rng = np.random.default_rng(seed + 2000)
+    J_true = rand_jones(rng, n_tiles)
+    a, b, idx = oracle._jones_blocks(n_tiles)
+    Mc = M.astype(np.complex128)
+    V = rng.standard_normal(Mc.shape) + 1j * rng.standard_normal(Mc.shape)  # autos, intra-tile: ignored
+    V *= noise * np.abs(M).mean()
+    for c in range(C):
+        V[c][idx] += J_true[a] @ Mc[c][idx] @ np.conj(np.swapaxes(J_true[b], -1, -2))
+    J = J_true + err * (rng.standard_normal(J_true.shape) + 1j * rng.standard_normal(J_true.shape))
+    return (np.ascontiguousarray(V, np.complex64), M, np.ascontiguousarray(J, np.complex64), J_true)
+
+
+def gpu_jones_loss_grad(mw, V, M, J):
+    import torch
+
+    loss, grad = mw.calib_jones_loss_grad(torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda(),
+                                          torch.from_numpy(J).cuda())
+    torch.cuda.synchronize()
+    return float(loss.item()), grad.cpu().numpy()
+
+
+def check_jones(V, M, J, loss, grad):
+    V64, M64, J64 = V.astype(np.complex128), M.astype(np.complex128), J.astype(np.complex128)
+    L64 = oracle.calib_jones_loss(V64, M64, J64)
+    G64 = oracle.calib_jones_grad(V64, M64, J64)
+    assert abs(loss - L64) <= 1e-5 * L64, (loss, L64)
+    assert np.abs(grad - G64).max() <= 1e-4 * np.abs(G64).max()
+
+
+@pytest.mark.parametrize("n_tiles,C", [(1, 2), (2, 1), (17, 3), (40, 5), (65, 9), (33, 25)])
+def test_calib_jones_small(mw, n_tiles, C):
+    """Ragged calibration tiles (tile counts not a multiple of 32), channel
+    counts above and below the 24 channel groups, one tile (no pairs)."""
+    V, M, J, _ = problem_jones(n_tiles, C, seed=400 + n_tiles + C)
+    loss, grad = gpu_jones_loss_grad(mw, V, M, J)
+    if n_tiles == 1:
+        assert loss == 0.0 and np.all(grad == 0)
+        return
+    check_jones(V, M, J, loss, grad)
+
+
+def test_calib_jones_deterministic(mw):
+    V, M, J, _ = problem_jones(50, 6, seed=8)
+    a = gpu_jones_loss_grad(mw, V, M, J)
+    b = gpu_jones_loss_grad(mw, V, M, J)
+    assert a[0] == b[0]
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_calib_jones_diagonal_matches_per_input_kernel(mw):
+    """Diagonal Jones with the intra-tile pairs zeroed: the loss and the
+    diagonal of the gradient equal the per-input kernel's (two kernels, the
+    same mathematics)."""
+    n_tiles, C = 45, 4
+    V, M, g = problem(2 * n_tiles, C, seed=13)
+    for a in range(n_tiles):
+        V[:, oracle.baseline_index(2 * a + 1, 2 * a)] = 0
+        M[:, oracle.baseline_index(2 * a + 1, 2 * a)] = 0
+    J = np.zeros((n_tiles, 2, 2), np.complex64)
+    J[:, 0, 0], J[:, 1, 1] = g[0::2], g[1::2]
+    lj, gj = gpu_jones_loss_grad(mw, V, M, J)
+    l1, g1 = gpu_loss_grad(mw, V, M, g)
+    assert abs(lj - l1) <= 1e-5 * l1
+    scale = np.abs(g1).max()
+    assert np.abs(gj[:, 0, 0] - g1[0::2]).max() <= 1e-4 * scale
+    assert np.abs(gj[:, 1, 1] - g1[1::2]).max() <= 1e-4 * scale
+
+
+def gpu_jones_solve(mw, V, M, J0, n_iter):
+    import torch
+
+    J, hist = mw.calib_jones_solve(torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda(),
+                                   torch.from_numpy(J0).cuda(), n_iter)
+    torch.cuda.synchronize()
+    return J.cpu().numpy(), hist.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_tiles,C,n_iter", [(2, 1, 1), (17, 3, 2), (40, 5, 5)])
+def test_calib_jones_solve_small(mw, n_tiles, C, n_iter):
+    V, M, J0, _ = problem_jones(n_tiles, C, seed=500 + n_tiles + C)
+    J, hist = gpu_jones_solve(mw, V, M, J0, n_iter)
+    J64, l64 = oracle.calib_jones_solve(V.astype(np.complex128), M.astype(np.complex128),
+                                        J0.astype(np.complex128), n_iter)
+    assert np.abs(J - J64).max() <= 1e-4 * np.abs(J64).max()
+    assert abs(hist[0] - l64[0]) <= 1e-5 * l64[0]
+    np.testing.assert_allclose(hist, l64, rtol=1e-4)
+
+
+def test_calib_jones_solve_recovers_leaky_jones(mw):
+    """Noise-free data: the Jones matrices come back to FP32 accuracy up to
+    one global phase."""
+    V, M, J0, J_true = problem_jones(32, 6, seed=22, noise=0.0, err=0.1)
+    J, hist = gpu_jones_solve(mw, V, M, J0, 60)
+    ph = np.vdot(J.ravel(), J_true.ravel())
+    err = np.abs(J * ph / abs(ph) - J_true).max() / np.abs(J_true).max()
+    assert err <= 2e-5, err
+    assert hist[-1] <= 1e-8 * hist[0]
+
+
+def test_calib_jones_full_size(mw):
+    """1024 inputs (512 tiles) x 96 channels against the FP64 oracle."""
+    V, M, g = big_problem(1024, 96, seed=16)
+    rng = np.random.default_rng(17)
+    J = rand_jones(rng, 512).astype(np.complex64)
+    loss, grad = gpu_jones_loss_grad(mw, V, M, J)
+    check_jones(V, M, J, loss, grad)
+
+
+def test_calib_jones_rejects_bad_shapes(mw):
+    import torch
+
+    V, M, J, _ = problem_jones(5, 2, seed=3)
+    Vd, Md = torch.from_numpy(V).cuda(), torch.from_numpy(M).cuda()
+    with pytest.raises(ValueError):
+        mw.calib_jones_loss_grad(Vd, Md, torch.from_numpy(J[:4]).cuda())
+    assert mw.lib().mwax_calib_jones_workspace_bytes(11, 2) == -1  # odd input count
