@@ -276,27 +276,21 @@ __global__ void __launch_bounds__(kCalThreads) calib_gather_kernel(
   __shared__ float sden[8][kCT];
   const int r = threadIdx.x & 31, l = threadIdx.x >> 5;
   Kahan ar, ai, ad;
-  // tiles (K, J), J <= K contribute row partials; tiles (I, K), I >= K column partials
-  int n = 0;
-  for (int Jt = 0; Jt <= K; ++Jt) {
-    const int tile = K * (K + 1) / 2 + Jt;
-    for (int cg = 0; cg < n_cg; ++cg, ++n) {
-      if ((n & 7) != l) continue;
-      const float2 v = part_row[((int64_t)tile * n_cg + cg) * kCT + r];
-      ar.add(v.x);
-      ai.add(v.y);
-      if constexpr (SOLVE) ad.add(part_rden[((int64_t)tile * n_cg + cg) * kCT + r]);
-    }
-  }
-  for (int It = K; It < n_blocks; ++It) {
-    const int tile = It * (It + 1) / 2 + K;
-    for (int cg = 0; cg < n_cg; ++cg, ++n) {
-      if ((n & 7) != l) continue;
-      const float2 v = part_col[((int64_t)tile * n_cg + cg) * kCT + r];
-      ar.add(v.x);
-      ai.add(v.y);
-      if constexpr (SOLVE) ad.add(part_cden[((int64_t)tile * n_cg + cg) * kCT + r]);
-    }
+  // contributions n = 0, 1, ...: the row partials of tiles (K, J <= K), then
+  // the column partials of tiles (I >= K, K), each over the channel groups;
+  // thread l takes n = l, l + 8, ...
+  const int n_row = (K + 1) * n_cg;
+  const int n_tot = n_row + (n_blocks - K) * n_cg;
+  for (int n = l; n < n_tot; n += 8) {
+    const bool is_row = n < n_row;
+    const int m = is_row ? n : n - n_row;
+    const int t = m / n_cg, cg = m - t * n_cg;
+    const int tile = is_row ? K * (K + 1) / 2 + t : (K + t) * (K + t + 1) / 2 + K;
+    const int64_t idx = ((int64_t)tile * n_cg + cg) * kCT + r;
+    const float2 v = is_row ? part_row[idx] : part_col[idx];
+    ar.add(v.x);
+    ai.add(v.y);
+    if constexpr (SOLVE) ad.add(is_row ? part_rden[idx] : part_cden[idx]);
   }
   sacc[l][r] = make_float2(ar.s, ai.s);
   if constexpr (SOLVE) sden[l][r] = ad.s;
