@@ -61,6 +61,10 @@ def test_plan_rejects_bad_jobs_before_touching_the_device(mwax_lib):
 
     assert plan(n_inputs=4, n_chan=1, n_time=66573, sample_bits=8) == 3  # OVERFLOW_BOUND
     assert plan(n_inputs=0, n_chan=1, n_time=10, sample_bits=8) == 1
+    # empty integrations and empty bands are rejected, not planned
+    assert plan(n_inputs=4, n_chan=0, n_time=10, sample_bits=8) == 1
+    assert plan(n_inputs=4, n_chan=1, n_time=0, sample_bits=4) == 1
+    assert plan(n_inputs=-2, n_chan=1, n_time=10, sample_bits=4) == 1
     assert plan(n_inputs=4, n_chan=1, n_time=10, sample_bits=6) == 1
     assert plan(n_inputs=4, n_chan=1, n_time=10, sample_bits=4, kind=1) == 4  # FP16 needs 8-bit
     assert L.mwax_plan(None, None, None) == 1
