@@ -142,3 +142,36 @@ def test_calib_workspace_sizes(mwax_lib):
         assert L.mwax_calib_chan_workspace_bytes(n, c) == -1
         assert L.mwax_calib_chan_solve_workspace_bytes(n, c) == -1
     assert L.mwax_calib_chan_workspace_bytes(2, 65535 * 8) > 0
+
+
+def test_plain_c_client_builds_and_runs(mwax_lib, tmp_path):
+    """The boundary is a C library: a plain C program compiled against
+    include/mwax.h (gcc, C11) links libmwax.so and gets the host-only answers
+    (baseline helpers, the int32 bound, a refused plan, the pair-mode work
+    list) without Python or torch."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    mw = mwax_lib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lib_dir = os.path.dirname(mw.LIB_PATH)
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    exe = str(tmp_path / "abi_client")
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    "-I", cuda_inc, os.path.join(root, "tests", "c_client", "abi_client.c"),
+                    "-L", lib_dir, "-lmwax", "-Wl,-rpath," + lib_dir, "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    got = dict(line.split(" ", 1) for line in out.strip().splitlines())
+    assert got["n_baselines_512"] == "131328"
+    assert got["n_baselines_1024"] == "524800"
+    assert got["baseline_index_5_3"] == "18"
+    assert got["baseline_pair_status"] == "0" and got["baseline_pair_18"] == "5 3"
+    assert got["max_n_time_8"] == "66572" and got["max_n_time_4"] == "21913098"
+    assert got["plan_overflow_status"] == "3"
+    assert got["plan_overflow_string"]
+    assert got["work_list_tile_pairs"] == str(2 * 36)
+    assert int(got["work_list_items"]) == 36  # 2 x 36 pairs, two per item
+    assert got["calib_jones_ws_odd"] == "-1"
