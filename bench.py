@@ -138,7 +138,10 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.proc = None
 
-    def start(self):
+    def start(self, first_sample_s: float = 3.0):
+        """Start sampling; wait (up to first_sample_s) for the first sample, so
+        that even a timed region shorter than the 200 ms period is bracketed
+        by a sample taken just before it."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
@@ -146,6 +149,12 @@ class Clocks:
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+            return
+        t_end = time.monotonic() + first_sample_s
+        while time.monotonic() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:

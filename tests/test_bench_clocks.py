@@ -1,0 +1,60 @@
+"""The bench's clock sampler (CPU, with a stand-in for nvidia-smi on PATH):
+it waits for a first sample before the timed region, takes the median SM
+clock, and reports every active throttle reason by name."""
+import os
+import stat
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+FAKE = """#!/bin/sh
+# prints one CSV sample every 0.2 s, as nvidia-smi -lms 200 does
+sleep 0.3
+i=0
+while true; do
+  if [ $i -lt 2 ]; then sm=2070; else sm=1800; fi
+  echo "0, $sm, 2070, 900.5, 0x4, Not Active, Not Active, Not Active, Active"
+  i=$((i+1))
+  sleep 0.2
+done
+"""
+
+
+def test_clock_sampler_waits_and_summarises(tmp_path, monkeypatch):
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text(FAKE)
+    exe.chmod(exe.stat().st_mode | stat.S_IEXEC)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    c = bench.Clocks(0)
+    t0 = time.monotonic()
+    c.start()
+    waited = time.monotonic() - t0
+    assert 0.2 <= waited < 3.0  # returned once the first sample was there
+    r = c.stop()  # a timed region far shorter than the sampling period
+    assert r is not None and r["samples"] >= 1
+    assert r["sm_max_mhz"] == 2070.0 and r["reasons"] == ["sw_power_cap"]
+    c = bench.Clocks(0)
+    c.start()
+    time.sleep(1.6)
+    r = c.stop()
+    assert r["samples"] >= 3
+    if r["samples"] >= 5:  # 2070, 2070, then 1800s: the median is 1800
+        assert r["sm_mhz"] == 1800.0
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    c = bench.Clocks(0)
+    c.start()
+    assert c.stop() is None
