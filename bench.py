@@ -933,15 +933,14 @@ def main():
         plan.correlate(vol, out)
     if plan.status() != 0:
         raise RuntimeError("device status not OK after warm-up")
-    torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
-
     clocks = Clocks(local)
+    clocks.start()  # waits for its first sample, so before the barrier
     plan.set_timing(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    clocks.start()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
         plan.correlate(vol, out)
