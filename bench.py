@@ -158,6 +158,8 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            self.f.close()
+            os.unlink(self.f.name)
             return None
         self.proc.terminate()
         try:
@@ -167,6 +169,7 @@ class Clocks:
         self.f.flush()
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
         os.unlink(self.f.name)
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]

@@ -56,5 +56,7 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     finally:
         sys.path.remove(ROOT)
     c = bench.Clocks(0)
+    name = c.f.name
     c.start()
     assert c.stop() is None
+    assert not os.path.exists(name)  # the sample file is removed either way
