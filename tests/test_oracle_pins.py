@@ -569,6 +569,30 @@ def test_jones_target_zeroes_its_gradient_block():
         assert np.abs(oracle.calib_jones_grad(V, M, Ja)[a]).max() <= 1e-11 * scale
 
 
+def test_jones_unitary_invariance_for_unpolarised_model():
+    """M_ab = m_ab I (an unpolarised model): J_a M J_b^H = m J_a J_b^H, so
+    replacing every J_a by J_a U for one unitary U leaves the loss unchanged
+    and turns the gradient into grad U (grad_a = 2 sum R J_b M^H ...).  Using
+    J^T or conj(J) where J^H belongs breaks both for a complex U."""
+    rng = np.random.default_rng(46)
+    n_tiles, C = 6, 3
+    N = 2 * n_tiles
+    B = N * (N + 1) // 2
+    V = rng.standard_normal((C, B)) + 1j * rng.standard_normal((C, B))
+    M = np.zeros((C, B), complex)
+    a, b, idx = oracle._jones_blocks(n_tiles)
+    m = rng.standard_normal((C, len(a))) + 1j * rng.standard_normal((C, len(a)))
+    for c in range(C):
+        M[c][idx[:, 0, 0]] = m[c]
+        M[c][idx[:, 1, 1]] = m[c]
+    J = rand_jones(rng, n_tiles)
+    Q, _ = np.linalg.qr(rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2)))
+    JU = J @ Q
+    assert oracle.calib_jones_loss(V, M, JU) == pytest.approx(oracle.calib_jones_loss(V, M, J), rel=1e-12)
+    np.testing.assert_allclose(oracle.calib_jones_grad(V, M, JU), oracle.calib_jones_grad(V, M, J) @ Q,
+                               rtol=1e-10, atol=1e-12)
+
+
 def test_jones_solve_recovers_leaky_jones():
     """Noise-free data from Jones matrices with leakage: the solve recovers
     them up to one global phase (the only freedom the loss leaves for a
