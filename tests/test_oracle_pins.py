@@ -424,6 +424,20 @@ def test_calib_chan_reduces_to_shared_gains():
                                oracle.calib_als_target(V[:1], M[:1], g), rtol=1e-13)
 
 
+def test_calib_chan_phase_per_channel():
+    """Each channel's loss sees only that channel's gains, up to a phase of
+    its own: G[c] -> G[c] e^{i th_c} with independent th_c leaves the loss
+    unchanged and rotates channel c's gradient by e^{i th_c}."""
+    rng = np.random.default_rng(35)
+    N, C = 7, 4
+    V, M, _ = rand_cal(rng, N, C)
+    G = rng.uniform(0.8, 1.2, (C, N)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (C, N)))
+    ph = np.exp(1j * rng.uniform(0, 2 * np.pi, C))[:, None]
+    assert oracle.calib_chan_loss(V, M, G * ph) == pytest.approx(oracle.calib_chan_loss(V, M, G), rel=1e-12)
+    np.testing.assert_allclose(oracle.calib_chan_grad(V, M, G * ph), oracle.calib_chan_grad(V, M, G) * ph,
+                               rtol=1e-10, atol=1e-12)
+
+
 def test_calib_chan_target_zeroes_its_gradient_component():
     rng = np.random.default_rng(33)
     N, C = 7, 3
