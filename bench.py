@@ -126,6 +126,28 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------
+def nvsmi_gpu_id(dev: int) -> str:
+    """The id nvidia-smi knows the CUDA device `dev` by.  nvidia-smi numbers
+    GPUs physically and ignores CUDA_VISIBLE_DEVICES, so a CUDA ordinal would
+    name another GPU whenever the visible set is not the first GPUs of the
+    machine: use the device's UUID, else the CUDA_VISIBLE_DEVICES entry."""
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            u = str(torch.cuda.get_device_properties(dev).uuid).strip()
+            if u:
+                return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+    if vis:
+        entries = [x.strip() for x in vis.split(",") if x.strip()]
+        if 0 <= dev < len(entries):
+            return entries[dev]
+    return str(dev)
+
+
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -135,6 +157,7 @@ class Clocks:
 
     def __init__(self, index: int):
         self.index = index
+        self.gpu_id = nvsmi_gpu_id(index)
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.proc = None
 
@@ -144,7 +167,7 @@ class Clocks:
         by a sample taken just before it."""
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):

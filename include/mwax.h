@@ -429,7 +429,8 @@ mwax_status mwax_grid_destroy(mwax_grid_plan_t plan);
  * (I, Q, U, V) = (B00 + B11, B00 - B11, B01 + B10, -i (B01 - B10)).
  * Pixels on or below the horizon are zero.
  *   inst:   device float [4][n][n][2] (XX, XY, YX, YY; re, im)
- *   stokes: device float [4][n][n][2] (I, Q, U, V), a different buffer
+ *   stokes: device float [4][n][n][2] (I, Q, U, V); the two ranges of
+ *           4 n^2 complex values must not overlap at all (INVALID_ARG)
  * Both 8-byte aligned; n even in [2, 65536], dl > 0; INVALID_ARG otherwise.
  * Asynchronous on `stream`. */
 mwax_status mwax_stokes(const float *inst, int n, double dl, double chi, float *stokes,
@@ -447,8 +448,12 @@ mwax_status mwax_stokes(const float *inst, int n, double dl, double chi, float *
  *   - Shapes whose mwax_calib_workspace_bytes(n_inputs, n_chan) exceeds the
  *     array are rejected with MWAX_ERR_INVALID_ARG before any launch
  *     (1024 inputs need about 3.3 MB, for any n_chan; up to about 1150 inputs fit).
- *   - The first call on each device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *   - Outside stream capture every call looks up the array's device address
+ *     with the current device (no allocation), so the call stays valid after
+ *     a cudaDeviceReset.  A call made while `stream` is being captured uses
+ *     the address from the device's last uncaptured call: make one call on
+ *     each device before capturing (a captured first call returns
+ *     MWAX_ERR_CUDA).
  *   - All calls on a device share the array: calls that overlap on the GPU
  *     (different streams without ordering between them) race and give wrong
  *     results.  The array keeps the last call's contents; each call writes

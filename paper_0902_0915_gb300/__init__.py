@@ -648,10 +648,15 @@ def _make_calib_function():
         """L(g) = sum_nu sum_{i>j} |g_i conj(g_j) M_ij - V_ij|^2 with the
         hand-written forward and adjoint kernels; the gradient returned for
         g is PyTorch's complex convention dL/dRe g + i dL/dIm g.  One kernel
-        pass computes both, the gradient is kept for backward."""
+        pass computes both, the gradient is kept for backward.  The loss is
+        differentiable in g only: V and M requiring a gradient is an error
+        (their gradient would otherwise be silently dropped)."""
 
         @staticmethod
         def forward(ctx, g, V, M):
+            if V.requires_grad or M.requires_grad:
+                raise ValueError("calib_loss is differentiable in g only; "
+                                 "detach V and M (their gradient is not computed)")
             # g [N]: one gain per input; g [n_chan, N]: per-channel gains
             fn = calib_chan_loss_grad if g.dim() == 2 else calib_loss_grad
             loss, grad = fn(V, M, g.detach().contiguous(), want_grad=g.requires_grad)

@@ -1075,19 +1075,29 @@ constexpr int kMaxStaticDevices = 256;
 std::mutex g_static_ws_mu;
 void *g_static_ws_addr[kMaxStaticDevices];
 
-// Device address of the array on the current device, looked up once per
-// device (host code cannot use the array's name as a device pointer).
-cudaError_t static_ws_address(void **out) {
+// Device address of the array on the current device.  Host code cannot use
+// the array's name as a device pointer, so the address is asked of the
+// runtime with the device current.  Outside stream capture it is looked up
+// on every call (no allocation; this also follows a cudaDeviceReset, after
+// which the module is loaded again at another address); during a capture the
+// address remembered from the device's last uncaptured call is used, and a
+// device with no such call is refused.
+cudaError_t static_ws_address(cudaStream_t stream, void **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxStaticDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_static_ws_mu);
-  if (!g_static_ws_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_calib_static_ws);
     if (e != cudaSuccess) return e;
     g_static_ws_addr[dev] = p;
+  } else if (!g_static_ws_addr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_static_ws_addr[dev];
   return cudaSuccess;
@@ -1104,7 +1114,7 @@ extern "C" mwax_status mwax_calib_loss_grad_static(const float *V, const float *
   const int64_t need = mwax_calib_workspace_bytes(n_inputs, n_chan);
   if (need < 0 || need > mwax::kStaticWsBytes) return MWAX_ERR_INVALID_ARG;
   void *ws = nullptr;
-  if (mwax::static_ws_address(&ws) != cudaSuccess) return MWAX_ERR_CUDA;
+  if (mwax::static_ws_address(stream, &ws) != cudaSuccess) return MWAX_ERR_CUDA;
   // Every partial-sum slot the gather kernel reads is written first by the
   // tile kernel of the same call, so nothing in the array needs clearing.
   return mwax_calib_loss_grad(V, M, g, n_inputs, n_chan, ws, loss, grad, stream);

@@ -94,8 +94,14 @@ extern "C" mwax_status mwax_stokes(const float *inst, int n, double dl, double c
   using namespace mwax;
   NvtxRange nvtx_("mwax_stokes");
   if (n < 2 || n % 2 || n > 65536 || !(dl > 0.0)) return MWAX_ERR_INVALID_ARG;
-  if (!dev_ptr8(inst) || !dev_ptr8(stokes) || inst == stokes) return MWAX_ERR_INVALID_ARG;
+  if (!dev_ptr8(inst) || !dev_ptr8(stokes)) return MWAX_ERR_INVALID_ARG;
   const int64_t npix = (int64_t)n * n;
+  // each thread reads its pixel's four inputs and writes its four outputs,
+  // so any overlap of the two ranges lets one pixel's writes clobber the
+  // inputs of another: reject it
+  const uintptr_t bytes = (uintptr_t)(4 * npix) * sizeof(float2);
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(inst), b0 = reinterpret_cast<uintptr_t>(stokes);
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return MWAX_ERR_INVALID_ARG;
   const int T = 256;
   stokes_kernel<<<(unsigned)((npix + T - 1) / T), T, 0, stream>>>(
       reinterpret_cast<const float2 *>(inst), n, (float)dl, (float)cos(chi), (float)sin(chi),

@@ -144,27 +144,42 @@ def test_calib_workspace_sizes(mwax_lib):
     assert L.mwax_calib_chan_workspace_bytes(2, 65535 * 8) > 0
 
 
-def test_plain_c_client_builds_and_runs(mwax_lib, tmp_path):
-    """The boundary is a C library: a plain C program compiled against
-    include/mwax.h (gcc, C11) links libmwax.so and gets the host-only answers
-    (baseline helpers, the int32 bound, a refused plan, the pair-mode work
-    list) without Python or torch."""
+def _build_c_client(mw, tmp_path):
     import shutil
     import subprocess
 
     gcc = shutil.which("gcc")
     if gcc is None:
         pytest.skip("no C compiler")
-    mw = mwax_lib
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     lib_dir = os.path.dirname(mw.LIB_PATH)
-    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    cuda_lib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                     if os.path.isdir(d)), os.path.join(cuda, "lib64"))
     exe = str(tmp_path / "abi_client")
     subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
-                    "-I", cuda_inc, os.path.join(root, "tests", "c_client", "abi_client.c"),
-                    "-L", lib_dir, "-lmwax", "-Wl,-rpath," + lib_dir, "-o", exe], check=True)
-    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
-    got = dict(line.split(" ", 1) for line in out.strip().splitlines())
+                    "-I", os.path.join(cuda, "include"),
+                    os.path.join(root, "tests", "c_client", "abi_client.c"),
+                    "-L", lib_dir, "-lmwax", "-Wl,-rpath," + lib_dir,
+                    "-L", cuda_lib, "-lcudart", "-Wl,-rpath," + cuda_lib, "-o", exe], check=True)
+    case = os.path.join(root, "tests", "golden", "c_client_corr.txt")
+    return exe, case
+
+
+def _run_c_client(exe, case):
+    import subprocess
+
+    out = subprocess.run([exe, case], check=True, capture_output=True, text=True).stdout
+    return dict(line.split(" ", 1) for line in out.strip().splitlines())
+
+
+def test_plain_c_client_builds_and_runs(mwax_lib, tmp_path):
+    """The boundary is a C library: a plain C program compiled against
+    include/mwax.h (gcc, C11) links libmwax.so and gets the host-only answers
+    (baseline helpers, the int32 bound, a refused plan, the pair-mode work
+    list) without Python or torch."""
+    exe, case = _build_c_client(mwax_lib, tmp_path)
+    got = _run_c_client(exe, case)
     assert got["n_baselines_512"] == "131328"
     assert got["n_baselines_1024"] == "524800"
     assert got["baseline_index_5_3"] == "18"
@@ -175,3 +190,18 @@ def test_plain_c_client_builds_and_runs(mwax_lib, tmp_path):
     assert got["work_list_tile_pairs"] == str(2 * 36)
     assert int(got["work_list_items"]) == 36  # 2 x 36 pairs, two per item
     assert got["calib_jones_ws_odd"] == "-1"
+
+
+@pytest.mark.gpu
+def test_plain_c_client_correlates_on_the_device(mwax_lib, tmp_path):
+    """The same C program on a GPU: plan, correlate with device buffers and
+    with host buffers, destroy -- every visibility equal to the oracle's
+    (stored by tests/golden/make_c_client_golden.py)."""
+    exe, case = _build_c_client(mwax_lib, tmp_path)
+    got = _run_c_client(exe, case)
+    assert "device_skipped" not in got
+    assert got["plan_status"] == "0" and got["correlate_status"] == "0"
+    assert got["plan_device_status"] == "0" and got["correlate_host_status"] == "0"
+    assert got["destroy_status"] == "0"
+    assert int(got["values_compared"]) == 2 * 20 * 21
+    assert got["device_mismatches"] == "0" and got["host_mismatches"] == "0"

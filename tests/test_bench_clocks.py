@@ -60,3 +60,37 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     c.start()
     assert c.stop() is None
     assert not os.path.exists(name)  # the sample file is removed either way
+
+
+ARGS_FAKE = """#!/bin/sh
+# records its arguments, then prints one sample
+echo "$@" > "$(dirname "$0")/args.txt"
+echo "0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active"
+sleep 5
+"""
+
+
+def test_clock_sampler_names_the_visible_gpu(tmp_path, monkeypatch):
+    """Under CUDA_VISIBLE_DEVICES=3 CUDA device 0 is physical GPU 3: the sampler
+    must ask nvidia-smi (which ignores the variable) about GPU 3, not GPU 0."""
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text(ARGS_FAKE)
+    exe.chmod(exe.stat().st_mode | stat.S_IEXEC)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3")
+    import torch
+
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)  # the CPU-side fallback
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path.remove(ROOT)
+    c = bench.Clocks(0)
+    assert c.gpu_id == "3"
+    c.start()
+    c.stop()
+    args = (tmp_path / "args.txt").read_text().split()
+    assert args[args.index("-i") + 1] == "3"
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-0c1d2e3f, GPU-aabbccdd")
+    assert bench.Clocks(1).gpu_id == "GPU-aabbccdd"

@@ -86,6 +86,13 @@ def test_calib_autograd_function(mw):
     G64 = oracle.calib_grad(V.astype(np.complex128), M.astype(np.complex128), g.astype(np.complex128))
     got = gt.grad.cpu().numpy()
     assert np.abs(got - 3.0 * G64).max() / np.abs(3.0 * G64).max() <= 1e-4
+    # differentiable in g only: V or M asking for a gradient is refused, not dropped
+    Vt = torch.from_numpy(V).cuda().requires_grad_(True)
+    with pytest.raises(ValueError):
+        mw.calib_loss(gt, Vt, torch.from_numpy(M).cuda())
+    Mt = torch.from_numpy(M).cuda().requires_grad_(True)
+    with pytest.raises(ValueError):
+        mw.calib_loss(gt, torch.from_numpy(V).cuda(), Mt)
 
 
 def test_calib_central_differences(mw):

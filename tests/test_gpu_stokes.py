@@ -120,3 +120,12 @@ def test_stokes_invalid_args(mw):
     assert L.mwax_stokes(xp + 4, 8, 0.1, 0.0, yp, None) == 1  # misaligned
     h = torch.zeros((4, 8, 8), dtype=torch.complex64)
     assert L.mwax_stokes(torch.view_as_real(h).data_ptr(), 8, 0.1, 0.0, yp, None) == 1
+    # partly overlapping ranges (either order, by one pixel or by most of a plane)
+    big = torch.zeros((2, 4, 8, 8), dtype=torch.complex64, device="cuda")
+    bp = torch.view_as_real(big).data_ptr()
+    for off in (8, 8 * 100, 8 * (4 * 64 - 1)):
+        assert L.mwax_stokes(bp, 8, 0.1, 0.0, bp + off, None) == 1
+        assert L.mwax_stokes(bp + off, 8, 0.1, 0.0, bp, None) == 1
+    # adjacent ranges do not overlap
+    assert L.mwax_stokes(bp, 8, 0.1, 0.0, bp + 8 * 4 * 64, None) == 0
+    torch.cuda.synchronize()
