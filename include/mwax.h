@@ -174,18 +174,27 @@ mwax_status mwax_destroy(mwax_plan_t plan);
 
 mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info);
 
-/* Device time of the kernels a plan launched while timing was enabled. */
+/* Device time of the kernels a plan launched while timing was enabled, and
+ * of the host<->device copies of mwax_correlate_host. */
 typedef struct {
   double unpack_ms;            /* summed device time of unpack launches            */
   double correlate_ms;         /* summed device time of correlate launches         */
   int64_t unpack_launches;
   int64_t correlate_launches;  /* tensor-core launches, or plain per-channel ones  */
+  double h2d_ms;               /* summed duration of the host-path input copies    */
+  double d2h_ms;               /* summed duration of the host-path output copies   */
+  int64_t h2d_bytes;           /* bytes those copies moved                         */
+  int64_t d2h_bytes;
+  int64_t h2d_copies;
+  int64_t d2h_copies;
 } mwax_timing;
 
 /* Record (enable != 0) or stop recording CUDA events on the plan's stream
- * around every kernel it launches.  A batch plan replays two CUDA graphs per
- * call -- all jobs' unpack launches, then the one persistent correlate
- * launch -- and times each graph launch as one unpack / correlate launch. */
+ * around every kernel it launches (and, in mwax_correlate_host, on the copy
+ * streams around every input and output copy).  A batch plan replays two
+ * CUDA graphs per call -- all jobs' unpack launches, then the one persistent
+ * correlate launch -- and times each graph launch as one unpack / correlate
+ * launch. */
 mwax_status mwax_plan_set_timing(mwax_plan_t plan, int enable);
 
 /* Sums since the previous call; synchronises the plan's stream, then resets. */

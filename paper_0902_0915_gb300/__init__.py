@@ -56,7 +56,10 @@ class PlanInfo(ctypes.Structure):
 
 class Timing(ctypes.Structure):
     _fields_ = [("unpack_ms", ctypes.c_double), ("correlate_ms", ctypes.c_double),
-                ("unpack_launches", ctypes.c_int64), ("correlate_launches", ctypes.c_int64)]
+                ("unpack_launches", ctypes.c_int64), ("correlate_launches", ctypes.c_int64),
+                ("h2d_ms", ctypes.c_double), ("d2h_ms", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+                ("h2d_copies", ctypes.c_int64), ("d2h_copies", ctypes.c_int64)]
 
 
 class TuneReport(ctypes.Structure):

@@ -99,8 +99,9 @@ struct mwax_plan_s {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
-    int kind;  // 0 unpack, 1 correlate
+    int kind;  // 0 unpack, 1 correlate, 2 host-to-device copy, 3 device-to-host copy
     cudaEvent_t start, stop;
+    int64_t bytes;
   };
   std::vector<Rec> recs;
 
@@ -217,12 +218,12 @@ struct TimedLaunch {
     }
     return used;
   }
-  void done() {
+  void done(int64_t bytes = 0) {
     if (start < 0) return;
     const int stop = next_event();
     if (stop < 0) return;
     cudaEventRecord(p->ev_pool[stop], st);
-    p->recs.push_back({kind, p->ev_pool[start], p->ev_pool[stop]});
+    p->recs.push_back({kind, p->ev_pool[start], p->ev_pool[stop], bytes});
     start = -1;
   }
 };
@@ -848,14 +849,23 @@ mwax_status mwax_plan_get_timing(mwax_plan_t plan, mwax_timing *t) {
   if (e != cudaSuccess) return cuda_status(e);
   for (const auto &r : plan->recs) {
     float ms = 0.f;
-    e = cudaEventElapsedTime(&ms, r.start, r.stop);
+    e = cudaEventSynchronize(r.stop);  // copy events live on the copy streams
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.start, r.stop);
     if (e != cudaSuccess) return cuda_status(e);
     if (r.kind == 0) {
       t->unpack_ms += ms;
       t->unpack_launches += 1;
-    } else {
+    } else if (r.kind == 1) {
       t->correlate_ms += ms;
       t->correlate_launches += 1;
+    } else if (r.kind == 2) {
+      t->h2d_ms += ms;
+      t->h2d_bytes += r.bytes;
+      t->h2d_copies += 1;
+    } else {
+      t->d2h_ms += ms;
+      t->d2h_bytes += r.bytes;
+      t->d2h_copies += 1;
     }
   }
   plan->recs.clear();
@@ -897,9 +907,12 @@ mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int
     const int nc = (int)std::min<int64_t>(G, n_chan - c0);
     // input stage k is free once the compute of group gi-2 finished
     if (gi >= 2) e = cudaStreamWaitEvent(plan->h2d, plan->ev_comp[k], 0);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+      TimedLaunch tc_in(plan, 2, plan->h2d);
       e = cudaMemcpyAsync(plan->stage_in[k], hin + c0 * s.in_chan_bytes, nc * s.in_chan_bytes,
                           cudaMemcpyHostToDevice, plan->h2d);
+      tc_in.done(nc * s.in_chan_bytes);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(plan->ev_in[k], plan->h2d);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->stream, plan->ev_in[k], 0);
     // output stage k is free once its copy-out of group gi-2 finished
@@ -919,9 +932,12 @@ mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int
     if (r != MWAX_OK) return r;
     e = cudaEventRecord(plan->ev_comp[k], plan->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->d2h, plan->ev_comp[k], 0);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+      TimedLaunch tc_out(plan, 3, plan->d2h);
       e = cudaMemcpyAsync(hout + c0 * s.out_chan_bytes, plan->stage_out[k], nc * s.out_chan_bytes,
                           cudaMemcpyDeviceToHost, plan->d2h);
+      tc_out.done(nc * s.out_chan_bytes);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[k], plan->d2h);
   }
   if (e == cudaSuccess && plan->checked && use_pair) e = checked_call_done(plan, plan->stream);

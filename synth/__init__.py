@@ -256,6 +256,28 @@ def spec_c4() -> Spec:
                 chan_base=3366, chan_width_hz=40e3, meta={"scale": scale})
 
 
+def model_visibilities_host(spec: Spec, chans) -> np.ndarray:
+    """The calibration sky model of a point-source workload (the input the
+    gain fit is made against, not part of the correlation): for channel c,
+    M_ij(c) = sum_s S_s exp(i (phi_is - phi_js)) with phi_is = 2 pi
+    frac(rate_is (c + chan_base) / 2^32), the same phase the generator
+    applies to source s on input i.  FP64, returned as complex128
+    [len(chans), N(N+1)/2] in the lower-triangle baseline order."""
+    if spec.src_rate is None or spec.src_flux is None:
+        raise ValueError("not a point-source workload with a flux model")
+    N = spec.n_inputs
+    ii, jj = np.tril_indices(N)
+    rate = np.asarray(spec.src_rate, np.uint64)  # [N, S]
+    flux = np.asarray(spec.src_flux, np.float64)
+    out = np.empty((len(chans), ii.size), np.complex128)
+    for k, c in enumerate(chans):
+        turns = (rate * np.uint64(c + spec.chan_base)) % np.uint64(2 ** 32)
+        e = np.exp(2j * np.pi * (turns.astype(np.float64) / 2.0 ** 32))  # [N, S]
+        full = (e * flux) @ e.conj().T
+        out[k] = full[ii, jj]
+    return out
+
+
 WORKLOADS = {"c0": spec_c0, "c1": spec_c1, "c2": spec_c2, "c4": spec_c4}
 
 

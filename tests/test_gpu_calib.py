@@ -497,3 +497,99 @@ def test_calib_jones_rejects_bad_shapes(mw):
     with pytest.raises(ValueError):
         mw.calib_jones_loss_grad(Vd, Md, torch.from_numpy(J[:4]).cuda())
     assert mw.lib().mwax_calib_jones_workspace_bytes(11, 2) == -1  # odd input count
+
+
+# ---------------------------------------------------------------------------
+# the c4 workload end to end: correlator output -> FP32 V -> calibration
+# ---------------------------------------------------------------------------
+def test_c4_workload_parity_sampled(mw):
+    """The configured data path at full size (1024 inputs x 768 channels,
+    T = 10000, 8-bit voltages carrying 20 point sources through true gains):
+    the library correlates all channels; on 8 sampled channels (first, last,
+    six seeded) its int32 visibilities equal the oracle's correlation of the
+    same seeded voltages, both sides form the FP32 V = vis / (2 T scale^2)
+    identically, and the GPU loss, gradient, one gain-solve sweep, per-channel
+    loss and gradient and the Jones loss and gradient agree with the FP64
+    oracle on those channels (loss 1e-5, gradient and iterates 1e-4
+    relative); the gradient also matches central differences (h = 1e-3) of
+    the FP64 loss on a few coordinates."""
+    import torch
+
+    import synth
+
+    spec = synth.spec_c4()
+    N, C, T = spec.n_inputs, spec.n_chan, spec.n_time
+    B = N * (N + 1) // 2
+    rng = np.random.default_rng(44)
+    sub = sorted({0, C - 1, *rng.choice(np.arange(1, C - 1), 6, replace=False).tolist()})
+    # GPU: every channel of the workload
+    vol = torch.empty(C * T * N * 2, dtype=torch.uint8, device="cuda")
+    synth.fill_device(spec, vol)
+    plan = mw.Plan(N, C, T, 8)
+    vis = plan.correlate(vol)
+    assert plan.status() == 0
+    plan.close()
+    del vol
+    subd = torch.tensor(sub, device="cuda")
+    vis_s = vis.index_select(0, subd)
+    del vis
+    scale2 = np.float32(2.0 * spec.meta["scale"] ** 2 * T)
+    # a CUDA 0-d divisor: element-wise IEEE division (torch turns a Python-scalar
+    # divisor into a multiply by its reciprocal, which can differ by one ulp)
+    sdev = torch.tensor(scale2, dtype=torch.float32, device="cuda")
+    V_gpu = torch.complex(vis_s[..., 0].float() / sdev, vis_s[..., 1].float() / sdev)
+    # oracle: the same channels correlated from the host copy of the voltages
+    vis64 = oracle.correlate(synth.fill_host(spec, chans=sub), 8, N, len(sub), T)
+    np.testing.assert_array_equal(vis_s.cpu().numpy(), vis64)
+    V_host = (vis64[..., 0].astype(np.float32) / scale2
+              + 1j * (vis64[..., 1].astype(np.float32) / scale2)).astype(np.complex64)
+    assert np.array_equal(V_gpu.cpu().numpy().view(np.uint32), V_host.view(np.uint32))
+    M_host = synth.model_visibilities_host(spec, sub).astype(np.complex64)
+    M_gpu = torch.from_numpy(M_host).cuda()
+    g_true = np.asarray(spec.gains, np.complex128)
+    g = (g_true * (1 + 0.05 * (rng.standard_normal(N) + 1j * rng.standard_normal(N)))).astype(np.complex64)
+    V64, M64, g64 = V_host.astype(np.complex128), M_host.astype(np.complex128), g.astype(np.complex128)
+    # loss and gradient
+    loss, grad = mw.calib_loss_grad(V_gpu, M_gpu, torch.from_numpy(g).cuda())
+    L64 = oracle.calib_loss(V64, M64, g64)
+    G64 = oracle.calib_grad(V64, M64, g64)
+    assert abs(float(loss) - L64) <= 1e-5 * L64, (float(loss), L64)
+    gg = grad.cpu().numpy()
+    assert np.abs(gg - G64).max() <= 1e-4 * np.abs(G64).max()
+    # central differences of the FP64 loss (h = 1e-3) on seeded coordinates
+    h = 1e-3
+    for k in rng.choice(N, 4, replace=False):
+        for unit in (1.0, 1j):
+            gp, gm = g64.copy(), g64.copy()
+            gp[k] += h * unit
+            gm[k] -= h * unit
+            fd = (oracle.calib_loss(V64, M64, gp) - oracle.calib_loss(V64, M64, gm)) / (2 * h)
+            an = gg[k].real if unit == 1.0 else gg[k].imag
+            assert abs(an - fd) <= 1e-4 * np.abs(G64).max() + 1e-3 * abs(fd), (k, unit, an, fd)
+    # one gain-solve sweep
+    gs, hist = mw.calib_solve(V_gpu, M_gpu, torch.from_numpy(g).cuda(), 1)
+    gs64, h64 = oracle.calib_solve(V64, M64, g64, 1)
+    assert np.abs(gs.cpu().numpy() - gs64).max() <= 1e-4 * np.abs(gs64).max()
+    assert abs(float(hist[0]) - h64[0]) <= 1e-5 * h64[0]
+    # per-channel gains
+    G = (g[None, :] * (1 + 0.02 * (rng.standard_normal((len(sub), N))
+                                   + 1j * rng.standard_normal((len(sub), N))))).astype(np.complex64)
+    lc, gc = mw.calib_chan_loss_grad(V_gpu, M_gpu, torch.from_numpy(G).cuda())
+    Lc64 = oracle.calib_chan_loss(V64, M64, G.astype(np.complex128))
+    Gc64 = oracle.calib_chan_grad(V64, M64, G.astype(np.complex128))
+    assert abs(float(lc) - Lc64) <= 1e-5 * Lc64
+    gcn = gc.cpu().numpy()
+    for c in range(len(sub)):
+        assert np.abs(gcn[c] - Gc64[c]).max() <= 1e-4 * np.abs(Gc64[c]).max(), c
+    # 2x2 Jones matrices: diagonal gains plus 5 % leakage
+    n_t = N // 2
+    J = np.zeros((n_t, 2, 2), np.complex64)
+    J[:, 0, 0], J[:, 1, 1] = g[0::2], g[1::2]
+    J[:, 0, 1] = 0.05 * (rng.standard_normal(n_t) + 1j * rng.standard_normal(n_t))
+    J[:, 1, 0] = 0.05 * (rng.standard_normal(n_t) + 1j * rng.standard_normal(n_t))
+    lj, gj = mw.calib_jones_loss_grad(V_gpu, M_gpu, torch.from_numpy(J).cuda())
+    Lj64 = oracle.calib_jones_loss(V64, M64, J.astype(np.complex128))
+    Gj64 = oracle.calib_jones_grad(V64, M64, J.astype(np.complex128))
+    assert abs(float(lj) - Lj64) <= 1e-5 * Lj64
+    assert np.abs(gj.cpu().numpy() - Gj64).max() <= 1e-4 * np.abs(Gj64).max()
+    torch.cuda.synchronize()

@@ -325,6 +325,38 @@ def test_fp16_variant_error(mw, shape):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("shape", [0, 1])
+def test_fp16_variant_error_full_scale(mw, shape):
+    """Full-scale 8-bit input (every component +-127) at T = 10000: the autos
+    reach 2 * 127^2 * T = 3.2e8 > 2^24, so the FP32 sums do round.  The error
+    against the exact oracle is non-zero and within the FP32 summation bound
+    2T * 2^-24 (autos-normalised), and the exact kind on the same input is
+    still bit-exact."""
+    import torch
+
+    spec = synth.Spec("hfs", 256, 2, 10000, 8, seed=23, kind=synth.SYNTH_RANDMAX)
+    v = device_volt(spec)
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8, kind=mw.KIND_FP16, mma_shape=shape)
+    out = p.correlate(v)
+    assert p.status() == 0
+    got = out.cpu().numpy().astype(np.float64)
+    p.close()
+    exact, ref = oracle_for(spec, range(spec.n_chan), want64=True)
+    N = spec.n_inputs
+    ii, jj = np.tril_indices(N)
+    auto = ref[:, [oracle.baseline_index(i, i) for i in range(N)], 0].astype(np.float64)
+    assert auto.min() == 2 * 127**2 * spec.n_time
+    norm = np.sqrt(auto[:, ii] * auto[:, jj])
+    abs_err = np.abs(got - ref).max(axis=2)
+    err = abs_err / norm
+    assert 0 < err.max() <= 2 * spec.n_time * 2.0**-24, err.max()
+    assert abs_err.max() >= 1.0  # FP32 rounding really happened
+    q = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 8)
+    assert_exact(q.correlate(v).cpu().numpy(), exact, "exact kind, full scale")
+    q.close()
+    torch.cuda.synchronize()
+
+
 def test_batch_uneven_jobs(mw):
     import torch
 
@@ -351,9 +383,15 @@ def test_host_buffers(mw, engine):
     p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, engine=engine, chan_group=7)
     out = torch.empty((spec.n_chan, spec.n_inputs * (spec.n_inputs + 1) // 2, 2),
                       dtype=torch.int32).pin_memory()
+    p.set_timing(True)
     p.correlate_host(h, out)
+    tm = p.timing()
     assert p.status() == 0
     assert_exact(out.numpy(), oracle_for(spec, range(spec.n_chan)), "host path")
+    # the timing hook saw every copy: 64 channels in groups of 7 -> 10 copies each way
+    assert tm.h2d_copies == 10 and tm.d2h_copies == 10
+    assert tm.h2d_bytes == h.numel() and tm.d2h_bytes == out.numel() * 4
+    assert tm.h2d_ms > 0 and tm.d2h_ms > 0
     p.close()
 
 
