@@ -24,6 +24,9 @@ struct Cand {
   int mma_shape, stages, prefetch, pipeline, chan_group;
 };
 
+// Timed calls per candidate (after one untimed call).
+constexpr int kTuneReps = 3;
+
 std::mutex g_cache_mu;
 
 std::string tune_key(const mwax_job &j) {
@@ -178,18 +181,22 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
   }
   mwax_job base = *job;
   apply(&base, Cand{0, 0, 0, 0, 0});
-  const int reps = 2;
-  // (pair-mode candidates fail to plan, and are skipped, where a job needs
-  // more than one exact segment)
+  // Candidate 0 is the plan's own default (every field automatic: the pair
+  // mode where the integration is one exact segment, the checked single
+  // segment for longer 8-bit exact jobs, else the narrow shape), so the
+  // report's default_ms is that plan's time and a tuned choice can only
+  // replace it by being measurably faster.  An explicit pair request
+  // (mma_shape 3) on a job longer than one exact segment plans as the
+  // checked single segment; explicit flush segments are not candidates.
   const std::vector<Cand> cands = {
-      {1, 2, -1, 1, 0}, {1, 2, 8, 1, 0}, {1, 2, -1, 2, 0}, {2, 4, -1, 1, 0},
-      {2, 3, -1, 1, 0}, {2, 4, 8, 1, 0},  {2, 4, -1, 2, 0}, {3, 2, -1, 1, 0},
+      {0, 0, 0, 0, 0},  {3, 0, -1, 1, 0}, {1, 2, -1, 1, 0}, {1, 2, 8, 1, 0}, {2, 4, -1, 1, 0},
+      {2, 3, -1, 1, 0}, {1, 2, -1, 2, 0}, {3, 0, -1, 2, 0},
   };
   best_ms = -1.0;
   for (const Cand &c : cands) {
     mwax_job j = base;
     apply(&j, c);
-    const double ms = time_single(j, voltages, out, stream, reps);
+    const double ms = time_single(j, voltages, out, stream, kTuneReps);
     // earlier (simpler) candidates win ties: a later one must be >1% faster
     if (ms > 0 && (best_ms < 0 || ms < 0.99 * best_ms)) {
       best_ms = ms;
@@ -213,8 +220,9 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
   mwax_tune_report rep;
   memset(&rep, 0, sizeof(rep));
   std::vector<mwax_job> base(jobs, jobs + n_jobs);
-  const std::vector<Cand> cands = {{1, 2, -1, 0, 0}, {1, 2, 8, 0, 0}, {2, 4, -1, 0, 0},
-                                   {2, 3, -1, 0, 0}, {2, 4, 8, 0, 0}, {3, 2, -1, 0, 0}};
+  // candidate 0: the batch plan's own default (all fields automatic)
+  const std::vector<Cand> cands = {{0, 0, 0, 0, 0},  {3, 0, -1, 0, 0}, {1, 2, -1, 0, 0},
+                                   {1, 2, 8, 0, 0},  {2, 4, -1, 0, 0}, {2, 3, -1, 0, 0}};
   Cand best{0, 0, 0, 0, 0};
   double best_ms = -1.0;
   for (const Cand &c : cands) {
@@ -224,7 +232,7 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
       j.stages = c.stages;
       j.prefetch = c.prefetch;
     }
-    const double ms = time_batch(js, voltages, out, stream, 2);
+    const double ms = time_batch(js, voltages, out, stream, kTuneReps);
     if (ms > 0 && (best_ms < 0 || ms < 0.99 * best_ms)) {
       best_ms = ms;
       best = c;
