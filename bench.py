@@ -79,15 +79,16 @@ def unpack_bytes_per_channel(spec) -> float:
 
 
 def unpack_kernel_name(spec) -> str:
-    """The unpack kernel the plan picks for this shape (the TMA tile kernel
-    where the raw rows are whole 16-byte units, else the fallbacks)."""
+    """The unpack kernel the plan picks for this shape: for 8-bit samples the
+    TMA tile kernel where the raw rows are whole 16-byte units, else the
+    fallbacks; for 4-bit samples the MN-major streaming kernel (one form,
+    templated on the vector width the row length allows)."""
     n = spec.n_inputs
-    if os.environ.get("MWAX_UNPACK") is None:
-        if spec.sample_bits == 8 and n % 2 == 0:
-            return "unpack8_tile_kernel"
-        if spec.sample_bits == 4 and n % 4 == 0:
-            return "unpack4_tile_kernel"
-    return "unpack_kernel<8>" if spec.sample_bits == 8 else "unpack4_line_kernel"
+    if spec.sample_bits == 4:
+        return f"unpack4_mn_kernel<{16 if n % 16 == 0 else 4 if n % 4 == 0 else 1}>"
+    if os.environ.get("MWAX_UNPACK") is None and n % 2 == 0:
+        return "unpack8_tile_kernel"
+    return "unpack8_kernel"
 
 
 def unpack_roofline(spec, info, tim, steps, peaks, peak_src):

@@ -7,15 +7,19 @@
 //     Im V_ij = sum_t xi_i xr_j - xr_i xi_j
 // as a dense rank-T Hermitian update on the 5th-generation tensor cores.
 //
-// Operands come from k_unpack.cu: for every block of S time samples and every
-// input, a 128-byte row [re x S | im x S] of exact small floats (binary16 for 8-bit samples, S = 32;
-// E4M3 for 4-bit samples, S = 64).  A block is one row of a 128-byte
-// swizzled K-major shared-memory tile, and one MMA consumes a 32-byte slice
-// of it: slices 0,1 hold re, slices 2,3 hold im.  Per block the MMA warp
-// issues eight M=128 N=128 MMAs:
-//     D_re += A[s] . B[s]                      s = 0..3
-//     D_im += A[2] . B[0] + A[3] . B[1]        (xi_i xr_j)
-//     D_im -= A[0] . B[2] + A[1] . B[3]        (xr_i xi_j; negate-B bit)
+// Operands come from k_unpack.cu as 128 x 128-byte tiles of exact small
+// floats, one per 128 inputs and block of S time samples, each holding two K
+// slices of re and two of im (one MMA consumes one slice):
+//   8-bit samples (binary16, S = 32), K-major: a row per input,
+//       [re x 32 | im x 32]; slice s of re is bytes 32s .. 32s+31 of every
+//       row, of im bytes 64 + 32s ..;
+//   4-bit samples (E4M3, S = 64), MN-major: rows 0..63 hold the re codes of
+//       the tile's 128 inputs at samples 0..63, rows 64..127 the im codes;
+//       slice s of re is rows 32s .. 32s+31, of im rows 64 + 32s ...
+// Per block the MMA warp issues eight M=128 N=128 MMAs:
+//     D_re += re_A[s] . re_B[s] + im_A[s] . im_B[s]     s = 0, 1
+//     D_im += im_A[s] . re_B[s]                         (xi_i xr_j)
+//     D_im -= re_A[s] . im_B[s]                         (xr_i xi_j; negate-B bit)
 // Every product of two sample values is an exact integer and every partial
 // sum stays an integer below 2^24 for `flush_blocks` blocks, so the FP32
 // accumulator in tensor memory is exact; at the end of each such segment
@@ -204,13 +208,66 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   return d;
 }
 
+// Shared-memory matrix descriptor, MN-major, 128-byte swizzle: atoms of 8 K
+// rows x 128 bytes of MN (1024 bytes, stride byte offset) and the next
+// 128-input tile along MN kTileBytes on (leading byte offset; used when B
+// spans two tiles, N = 256).
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(kTileBytes >> 4) << 16;  // leading byte offset: next MN atom
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: next 8 K rows
+  d |= (uint64_t)1 << 46;                  // version
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// Operand tile of each sample width: its descriptor and the descriptor
+// offsets (16-byte units) of the K slices re 0, re 1, im 0, im 1.
+template <int BITS>
+struct Op;
+template <>
+struct Op<8> {  // binary16, K-major
+  static constexpr bool mn = false;
+  static constexpr uint64_t re0 = 0, re1 = 2, im0 = 4, im1 = 6;
+  static __device__ __forceinline__ uint64_t desc(uint32_t addr) { return sw128_desc(addr); }
+};
+template <>
+struct Op<4> {  // E4M3, MN-major
+  static constexpr bool mn = true;
+  static constexpr uint64_t re0 = 0, re1 = 256, im0 = 512, im1 = 768;
+  static __device__ __forceinline__ uint64_t desc(uint32_t addr) { return sw128_mn_desc(addr); }
+};
+
 // Instruction descriptor: FP32 accumulate, A/B type code 0 (F16 for
-// kind::f16, E4M3 for kind::f8f6f4), optional negation of B, K-major A and
-// B, M = 128, N = n.
+// kind::f16, E4M3 for kind::f8f6f4), optional negation of B, K-major (8-bit
+// samples) or MN-major (4-bit samples) A and B, M = 128, N = n.
+template <int BITS>
 __host__ __device__ constexpr uint32_t make_idesc(bool negate_b, int n) {
-  return (1u << 4) | ((negate_b ? 1u : 0u) << 14) | ((uint32_t)(n >> 3) << 17) |
+  return (1u << 4) | ((negate_b ? 1u : 0u) << 14) | ((Op<BITS>::mn ? 1u : 0u) << 15) |
+         ((Op<BITS>::mn ? 1u : 0u) << 16) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(kTile >> 4) << 24);
 }
+
+// TMA coordinates of a tile: (x, y) of K block 0 and the row step per K block.
+//   8-bit: [chan][kb][row][128 B] viewed as rows of 128 bytes; tile I of
+//          channel c, block b at row (c * KB + b) * n_rows + 128 I;
+//   4-bit: [chan][kb][128 rows][n_rows bytes]; x = 128 I, row (c * KB + b) * 128.
+template <int BITS>
+struct TileAt {
+  int x, y, step;
+  __device__ __forceinline__ TileAt(int c, int tile, int KB, int n_rows) {
+    if constexpr (Op<BITS>::mn) {
+      x = tile * kTile;
+      y = c * KB * kTile;
+      step = kTile;
+    } else {
+      x = 0;
+      y = c * KB * n_rows + tile * kTile;
+      step = n_rows;
+    }
+  }
+};
 
 template <int BITS>
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -323,19 +380,28 @@ __device__ __forceinline__ PairItem decode_pair_item(const int4 d) {
   return it;
 }
 
+// The eight MMAs of one K block: N = 128 (one tile pair) or 256 (B spans two
+// tiles: two pairs sharing A).
+template <int BITS, int N>
+__device__ __forceinline__ void block_mmas(uint32_t d_re, uint32_t d_im, uint64_t da, uint64_t db,
+                                           uint32_t acc0) {
+  using O = Op<BITS>;
+  constexpr uint32_t id = make_idesc<BITS>(false, N), idn = make_idesc<BITS>(true, N);
+  tc_mma<BITS>(d_re, da + O::re0, db + O::re0, id, acc0);
+  tc_mma<BITS>(d_re, da + O::re1, db + O::re1, id, 1u);
+  tc_mma<BITS>(d_re, da + O::im0, db + O::im0, id, 1u);
+  tc_mma<BITS>(d_re, da + O::im1, db + O::im1, id, 1u);
+  tc_mma<BITS>(d_im, da + O::im0, db + O::re0, id, acc0);
+  tc_mma<BITS>(d_im, da + O::im1, db + O::re1, id, 1u);
+  tc_mma<BITS>(d_im, da + O::re0, db + O::im0, idn, 1u);
+  tc_mma<BITS>(d_im, da + O::re1, db + O::im1, idn, 1u);
+}
+
 // The eight M=128 N=128 MMAs of one K block of one tile pair.
 template <int BITS>
 __device__ __forceinline__ void narrow_block(uint32_t d_re, uint32_t d_im, uint64_t da, uint64_t db,
                                              uint32_t acc0) {
-  constexpr uint32_t id = make_idesc(false, kTile), idn = make_idesc(true, kTile);
-  tc_mma<BITS>(d_re, da + 0, db + 0, id, acc0);
-  tc_mma<BITS>(d_re, da + 2, db + 2, id, 1u);
-  tc_mma<BITS>(d_re, da + 4, db + 4, id, 1u);
-  tc_mma<BITS>(d_re, da + 6, db + 6, id, 1u);
-  tc_mma<BITS>(d_im, da + 4, db + 0, id, acc0);
-  tc_mma<BITS>(d_im, da + 6, db + 2, id, 1u);
-  tc_mma<BITS>(d_im, da + 0, db + 4, idn, 1u);
-  tc_mma<BITS>(d_im, da + 2, db + 6, idn, 1u);
+  block_mmas<BITS, kTile>(d_re, d_im, da, db, acc0);
 }
 
 // The three roles in pair mode (warp 0: producer, warp 1: MMA issuer, warps
@@ -371,22 +437,22 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
         const KJob &jb = p.job[it.job];
         const CUtensorMap *map = &maps.m[it.job];
         const int n_rows = jb.n_tiles * kTile;
-        const int y0 = it.c0 * jb.kb * n_rows, y1 = it.c1 * jb.kb * n_rows;
-        // first row of each tile of the item at K block 0, in shared-memory order
-        int ys[3] = {0, 0, 0};
+        // each tile of the item at K block 0, in shared-memory order
+        TileAt<BITS> ts[3] = {TileAt<BITS>(0, 0, 0, 0), TileAt<BITS>(0, 0, 0, 0),
+                              TileAt<BITS>(0, 0, 0, 0)};
         int nt;
         if (it.type == kItemShared) {
-          ys[0] = y0 + it.J0 * kTile;
-          ys[1] = y0 + it.J1 * kTile;  // A_I itself when J1 == I0
-          ys[2] = y0 + it.I0 * kTile;
+          ts[0] = TileAt<BITS>(it.c0, it.J0, jb.kb, n_rows);
+          ts[1] = TileAt<BITS>(it.c0, it.J1, jb.kb, n_rows);  // A_I itself when J1 == I0
+          ts[2] = TileAt<BITS>(it.c0, it.I0, jb.kb, n_rows);
           nt = it.J1 == it.I0 ? 2 : 3;
         } else if (it.type == kItemTwoDiag) {
-          ys[0] = y0 + it.I0 * kTile;
-          ys[1] = y1 + it.I1 * kTile;
+          ts[0] = TileAt<BITS>(it.c0, it.I0, jb.kb, n_rows);
+          ts[1] = TileAt<BITS>(it.c1, it.I1, jb.kb, n_rows);
           nt = 2;
         } else {
-          ys[0] = y0 + it.I0 * kTile;
-          ys[1] = y0 + it.J0 * kTile;
+          ts[0] = TileAt<BITS>(it.c0, it.I0, jb.kb, n_rows);
+          ts[1] = TileAt<BITS>(it.c0, it.J0, jb.kb, n_rows);
           nt = it.I0 == it.J0 ? 1 : 2;
         }
         const uint32_t blk_bytes = (uint32_t)nt * kTileBytes;
@@ -401,8 +467,8 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
           mbar_arrive_expect_tx(full(stage), (uint32_t)nb * blk_bytes);
           for (int j = 0; j < nb; ++j)
             for (int t = 0; t < nt; ++t)
-              tma_load_2d(a + (uint32_t)(j * Sh::block_bytes + t * kTileBytes), map, 0,
-                          ys[t] + (kb + j) * n_rows, full(stage));
+              tma_load_2d(a + (uint32_t)(j * Sh::block_bytes + t * kTileBytes), map, ts[t].x,
+                          ts[t].y + (kb + j) * ts[t].step, full(stage));
           ++issued;
           if (++stage == S) {
             stage = 0;
@@ -425,7 +491,6 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread) ----------------
     if (lane == 0) {
-      constexpr uint32_t id = make_idesc(false, 2 * kTile), idn = make_idesc(true, 2 * kTile);
       const uint32_t d_re = tmem_base, d_im = tmem_base + 2 * kTile;
       int stage = 0;
       uint32_t phase = 0, n_it = 0;
@@ -453,22 +518,15 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
             const uint32_t acc0 = kb + j == 0 ? 0u : 1u;
             if (it.type == kItemShared) {
               // B = [A_J0 ; A_J1]: columns 0..127 give pair (I, J0), 128..255 pair (I, J1)
-              const uint64_t da = sw128_desc(a + a_off), db = sw128_desc(a);
-              tc_mma<BITS>(d_re, da + 0, db + 0, id, acc0);
-              tc_mma<BITS>(d_re, da + 2, db + 2, id, 1u);
-              tc_mma<BITS>(d_re, da + 4, db + 4, id, 1u);
-              tc_mma<BITS>(d_re, da + 6, db + 6, id, 1u);
-              tc_mma<BITS>(d_im, da + 4, db + 0, id, acc0);
-              tc_mma<BITS>(d_im, da + 6, db + 2, id, 1u);
-              tc_mma<BITS>(d_im, da + 0, db + 4, idn, 1u);
-              tc_mma<BITS>(d_im, da + 2, db + 6, idn, 1u);
+              const uint64_t da = Op<BITS>::desc(a + a_off), db = Op<BITS>::desc(a);
+              block_mmas<BITS, 2 * kTile>(d_re, d_im, da, db, acc0);
             } else if (it.type == kItemTwoDiag) {
-              const uint64_t d0 = sw128_desc(a), d1 = sw128_desc(a + kTileBytes);
+              const uint64_t d0 = Op<BITS>::desc(a), d1 = Op<BITS>::desc(a + kTileBytes);
               narrow_block<BITS>(d_re, d_im, d0, d0, acc0);
               narrow_block<BITS>(d_re + kTile, d_im + kTile, d1, d1, acc0);
             } else {
-              const uint64_t da = sw128_desc(a);
-              const uint64_t db = it.I0 == it.J0 ? da : sw128_desc(a + kTileBytes);
+              const uint64_t da = Op<BITS>::desc(a);
+              const uint64_t db = it.I0 == it.J0 ? da : Op<BITS>::desc(a + kTileBytes);
               narrow_block<BITS>(d_re, d_im, da, db, acc0);
             }
           }
@@ -651,23 +709,22 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
         // operand rows: [chan][kb][row][128 B]; block kb of tile I starts at row
         // (c * KB + kb) * n_rows + I * 128
         const int n_rows = jb.n_tiles * kTile;
-        const int y0 = it.c * jb.kb * n_rows;
-        const int yA = y0 + it.I * kTile, yB = y0 + it.J * kTile;
+        const TileAt<BITS> tA(it.c, it.I, jb.kb, n_rows), tB(it.c, it.J, jb.kb, n_rows);
         const bool diag = it.I == it.J;
         const uint32_t blk_bytes = diag ? kTileBytes : 2 * kTileBytes;  // TMA bytes per block
         // warm L2 for the first blocks of the item; later blocks are prefetched
         // `prefetch` blocks ahead of their TMA load (first-touch misses go to DRAM)
         const int pf = p.prefetch;
         for (int kb = 0; kb < pf && kb < jb.kb; ++kb) {
-          tma_prefetch_2d(map, 0, yA + kb * n_rows);
-          if (!diag) tma_prefetch_2d(map, 0, yB + kb * n_rows);
+          tma_prefetch_2d(map, tA.x, tA.y + kb * tA.step);
+          if (!diag) tma_prefetch_2d(map, tB.x, tB.y + kb * tB.step);
         }
         for (int kb = 0; kb < jb.kb; kb += Sh::kps) {
           const int nb = min(Sh::kps, jb.kb - kb);
           if (pf > 0)
             for (int j = 0; j < nb && kb + j + pf < jb.kb; ++j) {
-              tma_prefetch_2d(map, 0, yA + (kb + j + pf) * n_rows);
-              if (!diag) tma_prefetch_2d(map, 0, yB + (kb + j + pf) * n_rows);
+              tma_prefetch_2d(map, tA.x, tA.y + (kb + j + pf) * tA.step);
+              if (!diag) tma_prefetch_2d(map, tB.x, tB.y + (kb + j + pf) * tB.step);
             }
           if (!mbar_wait(empty(stage), phase ^ 1u, abort_flag, tmo)) {
             raise_timeout(abort_flag, p.status);
@@ -678,8 +735,8 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
           mbar_arrive_expect_tx(full(stage), (uint32_t)nb * blk_bytes);
           for (int j = 0; j < nb; ++j) {
             const uint32_t aj = a + (uint32_t)(j * Sh::block_bytes);
-            tma_load_2d(aj, map, 0, yA + (kb + j) * n_rows, full(stage));
-            if (!diag) tma_load_2d(aj + kTileBytes, map, 0, yB + (kb + j) * n_rows, full(stage));
+            tma_load_2d(aj, map, tA.x, tA.y + (kb + j) * tA.step, full(stage));
+            if (!diag) tma_load_2d(aj + kTileBytes, map, tB.x, tB.y + (kb + j) * tB.step, full(stage));
           }
           ++issued;
           if (++stage == S) {
@@ -703,8 +760,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread) ----------------
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc(false, WIDE ? 2 * kTile : kTile);
-      constexpr uint32_t idesc_neg = make_idesc(true, kTile);
+      constexpr uint32_t idesc = make_idesc<BITS>(false, WIDE ? 2 * kTile : kTile);
       int stage = 0;
       uint32_t phase = 0;
       uint32_t seg = 0;
@@ -737,26 +793,20 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
             }
             const uint32_t a = smem_base + (uint32_t)stage * kStageBytes + (uint32_t)(j * Sh::block_bytes);
             // descriptors of the 32-byte K slices: start address advances by 2 units of 16 B
-            const uint64_t da = sw128_desc(a);
-            const uint64_t db = diag ? da : sw128_desc(a + kTileBytes);
+            const uint64_t da = Op<BITS>::desc(a);
+            const uint64_t db = diag ? da : Op<BITS>::desc(a + kTileBytes);
             const uint32_t d_re = tmem_base + buf * kAccCols;
             const uint32_t acc0 = seg_start ? 0u : 1u;
             if constexpr (WIDE) {
-              // B = [A_J ; B'_J]: columns 0..127 give Re, 128..255 give Im
-              tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
-              tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
-              tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
-              tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
+              // B = [A_J ; B'_J], B'_J holding -im_J in place of re_J and re_J in
+              // place of im_J: columns 0..127 give Re, 128..255 give Im
+              using O = Op<BITS>;
+              tc_mma<BITS>(d_re, da + O::re0, db + O::re0, idesc, acc0);
+              tc_mma<BITS>(d_re, da + O::re1, db + O::re1, idesc, 1u);
+              tc_mma<BITS>(d_re, da + O::im0, db + O::im0, idesc, 1u);
+              tc_mma<BITS>(d_re, da + O::im1, db + O::im1, idesc, 1u);
             } else {
-              const uint32_t d_im = d_re + kTile;
-              tc_mma<BITS>(d_re, da + 0, db + 0, idesc, acc0);
-              tc_mma<BITS>(d_re, da + 2, db + 2, idesc, 1u);
-              tc_mma<BITS>(d_re, da + 4, db + 4, idesc, 1u);
-              tc_mma<BITS>(d_re, da + 6, db + 6, idesc, 1u);
-              tc_mma<BITS>(d_im, da + 4, db + 0, idesc, acc0);
-              tc_mma<BITS>(d_im, da + 6, db + 2, idesc, 1u);
-              tc_mma<BITS>(d_im, da + 0, db + 4, idesc_neg, 1u);
-              tc_mma<BITS>(d_im, da + 2, db + 6, idesc_neg, 1u);
+              narrow_block<BITS>(d_re, d_re + kTile, da, db, acc0);
             }
             if (++in_seg == F || kb + j == KB - 1) {
               tc_commit(tfull(buf));
@@ -779,17 +829,16 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
     __syncwarp();
   } else if (WIDE && warp < Sh::epi0) {
     // ---------------- B' builder (wide shape) ----------------
-    // B'_J row r = [-im_j | re_j]: 16-byte chunk c of the (128-byte swizzled)
-    // row is chunk c ^ 4 of the A_J row, negated for c < 4.  Thread t copies
-    // chunk c = t & 7 of rows (t >> 3) + 8m, m = 0..15, so its swizzle term
-    // (row & 7) and its negation flag are fixed; all 16 loads are issued
-    // before the stores.
+    // B'_J holds -im_J where A_J holds re_J and re_J where it holds im_J.
+    // 8-bit (K-major): B' row r = [-im_j | re_j]: 16-byte chunk c of the
+    //   (128-byte swizzled) row is chunk c ^ 4 of the A_J row, negated for c < 4.
+    // 4-bit (MN-major): B' row r is A_J row (r + 64) mod 128 (the other plane,
+    //   same swizzle phase since r and r + 64 agree mod 8), negated for r < 64.
+    // Thread t copies chunk c = t & 7 of rows (t >> 3) + 8m, m = 0..15; all 16
+    // loads are issued before the stores.
     constexpr uint32_t neg = BITS == 8 ? 0x80008000u : 0x80808080u;  // packed sign bits
     const int ct = (warp - 2) * 32 + lane;                           // 0 .. 63
     const int c = ct & 7, r0 = ct >> 3, sw = r0 & 7;
-    const uint32_t flip = c < 4 ? neg : 0u;
-    const int src_off = r0 * kRowBytes + (((c ^ 4) ^ sw) << 4);
-    const int dst_off = r0 * kRowBytes + ((c ^ sw) << 4);
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
@@ -807,16 +856,23 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
         uint8_t *dst = smem + (size_t)stage * kStageBytes + (diag ? kTileBytes : 2 * kTileBytes);
         uint4 v[16];
 #pragma unroll
-        for (int m = 0; m < 16; ++m)
-          v[m] = *reinterpret_cast<const uint4 *>(src + src_off + m * 8 * kRowBytes);
+        for (int m = 0; m < 16; ++m) {
+          const int r = r0 + 8 * m;
+          const int so = Op<BITS>::mn ? ((r + 64) & 127) * kRowBytes + (c << 4)
+                                      : r * kRowBytes + (((c ^ 4) ^ sw) << 4);
+          v[m] = *reinterpret_cast<const uint4 *>(src + so);
+        }
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
+          const int r = r0 + 8 * m;
+          const uint32_t flip = (Op<BITS>::mn ? r < 64 : c < 4) ? neg : 0u;
+          const int doff = Op<BITS>::mn ? r * kRowBytes + (c << 4) : r * kRowBytes + ((c ^ sw) << 4);
           uint4 w = v[m];
           w.x ^= flip;
           w.y ^= flip;
           w.z ^= flip;
           w.w ^= flip;
-          *reinterpret_cast<uint4 *>(dst + dst_off + m * 8 * kRowBytes) = w;
+          *reinterpret_cast<uint4 *>(dst + doff) = w;
         }
         // generic-proxy writes -> visible to the tensor core's async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1106,11 +1162,14 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   for (int j = 0; j < n_jobs; ++j) {
     const TcJob &job = jobs[j];
     if (job.flush_blocks < 1 || job.kb < 1 || job.n_tiles < 1) return cudaErrorInvalidValue;
-    // [chan][kb][row][128 B] viewed as rows of 128 bytes
-    const cuuint64_t rows = (cuuint64_t)job.n_chan * job.kb * job.n_tiles * kTile;
+    // 8-bit: [chan][kb][row][128 B] viewed as rows of 128 bytes;
+    // 4-bit: [chan][kb][128 rows][n_rows bytes]; the box is one 16 KB tile
+    const cuuint64_t n_rows = (cuuint64_t)job.n_tiles * kTile;
+    const bool mn = cfg.sample_bits == 4;
+    const cuuint64_t rows = (cuuint64_t)job.n_chan * job.kb * (mn ? (cuuint64_t)kTile : n_rows);
     if (rows > 0x7FFFFFFFull) return cudaErrorInvalidValue;  // TMA row coordinate is int32
-    cuuint64_t dims[2] = {(cuuint64_t)kRowBytes, rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kRowBytes};
+    cuuint64_t dims[2] = {mn ? n_rows : (cuuint64_t)kRowBytes, rows};
+    cuuint64_t strides[1] = {mn ? n_rows : (cuuint64_t)kRowBytes};
     cuuint32_t box[2] = {(cuuint32_t)kRowBytes, (cuuint32_t)kTile};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(&maps.m[j], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,

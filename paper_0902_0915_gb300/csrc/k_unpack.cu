@@ -1,23 +1,29 @@
-// k_unpack.cu -- packed complex samples -> tensor-core operand rows.
+// k_unpack.cu -- packed complex samples -> tensor-core operand tiles.
 //
 // Input  volt[chan][t][input]: 4+4-bit (one byte, low nibble re) or 8+8-bit
 //        (re byte, im byte) two's-complement samples.
-// Output op[chan][kb][row][128 B]: for every block of S time samples, one
-//        128-byte row per input (rows >= N are zero padding up to a multiple
-//        of the 128-input tile), contiguous across inputs, holding
-//            [ re(t0) .. re(t0+S-1) | im(t0) .. im(t0+S-1) ]
-//        holding the samples as exact small floats:
-//            8-bit samples: S = 32, IEEE binary16 (exact for |v| <= 2048),
-//            4-bit samples: S = 64, FP8 E4M3 (exact for |v| <= 16).
-//        Time samples past T are zero; zeros add nothing to any product.
+// Output, per channel and block of S time samples, the operand tiles the
+//        correlator's MMAs read, holding the samples as exact small floats:
+//   8-bit samples (S = 32, IEEE binary16, exact for |v| <= 2048), K-major:
+//        op[chan][kb][row][128 B], one 128-byte row per input (rows >= N
+//        zero up to a multiple of the 128-input tile), contiguous across
+//        inputs, holding [ re(t0) .. re(t0+31) | im(t0) .. im(t0+31) ]: one
+//        row of a 128-byte-swizzled K-major shared-memory tile, 16 KB per
+//        tile and time block.  The transpose goes through shared memory.
+//   4-bit samples (S = 64, FP8 E4M3, exact for |v| <= 16), MN-major:
+//        op[chan][kb][plane][s][n_rows] bytes, n_rows = 128 x tiles: row
+//        (plane 0, s) holds the re codes of every input at sample 64 kb + s
+//        (inputs contiguous, the order they arrive in), row (plane 1, s) the
+//        im codes.  One tile of one time block is a 128 x 128-byte box (rows:
+//        64 re, then 64 im samples; columns: the tile's 128 inputs), the
+//        MN-major 128-byte-swizzled tile the MMAs read.  No transpose is
+//        needed: a register-only streaming kernel converts each byte's two
+//        nibbles in place.
+// Time samples past T and inputs past N are zero (the plan zeroes its
+// operand buffers once; these positions are never written): zeros add
+// nothing to any product.
 //
-// This is the K-major operand layout of the correlator's MMAs: the 128-byte
-// block is one row of a 128-byte-swizzled shared-memory tile, each MMA
-// consumes a 32-byte slice of it (K = 16 halves or K = 32 E4M3 values), and
-// the 128 rows of one tile and time block are one contiguous 16 KB piece.
-//
-// HBM-bound: loads are coalesced across inputs, the transpose goes through
-// shared memory, and stores are 16-byte vectors, 8 threads per 128-byte row.
+// HBM-bound: loads and stores are 16-byte vectors where the row lengths allow.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -26,6 +32,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "mwax_internal.h"
 
@@ -35,18 +42,12 @@ namespace {
 constexpr int kRowsPerCta = 64;
 constexpr int kStride = kRowBytes + 16;  // shared row stride (keeps 16-byte alignment)
 
-// E4M3 encodings of the integers -7..7, indexed by the two's-complement
-// nibble.  value = 2^(e-7) (1 + m/8): 1 = 0x38, 2 = 0x40, 3 = 0x44,
-// 4 = 0x48, 5 = 0x4A, 6 = 0x4C, 7 = 0x4E, 8 = 0x50; the sign is bit 7.
-__constant__ uint8_t kE4M3FromNibble[16] = {0x00, 0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E,
-                                            0xD0 /* -8: outside the supported range, still exact */,
-                                            0xCE, 0xCC, 0xCA, 0xC8, 0xC4, 0xC0, 0xB8};
-
-template <int BITS>
-__global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__ volt,
-                                                     uint8_t *__restrict__ op, int N, int T,
-                                                     int n_rows, int kb, int64_t chan0) {
-  constexpr int S = BITS == 4 ? 64 : 32;
+// 8-bit samples, shared-memory transpose (fallback for shapes the tile and
+// line kernels do not take).
+__global__ void __launch_bounds__(256) unpack8_kernel(const uint8_t *__restrict__ volt,
+                                                      uint8_t *__restrict__ op, int N, int T,
+                                                      int n_rows, int kb, int64_t chan0) {
+  constexpr int S = 32;
   __shared__ __align__(16) uint8_t sblk[kRowsPerCta][kStride];
 
   const int tb = blockIdx.y;        // time block
@@ -59,20 +60,14 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
     const int t = k / kRowsPerCta, l = k % kRowsPerCta;
     const int i = r0 + l, tg = tb * S + t;
     const bool valid = i < N && tg < T;
-    if (BITS == 4) {
-      uint8_t b = valid ? volt[(chan * T + tg) * (int64_t)N + i] : (uint8_t)0;
-      sblk[l][t] = kE4M3FromNibble[b & 15u];
-      sblk[l][S + t] = kE4M3FromNibble[b >> 4];
-    } else {
-      short2 v = make_short2(0, 0);
-      if (valid) {
-        const char2 s = reinterpret_cast<const char2 *>(volt)[(chan * T + tg) * (int64_t)N + i];
-        v = make_short2(s.x, s.y);
-      }
-      const __half hr = __short2half_rn(v.x), hi = __short2half_rn(v.y);
-      *reinterpret_cast<__half *>(&sblk[l][2 * t]) = hr;
-      *reinterpret_cast<__half *>(&sblk[l][2 * (S + t)]) = hi;
+    short2 v = make_short2(0, 0);
+    if (valid) {
+      const char2 sv = reinterpret_cast<const char2 *>(volt)[(chan * T + tg) * (int64_t)N + i];
+      v = make_short2(sv.x, sv.y);
     }
+    const __half hr = __short2half_rn(v.x), hi = __short2half_rn(v.y);
+    *reinterpret_cast<__half *>(&sblk[l][2 * t]) = hr;
+    *reinterpret_cast<__half *>(&sblk[l][2 * (S + t)]) = hi;
   }
   __syncthreads();
   for (int k = tid; k < kRowsPerCta * 8; k += 256) {
@@ -85,14 +80,11 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
   }
 }
 
-// ---- full-line paths -----------------------------------------------------------
-// Each thread converts whole operand-row pieces so that every store covers
-// complete 32-byte sectors (4-bit) or 128-byte lines (8-bit), while every warp
-// load is one contiguous 128-byte line (consecutive threads take consecutive
-// inputs at the same time sample):
-//   8-bit: 2 inputs x one 32-sample block (two full 128-byte rows),
-//   4-bit: 4 inputs x 32 of the 64 samples of a block (32 B of re, 32 B of im each).
-// Requires N even (8-bit) or N % 4 == 0 (4-bit) for aligned 4-byte loads.
+// ---- full-line path (8-bit) -------------------------------------------------------
+// Each thread converts two inputs x one 32-sample block (two full 128-byte
+// rows), so every store covers complete 128-byte lines, while every warp load
+// is one contiguous line (consecutive threads take consecutive inputs at the
+// same time sample).  Requires N even for aligned 4-byte loads.
 
 // int8 in the low byte of each 16-bit lane -> binary16: 0x6400 | (v ^ 0x80)
 // encodes 1024 + v + 128 exactly; subtracting 1152 leaves v.
@@ -162,79 +154,124 @@ __global__ void __launch_bounds__(512) unpack8_persist_kernel(const uint8_t *__r
   }
 }
 
-// Four nibbles (the low nibble of each byte of x) -> four E4M3 codes, one per
-// byte.  The low three bits index an 8-entry byte table held in two registers
-// (byte_perm, whose selectors use three bits per byte); the sign bit picks
-// the table of negative values.  The four 3-bit indices are packed into the
-// selector with one shift-or and one byte permute (l | l >> 4 holds index k
-// | index k+1 << 4 in byte k).
-__device__ __forceinline__ uint32_t nib4_to_e4m3(uint32_t x) {
-  const uint32_t pos_lo = 0x44403800u, pos_hi = 0x4E4C4A48u;  // 0..7
-  const uint32_t neg_lo = 0xCACCCED0u, neg_hi = 0xB8C0C4C8u;  // -8..-1
-  const uint32_t l = x & 0x07070707u;
-  const uint32_t sel = __byte_perm(l | (l >> 4), 0u, 0x0020u);
-  const uint32_t p = __byte_perm(pos_lo, pos_hi, sel);
-  const uint32_t n = __byte_perm(neg_lo, neg_hi, sel);
-  const uint32_t m = ((x >> 3) & 0x01010101u) * 0xFFu;  // 0xFF where the nibble is negative
-  return (p & ~m) | (n & m);
+// Four nibbles (the low nibble of each byte of x, two's complement) -> four
+// E4M3 codes, one per byte.  Each nibble n, biased to n + 8 in [0, 15], is the
+// low byte of the binary16 1024 + (n + 8) (exponent 10: the byte is the
+// integer part of the fraction); subtracting 1032 leaves n exactly, and the
+// hardware's packed binary16 -> E4M3 conversion, exact for |n| <= 16, gives
+// the codes.  (Integer work: one logic op and two byte permutes per four
+// nibbles; a byte-permute lookup of the 16 codes with a sign select took
+// about three times as many integer instructions.)
+__device__ __forceinline__ uint32_t nib4_to_e4m3_f16(uint32_t x) {
+  const uint32_t u = (x & 0x0F0F0F0Fu) ^ 0x08080808u;  // n + 8 in each byte
+  uint32_t lo = __byte_perm(u, 0x64646464u, 0x4140), hi = __byte_perm(u, 0x64646464u, 0x4342);
+  const __half2 bias = __halves2half2(__ushort_as_half(0x6408), __ushort_as_half(0x6408));  // 1032
+  const __half2 hl = __hsub2(*reinterpret_cast<const __half2 *>(&lo), bias);
+  const __half2 hh = __hsub2(*reinterpret_cast<const __half2 *>(&hi), bias);
+  uint16_t el, eh;
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(el) : "r"(*reinterpret_cast<const uint32_t *>(&hl)));
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;" : "=h"(eh) : "r"(*reinterpret_cast<const uint32_t *>(&hh)));
+  return (uint32_t)el | ((uint32_t)eh << 16);
 }
 
-// Inputs i0..i0+3, half h (samples 32h .. 32h+31) of time block tb of channel c.
-__device__ __forceinline__ void unpack4_task(const uint8_t *__restrict__ volt,
-                                             uint8_t *__restrict__ op, int N, int T, int n_rows,
-                                             int kb, int64_t chan0, int c, int tb, int h, int i0) {
-  const int64_t chan = chan0 + c;
-  uint32_t re[32], im[32];  // byte k = E4M3 of input i0+k at sample r
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
-    const int t = tb * 64 + h * 32 + r;
-    const uint32_t w = (i0 < N && t < T)
-                           ? __ldg(reinterpret_cast<const uint32_t *>(volt + (chan * T + t) * (int64_t)N + i0))
-                           : 0u;
-    re[r] = nib4_to_e4m3(w);
-    im[r] = nib4_to_e4m3(w >> 4);
-  }
-  uint8_t *row = op + (((int64_t)c * kb + tb) * n_rows + i0) * kRowBytes + 32 * h;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t sel = (uint32_t)(k | ((k + 4) << 4));  // byte k of a, byte k of b
-    uint32_t vr[8], vi[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      vr[g] = __byte_perm(__byte_perm(re[4 * g], re[4 * g + 1], sel),
-                          __byte_perm(re[4 * g + 2], re[4 * g + 3], sel), 0x5410);
-      vi[g] = __byte_perm(__byte_perm(im[4 * g], im[4 * g + 1], sel),
-                          __byte_perm(im[4 * g + 2], im[4 * g + 3], sel), 0x5410);
+// ---- 4-bit samples: MN-major streaming unpack --------------------------------------
+// One thread takes VEC consecutive inputs (16, 4 or 1 bytes of samples, as N
+// allows aligned loads) of one (channel, sample) row at a time and writes
+// their re codes to the re plane and their im codes to the im plane of the
+// row's time block: a pure element-wise conversion, coalesced on both sides.
+// Threads of a CTA cover whole rows (rows per CTA step = 256 / (N / VEC)) or,
+// for long rows, stride along one row; the (channel, sample) position
+// advances incrementally, without a division per element.  U rows are loaded
+// before any is converted, for memory-level parallelism.  The kernel uses no
+// shared memory; a nonzero dynamic request (set-aside SMs of the overlapped
+// pipeline) only keeps it off SMs that hold a correlate CTA.
+#ifndef MWAX_U4_ROWS
+#define MWAX_U4_ROWS 2  // rows in flight per thread with 16-byte units (more with narrower ones)
+#endif
+#ifndef MWAX_U4_CTAS_PER_SM
+#define MWAX_U4_CTAS_PER_SM 8
+#endif
+template <int VEC>
+__global__ void __launch_bounds__(256) unpack4_mn_kernel(const uint8_t *__restrict__ volt,
+                                                         uint8_t *__restrict__ op, int N, int T,
+                                                         int n_rows, int kb, int64_t chan0,
+                                                         int n_chan) {
+  constexpr int U = VEC == 16 ? MWAX_U4_ROWS : VEC == 4 ? 2 * MWAX_U4_ROWS : 4 * MWAX_U4_ROWS;
+  using Vec = typename std::conditional<VEC == 16, uint4, typename std::conditional<VEC == 4, uint32_t, uint8_t>::type>::type;
+  const int upr = N / VEC;  // units per row
+  const bool long_rows = upr >= (int)blockDim.x;
+  const int rpb = long_rows ? 1 : (int)blockDim.x / upr;
+  const int r_off = long_rows ? 0 : (int)threadIdx.x / upr;
+  const int g0 = long_rows ? (int)threadIdx.x : (int)threadIdx.x - r_off * upr;
+  const int gstep = long_rows ? (int)blockDim.x : upr;
+  if (r_off >= rpb) return;
+  const int64_t rows = (int64_t)n_chan * T;
+  const int64_t rstride = (int64_t)gridDim.x * rpb;
+  const int64_t plane = (int64_t)64 * n_rows;
+  const int64_t dc = rstride / T;
+  const int dt = (int)(rstride - dc * T);
+  int64_t r = (int64_t)blockIdx.x * rpb + r_off;
+  int64_t c = r / T;
+  int t = (int)(r - c * T);
+  auto advance = [&](int64_t &cc, int &tt) {
+    tt += dt;
+    cc += dc;
+    if (tt >= T) {
+      tt -= T;
+      ++cc;
     }
-    uint8_t *dst = row + k * kRowBytes;
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
-    *reinterpret_cast<uint4 *>(dst + 16) = make_uint4(vr[4], vr[5], vr[6], vr[7]);
-    *reinterpret_cast<uint4 *>(dst + 64) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
-    *reinterpret_cast<uint4 *>(dst + 80) = make_uint4(vi[4], vi[5], vi[6], vi[7]);
-  }
-}
-
-__global__ void __launch_bounds__(128) unpack4_line_kernel(const uint8_t *__restrict__ volt,
-                                                           uint8_t *__restrict__ op, int N, int T,
-                                                           int n_rows, int kb, int64_t chan0) {
-  const int i0 = 4 * (blockIdx.x * 128 + threadIdx.x);
-  if (i0 >= n_rows) return;
-  unpack4_task(volt, op, N, T, n_rows, kb, chan0, blockIdx.z, blockIdx.y >> 1, blockIdx.y & 1, i0);
-}
-
-__global__ void __launch_bounds__(512) unpack4_persist_kernel(const uint8_t *__restrict__ volt,
-                                                              uint8_t *__restrict__ op, int N,
-                                                              int T, int n_rows, int kb,
-                                                              int64_t chan0, int n_chan) {
-  const int quads = n_rows / 4;
-  const int64_t tasks = (int64_t)n_chan * kb * 2 * quads;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < tasks;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int iq = (int)(k % quads);
-    const int64_t r = k / quads;  // (c, tb, h)
-    const int h = (int)(r & 1);
-    const int64_t r2 = r >> 1;
-    unpack4_task(volt, op, N, T, n_rows, kb, chan0, (int)(r2 / kb), (int)(r2 % kb), h, 4 * iq);
+  };
+  for (; r < rows; r += rstride * U) {
+    int64_t cu[U];
+    int tu[U];
+    cu[0] = c;
+    tu[0] = t;
+#pragma unroll
+    for (int k = 1; k < U; ++k) {
+      cu[k] = cu[k - 1];
+      tu[k] = tu[k - 1];
+      advance(cu[k], tu[k]);
+    }
+    for (int g = g0; g < upr; g += gstep) {
+      Vec w[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (r + k * rstride < rows) {
+          const Vec *src = reinterpret_cast<const Vec *>(volt + ((chan0 + cu[k]) * T + tu[k]) * (int64_t)N) + g;
+          if constexpr (VEC == 16) {
+            asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(w[k].x), "=r"(w[k].y), "=r"(w[k].z), "=r"(w[k].w)
+                         : "l"(src));
+          } else {
+            w[k] = __ldg(src);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (r + k * rstride >= rows) break;
+        const int tk = tu[k];
+        uint8_t *dst = op + ((cu[k] * kb + (tk >> 6)) * 128 + (tk & 63)) * (int64_t)n_rows + (int64_t)g * VEC;
+        if constexpr (VEC == 16) {
+          const uint4 re = make_uint4(nib4_to_e4m3_f16(w[k].x), nib4_to_e4m3_f16(w[k].y),
+                                      nib4_to_e4m3_f16(w[k].z), nib4_to_e4m3_f16(w[k].w));
+          const uint4 im = make_uint4(nib4_to_e4m3_f16(w[k].x >> 4), nib4_to_e4m3_f16(w[k].y >> 4),
+                                      nib4_to_e4m3_f16(w[k].z >> 4), nib4_to_e4m3_f16(w[k].w >> 4));
+          *reinterpret_cast<uint4 *>(dst) = re;
+          *reinterpret_cast<uint4 *>(dst + plane) = im;
+        } else if constexpr (VEC == 4) {
+          *reinterpret_cast<uint32_t *>(dst) = nib4_to_e4m3_f16(w[k]);
+          *reinterpret_cast<uint32_t *>(dst + plane) = nib4_to_e4m3_f16(w[k] >> 4);
+        } else {
+          const uint32_t b = w[k];
+          dst[0] = (uint8_t)nib4_to_e4m3_f16(b);
+          dst[plane] = (uint8_t)nib4_to_e4m3_f16(b >> 4);
+        }
+      }
+    }
+    c = cu[U - 1];
+    t = tu[U - 1];
+    advance(c, t);
   }
 }
 
@@ -415,134 +452,6 @@ __global__ void __launch_bounds__(kTileThreads, 6)
   __syncthreads();
 }
 
-// 4-bit samples, small footprint: one task is one 128-input tile of one
-// 64-sample time block.  A 2D TMA load brings the raw box (64 samples x 128
-// bytes, rows N bytes apart; inputs past N read as zeros) into shared memory;
-// warp w converts samples 16w .. 16w+15, lane q the inputs 4q .. 4q+3 (four-byte
-// loads, nibbles -> E4M3 by byte permutes), writing one re and one im chunk
-// of each of its four rows with the row rotation that keeps the stores free
-// of bank conflicts; one TMA tensor store writes the 16 KB tile.  About 25 KB
-// of shared memory and 128 threads, so several CTAs share an SM and hide each
-// other's load latency.
-template <bool TMA_IN>
-__global__ void __launch_bounds__(kTileThreads)
-    unpack4_tile_kernel(const __grid_constant__ CUtensorMap in_map,
-                        const __grid_constant__ CUtensorMap out_map, const uint8_t *volt, int N,
-                        int T, int n_tiles, int kb, int64_t chan0, int n_chan, int32_t *status,
-                        unsigned long long tmo) {
-  extern __shared__ __align__(1024) uint8_t sm_base[];
-  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_base) + 1023) &
-                                            ~static_cast<uintptr_t>(1023));
-  uint8_t *stage = sm;                    // 128 rows x 128 B, swizzled
-  uint8_t *raw = sm + kTile * kRowBytes;  // 64 samples x 128 B
-  __shared__ __align__(8) uint64_t bar;
-  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
-  const int64_t tasks = (int64_t)n_chan * kb * n_tiles;  // tile fastest
-  const int n_rows = n_tiles * kTile;
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (TMA_IN)
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&out_map)) : "memory");
-  }
-  __syncthreads();
-  const uint32_t raw_u32 = (uint32_t)__cvta_generic_to_shared(raw);
-  auto issue = [&](int64_t k) {
-    const int tile = (int)(k % n_tiles);
-    const int64_t cb = k / n_tiles;
-    const int c = (int)(cb / kb), tb = (int)(cb % kb);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
-                 "r"((uint32_t)kTileRawBytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(raw_u32),
-        "l"(reinterpret_cast<uint64_t>(&in_map)), "r"(tile * kTile),
-        "r"((int)((chan0 + c) * (int64_t)T + (int64_t)tb * 64)), "r"(b)
-        : "memory");
-  };
-  int64_t k = blockIdx.x;
-  if (TMA_IN && threadIdx.x == 0 && k < tasks) issue(k);
-  uint32_t rv[kRawWords];  // thread-loaded form: the raw words of the task in hand
-  auto fetch = [&](int64_t kk) {
-    const int tile_l = (int)(kk % n_tiles);
-    const int64_t cb_l = kk / n_tiles;
-    const int c_l = (int)(cb_l / kb), tb_l = (int)(cb_l % kb);
-    fetch_raw_box<4>(volt, rv, (int64_t)N, (chan0 + c_l) * (int64_t)T + (int64_t)tb_l * 64,
-                       min(64, T - tb_l * 64), tile_l * 128);
-  };
-  if (!TMA_IN && k < tasks) fetch(k);
-  uint32_t phase = 0;
-  bool ok = true;
-  const uint32_t stage_u32 = (uint32_t)__cvta_generic_to_shared(stage);
-  const int q = threadIdx.x & 31, quarter = threadIdx.x >> 5;
-  for (int it = 0; k < tasks && ok; k += gridDim.x, ++it) {
-    if constexpr (TMA_IN) {
-      if (!u_wait(b, phase, tmo)) {
-        if (threadIdx.x == 0) atomicExch(status, (int32_t)MWAX_ERR_TIMEOUT);
-        ok = false;
-        break;
-      }
-      phase ^= 1u;
-    } else {
-      // (raw was last read before the barrier that follows the conversion)
-      put_raw_box(raw, rv);
-    }
-    if (threadIdx.x == 0 && it > 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-    __syncthreads();
-    const int tile = (int)(k % n_tiles);
-    const int64_t cb = k / n_tiles;
-    const int c = (int)(cb / kb), tb = (int)(cb % kb);
-    const int rows = min(64, T - tb * 64);  // the box may run into the next channel
-    uint32_t re[16], im[16];                // byte m = E4M3 of input 4q+m at sample 16 quarter + r
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int sidx = 16 * quarter + r;
-      const uint32_t w = sidx < rows ? *reinterpret_cast<const uint32_t *>(raw + sidx * kTile + 4 * q) : 0u;
-      re[r] = nib4_to_e4m3(w);
-      im[r] = nib4_to_e4m3(w >> 4);
-    }
-    __syncthreads();  // raw is free: fetch the next task's box while this one is converted
-    if (TMA_IN && threadIdx.x == 0 && k + gridDim.x < tasks) issue(k + gridDim.x);
-    if (!TMA_IN && k + gridDim.x < tasks) fetch(k + gridDim.x);
-#pragma unroll
-    for (int step = 0; step < 4; ++step) {
-      const int kk = (step + (q >> 1)) & 3;
-      const uint32_t sel = (uint32_t)(kk | ((kk + 4) << 4));
-      uint32_t vr[4], vi[4];
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        vr[g] = __byte_perm(__byte_perm(re[4 * g], re[4 * g + 1], sel),
-                            __byte_perm(re[4 * g + 2], re[4 * g + 3], sel), 0x5410);
-        vi[g] = __byte_perm(__byte_perm(im[4 * g], im[4 * g + 1], sel),
-                            __byte_perm(im[4 * g + 2], im[4 * g + 3], sel), 0x5410);
-      }
-      const int row = 4 * q + kk;
-      const int sw = row & 7;
-      uint8_t *dst = stage + row * kRowBytes;
-      *reinterpret_cast<uint4 *>(dst + ((quarter ^ sw) << 4)) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
-      *reinterpret_cast<uint4 *>(dst + (((4 + quarter) ^ sw) << 4)) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int y0 = (int)(((int64_t)c * kb + tb) * n_rows + tile * kTile);
-      asm volatile(
-          "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-              reinterpret_cast<uint64_t>(&out_map)),
-          "r"(0), "r"(y0), "r"(stage_u32)
-          : "memory");
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-    }
-  }
-  if (threadIdx.x == 0) {
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    if (TMA_IN && !ok) u_wait(b, phase, tmo);
-  }
-  __syncthreads();
-}
-
 // Function attributes apply to the current device: set them once per device.
 constexpr int kMaxDevices = 64;
 std::mutex g_attr_mu;
@@ -563,39 +472,70 @@ cudaError_t once_per_device(bool (&done)[kMaxDevices], F &&set) {
 
 }  // namespace
 
+// 4-bit samples, every path: the MN-major streaming kernel on `ctas` CTAs of
+// 256 threads, with `smem` bytes of (unused) dynamic shared memory.
+cudaError_t launch_unpack4(const uint8_t *volt, int n_inputs, int n_time, int n_tiles, int kb,
+                           int64_t chan0, int n_chan, uint8_t *op, int ctas, int smem,
+                           cudaStream_t s) {
+  const int n_rows = n_tiles * kTile;
+  if (n_chan <= 0) return cudaSuccess;
+  if (ctas < 1 || n_inputs < 1 || n_inputs > n_rows) return cudaErrorInvalidValue;
+  if (smem > 0) {
+    cudaError_t e = once_per_device(g_attr_persist, [smem] {
+      cudaError_t r = cudaFuncSetAttribute(unpack8_persist_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+      for (const void *f : {reinterpret_cast<const void *>(unpack4_mn_kernel<16>),
+                            reinterpret_cast<const void *>(unpack4_mn_kernel<4>),
+                            reinterpret_cast<const void *>(unpack4_mn_kernel<1>)})
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+      return r;
+    });
+    if (e != cudaSuccess) return e;
+    if (smem > kPersistSmem) return cudaErrorInvalidValue;
+  }
+  if (n_inputs % 16 == 0)
+    unpack4_mn_kernel<16><<<ctas, 256, smem, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0, n_chan);
+  else if (n_inputs % 4 == 0)
+    unpack4_mn_kernel<4><<<ctas, 256, smem, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0, n_chan);
+  else
+    unpack4_mn_kernel<1><<<ctas, 256, smem, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0, n_chan);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
                                      int n_time, int n_tiles, int kb, int64_t chan0, int n_chan,
                                      uint8_t *op, int ctas, cudaStream_t s) {
   const int n_rows = n_tiles * kTile;
   if (n_chan <= 0) return cudaSuccess;
-  if (ctas < 1 || (sample_bits == 8 && n_inputs % 2) || (sample_bits == 4 && n_inputs % 4))
-    return cudaErrorInvalidValue;
+  if (ctas < 1 || (sample_bits == 8 && n_inputs % 2)) return cudaErrorInvalidValue;
+  if (sample_bits == 4)  // kept off the correlate's SMs by its dynamic shared-memory request
+    return launch_unpack4(volt, n_inputs, n_time, n_tiles, kb, chan0, n_chan, op, ctas,
+                          kPersistSmem, s);
   cudaError_t e = once_per_device(g_attr_persist, [] {
     cudaError_t r = cudaFuncSetAttribute(unpack8_persist_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(unpack4_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kPersistSmem);
+    for (const void *f : {reinterpret_cast<const void *>(unpack4_mn_kernel<16>),
+                          reinterpret_cast<const void *>(unpack4_mn_kernel<4>),
+                          reinterpret_cast<const void *>(unpack4_mn_kernel<1>)})
+      if (r == cudaSuccess) r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
     return r;
   });
   if (e != cudaSuccess) return e;
-  if (sample_bits == 8)
-    unpack8_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
-                                                           chan0, n_chan);
-  else
-    unpack4_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
-                                                           chan0, n_chan);
+  unpack8_persist_kernel<<<ctas, 512, kPersistSmem, s>>>(volt, op, n_inputs, n_time, n_rows, kb,
+                                                         chan0, n_chan);
   return cudaGetLastError();
 }
 
 // Raw rows that are whole 16-byte units: the box comes by 2D TMA; rows that
-// are whole 4-byte units: the threads load it.
+// are whole 4-byte units: the threads load it (8-bit samples).
 bool unpack_tile_tma_in(int sample_bits, int n_inputs) {
-  return (sample_bits == 8 && n_inputs % 8 == 0) || (sample_bits == 4 && n_inputs % 16 == 0);
+  return sample_bits == 8 && n_inputs % 8 == 0;
 }
 
+// The small-footprint form (the tile kernel for 8-bit samples, the streaming
+// kernel for 4-bit samples, which takes any N).
 bool unpack_tile_supported(int sample_bits, int n_inputs) {
-  return (sample_bits == 8 && n_inputs % 2 == 0) || (sample_bits == 4 && n_inputs % 4 == 0);
+  return (sample_bits == 8 && n_inputs % 2 == 0) || sample_bits == 4;
 }
 
 int unpack_tile_smem_bytes() { return 1024 + kTile * kRowBytes + kTileRawBytes; }
@@ -606,6 +546,16 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
                                cudaStream_t s) {
   if (n_chan <= 0) return cudaSuccess;
   if (ctas < 1 || !unpack_tile_supported(sample_bits, n_inputs)) return cudaErrorInvalidValue;
+  if (sample_bits == 4) {
+    // (`ctas` counts 128-thread tile CTAs; the streaming kernel's CTAs have 256;
+    // run alone it takes MWAX_U4_CTAS_PER_SM per SM)
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorInvalidDevice;
+    const int n = ctas >= 6 * sms ? MWAX_U4_CTAS_PER_SM * sms : (ctas > 1 ? ctas / 2 : 1);
+    return launch_unpack4(volt, n_inputs, n_time, n_tiles, kb, chan0, n_chan, op, n, 0, s);
+  }
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *ptr = nullptr;
@@ -616,19 +566,18 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
       return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
   }
-  // input: [ (chan0 + n_chan) * T rows ][ row bytes ], no swizzle; the box is
-  // one 128-input tile of one time block: 256 B x 32 rows (8-bit samples) or
-  // 128 B x 64 rows (4-bit samples)
+  // input: [ (chan0 + n_chan) * T rows ][ 2N bytes ], no swizzle; the box is
+  // one 128-input tile of one time block: 256 B x 32 rows
   const cuuint64_t in_rows = (cuuint64_t)(chan0 + n_chan) * n_time;
   const cuuint64_t out_rows = (cuuint64_t)n_chan * kb * n_tiles * kTile;
   if (in_rows > 0x7FFFFFFFull || out_rows > 0x7FFFFFFFull) return cudaErrorInvalidValue;
   CUtensorMap in_map, out_map;
   memset(&in_map, 0, sizeof(in_map));
   const bool tma_in = unpack_tile_tma_in(sample_bits, n_inputs);
-  const cuuint64_t row_bytes = (cuuint64_t)n_inputs * (sample_bits == 8 ? 2 : 1);
+  const cuuint64_t row_bytes = (cuuint64_t)n_inputs * 2;
   cuuint64_t idims[2] = {row_bytes, in_rows};
   cuuint64_t istr[1] = {row_bytes};
-  cuuint32_t ibox[2] = {sample_bits == 8 ? 256u : 128u, sample_bits == 8 ? 32u : 64u};
+  cuuint32_t ibox[2] = {256u, 32u};
   cuuint32_t estr[2] = {1, 1};
   if (tma_in &&
       encode(&in_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(volt), idims, istr, ibox,
@@ -649,20 +598,14 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
     };
     cudaError_t r = set(reinterpret_cast<const void *>(unpack8_tile_kernel<true>));
     if (r == cudaSuccess) r = set(reinterpret_cast<const void *>(unpack8_tile_kernel<false>));
-    if (r == cudaSuccess) r = set(reinterpret_cast<const void *>(unpack4_tile_kernel<true>));
-    if (r == cudaSuccess) r = set(reinterpret_cast<const void *>(unpack4_tile_kernel<false>));
     return r;
   });
   if (ea != cudaSuccess) return ea;
 #define MWAX_TILE_ARGS in_map, out_map, volt, n_inputs, n_time, n_tiles, kb, chan0, n_chan, status, timeout_ns
-  if (sample_bits == 8 && tma_in)
+  if (tma_in)
     unpack8_tile_kernel<true><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
-  else if (sample_bits == 8)
-    unpack8_tile_kernel<false><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
-  else if (tma_in)
-    unpack4_tile_kernel<true><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
   else
-    unpack4_tile_kernel<false><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
+    unpack8_tile_kernel<false><<<ctas, kTileThreads, smem, s>>>(MWAX_TILE_ARGS);
 #undef MWAX_TILE_ARGS
   return cudaGetLastError();
 }
@@ -672,6 +615,14 @@ cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, in
                           int variant_req, cudaStream_t s) {
   const int n_rows = n_tiles * kTile;
   if (n_chan <= 0) return cudaSuccess;
+  if (sample_bits == 4) {  // one form for 4-bit samples: 8 streaming CTAs per SM
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorInvalidDevice;
+    return launch_unpack4(volt, n_inputs, n_time, n_tiles, kb, chan0, n_chan, op,
+                          MWAX_U4_CTAS_PER_SM * sms, 0, s);
+  }
   // variant: 0 = automatic, 1 = shared-memory transpose, 2 = full-line;
   // MWAX_UNPACK overrides the automatic choice (tuning experiments)
   static const int env_variant = [] {
@@ -680,23 +631,14 @@ cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, in
   }();
   const int variant = variant_req != 0 ? variant_req : env_variant;
   const bool line8 = variant == 2;
-  const bool line4 = variant != 1;
-  if (line8 && sample_bits == 8 && n_inputs % 2 == 0 && kb <= 65535 && n_chan <= 65535) {
+  if (line8 && n_inputs % 2 == 0 && kb <= 65535 && n_chan <= 65535) {
     dim3 g((n_rows / 2 + 127) / 128, kb, n_chan);
     unpack8_line_kernel<<<g, 128, 0, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0);
     return cudaGetLastError();
   }
-  if (line4 && sample_bits == 4 && n_inputs % 4 == 0 && kb * 2 <= 65535 && n_chan <= 65535) {
-    dim3 g((n_rows / 4 + 127) / 128, kb * 2, n_chan);
-    unpack4_line_kernel<<<g, 128, 0, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0);
-    return cudaGetLastError();
-  }
   if (kb > 65535 || n_chan > 65535) return cudaErrorInvalidValue;
   dim3 grid((n_rows + kRowsPerCta - 1) / kRowsPerCta, kb, n_chan);
-  if (sample_bits == 4)
-    unpack_kernel<4><<<grid, 256, 0, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0);
-  else
-    unpack_kernel<8><<<grid, 256, 0, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0);
+  unpack8_kernel<<<grid, 256, 0, s>>>(volt, op, n_inputs, n_time, n_rows, kb, chan0);
   return cudaGetLastError();
 }
 

@@ -582,7 +582,7 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
       return MWAX_ERR_INVALID_ARG;
     }
     const int64_t one = s.op_chan_bytes * s.chan_group;
-    const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : s.job.n_inputs % 4 == 0;
+    const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : true;
     // unpack_sms 0: the small unpack CTA runs beside the correlate on every SM
     // where the shape allows it, else 20 SMs are set aside for the unpack
     // (pair mode fills the shared memory: no room for a co-resident unpack CTA)

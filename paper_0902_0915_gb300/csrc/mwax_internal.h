@@ -22,9 +22,11 @@ struct NvtxRange {
 
 namespace mwax {
 
-// Tensor-core tiling: a tile is 128 inputs (the MMA M and N extent); an
-// operand row block is 128 bytes, one 128-byte swizzle row, holding S
-// samples of re followed by S samples of im for one input.
+// Tensor-core tiling: a tile is 128 inputs (the MMA M and N extent) of one
+// block of S time samples, 128 rows of 128 bytes (one 128-byte swizzle row
+// each): for 8-bit samples a row per input, S re then S im values; for 4-bit
+// samples a row per sample and plane (S re rows, then S im rows), each row the
+// tile's 128 inputs.
 constexpr int kTile = 128;
 constexpr int kRowBytes = 128;
 
@@ -36,28 +38,30 @@ inline int sample_max(int sample_bits) { return sample_bits == 4 ? 7 : 127; }
 cudaError_t launch_plain_channel(const uint8_t *volt_chan, int sample_bits, int n_inputs,
                                  int n_time, int32_t *out_chan, cudaStream_t s);
 
-// ---- unpack: packed samples -> tensor-core operand rows --------------------
-// volt: [n_chan_total][T][N] packed; op: [n_chan][kb][n_tiles*128][128 B].
-// variant: 0 = automatic, 1 = shared-memory transpose, 2 = full-line (no
-// shared memory, 128 threads: fits beside a running correlate CTA).
+// ---- unpack: packed samples -> tensor-core operand tiles -------------------
+// volt: [n_chan_total][T][N] packed.  op, 8-bit samples (K-major):
+// [n_chan][kb][n_tiles*128][128 B]; 4-bit samples (MN-major):
+// [n_chan][kb][2 planes x 64 samples][n_tiles*128 bytes].  Same size per
+// channel either way.  variant (8-bit): 0 = automatic, 1 = shared-memory
+// transpose, 2 = full-line; 4-bit samples have one form (the streaming kernel).
 cudaError_t launch_unpack(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
                           int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
                           int variant, cudaStream_t s);
 
 // Persistent unpack on `ctas` CTAs that cannot share an SM with a correlate
 // CTA (used when the unpack of the next channel group runs beside the
-// correlation of the current one on disjoint SMs).  Needs even N (8-bit) or
-// N % 4 == 0 (4-bit).
+// correlation of the current one on disjoint SMs).  Needs even N (8-bit).
 cudaError_t launch_unpack_persistent(const uint8_t *volt, int sample_bits, int n_inputs,
                                      int n_time, int n_tiles, int kb, int64_t chan0, int n_chan,
                                      uint8_t *op, int ctas, cudaStream_t s);
 
-// Tile unpack (one 128-input tile x one time block per task, ~25 KB of
-// shared memory: several CTAs per SM when it runs alone, one beside a
-// resident correlate CTA when it overlaps; TMA store of the operand tile; the
-// raw box by 2D TMA where the sample rows are whole 16-byte units, else loaded
-// by the threads); 8-bit samples with n_inputs even, 4-bit samples with
-// n_inputs % 4 == 0.
+// Small-footprint unpack.  8-bit samples with n_inputs even: the tile kernel
+// (one 128-input tile x one time block per task, ~25 KB of shared memory:
+// several CTAs per SM when it runs alone, one beside a resident correlate CTA
+// when it overlaps; TMA store of the operand tile; the raw box by 2D TMA where
+// the sample rows are whole 16-byte units, else loaded by the threads).
+// 4-bit samples, any n_inputs: the streaming kernel (no shared memory) on
+// ctas / 2 CTAs of 256 threads.
 bool unpack_tile_supported(int sample_bits, int n_inputs);
 cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_inputs, int n_time,
                                int n_tiles, int kb, int64_t chan0, int n_chan, uint8_t *op,
@@ -67,7 +71,7 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
 #define MWAX_MAX_JOBS 8
 
 struct TcJob {
-  const uint8_t *op;  // operand rows [n_chan][kb][n_tiles*128][128 B]
+  const uint8_t *op;  // operand tiles of n_chan channels (layout: see launch_unpack)
   void *out;          // visibilities of the first of these n_chan channels
   int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks, n_chan;
   int64_t n_bl;
