@@ -1102,6 +1102,7 @@ def main():
                    "l2": f"inputs {vol.numel() / 1e9:.1f} GB > 129 MB L2 (no flush needed)",
                    "chan_group": info.chan_group, "flush_blocks": info.flush_blocks,
                    "mma_shape": info.mma_shape, "stages": info.stages, "prefetch": info.prefetch,
+                   "k_split": info.k_split,
                    "pipeline": info.pipeline,
                    "checked_segment": None if not info.checked_segment else {
                        "recomputed_channels": recomputed,

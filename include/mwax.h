@@ -113,7 +113,17 @@ typedef struct {
                               CTA beside the correlate CTA on every SM (8-bit samples,
                               n_inputs a multiple of 8; other shapes use 20); k > 0 = k
                               SMs run the unpack while the correlate runs on the others */
-  int32_t reserved[1];     /* must be zero                                                */
+  int32_t k_split;         /* tuning, exact kind in pair mode (mma_shape 3, or auto where it
+                              applies) only: every work item's time blocks are cut into
+                              k_split consecutive ranges, each a work item of its own
+                              (the time-chunk depth of an item), whose partial int32
+                              sums are added into the output with integer atomic adds
+                              (exact: every partial is bounded by the whole integration's
+                              int32 bound; the plan zeroes the output first).  For jobs
+                              whose items alone cannot fill the SMs.  1..8 and at most
+                              half the time blocks; 0 = auto: 1, or, when a launch has
+                              at most half as many items as SMs, the largest k <= 8 with
+                              items x k <= SMs and k <= time blocks / 2            */
 } mwax_job;
 
 /* Read-only description of a plan's choices. */
@@ -144,7 +154,7 @@ typedef struct {
                                 next 8 calls run the narrow shape directly.  Chosen
                                 when kind is exact and mma_shape and flush_blocks are
                                 auto (0) or mma_shape is 3.  0 otherwise.               */
-  int32_t reserved_info;
+  int32_t k_split;           /* time ranges per pair-mode item (largest over the jobs) */
 } mwax_plan_info;
 
 typedef struct mwax_plan_s *mwax_plan_t;
@@ -230,7 +240,7 @@ typedef struct {
 } mwax_tune_report;
 
 /* Choose the tuning fields of a tensor-engine job (mma_shape, stages,
- * prefetch, pipeline, chan_group) by timing candidate configurations with
+ * prefetch, pipeline, chan_group, k_split) by timing candidate configurations with
  * CUDA events on `voltages` / `out` (device buffers of the job's shape,
  * contents of `out` are overwritten) on `stream`.  Writes the choice into
  * *job and, when the environment variable MWAX_TUNE_CACHE names a file,
@@ -240,8 +250,12 @@ typedef struct {
 mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaStream_t stream,
                           mwax_tune_report *report);
 
-/* The same for a batch: one shared choice of mma_shape, stages and prefetch
- * for all jobs (voltages[k], out[k] as for mwax_correlate_batch). */
+/* The same for a batch (voltages[k], out[k] as for mwax_correlate_batch):
+ * first one choice of mma_shape, stages and prefetch for the launch (every
+ * job runs in the one persistent kernel), then, job by job with the others
+ * fixed, each job's k_split (1, 2, 4 or 8 time ranges per work item; a
+ * setting replaces the automatic one only when the whole batch call is more
+ * than 1 % faster).  default_ms is the batch plan's own default. */
 mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *voltages,
                                 void *const *out, cudaStream_t stream, mwax_tune_report *report);
 

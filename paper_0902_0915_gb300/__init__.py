@@ -41,7 +41,7 @@ class Job(ctypes.Structure):
                 ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("mma_shape", ctypes.c_int32), ("pipeline", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("test_fault", ctypes.c_int32),
-                ("unpack_sms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("unpack_sms", ctypes.c_int32), ("k_split", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -51,7 +51,7 @@ class PlanInfo(ctypes.Structure):
                 ("stages", ctypes.c_int32), ("prefetch", ctypes.c_int32),
                 ("mma_shape", ctypes.c_int32), ("pipeline", ctypes.c_int32),
                 ("scratch_bytes", ctypes.c_int64), ("work_items", ctypes.c_int64),
-                ("checked_segment", ctypes.c_int32), ("reserved_info", ctypes.c_int32)]
+                ("checked_segment", ctypes.c_int32), ("k_split", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -199,12 +199,12 @@ def _stream_handle(stream=None) -> int:
 
 def _job(n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, engine=ENGINE_TENSOR,
          flush_blocks=0, chan_group=0, stages=0, prefetch=0, mma_shape=0, pipeline=0,
-         timeout_ms=0, test_fault=0, unpack_sms=0) -> Job:
+         timeout_ms=0, test_fault=0, unpack_sms=0, k_split=0) -> Job:
     j = Job()
     j.n_inputs, j.n_chan, j.n_time, j.sample_bits = n_inputs, n_chan, n_time, sample_bits
     j.kind, j.engine, j.flush_blocks, j.chan_group = kind, engine, flush_blocks, chan_group
     j.stages, j.prefetch, j.mma_shape, j.pipeline = stages, prefetch, mma_shape, pipeline
-    j.timeout_ms, j.test_fault, j.unpack_sms = timeout_ms, test_fault, unpack_sms
+    j.timeout_ms, j.test_fault, j.unpack_sms, j.k_split = timeout_ms, test_fault, unpack_sms, k_split
     return j
 
 
@@ -219,10 +219,10 @@ class Plan:
     def __init__(self, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,
                  engine=ENGINE_TENSOR, flush_blocks=0, chan_group=0, stages=0, prefetch=0,
                  mma_shape=0, pipeline=0, timeout_ms=0, test_fault=0, unpack_sms=0,
-                 stream=None):
+                 k_split=0, stream=None):
         self.job = _job(n_inputs, n_chan, n_time, sample_bits, kind, engine, flush_blocks,
                         chan_group, stages, prefetch, mma_shape, pipeline, timeout_ms, test_fault,
-                        unpack_sms)
+                        unpack_sms, k_split)
         self.shape = (n_inputs, n_chan, n_time)
         self.sample_bits, self.kind, self.engine = sample_bits, kind, engine
         self._h = _P()
@@ -379,11 +379,17 @@ class BatchPlan:
     replayed from a CUDA graph (see include/mwax.h: mwax_plan_batch)."""
 
     def __init__(self, jobs, sample_bits=4, kind=KIND_EXACT, stream=None, mma_shape=0, stages=0,
-                 prefetch=0):
+                 prefetch=0, k_split=None):
+        """jobs: (n_inputs, n_chan, n_time) per job; k_split: None (every job
+        automatic) or one value per job (see mwax_job.k_split)."""
         self.shapes = [tuple(j) for j in jobs]
         self.sample_bits, self.kind = sample_bits, kind
+        ks = [0] * len(jobs) if k_split is None else list(k_split)
+        if len(ks) != len(jobs):
+            raise ValueError("k_split needs one value per job")
         arr = (Job * len(jobs))(*[_job(n, c, t, sample_bits, kind, mma_shape=mma_shape,
-                                       stages=stages, prefetch=prefetch) for (n, c, t) in jobs])
+                                       stages=stages, prefetch=prefetch, k_split=k)
+                                  for (n, c, t), k in zip(jobs, ks)])
         self._h = _P()
         self.stream = stream if stream is not None else _torch().cuda.current_stream()
         _check(lib().mwax_plan_batch(ctypes.byref(self._h), arr, len(jobs), self.stream.cuda_stream),
@@ -432,7 +438,7 @@ class BatchPlan:
             pass
 
 
-TUNE_FIELDS = ("mma_shape", "stages", "prefetch", "pipeline", "chan_group")
+TUNE_FIELDS = ("mma_shape", "stages", "prefetch", "pipeline", "chan_group", "k_split")
 
 
 def autotune(voltages, out, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT, stream=None):
@@ -446,7 +452,8 @@ def autotune(voltages, out, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXA
 
 
 def autotune_batch(jobs, voltages, outs, sample_bits=4, kind=KIND_EXACT, stream=None):
-    """Batch variant: one shared (mma_shape, stages, prefetch) for all jobs."""
+    """Batch variant: one (mma_shape, stages, prefetch) for the launch, then
+    each job's k_split; returns the BatchPlan keyword arguments and the report."""
     k = len(jobs)
     arr = (Job * k)(*[_job(n, c, t, sample_bits, kind) for (n, c, t) in jobs])
     vin = (_P * k)(*[v.data_ptr() for v in voltages])
@@ -454,7 +461,9 @@ def autotune_batch(jobs, voltages, outs, sample_bits=4, kind=KIND_EXACT, stream=
     rep = TuneReport()
     _check(lib().mwax_autotune_batch(arr, k, vin, vout, _stream_handle(stream), ctypes.byref(rep)),
            "mwax_autotune_batch")
-    return {f: getattr(arr[0], f) for f in ("mma_shape", "stages", "prefetch")}, rep
+    fields = {f: getattr(arr[0], f) for f in ("mma_shape", "stages", "prefetch")}
+    fields["k_split"] = [arr[i].k_split for i in range(k)]
+    return fields, rep
 
 
 def correlate(voltages, n_inputs, n_chan, n_time, sample_bits, kind=KIND_EXACT,

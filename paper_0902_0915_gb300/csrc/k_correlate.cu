@@ -355,7 +355,10 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
 // ---- pair-mode work items -------------------------------------------------
 // One int4 per item: x = channel of the first pair, y = channel of the second
 // (both relative to the launch's first channel), z = job | type << 8 |
-// I0 << 16 | J0 << 24, w = I1 | J1 << 8.
+// I0 << 16 | J0 << 24, w = I1 | J1 << 8 | split << 16 | n_split << 24: the
+// item covers time blocks [split KB / n_split, (split + 1) KB / n_split)
+// (n_split 1: the whole integration, results stored; n_split > 1: the
+// partial sums are added into the zeroed output with int32 atomics).
 //   kItemShared:  (I0, J0) and (I0, J1 = J0 + 1 <= I0) of channel x; tiles
 //                 [A_J0 | A_J1 | A_I0] (two tiles, [A_J0 | A_I0], when J1 = I0)
 //   kItemTwoDiag: (I0, I0) of channel x and (I1, I1) of channel y; [A_I0 | A_I1]
@@ -363,7 +366,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
 enum : uint32_t { kItemOne = 0, kItemShared = 1, kItemTwoDiag = 2 };
 
 struct PairItem {
-  int job, type, c0, c1, I0, J0, I1, J1;
+  int job, type, c0, c1, I0, J0, I1, J1, split, n_split;
 };
 
 __device__ __forceinline__ PairItem decode_pair_item(const int4 d) {
@@ -377,7 +380,15 @@ __device__ __forceinline__ PairItem decode_pair_item(const int4 d) {
   it.J0 = (int)(z >> 24);
   it.I1 = (int)(w & 0xFFu);
   it.J1 = (int)((w >> 8) & 0xFFu);
+  it.split = (int)((w >> 16) & 0xFFu);
+  it.n_split = (int)(w >> 24);
   return it;
+}
+
+// Time blocks [k0, k1) of an item of a job with KB blocks.
+__device__ __forceinline__ void item_blocks(const PairItem &it, int KB, int &k0, int &k1) {
+  k0 = (int)((int64_t)it.split * KB / it.n_split);
+  k1 = (int)((int64_t)(it.split + 1) * KB / it.n_split);
 }
 
 // The eight MMAs of one K block: N = 128 (one tile pair) or 256 (B spans two
@@ -456,8 +467,10 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
           nt = it.I0 == it.J0 ? 1 : 2;
         }
         const uint32_t blk_bytes = (uint32_t)nt * kTileBytes;
-        for (int kb = 0; kb < jb.kb; kb += Sh::kps) {
-          const int nb = min(Sh::kps, jb.kb - kb);
+        int k0, k1;
+        item_blocks(it, jb.kb, k0, k1);
+        for (int kb = k0; kb < k1; kb += Sh::kps) {
+          const int nb = min(Sh::kps, k1 - kb);
           if (!mbar_wait(empty(stage), phase ^ 1u, abort_flag, tmo)) {
             raise_timeout(abort_flag, p.status);
             ok = false;
@@ -497,7 +510,8 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
       bool ok = true;
       for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const PairItem it = decode_pair_item(__ldg(p.items + item));
-        const int KB = p.job[it.job].kb;
+        int k0, k1;
+        item_blocks(it, p.job[it.job].kb, k0, k1);
         // the accumulator is free once the epilogue has read the previous item
         if (!mbar_wait(tempty, (n_it & 1u) ^ 1u, abort_flag, tmo)) {
           raise_timeout(abort_flag, p.status);
@@ -505,8 +519,8 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
         }
         tc_fence_after();
         const uint32_t a_off = it.J1 == it.I0 ? kTileBytes : 2 * kTileBytes;  // A_I of a shared item
-        for (int kb = 0; kb < KB; kb += Sh::kps) {
-          const int nb = min(Sh::kps, KB - kb);
+        for (int kb = k0; kb < k1; kb += Sh::kps) {
+          const int nb = min(Sh::kps, k1 - kb);
           if (!mbar_wait(full(stage), phase, abort_flag, tmo)) {
             raise_timeout(abort_flag, p.status);
             ok = false;
@@ -515,7 +529,7 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
           tc_fence_after();
           for (int j = 0; j < nb; ++j) {
             const uint32_t a = smem_base + (uint32_t)stage * kStageBytes + (uint32_t)(j * Sh::block_bytes);
-            const uint32_t acc0 = kb + j == 0 ? 0u : 1u;
+            const uint32_t acc0 = kb + j == k0 ? 0u : 1u;
             if (it.type == kItemShared) {
               // B = [A_J0 ; A_J1]: columns 0..127 give pair (I, J0), 128..255 pair (I, J1)
               const uint64_t da = Op<BITS>::desc(a + a_off), db = Op<BITS>::desc(a);
@@ -530,7 +544,7 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
               narrow_block<BITS>(d_re, d_im, da, db, acc0);
             }
           }
-          if (kb + nb == KB) tc_commit(tfull);
+          if (kb + nb == k1) tc_commit(tfull);
           tc_commit(empty(stage));
           if (++stage == S) {
             stage = 0;
@@ -622,8 +636,15 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
             const int r = 2 * r2 + (lane >> 4);
             const uint2 val = *reinterpret_cast<const uint2 *>(stg + r * 128 + ((col ^ (r & 15)) << 3));
             const int i = I * kTile + q * 32 + r;
-            if (i < n && j <= i)
-              *reinterpret_cast<uint2 *>(out + 2 * ((int64_t)i * (i + 1) / 2 + j)) = val;
+            if (i < n && j <= i) {
+              uint32_t *dst = out + 2 * ((int64_t)i * (i + 1) / 2 + j);
+              if (it.n_split > 1) {  // one time range of several: exact integer adds
+                atomicAdd(reinterpret_cast<int *>(dst), (int)val.x);
+                atomicAdd(reinterpret_cast<int *>(dst) + 1, (int)val.y);
+              } else {
+                *reinterpret_cast<uint2 *>(dst) = val;
+              }
+            }
           }
           __syncwarp();
         }
@@ -1041,9 +1062,10 @@ void launch_shape(int sample_bits, int kind, int grid, int smem, cudaStream_t s,
     correlate_tc_kernel<8, MWAX_KIND_EXACT, MODE><<<grid, threads, smem, s>>>(maps, kp);
 }
 
-int4 encode_item(int job, uint32_t type, int c0, int c1, int I0, int J0, int I1, int J1) {
+int4 encode_item(int job, uint32_t type, int c0, int c1, int I0, int J0, int I1, int J1,
+                 int split = 0, int n_split = 1) {
   const uint32_t z = (uint32_t)job | type << 8 | (uint32_t)I0 << 16 | (uint32_t)J0 << 24;
-  const uint32_t w = (uint32_t)I1 | (uint32_t)J1 << 8;
+  const uint32_t w = (uint32_t)I1 | (uint32_t)J1 << 8 | (uint32_t)split << 16 | (uint32_t)n_split << 24;
   return make_int4(c0, c1, (int)z, (int)w);
 }
 
@@ -1080,7 +1102,9 @@ cudaError_t launch_exact_check(const int32_t *out, int64_t n_bl, int n_inputs, i
 
 bool pair_mode_supported(const TcJob *jobs, int n_jobs) {
   for (int j = 0; j < n_jobs; ++j)
-    if (jobs[j].kb > jobs[j].flush_blocks || jobs[j].n_tiles > 255) return false;
+    if (jobs[j].kb > jobs[j].flush_blocks || jobs[j].n_tiles > 255 || jobs[j].k_split < 1 ||
+        jobs[j].k_split > jobs[j].kb || jobs[j].k_split > 255)
+      return false;
   return n_jobs >= 1 && n_jobs <= kMaxJobs;
 }
 
@@ -1089,20 +1113,25 @@ bool pair_mode_supported(const TcJob *jobs, int n_jobs) {
 // diagonal pair (I, I) is left over; consecutive leftovers (in the same or the
 // next channel of the job) form a two-diagonal item, and a last unmatched one
 // a single item.  Items of one channel are adjacent, so the CTAs working on a
-// channel at the same time share its operand tiles in L2.
+// channel at the same time share its operand tiles in L2.  A job with
+// k_split > 1 gives every item k_split times, one per time range.
 void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items) {
   items.clear();
   for (int jn = 0; jn < n_jobs; ++jn) {
     const TcJob &job = jobs[jn];
+    const int S = job.k_split;
+    auto push = [&](uint32_t type, int c0, int c1, int I0, int J0, int I1, int J1) {
+      for (int sp = 0; sp < S; ++sp)
+        items.push_back(encode_item(jn, type, c0, c1, I0, J0, I1, J1, sp, S));
+    };
     bool pending = false;
     int pc = 0, pI = 0;
     for (int c = 0; c < job.n_chan; ++c)
       for (int I = 0; I < job.n_tiles; ++I) {
-        for (int J = 0; J + 1 <= I; J += 2)
-          items.push_back(encode_item(jn, kItemShared, c, c, I, J, I, J + 1));
+        for (int J = 0; J + 1 <= I; J += 2) push(kItemShared, c, c, I, J, I, J + 1);
         if ((I + 1) % 2 == 1) {
           if (pending) {
-            items.push_back(encode_item(jn, kItemTwoDiag, pc, c, pI, pI, I, I));
+            push(kItemTwoDiag, pc, c, pI, pI, I, I);
             pending = false;
           } else {
             pending = true;
@@ -1111,7 +1140,7 @@ void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items) {
           }
         }
       }
-    if (pending) items.push_back(encode_item(jn, kItemOne, pc, pc, pI, pI, 0, 0));
+    if (pending) push(kItemOne, pc, pc, pI, pI, 0, 0);
   }
 }
 

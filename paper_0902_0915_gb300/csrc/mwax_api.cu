@@ -24,10 +24,12 @@ namespace {
 constexpr int64_t kExactWindow = int64_t(1) << 24;  // integers exact in FP32
 constexpr int64_t kDefaultScratchBudget = int64_t(8) << 30;
 constexpr unsigned long long kDefaultTimeoutNs = 2000000000ull;  // 2 s per wait
+constexpr int kMaxSplit = 8;  // time ranges per pair-mode work item
 
 struct JobState {
   mwax_job job;
   int n_tiles = 0, n_pairs = 0, spb = 0, kb = 0, flush_blocks = 1, chan_group = 1;
+  int k_split = 1;  // pair mode: time ranges per work item (resolved at plan time)
   int64_t n_bl = 0;
   int64_t op_chan_bytes = 0;  // operand bytes of one channel
   int64_t in_chan_bytes = 0;  // packed input bytes of one channel
@@ -152,8 +154,7 @@ mwax_status check_job(const mwax_job &j) {
     return MWAX_ERR_INVALID_ARG;
   if (j.prefetch < -1 || j.prefetch > 64) return MWAX_ERR_INVALID_ARG;
   if (j.timeout_ms < 0 || j.test_fault < 0 || j.unpack_sms < 0) return MWAX_ERR_INVALID_ARG;
-  for (int k = 0; k < 1; ++k)
-    if (j.reserved[k] != 0) return MWAX_ERR_INVALID_ARG;
+  if (j.k_split < 0 || j.k_split > kMaxSplit) return MWAX_ERR_INVALID_ARG;
   if (j.kind == MWAX_KIND_FP16 && (j.sample_bits != 8 || j.engine != MWAX_ENGINE_TENSOR))
     return MWAX_ERR_UNSUPPORTED;
   if (j.n_inputs > 65536) return MWAX_ERR_UNSUPPORTED;
@@ -239,7 +240,24 @@ TcJob tc_job(const JobState &s, const uint8_t *op, void *out_c0, int nc) {
   tj.flush_blocks = s.flush_blocks;
   tj.n_chan = nc;
   tj.n_bl = s.n_bl;
+  tj.k_split = s.k_split;
   return tj;
+}
+
+// The time ranges per pair-mode work item of a job: the job's own k_split,
+// checked, or automatic -- 1 unless the launch's items (base_items) fill at
+// most half the SMs, then the largest k <= 8 with base_items * k <= SMs and
+// k <= time blocks / 2.  -1: a k_split the job cannot take.
+int resolve_split(const mwax_job &job, int mode, int kb, int64_t base_items, int sm_count) {
+  const bool can = mode == 2 && job.kind == MWAX_KIND_EXACT;
+  if (job.k_split > 0) {
+    if (job.k_split == 1) return 1;
+    return can && 2 * job.k_split <= kb ? job.k_split : -1;
+  }
+  if (!can || base_items < 1 || base_items * 2 > sm_count) return 1;
+  int k = (int)std::min<int64_t>(kMaxSplit, sm_count / base_items);
+  k = std::min(k, kb / 2);
+  return std::max(k, 1);
 }
 
 // Kernel mode for a job's mma_shape (0 = auto: pair mode where every job
@@ -372,7 +390,10 @@ mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op
     if (p->checked) tj.flush_blocks = s.kb;  // one optimistic segment per item
   }
   TimedLaunch tc(p, 1, st);
-  cudaError_t e = launch_correlate_tc(&tj, 1, cfg, st);
+  cudaError_t e = cudaSuccess;
+  if (p->mode == 2 && s.k_split > 1)  // the time ranges' partial sums are added into it
+    e = cudaMemsetAsync(out_c0, 0, (size_t)(nc * s.out_chan_bytes), st);
+  if (e == cudaSuccess) e = launch_correlate_tc(&tj, 1, cfg, st);
   if (e == cudaSuccess && p->checked) {
     e = launch_exact_check(reinterpret_cast<const int32_t *>(out_c0), s.n_bl, s.job.n_inputs, nc,
                            p->bad, p->recomputed, st);
@@ -576,6 +597,15 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
       free_plan(p);
       return MWAX_ERR_UNSUPPORTED;
     }
+    // time ranges per pair-mode item, from the items of one channel group
+    std::vector<int4> base;
+    if (p->mode == 2) build_pair_items(full.data(), 1, base);
+    const int split = resolve_split(*job, p->mode, s.kb, (int64_t)base.size(), p->sm_count);
+    if (split < 0) {
+      free_plan(p);
+      return MWAX_ERR_UNSUPPORTED;
+    }
+    s.k_split = p->jobs[0].k_split = full[0].k_split = split;
     p->stages = job->stages > 0 ? job->stages : correlate_tc_max_stages(p->mode);
     if (p->stages > correlate_tc_max_stages(p->mode)) {
       free_plan(p);
@@ -681,6 +711,17 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
     free_plan(p);
     return MWAX_ERR_UNSUPPORTED;
   }
+  // each job's time ranges per pair-mode item, from the launch's items
+  std::vector<int4> base;
+  if (p->mode == 2) build_pair_items(tj.data(), (int)tj.size(), base);
+  for (int k = 0; k < n_jobs; ++k) {
+    const int split = resolve_split(jobs[k], p->mode, p->jobs[k].kb, (int64_t)base.size(), p->sm_count);
+    if (split < 0) {
+      free_plan(p);
+      return MWAX_ERR_UNSUPPORTED;
+    }
+    p->jobs[k].k_split = tj[k].k_split = split;
+  }
   p->stages = jobs[0].stages > 0 ? jobs[0].stages : correlate_tc_max_stages(p->mode);
   cudaError_t e = p->stages <= correlate_tc_max_stages(p->mode) ? cudaSuccess : cudaErrorInvalidValue;
   if (e == cudaSuccess && p->mode == 2) e = upload_items(p, tj, {});
@@ -713,6 +754,8 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   info->stages = plan->stages;
   info->mma_shape = plan->mode + 1;
   info->checked_segment = plan->checked ? 1 : 0;
+  info->k_split = 1;
+  for (const auto &j : plan->jobs) info->k_split = std::max(info->k_split, j.k_split);
   info->pipeline = plan->overlap ? 2 : 1;
   info->prefetch = plan->prefetch;
   info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
@@ -804,10 +847,14 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
                               s.job.n_chan, s.op, 0, cs);
         }
       } else if (e == cudaSuccess) {
+        // jobs whose items are cut into time ranges add into a zeroed output
+        for (int k = 0; k < nj && e == cudaSuccess; ++k)
+          if (plan->jobs[k].k_split > 1)
+            e = cudaMemsetAsync(out[k], 0, (size_t)(plan->jobs[k].job.n_chan * plan->jobs[k].out_chan_bytes), cs);
         TcLaunch cfg = launch_cfg(plan);
         cfg.items = plan->items;
         cfg.n_items = plan->n_items_full;
-        e = launch_correlate_tc(tj.data(), nj, cfg, cs);
+        if (e == cudaSuccess) e = launch_correlate_tc(tj.data(), nj, cfg, cs);
       }
       cudaError_t e2 = cudaStreamEndCapture(cs, &g);
       if (e == cudaSuccess) e = e2;

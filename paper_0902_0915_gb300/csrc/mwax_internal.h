@@ -75,6 +75,9 @@ struct TcJob {
   void *out;          // visibilities of the first of these n_chan channels
   int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks, n_chan;
   int64_t n_bl;
+  // pair mode: time ranges per work item (1: whole integration; > 1: each
+  // range's partial sums are added into the zeroed output with int32 atomics)
+  int32_t k_split = 1;
 };
 
 struct TcLaunch {
@@ -106,7 +109,7 @@ int correlate_tc_max_stages(int mode);
 cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode);
 
 // Pair mode needs every job's integration in one exact segment (kb <=
-// flush_blocks) and at most 255 tiles.
+// flush_blocks), at most 255 tiles and 1 <= k_split <= min(kb, 255).
 bool pair_mode_supported(const TcJob *jobs, int n_jobs);
 // The pair-mode work list of one launch over `jobs` (16 bytes per item).
 void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items);

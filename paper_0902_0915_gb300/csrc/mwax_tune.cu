@@ -1,9 +1,10 @@
 // mwax_tune.cu -- autotuner for the tensor-core correlator.
 //
 // Picks the tuning fields of an mwax_job (MMA shape, shared-memory stages,
-// L2 prefetch distance, unpack/correlate pipelining, channels per pass) by
-// timing candidate configurations with CUDA events on the caller's own
-// device buffers, on the caller's stream.  The choice can be cached in a
+// L2 prefetch distance, unpack/correlate pipelining, channels per pass, time
+// ranges per work item) by timing candidate configurations with CUDA events
+// on the caller's own device buffers, on the caller's stream.  For a batch,
+// the launch-wide fields first, then each job's time ranges per work item.  The choice can be cached in a
 // text file named by the environment variable MWAX_TUNE_CACHE, one line per
 // (device, shape) key; mwax_plan applies a cached choice to jobs whose
 // tuning fields are all zero.
@@ -21,7 +22,7 @@ namespace mwax {
 namespace {
 
 struct Cand {
-  int mma_shape, stages, prefetch, pipeline, chan_group;
+  int mma_shape, stages, prefetch, pipeline, chan_group, k_split;
 };
 
 // Timed calls per candidate (after one untimed call).
@@ -54,8 +55,8 @@ bool cache_lookup(const std::string &key, Cand *c, double *ms) {
     char k[600];
     Cand t;
     double m = 0;
-    if (sscanf(line, "%599s %d %d %d %d %d %lf", k, &t.mma_shape, &t.stages, &t.prefetch,
-               &t.pipeline, &t.chan_group, &m) == 7 &&
+    if (sscanf(line, "%599s %d %d %d %d %d %d %lf", k, &t.mma_shape, &t.stages, &t.prefetch,
+               &t.pipeline, &t.chan_group, &t.k_split, &m) == 8 &&
         key == k) {
       *c = t;  // the last matching line wins
       *ms = m;
@@ -72,8 +73,8 @@ void cache_store(const std::string &key, const Cand &c, double ms) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   FILE *f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d %d %.6f\n", key.c_str(), c.mma_shape, c.stages, c.prefetch,
-          c.pipeline, c.chan_group, ms);
+  fprintf(f, "%s %d %d %d %d %d %d %.6f\n", key.c_str(), c.mma_shape, c.stages, c.prefetch,
+          c.pipeline, c.chan_group, c.k_split, ms);
   fclose(f);
 }
 
@@ -83,6 +84,7 @@ void apply(mwax_job *j, const Cand &c) {
   j->prefetch = c.prefetch;
   j->pipeline = c.pipeline;
   j->chan_group = c.chan_group;
+  j->k_split = c.k_split;
 }
 
 // Mean device time of `reps` calls (after one warm-up), or a negative value
@@ -133,12 +135,13 @@ double time_batch(const std::vector<mwax_job> &jobs, const void *const *volt, vo
 bool valid(const Cand &c) {
   const bool shape_ok = c.mma_shape >= 0 && c.mma_shape <= 3;
   const int max_st = correlate_tc_max_stages(c.mma_shape > 0 ? c.mma_shape - 1 : 0);
-  return shape_ok && (c.stages == 0 || (c.stages >= 2 && c.stages <= max_st));
+  return shape_ok && (c.stages == 0 || (c.stages >= 2 && c.stages <= max_st)) && c.k_split >= 0 &&
+         c.k_split <= 8;
 }
 
 bool all_auto(const mwax_job &j) {
   return j.mma_shape == 0 && j.stages == 0 && j.prefetch == 0 && j.pipeline == 0 &&
-         j.chan_group == 0;
+         j.chan_group == 0 && j.k_split == 0;
 }
 
 }  // namespace
@@ -180,7 +183,7 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
     return MWAX_OK;
   }
   mwax_job base = *job;
-  apply(&base, Cand{0, 0, 0, 0, 0});
+  apply(&base, Cand{0, 0, 0, 0, 0, 0});
   // Candidate 0 is the plan's own default (every field automatic: the pair
   // mode where the integration is one exact segment, the checked single
   // segment for longer 8-bit exact jobs, else the narrow shape), so the
@@ -188,9 +191,12 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
   // replace it by being measurably faster.  An explicit pair request
   // (mma_shape 3) on a job longer than one exact segment plans as the
   // checked single segment; explicit flush segments are not candidates.
+  // Pair-mode candidates with time ranges per item fail to plan (and are
+  // skipped) where the job cannot take them (FP16 kind, too few time blocks).
   const std::vector<Cand> cands = {
-      {0, 0, 0, 0, 0},  {3, 0, -1, 1, 0}, {1, 2, -1, 1, 0}, {1, 2, 8, 1, 0}, {2, 4, -1, 1, 0},
-      {2, 3, -1, 1, 0}, {1, 2, -1, 2, 0}, {3, 0, -1, 2, 0},
+      {0, 0, 0, 0, 0, 0},  {3, 0, -1, 1, 0, 1}, {3, 0, -1, 1, 0, 2}, {3, 0, -1, 1, 0, 4},
+      {3, 0, -1, 1, 0, 8}, {1, 2, -1, 1, 0, 0}, {1, 2, 8, 1, 0, 0},  {2, 4, -1, 1, 0, 0},
+      {2, 3, -1, 1, 0, 0}, {1, 2, -1, 2, 0, 0}, {3, 0, -1, 2, 0, 1},
   };
   best_ms = -1.0;
   for (const Cand &c : cands) {
@@ -221,9 +227,9 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
   memset(&rep, 0, sizeof(rep));
   std::vector<mwax_job> base(jobs, jobs + n_jobs);
   // candidate 0: the batch plan's own default (all fields automatic)
-  const std::vector<Cand> cands = {{0, 0, 0, 0, 0},  {3, 0, -1, 0, 0}, {1, 2, -1, 0, 0},
-                                   {1, 2, 8, 0, 0},  {2, 4, -1, 0, 0}, {2, 3, -1, 0, 0}};
-  Cand best{0, 0, 0, 0, 0};
+  const std::vector<Cand> cands = {{0, 0, 0, 0, 0, 0}, {3, 0, -1, 0, 0, 0}, {1, 2, -1, 0, 0, 0},
+                                   {1, 2, 8, 0, 0, 0}, {2, 4, -1, 0, 0, 0}, {2, 3, -1, 0, 0, 0}};
+  Cand best{0, 0, 0, 0, 0, 0};
   double best_ms = -1.0;
   for (const Cand &c : cands) {
     std::vector<mwax_job> js = base;
@@ -245,6 +251,21 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
     jobs[k].mma_shape = best.mma_shape;
     jobs[k].stages = best.stages;
     jobs[k].prefetch = best.prefetch;
+    jobs[k].k_split = 0;
+  }
+  // then each job's time ranges per work item, one job at a time with the
+  // others fixed (the automatic choice first; a split must be >1% faster)
+  for (int k = 0; k < n_jobs; ++k) {
+    for (const int ks : {1, 2, 4, 8}) {
+      std::vector<mwax_job> js(jobs, jobs + n_jobs);
+      js[k].k_split = ks;
+      const double ms = time_batch(js, voltages, out, stream, kTuneReps);
+      rep.candidates++;
+      if (ms > 0 && ms < 0.99 * best_ms) {
+        best_ms = ms;
+        jobs[k].k_split = ks;
+      }
+    }
   }
   rep.best_ms = best_ms;
   if (report) *report = rep;

@@ -484,3 +484,90 @@ def test_full_size_c3_batched_sampled(mw):
     torch.cuda.empty_cache()
     for s, chans, got in picks:
         assert_exact(got, oracle_for(s, chans), s.name)
+
+
+# ---------------------------------------------------------------------------
+# time ranges per work item (k_split): partial sums added with int32 atomics
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("bits,N,T,C,G,ks", [
+    (4, 64, 1000, 5, 0, 2), (4, 64, 1000, 3, 0, 8), (4, 200, 333, 4, 3, 3), (4, 300, 640, 2, 0, 5),
+    (8, 100, 500, 3, 0, 2), (8, 256, 2000, 3, 2, 4), (8, 130, 96, 2, 0, 1)])
+def test_split_items_exact(mw, bits, N, T, C, G, ks):
+    """Every pair-mode item cut into ks time ranges (ragged range lengths,
+    channel groups with a ragged last group, the 8-bit checked segment at
+    T = 2000): bit-exact, and a second call on the same output buffer too
+    (the plan zeroes it before adding)."""
+    import torch
+
+    spec = synth.Spec("ks", N, C, T, bits, seed=N + T + ks, sigma=2 if bits == 4 else 40,
+                      tone_amp=0.3)
+    v = device_volt(spec)
+    kw = {"chan_group": G} if G else {}
+    p = mw.Plan(N, C, T, bits, mma_shape=3, k_split=ks, **kw)
+    assert p.info().k_split == ks
+    out = p.correlate(v)
+    out = p.correlate(v, out)
+    assert p.status() == 0
+    assert_exact(out.cpu().numpy(), oracle_for(spec, range(C)), f"split {ks}")
+    p.close()
+    torch.cuda.synchronize()
+
+
+def test_split_auto_for_small_jobs(mw):
+    """A job whose items cannot fill the SMs gets time ranges automatically
+    (c0: 32 two-diagonal items on 152 SMs -> 4 ranges); a large one does not;
+    the host-buffer path with ranges is exact."""
+    import torch
+
+    spec = synth.spec_c0()
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4)
+    ks = p.info().k_split
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ks > 1 and p.info().work_items * 1 <= sms * 8
+    ref = oracle_for(spec, range(spec.n_chan))
+    assert_exact(p.correlate(device_volt(spec)).cpu().numpy(), ref, "auto split")
+    h = torch.from_numpy(synth.fill_host(spec).ravel()).pin_memory()
+    out = torch.empty((spec.n_chan, spec.n_inputs * (spec.n_inputs + 1) // 2, 2),
+                      dtype=torch.int32).pin_memory()
+    p.correlate_host(h, out)
+    assert p.status() == 0
+    assert_exact(out.numpy(), ref, "auto split, host buffers")
+    p.close()
+    q = mw.Plan(1024, 64, 2000, 4)
+    assert q.info().k_split == 1
+    q.close()
+
+
+def test_split_rejected_where_it_cannot_apply(mw):
+    with pytest.raises(mw.MwaxError) as e:
+        mw.Plan(100, 2, 1000, 8, kind=mw.KIND_FP16, k_split=2)  # float sums: no atomics
+    assert e.value.status == mw.STATUS_BY_NAME["MWAX_ERR_UNSUPPORTED"]
+    with pytest.raises(mw.MwaxError) as e:
+        mw.Plan(100, 2, 100, 4, k_split=2)  # 2 time blocks: fewer than 2 per range
+    assert e.value.status == mw.STATUS_BY_NAME["MWAX_ERR_UNSUPPORTED"]
+    with pytest.raises(mw.MwaxError) as e:
+        mw.Plan(100, 2, 1000, 4, mma_shape=1, k_split=2)  # narrow shape: not pair mode
+    assert e.value.status == mw.STATUS_BY_NAME["MWAX_ERR_UNSUPPORTED"]
+    with pytest.raises(mw.MwaxError) as e:
+        mw.Plan(100, 2, 1000, 4, k_split=9)
+    assert e.value.status == mw.STATUS_BY_NAME["MWAX_ERR_INVALID_ARG"]
+
+
+def test_batch_per_job_split(mw):
+    """One persistent launch in which the jobs take different time ranges per
+    item (each job's own k_split): bit-exact for every job, twice."""
+    import torch
+
+    jobs = [(48, 6, 2000), (128, 3, 700), (300, 2, 1000)]
+    specs = [synth.Spec(f"bk{k}", n, c, t, 4, seed=80 + k, sigma=2, tone_amp=0.3)
+             for k, (n, c, t) in enumerate(jobs)]
+    vs = [device_volt(s) for s in specs]
+    bp = mw.BatchPlan(jobs, k_split=[4, 1, 3])
+    assert bp.info().k_split == 4
+    outs = bp.correlate(vs)
+    outs = bp.correlate(vs, outs)
+    assert bp.status() == 0
+    for s, o in zip(specs, outs):
+        assert_exact(o.cpu().numpy(), oracle_for(s, range(s.n_chan)), s.name)
+    bp.close()
+    torch.cuda.synchronize()

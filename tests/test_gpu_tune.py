@@ -74,6 +74,7 @@ def test_batch_autotune_and_graph_timing(mw):
     fields, rep = mw.autotune_batch(jobs, vs, outs)
     assert rep.candidates >= 3 and rep.best_ms > 0
     assert rep.default_ms > 0 and rep.best_ms <= rep.default_ms * 1.0001
+    assert len(fields["k_split"]) == len(jobs) and all(0 <= k <= 8 for k in fields["k_split"])
     bp = mw.BatchPlan(jobs, **fields)
     bp.set_timing(True)
     outs = bp.correlate(vs, outs)
