@@ -689,6 +689,265 @@ __global__ void __launch_bounds__(kCalThreads, 3) calib_jones_tile_kernel(
   }
 }
 
+// Two rows per step: the 24 tile-a quantities of rows ra and rb = ra + 4 (12
+// each) reduce-scattered together -- halving over lane bits 4 (row), 3 and 2,
+// then a sum over bits 1 and 0: 27 shuffles for the two rows instead of 36,
+// and twice the independent work in flight.  Lanes 4h .. 4h + 3 then hold
+// quantities 3h .. 3h + 2 of the 24 (h < 4: row ra, h >= 4: row rb).
+__device__ __forceinline__ void reduce_scatter24(float (&v)[2 * kJQ], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float send = b4 ? v[k] : v[k + 12];
+    const float keep = b4 ? v[k + 12] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float send = b3 ? v[k] : v[k + 6];
+    const float keep = b3 ? v[k + 6] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float send = b2 ? v[k] : v[k + 3];
+    const float keep = b2 ? v[k + 3] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+#pragma unroll
+  for (int o = 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// One row's block (a, b) of V and M into the lane's 64-byte slot
+// [V row 2a | V row 2a+1 | M row 2a | M row 2a+1], 16 bytes each (the two
+// entries of the block in that row).  Of the two rows of the triangle one
+// starts the block on a 16-byte boundary (one 16-byte copy), the other on an
+// 8-byte one (two 8-byte copies); the alignment is the same for every lane of
+// the warp.
+__device__ __forceinline__ void jones_load_row(float4 *slot, const float2 *Vn, const float2 *Mn,
+                                               int a, int b) {
+  const int64_t i0 = 2 * (int64_t)a, i1 = i0 + 1;
+  const int64_t o0 = i0 * (i0 + 1) / 2 + 2 * b, o1 = i1 * (i1 + 1) / 2 + 2 * b;
+  const float2 *src[4] = {Vn + o0, Vn + o1, Mn + o0, Mn + o1};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if ((reinterpret_cast<uintptr_t>(src[e]) & 15u) == 0) {
+      cp_async16(slot + e * 32, src[e]);
+    } else {
+      cp_async8(reinterpret_cast<float2 *>(slot + e * 32), src[e]);
+      cp_async8(reinterpret_cast<float2 *>(slot + e * 32) + 1, src[e] + 1);
+    }
+  }
+}
+
+// The per-row work of the Jones pass: loss, the lane's tile-b sums (col) and
+// the row's twelve tile-a quantities (v, for the reduce-scatter).
+template <bool DEN>
+__device__ __forceinline__ float jones_row(const float4 *slot, float2 ja00, float2 ja01,
+                                           float2 ja10, float2 ja11, float2 jb00, float2 jb01,
+                                           float2 jb10, float2 jb11, float (&col)[kJQ],
+                                           float *v) {
+  const float4 va = slot[0 * 32], vb = slot[1 * 32], ma = slot[2 * 32], mb = slot[3 * 32];
+  const float2 v00 = make_float2(va.x, va.y), v01 = make_float2(va.z, va.w);
+  const float2 v10 = make_float2(vb.x, vb.y), v11 = make_float2(vb.z, vb.w);
+  const float2 m00 = make_float2(ma.x, ma.y), m01 = make_float2(ma.z, ma.w);
+  const float2 m10 = make_float2(mb.x, mb.y), m11 = make_float2(mb.z, mb.w);
+  const float2 z = make_float2(0.f, 0.f);
+  const float2 B00 = cfmac(cfmac(z, m00, jb00), m01, jb01);
+  const float2 B01 = cfmac(cfmac(z, m00, jb10), m01, jb11);
+  const float2 B10 = cfmac(cfmac(z, m10, jb00), m11, jb01);
+  const float2 B11 = cfmac(cfmac(z, m10, jb10), m11, jb11);
+  const float2 R00 = cfma(cfma(make_float2(-v00.x, -v00.y), ja00, B00), ja01, B10);
+  const float2 R01 = cfma(cfma(make_float2(-v01.x, -v01.y), ja00, B01), ja01, B11);
+  const float2 R10 = cfma(cfma(make_float2(-v10.x, -v10.y), ja10, B00), ja11, B10);
+  const float2 R11 = cfma(cfma(make_float2(-v11.x, -v11.y), ja10, B01), ja11, B11);
+  const float l = cabs2(R00) + cabs2(R01) + cabs2(R10) + cabs2(R11);
+  {
+    const float2 g00 = cfmac(cfmac(z, R00, B00), R01, B01);
+    const float2 g01 = cfmac(cfmac(z, R00, B10), R01, B11);
+    const float2 g10 = cfmac(cfmac(z, R10, B00), R11, B01);
+    const float2 g11 = cfmac(cfmac(z, R10, B10), R11, B11);
+    v[0] = g00.x; v[1] = g00.y; v[2] = g01.x; v[3] = g01.y;
+    v[4] = g10.x; v[5] = g10.y; v[6] = g11.x; v[7] = g11.y;
+    if constexpr (DEN) {
+      const float2 d10 = cfmac(cfmac(z, B10, B00), B11, B01);
+      v[8] = cabs2(B00) + cabs2(B01);
+      v[9] = cabs2(B10) + cabs2(B11);
+      v[10] = d10.x;
+      v[11] = d10.y;
+    } else {
+      v[8] = v[9] = v[10] = v[11] = 0.f;
+    }
+  }
+  const float2 A00 = cfma(cfma(z, ja00, m00), ja01, m10);
+  const float2 A01 = cfma(cfma(z, ja00, m01), ja01, m11);
+  const float2 A10 = cfma(cfma(z, ja10, m00), ja11, m10);
+  const float2 A11 = cfma(cfma(z, ja10, m01), ja11, m11);
+  const float2 g00 = ccfma(ccfma(z, R00, A00), R10, A10);
+  const float2 g01 = ccfma(ccfma(z, R00, A01), R10, A11);
+  const float2 g10 = ccfma(ccfma(z, R01, A00), R11, A10);
+  const float2 g11 = ccfma(ccfma(z, R01, A01), R11, A11);
+  col[0] += g00.x; col[1] += g00.y; col[2] += g01.x; col[3] += g01.y;
+  col[4] += g10.x; col[5] += g10.y; col[6] += g11.x; col[7] += g11.y;
+  if constexpr (DEN) {
+    const float2 d10 = ccfma(ccfma(z, A01, A00), A11, A10);
+    col[8] += cabs2(A00) + cabs2(A10);
+    col[9] += cabs2(A01) + cabs2(A11);
+    col[10] += d10.x;
+    col[11] += d10.y;
+  }
+  return l;
+}
+
+// The Jones pass, two rows per step (see reduce_scatter24).  Each lane stages
+// the blocks of row pairs PAIRS - 1 pairs ahead in its own 128-byte slots of a
+// PAIRS-deep shared-memory ring (reads back only what it copied: no barrier);
+// the tile's 32 rows of J_a are staged once per CTA.  Same grid, outputs and
+// summation structure per row as calib_jones_tile_kernel; the quantities of
+// rows 8m + u and 8m + u + 4 (u < 4) are reduced together.
+#ifndef MWAX_JONES_PAIRS
+#define MWAX_JONES_PAIRS 3
+#endif
+constexpr int kJPairs = MWAX_JONES_PAIRS;  // row pairs in the ring: loads kJPairs - 1 pairs ahead
+constexpr int jones2_smem_bytes() {
+  return (kCalThreads / 32) * kJPairs * 2 * 4 * 32 * 16 + kJT * 4 * 8;
+}
+template <bool DEN>
+__global__ void __launch_bounds__(kCalThreads, 2) calib_jones_tile2_kernel(
+    const float2 *__restrict__ V, const float2 *__restrict__ M, const float2 *__restrict__ Jm,
+    int n_tiles, int C, int n_cg, float *__restrict__ part_loss, float *__restrict__ part_row,
+    float *__restrict__ part_col) {
+  constexpr int kWarps = kCalThreads / 32;
+  extern __shared__ __align__(16) float4 sdyn[];
+  // ring [warp][pair slot][row 0/1][4 entries][lane]; afterwards the same memory
+  // holds the per-warp partials [warp][32][12] and the per-warp losses
+  float4 *ringbase = sdyn;
+  float2 *sJ = reinterpret_cast<float2 *>(sdyn + kWarps * kJPairs * 2 * 4 * 32);  // [32 rows][4]
+  static_assert(sizeof(float) * (kWarps * kJT * kJQ + kWarps) <= sizeof(float4) * kWarps * kJPairs * 2 * 4 * 32,
+                "aliasing");
+  const int tile = blockIdx.x, cg = blockIdx.y;
+  int I, Jt;
+  tile_of(tile, I, Jt);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = Jt * kJT + lane;
+  for (int e = threadIdx.x; e < kJT * 4; e += kCalThreads) {
+    const int a = I * kJT + e / 4;
+    sJ[e] = a < n_tiles ? Jm[(int64_t)a * 4 + (e & 3)] : make_float2(0.f, 0.f);
+  }
+  float2 jb00 = make_float2(0.f, 0.f), jb01 = jb00, jb10 = jb00, jb11 = jb00;
+  if (b < n_tiles) {
+    jb00 = Jm[(int64_t)b * 4 + 0];
+    jb01 = Jm[(int64_t)b * 4 + 1];
+    jb10 = Jm[(int64_t)b * 4 + 2];
+    jb11 = Jm[(int64_t)b * 4 + 3];
+  }
+  __syncthreads();
+  const int64_t N = 2 * (int64_t)n_tiles, Bn = N * (N + 1) / 2;
+  const int first = cg + n_cg * w, stride = n_cg * kWarps;
+  const int n_mine = first < C ? (C - 1 - first) / stride + 1 : 0;
+  const int n_pairs = n_mine * (kJT / 2);  // pair p: channel k = p / 16, group m, row u
+  float4 *ring = ringbase + (int64_t)w * kJPairs * 2 * 4 * 32 + lane;
+  auto row_of = [](int p, int h) {  // row h (0/1) of pair p within its channel's tile
+    const int q = p & 15;
+    return 8 * (q >> 2) + (q & 3) + 4 * h;
+  };
+  auto issue = [&](int p) {
+    if (p < n_pairs) {
+      const int nu = first + stride * (p >> 4);
+      const float2 *Vn = V + (int64_t)nu * Bn, *Mn = M + (int64_t)nu * Bn;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float4 *slot = ring + ((p % kJPairs) * 2 + h) * 4 * 32;
+        const int a = I * kJT + row_of(p, h);
+        if (a < n_tiles && b < a) {
+          jones_load_row(slot, Vn, Mn, a, b);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) slot[e * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  float col[kJQ];
+  float row[4][3];
+#pragma unroll
+  for (int q = 0; q < kJQ; ++q) col[q] = 0.f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) row[m][0] = row[m][1] = row[m][2] = 0.f;
+  Kahan loss;
+#pragma unroll
+  for (int k = 0; k < kJPairs - 1; ++k) issue(k);
+  for (int kc = 0; kc < n_mine; ++kc) {
+    float lch = 0.f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll 1
+      for (int u = 0; u < 4; ++u) {
+        const int p = kc * (kJT / 2) + 4 * m + u;
+        issue(p + kJPairs - 1);
+        cp_async_wait<kJPairs - 1>();  // this thread's copies of pair p have landed
+        float v[2 * kJQ];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = 8 * m + u + 4 * h;
+          const float4 *slot = ring + ((p % kJPairs) * 2 + h) * 4 * 32;
+          lch += jones_row<DEN>(slot, sJ[4 * r + 0], sJ[4 * r + 1], sJ[4 * r + 2], sJ[4 * r + 3],
+                                jb00, jb01, jb10, jb11, col, v + kJQ * h);
+        }
+        reduce_scatter24(v, lane);
+        if ((lane & 3) == u) {
+          row[m][0] += v[0];
+          row[m][1] += v[1];
+          row[m][2] += v[2];
+        }
+      }
+    loss.add(lch);
+  }
+  cp_async_wait<0>();
+  __syncthreads();  // every warp is done with the ring
+  float(*sred)[kJT][kJQ] = reinterpret_cast<float(*)[kJT][kJQ]>(ringbase);
+  float *sloss = reinterpret_cast<float *>(ringbase) + kWarps * kJT * kJQ;
+  const int out_idx = tile * n_cg + cg;
+  // lane 16 hi + 4 g + u keeps quantities 3g .. 3g + 2 of row 8m + u + 4 hi
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      sred[w][8 * m + (lane & 3) + 4 * (lane >> 4)][3 * ((lane >> 2) & 3) + k] = row[m][k];
+  float l = loss.s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if (lane == 0) sloss[w] = l;
+  __syncthreads();
+  for (int e = threadIdx.x; e < kJT * kJQ; e += kCalThreads) {
+    float t = 0.f;
+    for (int k = 0; k < kWarps; ++k) t += (&sred[k][0][0])[e];
+    part_row[(int64_t)out_idx * kJT * kJQ + e] = t;
+  }
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < kWarps; ++k) t += sloss[k];
+    part_loss[out_idx] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kJQ; ++q) sred[w][lane][q] = col[q];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kJT * kJQ; e += kCalThreads) {
+    float t = 0.f;
+    for (int k = 0; k < kWarps; ++k) t += (&sred[k][0][0])[e];
+    part_col[(int64_t)out_idx * kJT * kJQ + e] = t;
+  }
+}
+
 // grid: n_jt + 1 blocks of kJT * kJQ threads.  Block K < n_jt: thread (t, q)
 // sums quantity q of tile K*32 + t over the row partials of calibration tiles
 // (K, J <= K) and the column partials of tiles (I >= K, K), every channel
@@ -1001,17 +1260,41 @@ static mwax_status jones_run(const float *V, const float *M, float *J, int n_inp
   float *ploss = pcol + slots * kJT * kJQ;
   const float2 *V2 = reinterpret_cast<const float2 *>(V), *M2 = reinterpret_cast<const float2 *>(M);
   float2 *J2 = reinterpret_cast<float2 *>(J);
+#ifndef MWAX_JONES_ONE_ROW
+  // the two-rows-per-step pass needs more than the default 48 KB of shared memory
+  constexpr int smem2 = jones2_smem_bytes();
+  if (cudaFuncSetAttribute(calib_jones_tile2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem2) != cudaSuccess ||
+      cudaFuncSetAttribute(calib_jones_tile2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem2) != cudaSuccess)
+    return MWAX_ERR_CUDA;
+  auto tile_pass = [&](bool den) {
+    if (den)
+      calib_jones_tile2_kernel<true><<<dim3(tiles, n_cg), kCalThreads, smem2, stream>>>(
+          V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
+    else
+      calib_jones_tile2_kernel<false><<<dim3(tiles, n_cg), kCalThreads, smem2, stream>>>(
+          V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
+  };
+#else
+  auto tile_pass = [&](bool den) {
+    if (den)
+      calib_jones_tile_kernel<true><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
+          V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
+    else
+      calib_jones_tile_kernel<false><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
+          V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
+  };
+#endif
   if (!solve) {
-    calib_jones_tile_kernel<false><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
-        V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
+    tile_pass(false);
     if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
     calib_jones_gather_kernel<false><<<n_jt + 1, kJT * kJQ, 0, stream>>>(
         n_tiles, n_jt, n_cg, ploss, prow, pcol, loss, reinterpret_cast<float2 *>(grad), nullptr, 0);
     return cudaGetLastError() == cudaSuccess ? MWAX_OK : MWAX_ERR_CUDA;
   }
   for (int t = 1; t <= n_iter; ++t) {
-    calib_jones_tile_kernel<true><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
-        V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
+    tile_pass(true);
     if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
     calib_jones_gather_kernel<true><<<n_jt + 1, kJT * kJQ, 0, stream>>>(
         n_tiles, n_jt, n_cg, ploss, prow, pcol, loss ? loss + (t - 1) : nullptr, nullptr, J2,
