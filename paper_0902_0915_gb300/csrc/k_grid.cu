@@ -220,8 +220,18 @@ __device__ __forceinline__ void point_xy(const GridGeom &g, int id, double &x, d
   }
 }
 
-// Patches: a warp owns rows r0 .. r0+3, columns s0 .. s0+7 (lane = row
-// lane / 8, column lane % 8); a CTA runs 8 patches.
+// Patches: a warp owns rows r0 .. r0+3, columns s0 .. s0+7.  The warp's lanes
+// form kGroups groups of 32 / kGroups lanes; group g takes candidates
+// j = g (mod kGroups), and lane l of a group holds kGroups cells of one row
+// (r0 + l / (8 / kGroups), columns s0 + kGroups (l % (8 / kGroups)) + {0 ..
+// kGroups-1}), so one value broadcast and one load of kGroups column factors
+// serve kGroups cells; the groups' sums are added at the end.  A CTA runs 8
+// patches.
+#ifndef MWAX_GRID_GROUPS
+#define MWAX_GRID_GROUPS 2
+#endif
+constexpr int kGroups = MWAX_GRID_GROUPS;  // 1, 2 or 4 (measured: 1.64, 1.42, 1.46 ms per c5 call)
+constexpr int kGLanes = 32 / kGroups, kRowLanes = 8 / kGroups;
 constexpr int kPatchR = 4, kPatchC = 8;
 constexpr int kPatchThreads = 32 * 8;
 
@@ -340,7 +350,7 @@ __global__ void grid_values_kernel(const int *__restrict__ slot, int n_pts, int 
 constexpr int kHeavy = 1024;  // patches with more candidates get a whole CTA
 
 struct Acc {
-  float2 v[4];
+  float2 v[kGroups][4];  // the lane's cells x four polarisation products
 };
 
 // Per-warp staging of 32 candidates: their values (8 floats) and factors
@@ -367,7 +377,10 @@ __device__ __forceinline__ void apply_range(const Patch &pt, int nbw, const int 
                                             const float *__restrict__ wf0,
                                             const float4 *__restrict__ vals, int k0, int k1,
                                             int lane, WarpStage &st, Acc &acc) {
-  const int fx = lane % kPatchC, fy = kPatchC + lane / kPatchC;  // this cell's two factors
+  // group hw takes candidates j + hw; this lane's column factors
+  // kGroups (l % kRowLanes) + {0 .. kGroups-1} and its row factor, l = lane % kGLanes
+  const int hw = lane / kGLanes, hl = lane % kGLanes;
+  const int fx = kGroups * (hl % kRowLanes), fy = kPatchC + hl / kRowLanes;
   // bin rows of the patch: candidate index of each row's first point
   const int n_rows = pt.br_end - pt.r0 + 1;
   if (lane == 0) {
@@ -408,29 +421,67 @@ __device__ __forceinline__ void apply_range(const Patch &pt, int nbw, const int 
     }
     __syncwarp();
     const int n = min(32, k1 - base);
-    for (int j = 0; j < n; ++j) {
-      const float w = st.f[buf][j][fx] * st.f[buf][j][fy];
-      const float4 a = st.v[buf][j][0], b = st.v[buf][j][1];
-      acc.v[0].x += w * a.x;
-      acc.v[0].y += w * a.y;
-      acc.v[1].x += w * a.z;
-      acc.v[1].y += w * a.w;
-      acc.v[2].x += w * b.x;
-      acc.v[2].y += w * b.y;
-      acc.v[3].x += w * b.z;
-      acc.v[3].y += w * b.w;
+    for (int j0 = 0; j0 < n; j0 += kGroups) {
+      const int j = j0 + hw;
+      if (j < n) {
+        float wx[kGroups];
+        if constexpr (kGroups == 4) {
+          const float4 t = *reinterpret_cast<const float4 *>(&st.f[buf][j][fx]);
+          wx[0] = t.x;
+          wx[1] = t.y;
+          wx[2] = t.z;
+          wx[3] = t.w;
+        } else if constexpr (kGroups == 2) {
+          const float2 t = *reinterpret_cast<const float2 *>(&st.f[buf][j][fx]);
+          wx[0] = t.x;
+          wx[1] = t.y;
+        } else {
+          wx[0] = st.f[buf][j][fx];
+        }
+        const float wy = st.f[buf][j][fy];
+        const float4 a = st.v[buf][j][0], b = st.v[buf][j][1];
+#pragma unroll
+        for (int c = 0; c < kGroups; ++c) {
+          const float w = wx[c] * wy;
+          acc.v[c][0].x += w * a.x;
+          acc.v[c][0].y += w * a.y;
+          acc.v[c][1].x += w * a.z;
+          acc.v[c][1].y += w * a.w;
+          acc.v[c][2].x += w * b.x;
+          acc.v[c][2].y += w * b.y;
+          acc.v[c][3].x += w * b.z;
+          acc.v[c][3].y += w * b.w;
+        }
+      }
     }
     __syncwarp();  // this buffer is refilled two steps on
   }
+  // the groups' sums into every lane of group 0 (fixed order: a butterfly
+  // over the group bits)
+#pragma unroll
+  for (int o = kGLanes; o < 32; o <<= 1)
+#pragma unroll
+    for (int c = 0; c < kGroups; ++c)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        acc.v[c][p].x += __shfl_xor_sync(0xffffffffu, acc.v[c][p].x, o);
+        acc.v[c][p].y += __shfl_xor_sync(0xffffffffu, acc.v[c][p].y, o);
+      }
 }
 
+// The lanes of group 0 store their cells (the other groups hold the same sums).
 __device__ __forceinline__ void store_cell(const Patch &pt, int lane, int Ng, const Acc &acc,
                                            float2 *__restrict__ grids) {
-  const int r = pt.r0 + lane / kPatchC, s = pt.s0 + lane % kPatchC;
-  if (r < Ng && s < Ng) {
-    const int64_t cell = (int64_t)r * Ng + s;
+  if (lane >= kGLanes) return;
+  const int r = pt.r0 + lane / kRowLanes, s = pt.s0 + kGroups * (lane % kRowLanes);
+  if (r >= Ng) return;
+  const int64_t cell = (int64_t)r * Ng + s;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) grids[(int64_t)p * Ng * Ng + cell] = acc.v[p];
+  for (int p = 0; p < 4; ++p) {
+    float2 *g = grids + (int64_t)p * Ng * Ng + cell;
+#pragma unroll
+    for (int c = 0; c < kGroups; ++c)
+      if (s + c < Ng) g[c] = acc.v[c][p];
   }
 }
 
@@ -449,26 +500,36 @@ __global__ void __launch_bounds__(kPatchThreads) grid_apply_heavy_kernel(
   const int nw = kPatchThreads / 32;
   Acc acc;
 #pragma unroll
-  for (int p = 0; p < 4; ++p) acc.v[p] = make_float2(0.f, 0.f);
+  for (int c = 0; c < kGroups; ++c)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc.v[c][p] = make_float2(0.f, 0.f);
   apply_range(pt, nbw, offsets, wts + (int64_t)first * kFactors, vals,
               (int)((int64_t)count * warp / nw), (int)((int64_t)count * (warp + 1) / nw), lane,
               stage[warp], acc);
   // the partial sums reuse the staging memory once every warp is done with it
   __syncthreads();
-  float2(*part)[4][32] = reinterpret_cast<float2(*)[4][32]>(stage);
+  float2(*part)[kGroups][4][kGLanes] = reinterpret_cast<float2(*)[kGroups][4][kGLanes]>(stage);
+  static_assert(sizeof(float2) * (kPatchThreads / 32) * 4 * 32 <= sizeof(WarpStage) * (kPatchThreads / 32),
+                "aliasing");
+  if (lane < kGLanes)
 #pragma unroll
-  for (int p = 0; p < 4; ++p) part[warp][p][lane] = acc.v[p];
+    for (int c = 0; c < kGroups; ++c)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) part[warp][c][p][lane] = acc.v[c][p];
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 0 && lane < kGLanes) {
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      float2 t = part[0][p][lane];
-      for (int w = 1; w < nw; ++w) {
-        t.x += part[w][p][lane].x;
-        t.y += part[w][p][lane].y;
+    for (int c = 0; c < kGroups; ++c)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        float2 t = part[0][c][p][lane];
+#pragma unroll 1
+        for (int w = 1; w < nw; ++w) {
+          t.x += part[w][c][p][lane].x;
+          t.y += part[w][c][p][lane].y;
+        }
+        acc.v[c][p] = t;
       }
-      acc.v[p] = t;
-    }
     store_cell(pt, lane, Ng, acc, grids);
   }
 }
@@ -487,7 +548,9 @@ __global__ void __launch_bounds__(kPatchThreads) grid_apply_kernel(
   const int first = __ldg(w_off + idx), count = __ldg(w_off + idx + 1) - first;
   Acc acc;
 #pragma unroll
-  for (int p = 0; p < 4; ++p) acc.v[p] = make_float2(0.f, 0.f);
+  for (int c = 0; c < kGroups; ++c)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc.v[c][p] = make_float2(0.f, 0.f);
   apply_range(pt, nbw, offsets, wts + (int64_t)first * kFactors, vals, 0, count, lane,
               stage[threadIdx.x >> 5], acc);
   store_cell(pt, lane, Ng, acc, grids);
