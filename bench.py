@@ -874,7 +874,7 @@ def run_calib(args):
         "loss": float(loss_j),
         "roofline": {"bound": "hbm", "achieved": ach_j, "peak": float(peaks["hbm_gbs"]),
                      "unit": "GB/s", "frac": ach_j / float(peaks["hbm_gbs"]), "traffic": None,
-                     "kernel": "calib_jones_tile_kernel + calib_jones_gather_kernel (one step)",
+                     "kernel": "calib_jones_tile2_kernel + calib_jones_gather_kernel (one step)",
                      "peak_source": src},
         "solve": {"sweeps": n_sweeps, "ms_per_sweep": ms_js,
                   "value": terms_j / (ms_js / 1e3) / 1e9, "unit": "Gterms/s per sweep",

@@ -444,13 +444,12 @@ __global__ void __launch_bounds__(kCalThreads) calib_chan_gather_kernel(
 //     tile b: G += R^H A,  D += A^H A     (the same for J_b, from V^H)
 // so that grad_t = 2 G_t (= 2 dL/d conj(J_t)) and the alternating least-squares
 // target is H_t = J_t - G_t D_t^-1, D_t Hermitian.  A calibration tile is
-// 32 x 32 blocks (64 x 64 inputs): lane = column block b, rows a walked one
+// 32 x 32 blocks (64 x 64 inputs): lane = column block b, rows a walked two
 // at a time.  The twelve tile-a quantities of a row (G: 8 floats, D: d00,
-// d11, Re d10, Im d10) are reduce-scattered across the warp (halving over lane
-// bits 4 and 3, then a sum over bits 2..0): lanes 8g..8g+7 all hold
-// quantities 3g..3g+2 of the row, and lane 8g + u keeps rows u, u + 8, ...
-// The tile-b quantities stay in the lane.  Entries outside the stored blocks
-// (a >= n_tiles, b >= a) load V = M = 0 and contribute exactly 0.
+// d11, Re d10, Im d10) are reduce-scattered across the warp together with
+// those of the row four on (see reduce_scatter24); the tile-b quantities
+// stay in the lane.  Entries outside the stored blocks (a >= n_tiles,
+// b >= a) load V = M = 0 and contribute exactly 0.
 constexpr int kJT = 32;  // Jones blocks per calibration tile side
 constexpr int kJQ = 12;  // per-tile partial quantities
 constexpr int kJonesChanGroups = 24;
@@ -467,30 +466,6 @@ __device__ __forceinline__ float2 ccfma(float2 acc, float2 a, float2 b) {
 }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
-// v[0..11] -> the full-warp sums of values 3g .. 3g + 2, g = lane >> 3, in a
-// fixed order (v[0..2] on return).
-__device__ __forceinline__ void reduce_scatter12(float (&v)[kJQ], int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const float send = b4 ? v[k] : v[k + 6];
-    const float keep = b4 ? v[k + 6] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float send = b3 ? v[k] : v[k + 3];
-    const float keep = b3 ? v[k + 3] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-}
-
-constexpr int kJStages = 3;  // rows of loads per warp in flight (shared-memory ring)
-
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -501,192 +476,6 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// grid: (calibration tiles, channel groups); CTA (tile, cg) covers channels
-// cg, cg + n_cg, ..., its warp w every eighth of them.  Each lane copies the
-// eight V and M values of its block of a row into its own slots of a
-// three-row shared-memory ring with 8-byte cp.async (the rows of the triangle
-// start on 8-byte boundaries), two rows ahead of the one it processes, and
-// reads back only what it copied itself.  Outputs per (tile, cg):
-// part_row [32 rows][12], part_col [32 columns][12], part_loss.  DEN: the D
-// quantities (left at 0 otherwise).
-template <bool DEN>
-__global__ void __launch_bounds__(kCalThreads, 3) calib_jones_tile_kernel(
-    const float2 *__restrict__ V, const float2 *__restrict__ M, const float2 *__restrict__ Jm,
-    int n_tiles, int C, int n_cg, float *__restrict__ part_loss, float *__restrict__ part_row,
-    float *__restrict__ part_col) {
-  constexpr int kWarps = kCalThreads / 32;
-  // ring [warp][stage][entry][lane] during the pass; afterwards the same memory
-  // holds the per-warp partials [warp][32][12] and the per-warp losses
-  __shared__ __align__(16) float2 sraw[kWarps * kJStages * 8 * 32];
-  static_assert(sizeof(float) * (kWarps * kJT * kJQ + kWarps) <= sizeof(sraw), "aliasing");
-  const int tile = blockIdx.x, cg = blockIdx.y;
-  int I, Jt;
-  tile_of(tile, I, Jt);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int b = Jt * kJT + lane;
-  float2 jb00 = make_float2(0.f, 0.f), jb01 = jb00, jb10 = jb00, jb11 = jb00;
-  if (b < n_tiles) {
-    jb00 = Jm[(int64_t)b * 4 + 0];
-    jb01 = Jm[(int64_t)b * 4 + 1];
-    jb10 = Jm[(int64_t)b * 4 + 2];
-    jb11 = Jm[(int64_t)b * 4 + 3];
-  }
-  const int64_t N = 2 * (int64_t)n_tiles, Bn = N * (N + 1) / 2;
-  // this warp's channels: cg + n_cg (w + 8k), k < n_mine; rows flattened as k * 32 + r
-  const int first = cg + n_cg * w, stride = n_cg * kWarps;
-  const int n_mine = first < C ? (C - 1 - first) / stride + 1 : 0;
-  const int n_rows = n_mine * kJT;
-  float2 *ring = sraw + (int64_t)w * kJStages * 8 * 32 + lane;
-  auto issue = [&](int t) {
-    if (t < n_rows) {
-      const int nu = first + stride * (t >> 5);
-      const int a = I * kJT + (t & 31);
-      float2 *slot = ring + (t % kJStages) * 8 * 32;
-      if (a < n_tiles && b < a) {
-        const float2 *Vn = V + (int64_t)nu * Bn, *Mn = M + (int64_t)nu * Bn;
-        const int64_t i0 = 2 * (int64_t)a, i1 = i0 + 1;
-        const int64_t o0 = i0 * (i0 + 1) / 2 + 2 * b, o1 = i1 * (i1 + 1) / 2 + 2 * b;
-        cp_async8(slot + 0 * 32, Vn + o0);
-        cp_async8(slot + 1 * 32, Vn + o0 + 1);
-        cp_async8(slot + 2 * 32, Vn + o1);
-        cp_async8(slot + 3 * 32, Vn + o1 + 1);
-        cp_async8(slot + 4 * 32, Mn + o0);
-        cp_async8(slot + 5 * 32, Mn + o0 + 1);
-        cp_async8(slot + 6 * 32, Mn + o1);
-        cp_async8(slot + 7 * 32, Mn + o1 + 1);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) slot[e * 32] = make_float2(0.f, 0.f);
-      }
-    }
-    cp_async_commit();
-  };
-  float col[kJQ];
-  float row[4][3];
-#pragma unroll
-  for (int q = 0; q < kJQ; ++q) col[q] = 0.f;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) row[m][0] = row[m][1] = row[m][2] = 0.f;
-  Kahan loss;
-  issue(0);
-  issue(1);
-  for (int kc = 0; kc < n_mine; ++kc) {
-    float lch = 0.f;
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll 1
-    for (int u = 0; u < 8; ++u) {
-      const int r = 8 * m + u;
-      const int t = kc * kJT + r;
-      issue(t + 2);
-      cp_async_wait<2>();  // this thread's copies of row t have landed
-      const float2 *slot = ring + (t % kJStages) * 8 * 32;
-      const float2 v00 = slot[0 * 32], v01 = slot[1 * 32], v10 = slot[2 * 32], v11 = slot[3 * 32];
-      const float2 m00 = slot[4 * 32], m01 = slot[5 * 32], m10 = slot[6 * 32], m11 = slot[7 * 32];
-      const int a = I * kJT + r;
-      float2 ja00 = make_float2(0.f, 0.f), ja01 = ja00, ja10 = ja00, ja11 = ja00;
-      if (a < n_tiles) {
-        ja00 = __ldg(Jm + (int64_t)a * 4 + 0);
-        ja01 = __ldg(Jm + (int64_t)a * 4 + 1);
-        ja10 = __ldg(Jm + (int64_t)a * 4 + 2);
-        ja11 = __ldg(Jm + (int64_t)a * 4 + 3);
-      }
-      const float2 z = make_float2(0.f, 0.f);
-      // B = M J_b^H
-      const float2 B00 = cfmac(cfmac(z, m00, jb00), m01, jb01);
-      const float2 B01 = cfmac(cfmac(z, m00, jb10), m01, jb11);
-      const float2 B10 = cfmac(cfmac(z, m10, jb00), m11, jb01);
-      const float2 B11 = cfmac(cfmac(z, m10, jb10), m11, jb11);
-      // R = J_a B - V
-      const float2 R00 = cfma(cfma(make_float2(-v00.x, -v00.y), ja00, B00), ja01, B10);
-      const float2 R01 = cfma(cfma(make_float2(-v01.x, -v01.y), ja00, B01), ja01, B11);
-      const float2 R10 = cfma(cfma(make_float2(-v10.x, -v10.y), ja10, B00), ja11, B10);
-      const float2 R11 = cfma(cfma(make_float2(-v11.x, -v11.y), ja10, B01), ja11, B11);
-      lch += cabs2(R00) + cabs2(R01) + cabs2(R10) + cabs2(R11);
-      // tile a: G = R B^H, D = B B^H
-      float v[kJQ];
-      {
-        const float2 g00 = cfmac(cfmac(z, R00, B00), R01, B01);
-        const float2 g01 = cfmac(cfmac(z, R00, B10), R01, B11);
-        const float2 g10 = cfmac(cfmac(z, R10, B00), R11, B01);
-        const float2 g11 = cfmac(cfmac(z, R10, B10), R11, B11);
-        v[0] = g00.x; v[1] = g00.y; v[2] = g01.x; v[3] = g01.y;
-        v[4] = g10.x; v[5] = g10.y; v[6] = g11.x; v[7] = g11.y;
-        if constexpr (DEN) {
-          const float2 d10 = cfmac(cfmac(z, B10, B00), B11, B01);
-          v[8] = cabs2(B00) + cabs2(B01);
-          v[9] = cabs2(B10) + cabs2(B11);
-          v[10] = d10.x;
-          v[11] = d10.y;
-        } else {
-          v[8] = v[9] = v[10] = v[11] = 0.f;
-        }
-      }
-      // tile b: A = J_a M, G = R^H A, D = A^H A
-      const float2 A00 = cfma(cfma(z, ja00, m00), ja01, m10);
-      const float2 A01 = cfma(cfma(z, ja00, m01), ja01, m11);
-      const float2 A10 = cfma(cfma(z, ja10, m00), ja11, m10);
-      const float2 A11 = cfma(cfma(z, ja10, m01), ja11, m11);
-      {
-        const float2 g00 = ccfma(ccfma(z, R00, A00), R10, A10);
-        const float2 g01 = ccfma(ccfma(z, R00, A01), R10, A11);
-        const float2 g10 = ccfma(ccfma(z, R01, A00), R11, A10);
-        const float2 g11 = ccfma(ccfma(z, R01, A01), R11, A11);
-        col[0] += g00.x; col[1] += g00.y; col[2] += g01.x; col[3] += g01.y;
-        col[4] += g10.x; col[5] += g10.y; col[6] += g11.x; col[7] += g11.y;
-        if constexpr (DEN) {
-          const float2 d10 = ccfma(ccfma(z, A01, A00), A11, A10);
-          col[8] += cabs2(A00) + cabs2(A10);
-          col[9] += cabs2(A01) + cabs2(A11);
-          col[10] += d10.x;
-          col[11] += d10.y;
-        }
-      }
-      reduce_scatter12(v, lane);
-      if (u == (lane & 7)) {
-        row[m][0] += v[0];
-        row[m][1] += v[1];
-        row[m][2] += v[2];
-      }
-    }
-    loss.add(lch);
-  }
-  cp_async_wait<0>();
-  __syncthreads();  // every warp is done with the ring
-  float(*sred)[kJT][kJQ] = reinterpret_cast<float(*)[kJT][kJQ]>(sraw);
-  float *sloss = reinterpret_cast<float *>(sraw) + kWarps * kJT * kJQ;
-  // the eight warps in a fixed order: rows, then columns, then the loss
-  const int out_idx = tile * n_cg + cg;
-#pragma unroll
-  for (int m = 0; m < 4; ++m)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sred[w][(lane & 7) + 8 * m][3 * (lane >> 3) + k] = row[m][k];
-  float l = loss.s;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if (lane == 0) sloss[w] = l;
-  __syncthreads();
-  for (int e = threadIdx.x; e < kJT * kJQ; e += kCalThreads) {
-    float t = 0.f;
-    for (int k = 0; k < kWarps; ++k) t += (&sred[k][0][0])[e];
-    part_row[(int64_t)out_idx * kJT * kJQ + e] = t;
-  }
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int k = 0; k < kWarps; ++k) t += sloss[k];
-    part_loss[out_idx] = t;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kJQ; ++q) sred[w][lane][q] = col[q];
-  __syncthreads();
-  for (int e = threadIdx.x; e < kJT * kJQ; e += kCalThreads) {
-    float t = 0.f;
-    for (int k = 0; k < kWarps; ++k) t += (&sred[k][0][0])[e];
-    part_col[(int64_t)out_idx * kJT * kJQ + e] = t;
-  }
 }
 
 // Two rows per step: the 24 tile-a quantities of rows ra and rb = ra + 4 (12
@@ -809,9 +598,12 @@ __device__ __forceinline__ float jones_row(const float4 *slot, float2 ja00, floa
 // The Jones pass, two rows per step (see reduce_scatter24).  Each lane stages
 // the blocks of row pairs PAIRS - 1 pairs ahead in its own 128-byte slots of a
 // PAIRS-deep shared-memory ring (reads back only what it copied: no barrier);
-// the tile's 32 rows of J_a are staged once per CTA.  Same grid, outputs and
-// summation structure per row as calib_jones_tile_kernel; the quantities of
-// rows 8m + u and 8m + u + 4 (u < 4) are reduced together.
+// the tile's 32 rows of J_a are staged once per CTA.  grid: (calibration
+// tiles, channel groups); CTA (tile, cg) covers channels cg, cg + n_cg, ...,
+// its warp w every eighth of them, and adds each channel's loss into a Kahan
+// accumulator; the eight warps' partials are summed in a fixed order.
+// Outputs per (tile, cg): part_row [32 rows][12], part_col [32 columns][12],
+// part_loss.  DEN: the D quantities (left at 0 otherwise).
 #ifndef MWAX_JONES_PAIRS
 #define MWAX_JONES_PAIRS 3
 #endif
@@ -1260,7 +1052,6 @@ static mwax_status jones_run(const float *V, const float *M, float *J, int n_inp
   float *ploss = pcol + slots * kJT * kJQ;
   const float2 *V2 = reinterpret_cast<const float2 *>(V), *M2 = reinterpret_cast<const float2 *>(M);
   float2 *J2 = reinterpret_cast<float2 *>(J);
-#ifndef MWAX_JONES_ONE_ROW
   // the two-rows-per-step pass needs more than the default 48 KB of shared memory
   constexpr int smem2 = jones2_smem_bytes();
   if (cudaFuncSetAttribute(calib_jones_tile2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1276,16 +1067,6 @@ static mwax_status jones_run(const float *V, const float *M, float *J, int n_inp
       calib_jones_tile2_kernel<false><<<dim3(tiles, n_cg), kCalThreads, smem2, stream>>>(
           V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
   };
-#else
-  auto tile_pass = [&](bool den) {
-    if (den)
-      calib_jones_tile_kernel<true><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
-          V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
-    else
-      calib_jones_tile_kernel<false><<<dim3(tiles, n_cg), kCalThreads, 0, stream>>>(
-          V2, M2, J2, n_tiles, n_chan, n_cg, ploss, prow, pcol);
-  };
-#endif
   if (!solve) {
     tile_pass(false);
     if (cudaGetLastError() != cudaSuccess) return MWAX_ERR_CUDA;
