@@ -75,6 +75,9 @@ constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
 // bubble in the tensor pipe, so the narrow shape takes three blocks (24
 // MMAs) per wait and per commit: two stages of 96 KB.
 constexpr int kModeNarrow = 0, kModeWide = 1, kModePair = 2;
+#ifndef MWAX_PAIR_KPS
+#define MWAX_PAIR_KPS 2  // pair mode: K blocks per stage (1 or 2; 192 KB of stages either way)
+#endif
 constexpr int kEpiStageBytes = 32 * 128;  // pair mode: one warp's 32 rows x 16 (re, im) words
 
 template <int MODE>
@@ -82,10 +85,10 @@ struct Shape {
   static constexpr int warps = MODE == kModeWide ? 12 : 10;
   static constexpr int conv_warps = MODE == kModeWide ? 2 : 0;  // warps 2 .. 2+conv_warps-1
   static constexpr int epi0 = 2 + conv_warps;                   // 8 epilogue warps from here
-  static constexpr int kps = MODE == kModeWide ? 1 : MODE == kModePair ? 2 : 3;  // K blocks per stage
+  static constexpr int kps = MODE == kModeWide ? 1 : MODE == kModePair ? MWAX_PAIR_KPS : 3;  // K blocks per stage
   static constexpr int block_bytes = (MODE == kModeNarrow ? 2 : 3) * kTileBytes;  // tiles of one block
   static constexpr int stage_bytes = kps * block_bytes;
-  static constexpr int max_stages = MODE == kModeWide ? 4 : 2;
+  static constexpr int max_stages = MODE == kModeWide ? 4 : MODE == kModePair ? 4 / MWAX_PAIR_KPS : 2;
   static constexpr int epi_bytes = MODE == kModePair ? 8 * kEpiStageBytes : 0;
 };
 constexpr uint32_t kTmemCols = 512;
@@ -387,8 +390,34 @@ __device__ __forceinline__ PairItem decode_pair_item(const int4 d) {
 
 // Time blocks [k0, k1) of an item of a job with KB blocks.
 __device__ __forceinline__ void item_blocks(const PairItem &it, int KB, int &k0, int &k1) {
-  k0 = (int)((int64_t)it.split * KB / it.n_split);
-  k1 = (int)((int64_t)(it.split + 1) * KB / it.n_split);
+  // 32-bit products: exact for n_split <= 8 and KB < 2^28 (pair_mode_supported)
+  k0 = (int)((uint32_t)(it.split * KB) / (uint32_t)it.n_split);
+  k1 = (int)((uint32_t)((it.split + 1) * KB) / (uint32_t)it.n_split);
+}
+
+// Pair-mode epilogue: each lane writes column j (lane & 15) of 16 of the 32
+// staged rows i0 + r (r = 2 r2 + lane / 16) of one half-block, lower triangle
+// only; ADD: add into the output with int32 atomics (one time range of several)
+// instead of storing.
+template <bool ADD>
+__device__ __forceinline__ void store_rows(const uint8_t *stg, uint32_t *out, int lane, int i0,
+                                           int j, int n) {
+  const int col = lane & 15;
+#pragma unroll
+  for (int r2 = 0; r2 < 16; ++r2) {
+    const int r = 2 * r2 + (lane >> 4);
+    const uint2 val = *reinterpret_cast<const uint2 *>(stg + r * 128 + ((col ^ (r & 15)) << 3));
+    const int i = i0 + r;
+    if (i < n && j <= i) {
+      uint32_t *dst = out + 2 * ((int64_t)i * (i + 1) / 2 + j);
+      if constexpr (ADD) {
+        atomicAdd(reinterpret_cast<int *>(dst), (int)val.x);
+        atomicAdd(reinterpret_cast<int *>(dst) + 1, (int)val.y);
+      } else {
+        *reinterpret_cast<uint2 *>(dst) = val;
+      }
+    }
+  }
 }
 
 // The eight MMAs of one K block: N = 128 (one tile pair) or 256 (B spans two
@@ -629,23 +658,12 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
             *reinterpret_cast<uint2 *>(stg + lane * 128 + ((k ^ (lane & 15)) << 3)) =
                 make_uint2(vre[16 * half + k], vim[16 * half + k]);
           __syncwarp();
-          const int col = lane & 15;
-          const int j = J * kTile + 32 * cc + 16 * half + col;
-#pragma unroll
-          for (int r2 = 0; r2 < 16; ++r2) {
-            const int r = 2 * r2 + (lane >> 4);
-            const uint2 val = *reinterpret_cast<const uint2 *>(stg + r * 128 + ((col ^ (r & 15)) << 3));
-            const int i = I * kTile + q * 32 + r;
-            if (i < n && j <= i) {
-              uint32_t *dst = out + 2 * ((int64_t)i * (i + 1) / 2 + j);
-              if (it.n_split > 1) {  // one time range of several: exact integer adds
-                atomicAdd(reinterpret_cast<int *>(dst), (int)val.x);
-                atomicAdd(reinterpret_cast<int *>(dst) + 1, (int)val.y);
-              } else {
-                *reinterpret_cast<uint2 *>(dst) = val;
-              }
-            }
-          }
+          const int j = J * kTile + 32 * cc + 16 * half + (lane & 15);
+          const int i0 = I * kTile + q * 32;
+          if (it.n_split > 1)  // one time range of several: exact integer adds
+            store_rows<true>(stg, out, lane, i0, j, n);
+          else
+            store_rows<false>(stg, out, lane, i0, j, n);
           __syncwarp();
         }
       }
@@ -1103,7 +1121,7 @@ cudaError_t launch_exact_check(const int32_t *out, int64_t n_bl, int n_inputs, i
 bool pair_mode_supported(const TcJob *jobs, int n_jobs) {
   for (int j = 0; j < n_jobs; ++j)
     if (jobs[j].kb > jobs[j].flush_blocks || jobs[j].n_tiles > 255 || jobs[j].k_split < 1 ||
-        jobs[j].k_split > jobs[j].kb || jobs[j].k_split > 255)
+        jobs[j].k_split > jobs[j].kb || jobs[j].k_split > 8 || jobs[j].kb >= (1 << 28))
       return false;
   return n_jobs >= 1 && n_jobs <= kMaxJobs;
 }

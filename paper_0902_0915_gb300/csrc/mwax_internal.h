@@ -109,7 +109,7 @@ int correlate_tc_max_stages(int mode);
 cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode);
 
 // Pair mode needs every job's integration in one exact segment (kb <=
-// flush_blocks), at most 255 tiles and 1 <= k_split <= min(kb, 255).
+// flush_blocks), at most 255 tiles, kb < 2^28 and 1 <= k_split <= min(kb, 8).
 bool pair_mode_supported(const TcJob *jobs, int n_jobs);
 // The pair-mode work list of one launch over `jobs` (16 bytes per item).
 void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items);
