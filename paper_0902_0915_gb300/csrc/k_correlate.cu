@@ -75,9 +75,6 @@ constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
 // bubble in the tensor pipe, so the narrow shape takes three blocks (24
 // MMAs) per wait and per commit: two stages of 96 KB.
 constexpr int kModeNarrow = 0, kModeWide = 1, kModePair = 2;
-#ifndef MWAX_PAIR_KPS
-#define MWAX_PAIR_KPS 2  // pair mode: K blocks per stage (1 or 2; 192 KB of stages either way)
-#endif
 constexpr int kEpiStageBytes = 32 * 128;  // pair mode: one warp's 32 rows x 16 (re, im) words
 
 template <int MODE>
@@ -85,10 +82,10 @@ struct Shape {
   static constexpr int warps = MODE == kModeWide ? 12 : 10;
   static constexpr int conv_warps = MODE == kModeWide ? 2 : 0;  // warps 2 .. 2+conv_warps-1
   static constexpr int epi0 = 2 + conv_warps;                   // 8 epilogue warps from here
-  static constexpr int kps = MODE == kModeWide ? 1 : MODE == kModePair ? MWAX_PAIR_KPS : 3;  // K blocks per stage
+  static constexpr int kps = MODE == kModeWide ? 1 : MODE == kModePair ? 2 : 3;  // K blocks per stage
   static constexpr int block_bytes = (MODE == kModeNarrow ? 2 : 3) * kTileBytes;  // tiles of one block
   static constexpr int stage_bytes = kps * block_bytes;
-  static constexpr int max_stages = MODE == kModeWide ? 4 : MODE == kModePair ? 4 / MWAX_PAIR_KPS : 2;
+  static constexpr int max_stages = MODE == kModeWide ? 4 : 2;
   static constexpr int epi_bytes = MODE == kModePair ? 8 * kEpiStageBytes : 0;
 };
 constexpr uint32_t kTmemCols = 512;
