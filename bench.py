@@ -1064,7 +1064,7 @@ def main():
     if engine == mw.ENGINE_TENSOR and tim.correlate_ms > 0:
         achieved = 8.0 * units * args.steps / (tim.correlate_ms / 1e3) / 1e12
         tkey = (f"correlate_tc_kernel<{rspec.sample_bits},EXACT,"
-                f"{ {1: 'narrow', 2: 'wide', 3: 'pair'}.get(info.mma_shape, 'narrow') }>"
+                f"{ {1: 'narrow', 2: 'wide', 3: 'pair', 4: 'fused'}.get(info.mma_shape, 'narrow') }>"
                 f"|N{rspec.n_inputs}|T{rspec.n_time}")
         tent = traffic_entry(tkey)
         traffic = tent["bytes_per_channel"] * info.chan_group if tent else None

@@ -96,8 +96,14 @@ typedef struct {
                               the FP16 kind, or flush_blocks >= the time blocks; or,
                               for longer exact single-job plans with flush_blocks 0,
                               one checked segment, see mwax_plan_info.checked_segment;
-                              else MWAX_ERR_UNSUPPORTED); 0 = auto: 3 where it applies,
-                              else 1                                                      */
+                              else MWAX_ERR_UNSUPPORTED), 4 = the same work items with
+                              the unpack folded into the correlate: converter warps
+                              read the packed samples and write the operand tiles into
+                              shared memory, so no operand buffer and no unpack pass
+                              (single-job plans of 4-bit exact samples in one exact
+                              segment with n_inputs a multiple of 16, else
+                              MWAX_ERR_UNSUPPORTED); 0 = auto: 4 where it applies and
+                              n_inputs <= 256, else 3 where it applies, else 1           */
   int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
                               plan's stream, 2 = unpack the next group (second stream,
                               second scratch buffer) while the current group correlates,

@@ -58,6 +58,7 @@
 #include <string.h>
 
 #include "mwax_internal.h"
+#include "mwax_nib4.h"
 
 namespace mwax {
 namespace {
@@ -74,19 +75,29 @@ constexpr int kTileBytes = kTile * kRowBytes;  // 16 KB
 // about as much as two N=128 MMA issues, and every stage boundary leaves a
 // bubble in the tensor pipe, so the narrow shape takes three blocks (24
 // MMAs) per wait and per commit: two stages of 96 KB.
-constexpr int kModeNarrow = 0, kModeWide = 1, kModePair = 2;
+// 3, fused pair: the pair mode for 4-bit samples with the unpack folded in:
+// the eight epilogue warps also convert: they read the packed samples from
+// global memory and write the E4M3 operand tiles into the stages themselves
+// (no operand buffer in HBM, no unpack pass), and drain each item's
+// accumulator after its last stage.
+constexpr int kModeNarrow = 0, kModeWide = 1, kModePair = 2, kModePairFused = 3;
 constexpr int kEpiStageBytes = 32 * 128;  // pair mode: one warp's 32 rows x 16 (re, im) words
 
 template <int MODE>
 struct Shape {
+  static constexpr bool pair = MODE == kModePair || MODE == kModePairFused;
   static constexpr int warps = MODE == kModeWide ? 12 : 10;
-  static constexpr int conv_warps = MODE == kModeWide ? 2 : 0;  // warps 2 .. 2+conv_warps-1
-  static constexpr int epi0 = 2 + conv_warps;                   // 8 epilogue warps from here
-  static constexpr int kps = MODE == kModeWide ? 1 : MODE == kModePair ? 2 : 3;  // K blocks per stage
+  // warps 2 .. 2+conv_warps-1: B' builders (wide only)
+  static constexpr int conv_warps = MODE == kModeWide ? 2 : 0;
+  static constexpr int epi0 = 2 + conv_warps;  // 8 epilogue warps from here to the last
+  static constexpr int epi_warps = warps - epi0;
+  // fused pair mode: the epilogue warps convert the samples (full-barrier arrivals per stage)
+  static constexpr int fill_arrivals = MODE == kModePairFused ? epi_warps : 1;
+  static constexpr int kps = MODE == kModeWide ? 1 : pair ? 2 : 3;  // K blocks per stage
   static constexpr int block_bytes = (MODE == kModeNarrow ? 2 : 3) * kTileBytes;  // tiles of one block
   static constexpr int stage_bytes = kps * block_bytes;
   static constexpr int max_stages = MODE == kModeWide ? 4 : 2;
-  static constexpr int epi_bytes = MODE == kModePair ? 8 * kEpiStageBytes : 0;
+  static constexpr int epi_bytes = pair ? epi_warps * kEpiStageBytes : 0;
 };
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccCols = 256;  // re 128 | im 128
@@ -97,7 +108,9 @@ struct KJob {
   void *out;           // visibilities of the job's first channel in this launch
   int64_t item_begin;  // first work item of this job
   int64_t n_bl;        // N(N+1)/2
-  int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks, pad_;
+  int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks;
+  int32_t n_time;       // fused pair mode: samples per integration
+  const uint8_t *volt;  // fused pair mode: packed samples of the launch's first channel
 };
 
 struct KParams {
@@ -441,15 +454,156 @@ __device__ __forceinline__ void narrow_block(uint32_t d_re, uint32_t d_im, uint6
   block_mmas<BITS, kTile>(d_re, d_im, da, db, acc0);
 }
 
-// The three roles in pair mode (warp 0: producer, warp 1: MMA issuer, warps
-// 2..9: epilogue).  Barriers as in the kernel: full[0..S) empty[S..2S)
-// tfull[3S] tempty[3S+2] drain[3S+4] (one accumulator buffer: index 0 only).
-template <int BITS, int KIND>
-__device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, uint32_t smem_base,
-                                           uint8_t *epi_smem, uint32_t bar0, uint32_t tmem_base,
-                                           volatile int *abort_flag, volatile int *epi_flag,
-                                           int warp, int lane) {
-  using Sh = Shape<kModePair>;
+// Fused pair mode: one converter thread's share of tile I of channel c, time
+// block kb (64 samples): the packed samples of 4 (sample, 16-input) units,
+// loaded first, then written as E4M3 codes, re plane at row t and im plane at
+// row 64 + t of the tile, each 16-byte chunk at its 128-byte swizzle position.
+// Samples past T and inputs past N read as zero (N is a multiple of 16).
+__device__ __forceinline__ uint4 ld_stream16(const uint8_t *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+constexpr int kConvThreads = 256;                  // fused pair mode: the 8 epilogue warps
+constexpr int kConvUnits = 64 * 8 / kConvThreads;  // (sample, 16 inputs) units per thread per tile
+
+struct FusedTile {
+  const uint8_t *row0;  // sample 0 of the block, input 128 I, channel c (never dereferenced as is)
+  int t_left;           // samples of the block that exist (T - 64 kb, may be <= 0)
+  int in_left;          // inputs of the tile that exist (N - 128 I)
+};
+
+__device__ __forceinline__ void fused_load(const FusedTile &f, int N, int ct, uint4 (&w)[kConvUnits]) {
+#pragma unroll
+  for (int m = 0; m < kConvUnits; ++m) {
+    const int u = ct + kConvThreads * m;
+    const int t = u >> 3, x = (u & 7) << 4;
+    w[m] = t < f.t_left && x < f.in_left ? ld_stream16(f.row0 + (int64_t)t * N + x) : make_uint4(0, 0, 0, 0);
+  }
+}
+
+__device__ __forceinline__ void fused_store(uint8_t *tile, int ct, const uint4 (&w)[kConvUnits]) {
+#pragma unroll
+  for (int m = 0; m < kConvUnits; ++m) {
+    const int u = ct + kConvThreads * m;
+    const int t = u >> 3, ch = u & 7;
+    const int off = t * kRowBytes + ((ch ^ (t & 7)) << 4);
+    const uint4 v = w[m];
+    *reinterpret_cast<uint4 *>(tile + off) =
+        make_uint4(nib4_to_e4m3_f16(v.x), nib4_to_e4m3_f16(v.y), nib4_to_e4m3_f16(v.z), nib4_to_e4m3_f16(v.w));
+    *reinterpret_cast<uint4 *>(tile + 64 * kRowBytes + off) =
+        make_uint4(nib4_to_e4m3_f16(v.x >> 4), nib4_to_e4m3_f16(v.y >> 4), nib4_to_e4m3_f16(v.z >> 4), nib4_to_e4m3_f16(v.w >> 4));
+  }
+}
+
+// Pair-mode epilogue of one work item (warp (q, h) of the eight epilogue
+// warps): wait for the accumulator (one thread; the result goes through a
+// two-entry flag so all eight warps take the same branch), convert, release
+// the accumulator, store the item's lower-triangle visibilities.  false: a
+// wait ran out (every warp stops).
+template <int KIND>
+__device__ __forceinline__ bool drain_item(const KParams &p, const PairItem &it, uint32_t n_it,
+                                           uint32_t tfull, uint32_t tempty, uint32_t tmem_base,
+                                           uint8_t *stg, volatile int *abort_flag,
+                                           volatile int *epi_flag, int warp, int lane, int epi0) {
+  const unsigned long long tmo = p.timeout_ns;
+  const int q = warp & 3;
+  const int h = (warp - epi0) >> 2;
+  const KJob &jb = p.job[it.job];
+  if (warp == epi0 && lane == 0) {
+    const bool got = mbar_wait(tfull, n_it & 1u, abort_flag, tmo);
+    if (!got) raise_timeout(abort_flag, p.status);
+    epi_flag[n_it & 1u] = got ? 1 : 0;
+  }
+  named_bar_sync(1, 8 * 32);
+  if (!epi_flag[n_it & 1u]) return false;
+  tc_fence_after();
+  const bool has = h == 0 || it.type != kItemOne;
+  int c, I, J;
+  if (it.type == kItemShared) {
+    c = it.c0;
+    I = it.I0;
+    J = h ? it.J1 : it.J0;
+  } else if (it.type == kItemTwoDiag) {
+    c = h ? it.c1 : it.c0;
+    I = h ? it.I1 : it.I0;
+    J = I;
+  } else {
+    c = it.c0;
+    I = it.I0;
+    J = it.J0;
+  }
+  const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kTile);
+  uint32_t *out = reinterpret_cast<uint32_t *>(jb.out) + (int64_t)c * jb.n_bl * 2;
+  const int n = jb.n_inputs;
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc) {
+    uint32_t vre[32], vim[32];
+    if (has) {
+      tc_ld32(trow + 32 * cc, vre);
+      tc_ld32(trow + 2 * kTile + 32 * cc, vim);
+      tc_wait_ld();
+    }
+    if (cc == 3) {
+      // every column of this warp is in registers: release the accumulator
+      // (test hook: withholding one release makes the MMA warp's bounded
+      // wait run out -> MWAX_ERR_TIMEOUT, clean exit)
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0 && (int)n_it != p.withhold_seg) mbar_arrive(tempty);
+    }
+    if (!has) continue;
+    if constexpr (KIND == MWAX_KIND_EXACT) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        vre[k] = (uint32_t)__float2int_rn(__uint_as_float(vre[k]));
+        vim[k] = (uint32_t)__float2int_rn(__uint_as_float(vim[k]));
+      }
+    }
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        *reinterpret_cast<uint2 *>(stg + lane * 128 + ((k ^ (lane & 15)) << 3)) =
+            make_uint2(vre[16 * half + k], vim[16 * half + k]);
+      __syncwarp();
+      const int j = J * kTile + 32 * cc + 16 * half + (lane & 15);
+      const int i0 = I * kTile + q * 32;
+      if (it.n_split > 1)  // one time range of several: exact integer adds
+        store_rows<true>(stg, out, lane, i0, j, n);
+      else
+        store_rows<false>(stg, out, lane, i0, j, n);
+      __syncwarp();
+    }
+  }
+  return true;
+}
+
+// The same as a separate call (fused pair mode: the converters' state stays
+// out of the epilogue's register allocation).
+template <int KIND>
+__device__ __noinline__ bool drain_item_call(const KParams &p, const PairItem &it, uint32_t n_it,
+                                             uint32_t tfull, uint32_t tempty, uint32_t tmem_base,
+                                             uint8_t *stg, volatile int *abort_flag,
+                                             volatile int *epi_flag, int warp, int lane, int epi0) {
+  return drain_item<KIND>(p, it, n_it, tfull, tempty, tmem_base, stg, abort_flag, epi_flag, warp,
+                          lane, epi0);
+}
+
+// The roles in pair mode.  Warp 0: TMA producer (idle in the fused pair
+// mode), warp 1: MMA issuer, warps 2..9: epilogue (in the fused pair mode
+// also the sample converters).  Barriers as in the kernel: full[0..S)
+// empty[S..2S) tfull[3S] tempty[3S+2] drain[3S+4] (one accumulator buffer:
+// index 0 only).
+template <int BITS, int KIND, bool FUSED>
+__device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, uint8_t *smem,
+                                           uint32_t smem_base, uint8_t *epi_smem, uint32_t bar0,
+                                           uint32_t tmem_base, volatile int *abort_flag,
+                                           volatile int *epi_flag, int warp, int lane) {
+  using Sh = Shape<FUSED ? kModePairFused : kModePair>;
   constexpr int kStageBytes = Sh::stage_bytes;
   const int S = p.stages;
   const unsigned long long tmo = p.timeout_ns;
@@ -461,7 +615,7 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
 
   if (warp == 0) {
     // ---------------- TMA producer (one thread) ----------------
-    if (lane == 0) {
+    if (!FUSED && lane == 0) {
       for (int j = 0; j < p.n_jobs; ++j)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[j]))
                      : "memory");
@@ -591,80 +745,97 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
     // columns at a time: lane r writes row r (16 (re, im) words, XOR-swizzled
     // so the 16 lanes of a phase hit distinct banks), then each store
     // instruction writes rows r and r+1 as two contiguous 128-byte runs.
-    const int q = warp & 3;
-    const int h = (warp - Sh::epi0) >> 2;
+    // One thread waits for the accumulator; the result goes through a
+    // two-entry flag so all eight warps take the same branch (false: stop).
     uint8_t *stg = epi_smem + (warp - Sh::epi0) * kEpiStageBytes;
+    auto drain = [&](const PairItem &it, uint32_t n_it) -> bool {
+      if constexpr (FUSED)
+        return drain_item_call<KIND>(p, it, n_it, tfull, tempty, tmem_base, stg, abort_flag,
+                                     epi_flag, warp, lane, Sh::epi0);
+      else
+        return drain_item<KIND>(p, it, n_it, tfull, tempty, tmem_base, stg, abort_flag, epi_flag,
+                                warp, lane, Sh::epi0);
+    };
     uint32_t n_it = 0;
-    for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
-      const PairItem it = decode_pair_item(__ldg(p.items + item));
-      const KJob &jb = p.job[it.job];
-      if (warp == Sh::epi0 && lane == 0) {
-        const bool got = mbar_wait(tfull, n_it & 1u, abort_flag, tmo);
-        if (!got) raise_timeout(abort_flag, p.status);
-        epi_flag[n_it & 1u] = got ? 1 : 0;
+    if constexpr (!FUSED) {
+      for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        if (!drain(decode_pair_item(__ldg(p.items + item)), n_it)) break;
+        ++n_it;
       }
-      named_bar_sync(1, 8 * 32);
-      if (!epi_flag[n_it & 1u]) break;
-      tc_fence_after();
-      const bool has = h == 0 || it.type != kItemOne;
-      int c, I, J;
-      if (it.type == kItemShared) {
-        c = it.c0;
-        I = it.I0;
-        J = h ? it.J1 : it.J0;
-      } else if (it.type == kItemTwoDiag) {
-        c = h ? it.c1 : it.c0;
-        I = h ? it.I1 : it.I0;
-        J = I;
-      } else {
-        c = it.c0;
-        I = it.I0;
-        J = it.J0;
-      }
-      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * kTile);
-      uint32_t *out = reinterpret_cast<uint32_t *>(jb.out) + (int64_t)c * jb.n_bl * 2;
-      const int n = jb.n_inputs;
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        uint32_t vre[32], vim[32];
-        if (has) {
-          tc_ld32(trow + 32 * cc, vre);
-          tc_ld32(trow + 2 * kTile + 32 * cc, vim);
-          tc_wait_ld();
+    } else {
+      // Fused pair mode: first every stage of the item (the same items and
+      // blocks as the MMA issuer; each stage written by all eight warps and
+      // released with one arrival per warp after a proxy fence, since the
+      // tensor core reads generic-proxy stores), then the item's drain.  A
+      // warp whose wait for a free stage runs out skips the rest of the item
+      // and still joins the drain, where the shared flag ends every warp.
+      const int ct = (int)threadIdx.x - 32 * Sh::epi0;
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        const PairItem it = decode_pair_item(__ldg(p.items + item));
+        const KJob &jb = p.job[it.job];
+        const int N = jb.n_inputs, T = jb.n_time;
+        // the item's tiles in shared-memory order (as the producer loads them)
+        int tc[3] = {it.c0, it.c0, it.c0}, ti[3] = {0, 0, 0};
+        int nt;
+        if (it.type == kItemShared) {
+          ti[0] = it.J0;
+          ti[1] = it.J1;
+          ti[2] = it.I0;
+          nt = it.J1 == it.I0 ? 2 : 3;
+        } else if (it.type == kItemTwoDiag) {
+          ti[0] = it.I0;
+          tc[1] = it.c1;
+          ti[1] = it.I1;
+          nt = 2;
+        } else {
+          ti[0] = it.I0;
+          ti[1] = it.J0;
+          nt = it.I0 == it.J0 ? 1 : 2;
         }
-        if (cc == 3) {
-          // every column of this warp is in registers: release the accumulator
-          // (test hook: withholding one release makes the MMA warp's bounded
-          // wait run out -> MWAX_ERR_TIMEOUT, clean exit)
-          tc_fence_before();
+        int k0, k1;
+        item_blocks(it, jb.kb, k0, k1);
+        for (int kb = k0; kb < k1; kb += Sh::kps) {
+          const int nb = min(Sh::kps, k1 - kb);
+          if (!warp_wait(empty(stage), phase ^ 1u, abort_flag, tmo, lane)) {
+            if (lane == 0) raise_timeout(abort_flag, p.status);
+            break;
+          }
+          uint8_t *st_base = smem + (size_t)stage * kStageBytes;
+          // every load of the stage first (one memory latency per stage), then
+          // the conversions and shared-memory stores
+          uint4 w[Sh::kps][3][kConvUnits];
+#pragma unroll
+          for (int j = 0; j < Sh::kps; ++j) {
+            const int s0 = (kb + j) * 64;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+              if (j < nb && t < nt) {
+                FusedTile f;
+                f.row0 = jb.volt + ((int64_t)tc[t] * T + s0) * N + ti[t] * kTile;
+                f.t_left = T - s0;
+                f.in_left = N - ti[t] * kTile;
+                fused_load(f, N, ct, w[j][t]);
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < Sh::kps; ++j)
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+              if (j < nb && t < nt) fused_store(st_base + j * Sh::block_bytes + t * kTileBytes, ct, w[j][t]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
-          if (lane == 0 && (int)n_it != p.withhold_seg) mbar_arrive(tempty);
-        }
-        if (!has) continue;
-        if constexpr (KIND == MWAX_KIND_EXACT) {
-#pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            vre[k] = (uint32_t)__float2int_rn(__uint_as_float(vre[k]));
-            vim[k] = (uint32_t)__float2int_rn(__uint_as_float(vim[k]));
+          if (lane == 0) mbar_arrive(full(stage));
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
           }
         }
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            *reinterpret_cast<uint2 *>(stg + lane * 128 + ((k ^ (lane & 15)) << 3)) =
-                make_uint2(vre[16 * half + k], vim[16 * half + k]);
-          __syncwarp();
-          const int j = J * kTile + 32 * cc + 16 * half + (lane & 15);
-          const int i0 = I * kTile + q * 32;
-          if (it.n_split > 1)  // one time range of several: exact integer adds
-            store_rows<true>(stg, out, lane, i0, j, n);
-          else
-            store_rows<false>(stg, out, lane, i0, j, n);
-          __syncwarp();
-        }
+        if (!drain(it, n_it)) break;
+        ++n_it;
       }
-      ++n_it;
     }
   }
 }
@@ -674,7 +845,8 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
     correlate_tc_kernel(const __grid_constant__ KMaps maps, const __grid_constant__ KParams p) {
   using Sh = Shape<MODE>;
   constexpr bool WIDE = MODE == kModeWide;
-  constexpr bool PAIR = MODE == kModePair;
+  constexpr bool PAIR = Sh::pair;
+  constexpr bool FUSED = MODE == kModePairFused;
   constexpr int kStageBytes = Sh::stage_bytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -699,13 +871,13 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full(s), 1);
+      mbar_init(full(s), Sh::fill_arrivals);  // the TMA producer, or the converting warps
       mbar_init(empty(s), 1);
       mbar_init(bfull(s), Sh::conv_warps > 0 ? Sh::conv_warps : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 8);
+      mbar_init(tempty(b), Sh::epi_warps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -725,8 +897,8 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
   const int64_t n_items = launch_items(p);
 
   if constexpr (PAIR) {
-    pair_roles<BITS, KIND>(maps, p, smem_base, epi_smem, smem_u32(bars), tmem_base, abort_flag,
-                           epi_flag, warp, lane);
+    pair_roles<BITS, KIND, FUSED>(maps, p, smem, smem_base, epi_smem, smem_u32(bars), tmem_base,
+                                  abort_flag, epi_flag, warp, lane);
   } else if (warp == 0) {
     // ---------------- TMA producer (one thread) ----------------
     if (lane == 0) {
@@ -1089,14 +1261,18 @@ int4 encode_item(int job, uint32_t type, int c0, int c1, int I0, int J0, int I1,
 int correlate_tc_max_stages(int mode) {
   return mode == kModeWide ? Shape<kModeWide>::max_stages
          : mode == kModePair ? Shape<kModePair>::max_stages
-                             : Shape<kModeNarrow>::max_stages;
+         : mode == kModePairFused ? Shape<kModePairFused>::max_stages
+                                  : Shape<kModeNarrow>::max_stages;
 }
 
 int correlate_tc_smem_bytes(int stages, int mode) {
   const int stage_bytes = mode == kModeWide ? Shape<kModeWide>::stage_bytes
                           : mode == kModePair ? Shape<kModePair>::stage_bytes
-                                              : Shape<kModeNarrow>::stage_bytes;
-  const int epi_bytes = mode == kModePair ? Shape<kModePair>::epi_bytes : 0;
+                          : mode == kModePairFused ? Shape<kModePairFused>::stage_bytes
+                                                   : Shape<kModeNarrow>::stage_bytes;
+  const int epi_bytes = mode == kModePair ? Shape<kModePair>::epi_bytes
+                        : mode == kModePairFused ? Shape<kModePairFused>::epi_bytes
+                                                 : 0;
   return 1024 + stages * stage_bytes + epi_bytes + (3 * stages + 5) * 8 + 32;
 }
 
@@ -1104,6 +1280,10 @@ cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode
   const int bytes = correlate_tc_smem_bytes(stages, mode);
   if (mode == kModeWide) return prepare_shape<kModeWide>(sample_bits, kind, bytes);
   if (mode == kModePair) return prepare_shape<kModePair>(sample_bits, kind, bytes);
+  if (mode == kModePairFused)
+    return sample_bits == 4 && kind == MWAX_KIND_EXACT
+               ? set_smem_attr<4, MWAX_KIND_EXACT, kModePairFused>(bytes)
+               : cudaErrorInvalidValue;
   return prepare_shape<kModeNarrow>(sample_bits, kind, bytes);
 }
 
@@ -1121,6 +1301,15 @@ bool pair_mode_supported(const TcJob *jobs, int n_jobs) {
         jobs[j].k_split > jobs[j].kb || jobs[j].k_split > 8 || jobs[j].kb >= (1 << 28))
       return false;
   return n_jobs >= 1 && n_jobs <= kMaxJobs;
+}
+
+bool fused_pair_supported(const TcJob *jobs, int n_jobs, int sample_bits, int kind) {
+  if (sample_bits != 4 || kind != MWAX_KIND_EXACT) return false;
+  for (int j = 0; j < n_jobs; ++j)
+    if (jobs[j].n_inputs % 16 != 0 || jobs[j].n_time < 1 ||
+        (jobs[j].op && (reinterpret_cast<uintptr_t>(jobs[j].op) & 15u) != 0))
+      return false;
+  return true;
 }
 
 // Channel by channel, row I of the tile triangle gives the shared items
@@ -1189,15 +1378,19 @@ namespace mwax {
 cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &cfg,
                                 cudaStream_t s) {
   if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;
-  if (cfg.mode < kModeNarrow || cfg.mode > kModePair) return cudaErrorInvalidValue;
+  if (cfg.mode < kModeNarrow || cfg.mode > kModePairFused) return cudaErrorInvalidValue;
   if (cfg.stages < 2 || cfg.stages > correlate_tc_max_stages(cfg.mode)) return cudaErrorInvalidValue;
-  if (cfg.mode == kModePair && (!pair_mode_supported(jobs, n_jobs) || !cfg.items || cfg.n_items < 0))
+  const bool pair = cfg.mode == kModePair || cfg.mode == kModePairFused;
+  const bool fused = cfg.mode == kModePairFused;
+  if (pair && (!pair_mode_supported(jobs, n_jobs) || !cfg.items || cfg.n_items < 0))
+    return cudaErrorInvalidValue;
+  if (fused && !fused_pair_supported(jobs, n_jobs, cfg.sample_bits, cfg.kind))
     return cudaErrorInvalidValue;
   if ((cfg.chan_map || cfg.n_chan_dev) &&
-      (cfg.mode == kModePair || n_jobs != 1 || !cfg.chan_map || !cfg.n_chan_dev))
+      (pair || n_jobs != 1 || !cfg.chan_map || !cfg.n_chan_dev))
     return cudaErrorInvalidValue;
-  PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode_fn();
-  if (!encode) return cudaErrorNotSupported;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = fused ? nullptr : get_encode_fn();
+  if (!fused && !encode) return cudaErrorNotSupported;
   KMaps maps;
   KParams kp;
   memset(&maps, 0, sizeof(maps));
@@ -1206,6 +1399,20 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
   for (int j = 0; j < n_jobs; ++j) {
     const TcJob &job = jobs[j];
     if (job.flush_blocks < 1 || job.kb < 1 || job.n_tiles < 1) return cudaErrorInvalidValue;
+    if (fused && !job.op) return cudaErrorInvalidValue;
+    KJob &kj = kp.job[j];
+    kj.out = job.out;
+    kj.item_begin = items;
+    kj.n_bl = job.n_bl;
+    kj.n_inputs = job.n_inputs;
+    kj.n_tiles = job.n_tiles;
+    kj.n_pairs = job.n_pairs;
+    kj.kb = job.kb;
+    kj.flush_blocks = job.flush_blocks;
+    kj.n_time = job.n_time;
+    kj.volt = fused ? job.op : nullptr;  // the fused pair mode reads the packed samples
+    items += (int64_t)job.n_chan * job.n_pairs;
+    if (fused) continue;  // no operand tiles, no tensor map
     // 8-bit: [chan][kb][row][128 B] viewed as rows of 128 bytes;
     // 4-bit: [chan][kb][128 rows][n_rows bytes]; the box is one 16 KB tile
     const cuuint64_t n_rows = (cuuint64_t)job.n_tiles * kTile;
@@ -1221,18 +1428,8 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    KJob &kj = kp.job[j];
-    kj.out = job.out;
-    kj.item_begin = items;
-    kj.n_bl = job.n_bl;
-    kj.n_inputs = job.n_inputs;
-    kj.n_tiles = job.n_tiles;
-    kj.n_pairs = job.n_pairs;
-    kj.kb = job.kb;
-    kj.flush_blocks = job.flush_blocks;
-    items += (int64_t)job.n_chan * job.n_pairs;
   }
-  if (cfg.mode == kModePair) {
+  if (pair) {
     kp.items = cfg.items;
     items = cfg.n_items;
   }
@@ -1252,6 +1449,9 @@ cudaError_t launch_correlate_tc(const TcJob *jobs, int n_jobs, const TcLaunch &c
     launch_shape<kModeWide>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
   else if (cfg.mode == kModePair)
     launch_shape<kModePair>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
+  else if (fused)
+    correlate_tc_kernel<4, MWAX_KIND_EXACT, kModePairFused>
+        <<<grid, Shape<kModePairFused>::warps * 32, smem, s>>>(maps, kp);
   else
     launch_shape<kModeNarrow>(cfg.sample_bits, cfg.kind, grid, smem, s, maps, kp);
   return cudaGetLastError();

@@ -50,7 +50,7 @@ struct mwax_plan_s {
   int kind = MWAX_KIND_EXACT;
   int stages = 2;
   int prefetch = 0;
-  int mode = 0;  // correlate kernel: 0 narrow, 1 wide, 2 pair (mma_shape - 1)
+  int mode = 0;  // correlate kernel: 0 narrow, 1 wide, 2 pair, 3 fused pair (mma_shape - 1)
   int withhold_seg = -1;
   int unpack_sms = 0;  // overlapped pipeline: SMs given to the persistent unpack (0: co-resident)
   unsigned long long timeout_ns = mwax::kDefaultTimeoutNs;
@@ -147,7 +147,7 @@ mwax_status check_job(const mwax_job &j) {
   if (j.kind != MWAX_KIND_EXACT && j.kind != MWAX_KIND_FP16) return MWAX_ERR_INVALID_ARG;
   if (j.engine != MWAX_ENGINE_TENSOR && j.engine != MWAX_ENGINE_PLAIN) return MWAX_ERR_INVALID_ARG;
   if (j.flush_blocks < 0 || j.chan_group < 0) return MWAX_ERR_INVALID_ARG;
-  if (j.mma_shape < 0 || j.mma_shape > 3) return MWAX_ERR_INVALID_ARG;
+  if (j.mma_shape < 0 || j.mma_shape > 4) return MWAX_ERR_INVALID_ARG;
   if (j.pipeline < 0 || j.pipeline > 2) return MWAX_ERR_INVALID_ARG;
   if (j.stages < 0 || j.stages == 1 ||
       j.stages > correlate_tc_max_stages(j.mma_shape > 0 ? j.mma_shape - 1 : 0))
@@ -239,6 +239,7 @@ TcJob tc_job(const JobState &s, const uint8_t *op, void *out_c0, int nc) {
   tj.kb = s.kb;
   tj.flush_blocks = s.flush_blocks;
   tj.n_chan = nc;
+  tj.n_time = s.job.n_time;
   tj.n_bl = s.n_bl;
   tj.k_split = s.k_split;
   return tj;
@@ -249,7 +250,7 @@ TcJob tc_job(const JobState &s, const uint8_t *op, void *out_c0, int nc) {
 // most half the SMs, then the largest k <= 8 with base_items * k <= SMs and
 // k <= time blocks / 2.  -1: a k_split the job cannot take.
 int resolve_split(const mwax_job &job, int mode, int kb, int64_t base_items, int sm_count) {
-  const bool can = mode == 2 && job.kind == MWAX_KIND_EXACT;
+  const bool can = (mode == 2 || mode == 3) && job.kind == MWAX_KIND_EXACT;
   if (job.k_split > 0) {
     if (job.k_split == 1) return 1;
     return can && 2 * job.k_split <= kb ? job.k_split : -1;
@@ -260,15 +261,28 @@ int resolve_split(const mwax_job &job, int mode, int kb, int64_t base_items, int
   return std::max(k, 1);
 }
 
-// Kernel mode for a job's mma_shape (0 = auto: pair mode where every job
-// integrates in one exact segment, else narrow); -1 when an explicit pair
-// request cannot be served.
-int choose_mode(int mma_shape, const std::vector<TcJob> &tj) {
+// Fused pair mode chosen automatically up to this many 128-input tiles: each
+// operand tile is converted once per work item that reads it (about n_tiles /
+// 2 + 1 times per channel and time block), against one write and one read of
+// the unpacked operands through HBM without the fusion.
+constexpr int kFusedAutoTiles = 2;
+
+// Kernel mode for a job's mma_shape (0 = auto: the fused pair mode for small
+// 4-bit exact arrays that allow it (fused_ok, at most kFusedAutoTiles tiles),
+// else the pair mode where every job integrates in one exact segment, else
+// narrow); -1 when an explicit pair or fused pair request cannot be served.
+int choose_mode(int mma_shape, const std::vector<TcJob> &tj, bool fused_ok) {
   const bool pair_ok = pair_mode_supported(tj.data(), (int)tj.size());
+  if (mma_shape == 4) return pair_ok && fused_ok ? 3 : -1;
   if (mma_shape == 3) return pair_ok ? 2 : -1;
   if (mma_shape == 1 || mma_shape == 2) return mma_shape - 1;
+  bool small = true;
+  for (const TcJob &j : tj) small = small && j.n_tiles <= kFusedAutoTiles;
+  if (pair_ok && fused_ok && small) return 3;
   return pair_ok ? 2 : 0;
 }
+
+bool pair_like(int mode) { return mode == 2 || mode == 3; }
 
 // Build the pair-mode work lists (a and, if non-empty, b after it) and copy
 // them to a device buffer owned by the plan.
@@ -375,7 +389,7 @@ mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op
                             void *out_c0, cudaStream_t st, bool use_pair = true) {
   TcJob tj = tc_job(s, op, out_c0, nc);
   TcLaunch cfg = launch_cfg(p);
-  if (p->mode == 2 && !use_pair) {  // a checked plan's narrow call
+  if (p->mode == 2 && !use_pair) {  // a checked plan's narrow call (never fused)
     cfg.mode = 0;
     cfg.stages = correlate_tc_max_stages(0);
     TimedLaunch tn(p, 1, st);
@@ -383,7 +397,7 @@ mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op
     tn.done();
     return cuda_status(e);
   }
-  if (p->mode == 2) {
+  if (pair_like(p->mode)) {
     const bool full = nc == s.chan_group;
     cfg.items = full ? p->items : p->items + p->n_items_full;
     cfg.n_items = full ? p->n_items_full : p->n_items_last;
@@ -391,7 +405,7 @@ mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op
   }
   TimedLaunch tc(p, 1, st);
   cudaError_t e = cudaSuccess;
-  if (p->mode == 2 && s.k_split > 1)  // the time ranges' partial sums are added into it
+  if (pair_like(p->mode) && s.k_split > 1)  // the time ranges' partial sums are added into it
     e = cudaMemsetAsync(out_c0, 0, (size_t)(nc * s.out_chan_bytes), st);
   if (e == cudaSuccess) e = launch_correlate_tc(&tj, 1, cfg, st);
   if (e == cudaSuccess && p->checked) {
@@ -415,9 +429,11 @@ mwax_status correlate_group(mwax_plan_s *p, const JobState &s, const uint8_t *op
 }
 
 // Channels [c0, c0+nc) of a single-job tensor plan, one after the other on
-// `st`: unpack into the scratch, then one persistent correlate launch.
+// `st`: unpack into the scratch, then one persistent correlate launch (the
+// fused pair mode reads the packed samples itself: the launch only).
 mwax_status run_group(mwax_plan_s *p, const JobState &s, const uint8_t *volt, int64_t c0, int nc,
                       void *out_c0, cudaStream_t st, bool use_pair = true) {
+  if (p->mode == 3) return correlate_group(p, s, volt + c0 * s.in_chan_bytes, nc, out_c0, st, use_pair);
   mwax_status r = unpack_group(p, s, volt, c0, nc, p->scratch, 0, st);
   if (r != MWAX_OK) return r;
   return correlate_group(p, s, p->scratch, nc, out_c0, st, use_pair);
@@ -592,14 +608,15 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
                  (job->mma_shape == 0 || job->mma_shape == 3) && s.flush_blocks < s.kb &&
                  s.n_tiles <= 255;
     if (p->checked) full[0].flush_blocks = s.kb;
-    p->mode = choose_mode(job->mma_shape, full);
+    const bool fused_ok = !p->checked && fused_pair_supported(full.data(), 1, job->sample_bits, job->kind);
+    p->mode = choose_mode(job->mma_shape, full, fused_ok);
     if (p->mode < 0) {
       free_plan(p);
       return MWAX_ERR_UNSUPPORTED;
     }
     // time ranges per pair-mode item, from the items of one channel group
     std::vector<int4> base;
-    if (p->mode == 2) build_pair_items(full.data(), 1, base);
+    if (pair_like(p->mode)) build_pair_items(full.data(), 1, base);
     const int split = resolve_split(*job, p->mode, s.kb, (int64_t)base.size(), p->sm_count);
     if (split < 0) {
       free_plan(p);
@@ -611,7 +628,7 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
       free_plan(p);
       return MWAX_ERR_INVALID_ARG;
     }
-    const int64_t one = s.op_chan_bytes * s.chan_group;
+    const int64_t one = p->mode == 3 ? 0 : s.op_chan_bytes * s.chan_group;  // fused: no operands
     const bool even = s.job.sample_bits == 8 ? s.job.n_inputs % 2 == 0 : true;
     // unpack_sms 0: the small unpack CTA runs beside the correlate on every SM
     // where the shape allows it, else 20 SMs are set aside for the unpack
@@ -621,10 +638,13 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
                         ? 0
                         : 20;
     p->overlap = job->pipeline == 2 && s.chan_group < s.job.n_chan && even &&
-                 p->unpack_sms < p->sm_count;
+                 p->unpack_sms < p->sm_count && p->mode != 3;
     p->scratch_bytes = one * (p->overlap ? 2 : 1);
-    cudaError_t e = plan_alloc(reinterpret_cast<void **>(&p->scratch), (size_t)one);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)one, stream);
+    cudaError_t e = cudaSuccess;
+    if (one > 0) {
+      e = plan_alloc(reinterpret_cast<void **>(&p->scratch), (size_t)one);
+      if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch, 0, (size_t)one, stream);
+    }
     if (e == cudaSuccess && p->overlap) {
       e = plan_alloc(reinterpret_cast<void **>(&p->scratch2), (size_t)one);
       if (e == cudaSuccess) e = cudaMemsetAsync(p->scratch2, 0, (size_t)one, stream);
@@ -635,7 +655,7 @@ mwax_status mwax_plan(mwax_plan_t *plan, const mwax_job *job, cudaStream_t strea
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_freed[k], cudaEventDisableTiming);
       }
     }
-    if (e == cudaSuccess && p->mode == 2) {
+    if (e == cudaSuccess && pair_like(p->mode)) {
       const int last = (int)(s.job.n_chan % s.chan_group);
       std::vector<TcJob> tail;
       if (last) {
@@ -706,7 +726,7 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
   }
   std::vector<TcJob> tj;
   for (const JobState &s : p->jobs) tj.push_back(tc_job(s, s.op, nullptr, s.job.n_chan));
-  p->mode = choose_mode(jobs[0].mma_shape, tj);
+  p->mode = choose_mode(jobs[0].mma_shape, tj, false);  // batch plans unpack every job
   if (p->mode < 0) {
     free_plan(p);
     return MWAX_ERR_UNSUPPORTED;
@@ -762,7 +782,7 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   int64_t items = 0;
   if (plan->mode == 2 && plan->batch) {
     items = plan->n_items_full;
-  } else if (plan->mode == 2) {
+  } else if (pair_like(plan->mode)) {
     items = (s.job.n_chan / s.chan_group) * plan->n_items_full + plan->n_items_last;
   } else {
     for (const auto &j : plan->jobs) items += (int64_t)j.job.n_chan * j.n_pairs;

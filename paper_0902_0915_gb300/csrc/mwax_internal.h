@@ -71,9 +71,11 @@ cudaError_t launch_unpack_tile(const uint8_t *volt, int sample_bits, int n_input
 #define MWAX_MAX_JOBS 8
 
 struct TcJob {
-  const uint8_t *op;  // operand tiles of n_chan channels (layout: see launch_unpack)
+  const uint8_t *op;  // operand tiles of n_chan channels (layout: see launch_unpack); fused
+                      // pair mode: the packed samples [n_chan][n_time][n_inputs] themselves
   void *out;          // visibilities of the first of these n_chan channels
   int32_t n_inputs, n_tiles, n_pairs, kb, flush_blocks, n_chan;
+  int32_t n_time = 0;  // samples per integration (read by the fused pair mode)
   int64_t n_bl;
   // pair mode: time ranges per work item (1: whole integration; > 1: each
   // range's partial sums are added into the zeroed output with int32 atomics)
@@ -87,7 +89,8 @@ struct TcLaunch {
   int stages;
   int prefetch;  // K-blocks of L2 prefetch ahead of the TMA loads (0 = none; narrow only)
   int mode;      // 0: narrow (N=128 MMAs), 1: wide (N=256 with B' built in shared
-                 // memory), 2: pair (two tile pairs per work item, see items)
+                 // memory), 2: pair (two tile pairs per work item, see items), 3: fused
+                 // pair (pair mode reading packed 4-bit samples, no unpack pass)
   int withhold_seg;  // test hook (-1: off): see mwax_job.test_fault
   int32_t *status;
   unsigned long long timeout_ns;
@@ -111,6 +114,9 @@ cudaError_t correlate_tc_prepare(int sample_bits, int kind, int stages, int mode
 // Pair mode needs every job's integration in one exact segment (kb <=
 // flush_blocks), at most 255 tiles, kb < 2^28 and 1 <= k_split <= min(kb, 8).
 bool pair_mode_supported(const TcJob *jobs, int n_jobs);
+// The fused pair mode also needs 4-bit exact samples, n_inputs a multiple of
+// 16 (whole 16-byte sample rows) and sample buffers on 16-byte boundaries.
+bool fused_pair_supported(const TcJob *jobs, int n_jobs, int sample_bits, int kind);
 // The pair-mode work list of one launch over `jobs` (16 bytes per item).
 void build_pair_items(const TcJob *jobs, int n_jobs, std::vector<int4> &items);
 

@@ -133,7 +133,7 @@ double time_batch(const std::vector<mwax_job> &jobs, const void *const *volt, vo
 }
 
 bool valid(const Cand &c) {
-  const bool shape_ok = c.mma_shape >= 0 && c.mma_shape <= 3;
+  const bool shape_ok = c.mma_shape >= 0 && c.mma_shape <= 4;
   const int max_st = correlate_tc_max_stages(c.mma_shape > 0 ? c.mma_shape - 1 : 0);
   return shape_ok && (c.stages == 0 || (c.stages >= 2 && c.stages <= max_st)) && c.k_split >= 0 &&
          c.k_split <= 8;
@@ -192,11 +192,14 @@ mwax_status mwax_autotune(mwax_job *job, const void *voltages, void *out, cudaSt
   // (mma_shape 3) on a job longer than one exact segment plans as the
   // checked single segment; explicit flush segments are not candidates.
   // Pair-mode candidates with time ranges per item fail to plan (and are
-  // skipped) where the job cannot take them (FP16 kind, too few time blocks).
+  // skipped) where the job cannot take them (FP16 kind, too few time blocks),
+  // and so do the fused pair mode's (mma_shape 4) outside 4-bit exact jobs of
+  // whole 16-input sample rows.
   const std::vector<Cand> cands = {
       {0, 0, 0, 0, 0, 0},  {3, 0, -1, 1, 0, 1}, {3, 0, -1, 1, 0, 2}, {3, 0, -1, 1, 0, 4},
-      {3, 0, -1, 1, 0, 8}, {1, 2, -1, 1, 0, 0}, {1, 2, 8, 1, 0, 0},  {2, 4, -1, 1, 0, 0},
-      {2, 3, -1, 1, 0, 0}, {1, 2, -1, 2, 0, 0}, {3, 0, -1, 2, 0, 1},
+      {3, 0, -1, 1, 0, 8}, {4, 0, -1, 1, 0, 1}, {4, 0, -1, 1, 0, 2}, {4, 0, -1, 1, 0, 4},
+      {1, 2, -1, 1, 0, 0}, {1, 2, 8, 1, 0, 0},  {2, 4, -1, 1, 0, 0}, {2, 3, -1, 1, 0, 0},
+      {1, 2, -1, 2, 0, 0}, {3, 0, -1, 2, 0, 1},
   };
   best_ms = -1.0;
   for (const Cand &c : cands) {

@@ -158,17 +158,30 @@ def test_pair_mode_shapes(mw, bits, N, T, C, G):
 
 
 def test_pair_mode_choice(mw):
-    """Auto takes the pair mode where the integration is one exact segment,
-    and the checked single segment for longer 8-bit exact jobs; explicit
-    segments or shapes are kept; a pair request that cannot be served is
-    refused."""
+    """Auto takes the fused pair mode for 4-bit exact jobs of at most two
+    tiles with whole 16-input sample rows, the pair mode where the
+    integration is one exact segment, and the checked single segment for
+    longer exact jobs; explicit segments or shapes are kept; a pair or fused
+    pair request that cannot be served is refused."""
     def info(*a, **kw):
         p = mw.Plan(*a, **kw)
         i = p.info()
         p.close()
         return i.mma_shape, i.checked_segment
 
-    assert info(256, 2, 20000, 4) == (3, 0)
+    assert info(256, 2, 20000, 4) == (4, 0)
+    assert info(64, 2, 1000, 4) == (4, 0)
+    assert info(384, 2, 2000, 4) == (3, 0)  # three tiles
+    assert info(200, 2, 2000, 4) == (3, 0)  # sample rows not whole 16-byte units
+    assert info(256, 2, 2000, 4, mma_shape=3) == (3, 0)
+    assert info(1024, 2, 2000, 4, mma_shape=4) == (4, 0)
+    assert info(256, 2, 200000, 4) == (3, 1)  # longer than one exact segment: checked
+    for bad in [dict(n=256, t=2000, bits=8), dict(n=200, t=2000, bits=4),
+                dict(n=256, t=200000, bits=4)]:
+        with pytest.raises(mw.MwaxError):
+            mw.Plan(bad["n"], 2, bad["t"], bad["bits"], mma_shape=4)
+    with pytest.raises(mw.MwaxError):
+        mw.BatchPlan([(256, 2, 2000), (128, 2, 2000)], sample_bits=4, mma_shape=4)
     assert info(256, 2, 512, 8) == (3, 0)  # exactly one segment (16 blocks)
     assert info(256, 2, 20000, 8) == (3, 1)  # 8-bit, 16 blocks per exact segment
     assert info(256, 2, 513, 8, mma_shape=3) == (3, 1)
@@ -179,6 +192,54 @@ def test_pair_mode_choice(mw):
         mw.Plan(256, 2, 2000, 4, mma_shape=3, flush_blocks=4)
     with pytest.raises(mw.MwaxError):
         mw.BatchPlan([(256, 2, 2000), (128, 2, 2000)], sample_bits=8, mma_shape=3)
+
+
+# ---------------------------------------------------------------------------
+# fused pair mode (mma_shape 4): converter warps write the operand tiles
+# from the packed 4-bit samples, no unpack pass
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,T,C,G,ks", [
+    (16, 33, 3, 0, 1), (48, 100, 5, 0, 1), (64, 1000, 5, 0, 0), (64, 1000, 3, 0, 8),
+    (128, 64, 3, 0, 1), (144, 65, 2, 0, 1), (256, 2000, 5, 2, 1), (256, 640, 4, 3, 3),
+    (272, 97, 2, 0, 1), (384, 333, 3, 2, 1), (512, 330, 2, 0, 2), (1024, 64, 2, 0, 1)])
+def test_fused_pair_mode(mw, N, T, C, G, ks):
+    """Every tile count from 1 to 8 (shared items with two and three tiles,
+    diagonal leftovers paired across channels, a last single item), the last
+    tile partly filled (N = 144, 272: inputs past N read as zero), ragged
+    last time blocks (one sample in the last block at T = 65), channel groups
+    with a ragged last group, time ranges per item (automatic at 64 inputs);
+    bit-exact on the first call and on a second call into the same buffer."""
+    spec = synth.Spec("fu", N, C, T, 4, seed=N + 7 * T + C, sigma=2, tone_amp=0.3)
+    v = device_volt(spec)
+    kw = {"chan_group": G} if G else {}
+    if ks:
+        kw["k_split"] = ks
+    p = mw.Plan(N, C, T, 4, mma_shape=4, **kw)
+    inf = p.info()
+    assert inf.mma_shape == 4 and inf.scratch_bytes == 0
+    if ks:
+        assert inf.k_split == ks
+    out = p.correlate(v)
+    out = p.correlate(v, out)
+    assert p.status() == 0
+    assert_exact(out.cpu().numpy(), oracle_for(spec, range(C)), f"fused {N},{T},{C},{G},{ks}")
+    p.close()
+
+
+def test_fused_pair_largest_single_segment(mw):
+    """All samples (7, 7) over the longest 4-bit integration that is one exact
+    segment: V_ii = 98 T = 16,771,328, just below 2^24."""
+    T = 2674 * 64
+    spec = synth.Spec("fmax", 144, 1, T, 4, seed=0, kind=synth.SYNTH_CONST, c_re=7, c_im=7)
+    out = run(mw, spec, mw.ENGINE_TENSOR, mma_shape=4)
+    assert out[0, 0, 0] == 98 * T == 16_771_328 and out[0, 0, 1] == 0
+    assert_exact(out, oracle_for(spec, [0]), "fused max")
+
+
+def test_fused_pair_big_then_small(mw):
+    spec = synth.Spec("fbs", 144, 2, 20000, 4, seed=11, kind=synth.SYNTH_BIGSMALL, t_split=19000)
+    assert_exact(run(mw, spec, mw.ENGINE_TENSOR, mma_shape=4), oracle_for(spec, range(2)),
+                 "fused big-small")
 
 
 def _volt8(arr):
@@ -443,7 +504,7 @@ def _full_size(mw, spec, chans, **kw):
     assert_exact(got, oracle_for(spec, chans), spec.name)
 
 
-@pytest.mark.parametrize("shape", SHAPES_ONE_SEGMENT)
+@pytest.mark.parametrize("shape", SHAPES_ONE_SEGMENT + [4])
 def test_full_size_c1_sampled(mw, shape):
     spec = synth.spec_c1()
     _full_size(mw, spec, [0, 1, 383, 766, 767], mma_shape=shape)

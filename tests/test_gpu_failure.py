@@ -47,16 +47,19 @@ def test_withheld_release_times_out_and_device_recovers(mw, shape):
     torch.cuda.synchronize()
 
 
-def test_withheld_release_times_out_pair_mode(mw):
-    """The same in pair mode (one accumulator buffer per CTA, released per work
-    item): CTA 0 withholds the release of its first item, so the MMA warp's
-    wait before its second item runs out."""
+@pytest.mark.parametrize("shape", [3, 4])
+def test_withheld_release_times_out_pair_mode(mw, shape):
+    """The same in pair mode and in the fused pair mode (one accumulator
+    buffer per CTA, released per work item): CTA 0 withholds the release of
+    its first item, so the MMA warp's wait before its second item runs out
+    (and the fused mode's converter warps, waiting for a free stage, end on
+    the abort flag)."""
     import torch
 
     spec = synth.Spec("ffp", 256, 400, 600, 4, seed=5, sigma=2)
     v = device_volt(spec)
     p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, timeout_ms=150, test_fault=1,
-                mma_shape=3)
+                mma_shape=shape)
     assert p.info().work_items > 2 * 152
     t0 = time.time()
     p.correlate(v)
@@ -64,7 +67,7 @@ def test_withheld_release_times_out_pair_mode(mw):
     assert st == mw.STATUS_BY_NAME["MWAX_ERR_TIMEOUT"]
     assert time.time() - t0 < 30.0
     p.close()
-    q = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, mma_shape=3)
+    q = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, mma_shape=shape)
     out = q.correlate(v)
     assert q.status() == 0
     chans = [0, 1, 199, 398, 399]
