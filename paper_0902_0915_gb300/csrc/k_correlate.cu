@@ -467,6 +467,10 @@ __device__ __forceinline__ uint4 ld_stream16(const uint8_t *p) {
   return v;
 }
 
+#ifndef MWAX_FUSED_PREFETCH
+#define MWAX_FUSED_PREFETCH 3  // fused pair mode: stages of L2 prefetch ahead of the converters (0: none)
+#endif
+constexpr int kFusedPrefetch = MWAX_FUSED_PREFETCH;
 constexpr int kConvThreads = 256;                  // fused pair mode: the 8 epilogue warps
 constexpr int kConvUnits = 64 * 8 / kConvThreads;  // (sample, 16 inputs) units per thread per tile
 
@@ -602,7 +606,8 @@ template <int BITS, int KIND, bool FUSED>
 __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, uint8_t *smem,
                                            uint32_t smem_base, uint8_t *epi_smem, uint32_t bar0,
                                            uint32_t tmem_base, volatile int *abort_flag,
-                                           volatile int *epi_flag, int warp, int lane) {
+                                           volatile int *epi_flag, volatile int *conv_done,
+                                           int warp, int lane) {
   using Sh = Shape<FUSED ? kModePairFused : kModePair>;
   constexpr int kStageBytes = Sh::stage_bytes;
   const int S = p.stages;
@@ -678,6 +683,47 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
           ph ^= 1u;
         }
         mbar_wait(full(st), ph, nullptr, tmo);
+      }
+    }
+    if (FUSED && kFusedPrefetch > 0 && lane == 0) {
+      // ------------ fused pair mode: L2 prefetch of the packed samples ------------
+      // The sample rows of each stage's channels, kFusedPrefetch stages ahead
+      // of the converters (paced by their count of filled stages, conv_done;
+      // a hint only: no result is read), so that their loads hit L2.
+      int64_t g = 0;  // stages of this CTA so far
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        const PairItem it = decode_pair_item(__ldg(p.items + item));
+        const KJob &jb = p.job[it.job];
+        const int N = jb.n_inputs, T = jb.n_time;
+        const int cb = it.type == kItemTwoDiag ? it.c1 : it.c0;
+        int k0, k1;
+        item_blocks(it, jb.kb, k0, k1);
+        for (int kb = k0; kb < k1; kb += Sh::kps, ++g) {
+          if (*conv_done < g - kFusedPrefetch) {
+            const uint64_t t0 = globaltimer();
+            while (*conv_done < g - kFusedPrefetch) {
+              if (*abort_flag || globaltimer() - t0 > tmo) {
+                ok = false;
+                break;
+              }
+              __nanosleep(128);
+            }
+            if (!ok) break;
+          }
+          const int r0 = kb * 64, r1 = min((kb + Sh::kps) * 64, T);
+          if (r1 <= r0) continue;
+          const uint32_t bytes = (uint32_t)(r1 - r0) * (uint32_t)N;
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                           jb.volt + ((int64_t)it.c0 * T + r0) * N),
+                       "r"(bytes)
+                       : "memory");
+          if (cb != it.c0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                             jb.volt + ((int64_t)cb * T + r0) * N),
+                         "r"(bytes)
+                         : "memory");
+        }
       }
     }
     __syncwarp();
@@ -772,6 +818,7 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
       const int ct = (int)threadIdx.x - 32 * Sh::epi0;
       int stage = 0;
       uint32_t phase = 0;
+      int64_t filled = 0;  // stages of this CTA filled so far
       for (int64_t item = blockIdx.x; item < p.n_items; item += gridDim.x) {
         const PairItem it = decode_pair_item(__ldg(p.items + item));
         const KJob &jb = p.job[it.job];
@@ -828,6 +875,8 @@ __device__ __forceinline__ void pair_roles(const KMaps &maps, const KParams &p, 
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(full(stage));
+          ++filled;
+          if (warp == Sh::epi0 && lane == 0) *conv_done = (int)filled;  // paces the L2 prefetch
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -857,7 +906,8 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
   // full[0..S) empty[S..2S) bfull[2S..3S) tfull[3S..3S+2) tempty[3S+2..3S+4) drain[3S+4]
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3 * S + 5);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  volatile int *epi_flag = abort_flag + 1;  // [2]: result of the epilogue's accumulator wait
+  // [0..1]: result of the epilogue's accumulator wait; [2]: fused pair mode's filled-stage count
+  volatile int *epi_flag = abort_flag + 1;
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + S + s); };
   auto bfull = [&](int s) { return smem_u32(bars + 2 * S + s); };
@@ -881,6 +931,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
+    epi_flag[2] = 0;  // fused pair mode: stages the converters have filled
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -898,7 +949,7 @@ __global__ void __launch_bounds__(Shape<MODE>::warps * 32, 1)
 
   if constexpr (PAIR) {
     pair_roles<BITS, KIND, FUSED>(maps, p, smem, smem_base, epi_smem, smem_u32(bars), tmem_base,
-                                  abort_flag, epi_flag, warp, lane);
+                                  abort_flag, epi_flag, epi_flag + 2, warp, lane);
   } else if (warp == 0) {
     // ---------------- TMA producer (one thread) ----------------
     if (lane == 0) {
