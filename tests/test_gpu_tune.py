@@ -84,3 +84,25 @@ def test_batch_autotune_and_graph_timing(mw):
     for s, o in zip(specs, outs):
         assert_exact(o.cpu().numpy(), oracle_for(s, range(s.n_chan)), s.name)
     bp.close()
+
+
+def test_autotune_4bit_with_fused_candidates(mw, tmp_path, monkeypatch):
+    """A 4-bit job of two tiles: the candidates include the fused pair mode
+    (mma_shape 4) with and without time ranges; the plan's default is
+    candidate 0, the choice is never slower than it, and it stays exact."""
+    import torch
+
+    monkeypatch.setenv("MWAX_TUNE_CACHE", str(tmp_path / "tune4.txt"))
+    spec = synth.Spec("t4", 256, 6, 2000, 4, seed=9, sigma=2, tone_amp=0.3)
+    v = device_volt(spec)
+    out = torch.empty((spec.n_chan, spec.n_inputs * (spec.n_inputs + 1) // 2, 2), dtype=torch.int32,
+                      device="cuda")
+    fields, rep = mw.autotune(v, out, spec.n_inputs, spec.n_chan, spec.n_time, 4)
+    assert rep.candidates >= 8 and rep.from_cache == 0
+    assert rep.default_ms > 0 and rep.best_ms <= rep.default_ms * 1.0001
+    p = mw.Plan(spec.n_inputs, spec.n_chan, spec.n_time, 4, **fields)
+    assert p.info().mma_shape in (1, 2, 3, 4)
+    got = p.correlate(v)
+    assert p.status() == 0
+    assert_exact(got.cpu().numpy(), oracle_for(spec, range(spec.n_chan)), "tuned 4-bit")
+    p.close()
