@@ -455,10 +455,12 @@ __device__ __forceinline__ void narrow_block(uint32_t d_re, uint32_t d_im, uint6
 }
 
 // Fused pair mode: one converter thread's share of tile I of channel c, time
-// block kb (64 samples): the packed samples of 4 (sample, 16-input) units,
-// loaded first, then written as E4M3 codes, re plane at row t and im plane at
-// row 64 + t of the tile, each 16-byte chunk at its 128-byte swizzle position.
-// Samples past T and inputs past N read as zero (N is a multiple of 16).
+// block kb (64 samples): the packed samples of kConvUnits (sample, 16-input)
+// units (unit u = sample u / 8, inputs 16 (u % 8) ..; thread ct takes units
+// ct + 256 m), loaded first (fused_load), then written as E4M3 codes
+// (fused_store), re plane at row t and im plane at row 64 + t of the tile,
+// each 16-byte chunk at its 128-byte swizzle position.  Samples past T and
+// inputs past N read as zero (N is a multiple of 16).
 __device__ __forceinline__ uint4 ld_stream16(const uint8_t *p) {
   uint4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
