@@ -1082,6 +1082,12 @@ def main():
                     "correlate_ms_per_step": tim.correlate_ms / args.steps}
         if tim.unpack_ms > 0:
             roofline["unpack"] = unpack_roofline(rspec, info, tim, args.steps, peaks, peak_src)
+        if info.mma_shape == 4:
+            roofline["note"] = ("fused pair mode: the kernel also converts the packed samples into its "
+                                "operand tiles (no unpack pass, no operand buffer), so its duration is the "
+                                "whole step; the tensor pipe waits on that conversion")
+            roofline["packed_samples_gbs"] = (rspec.n_chan * rspec.n_time * rspec.n_inputs * args.steps
+                                              / (tim.correlate_ms / 1e3) / 1e9)
         pk = tensor_peak_at_clock(rspec.sample_bits, clk,
                                   torch.cuda.get_device_properties(dev).multi_processor_count)
         if pk:
