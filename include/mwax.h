@@ -100,10 +100,11 @@ typedef struct {
                               the unpack folded into the correlate: converter warps
                               read the packed samples and write the operand tiles into
                               shared memory, so no operand buffer and no unpack pass
-                              (single-job plans of 4-bit exact samples in one exact
-                              segment with n_inputs a multiple of 16, else
+                              (4-bit exact samples in one exact segment with n_inputs a
+                              multiple of 16 -- every job of a batch plan --, else
                               MWAX_ERR_UNSUPPORTED); 0 = auto: 4 where it applies and
-                              n_inputs <= 256, else 3 where it applies, else 1           */
+                              n_inputs <= 256 (every job), else 3 where it applies,
+                              else 1                                                      */
   int32_t pipeline;        /* tuning: 1 = unpack then correlate each channel group on the
                               plan's stream, 2 = unpack the next group (second stream,
                               second scratch buffer) while the current group correlates,

@@ -714,26 +714,33 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
     JobState s;
     s.job = jobs[k];
     derive(s);
+    p->jobs.push_back(s);
+  }
+  std::vector<TcJob> tj;
+  for (const JobState &s : p->jobs) tj.push_back(tc_job(s, nullptr, nullptr, s.job.n_chan));
+  // the fused pair mode where every job allows it (the correlate then reads
+  // each job's voltages itself: no unpack graph, no operand buffers)
+  const bool fused_ok = fused_pair_supported(tj.data(), n_jobs, jobs[0].sample_bits, jobs[0].kind);
+  p->mode = choose_mode(jobs[0].mma_shape, tj, fused_ok);
+  if (p->mode < 0) {
+    free_plan(p);
+    return MWAX_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < n_jobs && p->mode != 3; ++k) {
+    JobState &s = p->jobs[k];
     cudaError_t e = plan_alloc(reinterpret_cast<void **>(&s.op), (size_t)(s.op_chan_bytes * s.job.n_chan));
     if (e == cudaSuccess)
       e = cudaMemsetAsync(s.op, 0, (size_t)(s.op_chan_bytes * s.job.n_chan), stream);
-    p->jobs.push_back(s);
     p->scratch_bytes += s.op_chan_bytes * s.job.n_chan;
+    tj[k].op = s.op;
     if (e != cudaSuccess) {
       free_plan(p);
       return cuda_status(e);
     }
   }
-  std::vector<TcJob> tj;
-  for (const JobState &s : p->jobs) tj.push_back(tc_job(s, s.op, nullptr, s.job.n_chan));
-  p->mode = choose_mode(jobs[0].mma_shape, tj, false);  // batch plans unpack every job
-  if (p->mode < 0) {
-    free_plan(p);
-    return MWAX_ERR_UNSUPPORTED;
-  }
   // each job's time ranges per pair-mode item, from the launch's items
   std::vector<int4> base;
-  if (p->mode == 2) build_pair_items(tj.data(), (int)tj.size(), base);
+  if (pair_like(p->mode)) build_pair_items(tj.data(), (int)tj.size(), base);
   for (int k = 0; k < n_jobs; ++k) {
     const int split = resolve_split(jobs[k], p->mode, p->jobs[k].kb, (int64_t)base.size(), p->sm_count);
     if (split < 0) {
@@ -744,7 +751,7 @@ mwax_status mwax_plan_batch(mwax_plan_t *plan, const mwax_job *jobs, int n_jobs,
   }
   p->stages = jobs[0].stages > 0 ? jobs[0].stages : correlate_tc_max_stages(p->mode);
   cudaError_t e = p->stages <= correlate_tc_max_stages(p->mode) ? cudaSuccess : cudaErrorInvalidValue;
-  if (e == cudaSuccess && p->mode == 2) e = upload_items(p, tj, {});
+  if (e == cudaSuccess && pair_like(p->mode)) e = upload_items(p, tj, {});
   if (e == cudaSuccess) e = correlate_tc_prepare(p->sample_bits, p->kind, p->stages, p->mode);
   if (e != cudaSuccess) {
     free_plan(p);
@@ -780,7 +787,7 @@ mwax_status mwax_plan_get_info(mwax_plan_t plan, mwax_plan_info *info) {
   info->prefetch = plan->prefetch;
   info->scratch_bytes = plan->scratch_bytes + plan->stage_in_bytes * 2 + plan->stage_out_bytes * 2;
   int64_t items = 0;
-  if (plan->mode == 2 && plan->batch) {
+  if (pair_like(plan->mode) && plan->batch) {
     items = plan->n_items_full;
   } else if (pair_like(plan->mode)) {
     items = (s.job.n_chan / s.chan_group) * plan->n_items_full + plan->n_items_last;
@@ -834,7 +841,8 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
     if (!is_device_ptr(voltages[k]) || !is_device_ptr(out[k]) || !aligned16(voltages[k]) ||
         !aligned16(out[k]))
       return MWAX_ERR_INVALID_ARG;
-  bool same = plan->graph != nullptr && plan->graph2 != nullptr;
+  const bool fused = plan->mode == 3;  // no unpack graph: the correlate reads the voltages
+  bool same = (fused || plan->graph != nullptr) && plan->graph2 != nullptr;
   for (int k = 0; k < nj && same; ++k)
     same = plan->graph_in[k] == voltages[k] && plan->graph_out[k] == out[k];
   if (!same) {
@@ -845,12 +853,15 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
       }
     std::vector<TcJob> tj(nj);
     for (int k = 0; k < nj; ++k)
-      tj[k] = tc_job(plan->jobs[k], plan->jobs[k].op, out[k], plan->jobs[k].job.n_chan);
+      tj[k] = tc_job(plan->jobs[k],
+                     fused ? reinterpret_cast<const uint8_t *>(voltages[k]) : plan->jobs[k].op, out[k],
+                     plan->jobs[k].job.n_chan);
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_status(e);
-    // graph 1: every job's unpack; graph 2: one persistent launch over all items
-    for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+    // graph 1: every job's unpack (none in the fused pair mode); graph 2: one
+    // persistent launch over all items
+    for (int part = fused ? 1 : 0; part < 2 && e == cudaSuccess; ++part) {
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (part == 0) {
@@ -893,10 +904,13 @@ mwax_status mwax_correlate_batch(mwax_plan_t plan, const void *const *voltages, 
     plan->graph_in.assign(voltages, voltages + nj);
     plan->graph_out.assign(out, out + nj);
   }
-  TimedLaunch tu(plan, 0, plan->stream);
-  cudaError_t e = cudaGraphLaunch(plan->graph, plan->stream);
-  tu.done();
-  if (e != cudaSuccess) return cuda_status(e);
+  cudaError_t e = cudaSuccess;
+  if (!fused) {
+    TimedLaunch tu(plan, 0, plan->stream);
+    e = cudaGraphLaunch(plan->graph, plan->stream);
+    tu.done();
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   TimedLaunch tc(plan, 1, plan->stream);
   e = cudaGraphLaunch(plan->graph2, plan->stream);
   tc.done();

@@ -229,9 +229,11 @@ mwax_status mwax_autotune_batch(mwax_job *jobs, int n_jobs, const void *const *v
   mwax_tune_report rep;
   memset(&rep, 0, sizeof(rep));
   std::vector<mwax_job> base(jobs, jobs + n_jobs);
-  // candidate 0: the batch plan's own default (all fields automatic)
-  const std::vector<Cand> cands = {{0, 0, 0, 0, 0, 0}, {3, 0, -1, 0, 0, 0}, {1, 2, -1, 0, 0, 0},
-                                   {1, 2, 8, 0, 0, 0}, {2, 4, -1, 0, 0, 0}, {2, 3, -1, 0, 0, 0}};
+  // candidate 0: the batch plan's own default (all fields automatic); the
+  // fused pair mode (4) fails to plan, and is skipped, unless every job allows it
+  const std::vector<Cand> cands = {{0, 0, 0, 0, 0, 0}, {3, 0, -1, 0, 0, 0}, {4, 0, -1, 0, 0, 0},
+                                   {1, 2, -1, 0, 0, 0}, {1, 2, 8, 0, 0, 0},  {2, 4, -1, 0, 0, 0},
+                                   {2, 3, -1, 0, 0, 0}};
   Cand best{0, 0, 0, 0, 0, 0};
   double best_ms = -1.0;
   for (const Cand &c : cands) {

@@ -181,7 +181,7 @@ def test_pair_mode_choice(mw):
         with pytest.raises(mw.MwaxError):
             mw.Plan(bad["n"], 2, bad["t"], bad["bits"], mma_shape=4)
     with pytest.raises(mw.MwaxError):
-        mw.BatchPlan([(256, 2, 2000), (128, 2, 2000)], sample_bits=4, mma_shape=4)
+        mw.BatchPlan([(256, 2, 2000), (200, 2, 2000)], sample_bits=4, mma_shape=4)
     assert info(256, 2, 512, 8) == (3, 0)  # exactly one segment (16 blocks)
     assert info(256, 2, 20000, 8) == (3, 1)  # 8-bit, 16 blocks per exact segment
     assert info(256, 2, 513, 8, mma_shape=3) == (3, 1)
@@ -224,6 +224,32 @@ def test_fused_pair_mode(mw, N, T, C, G, ks):
     assert p.status() == 0
     assert_exact(out.cpu().numpy(), oracle_for(spec, range(C)), f"fused {N},{T},{C},{G},{ks}")
     p.close()
+
+
+def test_fused_pair_batch(mw):
+    """A batch of small 4-bit jobs (every job at most two tiles with whole
+    16-input rows) takes the fused pair mode: one persistent launch reading
+    every job's voltages, no unpack graph, no operand buffers; bit-exact per
+    job, on the first call and again on new buffers (the graph is rebuilt)."""
+    import torch
+
+    jobs = [(48, 5, 300), (128, 3, 400), (256, 2, 700), (16, 4, 65)]
+    specs = [synth.Spec(f"fb{k}", n, c, t, 4, seed=90 + k, sigma=2, tone_amp=0.3)
+             for k, (n, c, t) in enumerate(jobs)]
+    bp = mw.BatchPlan(jobs, sample_bits=4)
+    inf = bp.info()
+    assert inf.mma_shape == 4 and inf.scratch_bytes == 0
+    for rep in range(2):
+        vs = [device_volt(s) for s in specs]
+        bp.set_timing(True)
+        outs = bp.correlate(vs)
+        t = bp.timing()
+        assert bp.status() == 0
+        assert t.unpack_launches == 0 and t.correlate_launches == 1
+        for s, o in zip(specs, outs):
+            assert_exact(o.cpu().numpy(), oracle_for(s, range(s.n_chan)), f"fused batch {s.name}")
+    bp.close()
+    torch.cuda.synchronize()
 
 
 def test_fused_pair_largest_single_segment(mw):
