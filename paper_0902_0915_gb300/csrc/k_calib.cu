@@ -452,7 +452,10 @@ __global__ void __launch_bounds__(kCalThreads) calib_chan_gather_kernel(
 // b >= a) load V = M = 0 and contribute exactly 0.
 constexpr int kJT = 32;  // Jones blocks per calibration tile side
 constexpr int kJQ = 12;  // per-tile partial quantities
-constexpr int kJonesChanGroups = 24;
+#ifndef MWAX_JONES_CHAN_GROUPS
+#define MWAX_JONES_CHAN_GROUPS 12  // channel groups of the Jones pass (CTAs per calibration tile)
+#endif
+constexpr int kJonesChanGroups = MWAX_JONES_CHAN_GROUPS;
 
 // acc + a b,  acc + a conj(b),  acc + conj(a) b
 __device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 b) {
@@ -537,7 +540,9 @@ __device__ __forceinline__ void jones_load_row(float4 *slot, const float2 *Vn, c
 }
 
 // The per-row work of the Jones pass: loss, the lane's tile-b sums (col) and
-// the row's twelve tile-a quantities (v, for the reduce-scatter).
+// the row's twelve tile-a quantities, added into v (the lane's sums over its
+// channels, reduce-scattered once per row pair; v[8..11] stay as they are
+// without DEN).
 template <bool DEN>
 __device__ __forceinline__ float jones_row(const float4 *slot, float2 ja00, float2 ja01,
                                            float2 ja10, float2 ja11, float2 jb00, float2 jb01,
@@ -559,20 +564,18 @@ __device__ __forceinline__ float jones_row(const float4 *slot, float2 ja00, floa
   const float2 R11 = cfma(cfma(make_float2(-v11.x, -v11.y), ja10, B01), ja11, B11);
   const float l = cabs2(R00) + cabs2(R01) + cabs2(R10) + cabs2(R11);
   {
-    const float2 g00 = cfmac(cfmac(z, R00, B00), R01, B01);
-    const float2 g01 = cfmac(cfmac(z, R00, B10), R01, B11);
-    const float2 g10 = cfmac(cfmac(z, R10, B00), R11, B01);
-    const float2 g11 = cfmac(cfmac(z, R10, B10), R11, B11);
+    const float2 g00 = cfmac(cfmac(make_float2(v[0], v[1]), R00, B00), R01, B01);
+    const float2 g01 = cfmac(cfmac(make_float2(v[2], v[3]), R00, B10), R01, B11);
+    const float2 g10 = cfmac(cfmac(make_float2(v[4], v[5]), R10, B00), R11, B01);
+    const float2 g11 = cfmac(cfmac(make_float2(v[6], v[7]), R10, B10), R11, B11);
     v[0] = g00.x; v[1] = g00.y; v[2] = g01.x; v[3] = g01.y;
     v[4] = g10.x; v[5] = g10.y; v[6] = g11.x; v[7] = g11.y;
     if constexpr (DEN) {
-      const float2 d10 = cfmac(cfmac(z, B10, B00), B11, B01);
-      v[8] = cabs2(B00) + cabs2(B01);
-      v[9] = cabs2(B10) + cabs2(B11);
+      const float2 d10 = cfmac(cfmac(make_float2(v[10], v[11]), B10, B00), B11, B01);
+      v[8] += cabs2(B00) + cabs2(B01);
+      v[9] += cabs2(B10) + cabs2(B11);
       v[10] = d10.x;
       v[11] = d10.y;
-    } else {
-      v[8] = v[9] = v[10] = v[11] = 0.f;
     }
   }
   const float2 A00 = cfma(cfma(z, ja00, m00), ja01, m10);
@@ -600,8 +603,11 @@ __device__ __forceinline__ float jones_row(const float4 *slot, float2 ja00, floa
 // PAIRS-deep shared-memory ring (reads back only what it copied: no barrier);
 // the tile's 32 rows of J_a are staged once per CTA.  grid: (calibration
 // tiles, channel groups); CTA (tile, cg) covers channels cg, cg + n_cg, ...,
-// its warp w every eighth of them, and adds each channel's loss into a Kahan
-// accumulator; the eight warps' partials are summed in a fixed order.
+// its warp w every eighth of them.  A warp walks its row pairs, each over all
+// its channels: the lane adds the pair's tile-a quantities over the channels
+// and the warp reduce-scatters them once per row pair; each row pair's loss
+// goes into a Kahan accumulator; the eight warps' partials are summed in a
+// fixed order.
 // Outputs per (tile, cg): part_row [32 rows][12], part_col [32 columns][12],
 // part_loss.  DEN: the D quantities (left at 0 otherwise).
 #ifndef MWAX_JONES_PAIRS
@@ -644,26 +650,31 @@ __global__ void __launch_bounds__(kCalThreads, 2) calib_jones_tile2_kernel(
   const int64_t N = 2 * (int64_t)n_tiles, Bn = N * (N + 1) / 2;
   const int first = cg + n_cg * w, stride = n_cg * kWarps;
   const int n_mine = first < C ? (C - 1 - first) / stride + 1 : 0;
-  const int n_pairs = n_mine * (kJT / 2);  // pair p: channel k = p / 16, group m, row u
+  // pair p = q n_mine + k: row pair q (rows 8 (q >> 2) + (q & 3) + {0, 4}) of
+  // the warp's k-th channel; row pairs outer, channels inner, so each lane
+  // sums a row pair's tile-a quantities over its channels before the one
+  // reduce-scatter of the row pair
+  const int n_pairs = n_mine * (kJT / 2);
   float4 *ring = ringbase + (int64_t)w * kJPairs * 2 * 4 * 32 + lane;
-  auto row_of = [](int p, int h) {  // row h (0/1) of pair p within its channel's tile
-    const int q = p & 15;
-    return 8 * (q >> 2) + (q & 3) + 4 * h;
-  };
+  int iq = 0, ik = 0;  // row pair and channel of the next pair to issue
   auto issue = [&](int p) {
     if (p < n_pairs) {
-      const int nu = first + stride * (p >> 4);
+      const int nu = first + stride * ik;
       const float2 *Vn = V + (int64_t)nu * Bn, *Mn = M + (int64_t)nu * Bn;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float4 *slot = ring + ((p % kJPairs) * 2 + h) * 4 * 32;
-        const int a = I * kJT + row_of(p, h);
+        const int a = I * kJT + 8 * (iq >> 2) + (iq & 3) + 4 * h;
         if (a < n_tiles && b < a) {
           jones_load_row(slot, Vn, Mn, a, b);
         } else {
 #pragma unroll
           for (int e = 0; e < 4; ++e) slot[e * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+      }
+      if (++ik == n_mine) {
+        ik = 0;
+        ++iq;
       }
     }
     cp_async_commit();
@@ -677,32 +688,36 @@ __global__ void __launch_bounds__(kCalThreads, 2) calib_jones_tile2_kernel(
   Kahan loss;
 #pragma unroll
   for (int k = 0; k < kJPairs - 1; ++k) issue(k);
-  for (int kc = 0; kc < n_mine; ++kc) {
-    float lch = 0.f;
 #pragma unroll
-    for (int m = 0; m < 4; ++m)
+  for (int m = 0; m < 4; ++m)
 #pragma unroll 1
-      for (int u = 0; u < 4; ++u) {
-        const int p = kc * (kJT / 2) + 4 * m + u;
+    for (int u = 0; u < 4; ++u) {
+      const int q = 4 * m + u;
+      float v[2 * kJQ];
+#pragma unroll
+      for (int k = 0; k < 2 * kJQ; ++k) v[k] = 0.f;
+      float lq = 0.f;
+#pragma unroll 1
+      for (int kc = 0; kc < n_mine; ++kc) {
+        const int p = q * n_mine + kc;
         issue(p + kJPairs - 1);
         cp_async_wait<kJPairs - 1>();  // this thread's copies of pair p have landed
-        float v[2 * kJQ];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int r = 8 * m + u + 4 * h;
           const float4 *slot = ring + ((p % kJPairs) * 2 + h) * 4 * 32;
-          lch += jones_row<DEN>(slot, sJ[4 * r + 0], sJ[4 * r + 1], sJ[4 * r + 2], sJ[4 * r + 3],
-                                jb00, jb01, jb10, jb11, col, v + kJQ * h);
-        }
-        reduce_scatter24(v, lane);
-        if ((lane & 3) == u) {
-          row[m][0] += v[0];
-          row[m][1] += v[1];
-          row[m][2] += v[2];
+          lq += jones_row<DEN>(slot, sJ[4 * r + 0], sJ[4 * r + 1], sJ[4 * r + 2], sJ[4 * r + 3],
+                               jb00, jb01, jb10, jb11, col, v + kJQ * h);
         }
       }
-    loss.add(lch);
-  }
+      reduce_scatter24(v, lane);
+      if ((lane & 3) == u) {
+        row[m][0] += v[0];
+        row[m][1] += v[1];
+        row[m][2] += v[2];
+      }
+      loss.add(lq);
+    }
   cp_async_wait<0>();
   __syncthreads();  // every warp is done with the ring
   float(*sred)[kJT][kJQ] = reinterpret_cast<float(*)[kJT][kJQ]>(ringbase);
