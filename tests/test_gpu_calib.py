@@ -413,7 +413,7 @@ def check_jones(V, M, J, loss, grad):
 @pytest.mark.parametrize("n_tiles,C", [(1, 2), (2, 1), (17, 3), (40, 5), (65, 9), (33, 25)])
 def test_calib_jones_small(mw, n_tiles, C):
     """Ragged calibration tiles (tile counts not a multiple of 32), channel
-    counts above and below the 24 channel groups, one tile (no pairs)."""
+    counts above and below the 12 channel groups, one tile (no pairs)."""
     V, M, J, _ = problem_jones(n_tiles, C, seed=400 + n_tiles + C)
     loss, grad = gpu_jones_loss_grad(mw, V, M, J)
     if n_tiles == 1:
