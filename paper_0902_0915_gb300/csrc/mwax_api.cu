@@ -447,7 +447,7 @@ mwax_status correlate_device(mwax_plan_s *p, const uint8_t *volt, void *out, cud
       cudaError_t e = launch_plain_channel(volt + (int64_t)c * s.in_chan_bytes, s.job.sample_bits,
                                            s.job.n_inputs, s.job.n_time,
                                            reinterpret_cast<int32_t *>(out) + (int64_t)c * s.n_bl * 2,
-                                           st);
+                                           p->sm_count, st);
       tl.done();
       if (e != cudaSuccess) return cuda_status(e);
     }
@@ -1006,7 +1006,7 @@ mwax_status mwax_correlate_host(mwax_plan_t plan, const void *voltages_host, int
         r = cuda_status(launch_plain_channel(
             plan->stage_in[k] + (int64_t)c * s.in_chan_bytes, s.job.sample_bits, s.job.n_inputs,
             s.job.n_time, reinterpret_cast<int32_t *>(plan->stage_out[k]) + (int64_t)c * s.n_bl * 2,
-            plan->stream));
+            plan->sm_count, plan->stream));
     } else {
       r = run_group(plan, s, plan->stage_in[k], 0, nc, plan->stage_out[k], plan->stream, use_pair);
     }

@@ -35,8 +35,10 @@ inline int bytes_per_sample(int sample_bits) { return sample_bits == 4 ? 1 : 2; 
 inline int sample_max(int sample_bits) { return sample_bits == 4 ? 7 : 127; }
 
 // ---- plain CUDA-core correlator (one launch per channel) ------------------
+// sm_count sizes the launch: a channel with few tile pairs has its
+// integration cut into ranges (the output is zeroed first, on s).
 cudaError_t launch_plain_channel(const uint8_t *volt_chan, int sample_bits, int n_inputs,
-                                 int n_time, int32_t *out_chan, cudaStream_t s);
+                                 int n_time, int32_t *out_chan, int sm_count, cudaStream_t s);
 
 // ---- unpack: packed samples -> tensor-core operand tiles -------------------
 // volt: [n_chan_total][T][N] packed.  op, 8-bit samples (K-major):

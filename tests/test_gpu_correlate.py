@@ -362,6 +362,18 @@ def test_exact_random_max_magnitude(mw, shape):
                  "randmax")
 
 
+@pytest.mark.parametrize("bits", [4, 8])
+@pytest.mark.parametrize("N", [200, 300])
+def test_plain_random_max_magnitude(mw, bits, N):
+    """Plain engine (32- and 64-input tiles) on samples at the ends of the
+    supported range (its byte dot products negate the imaginary parts of the
+    column inputs); T = 5001 cuts each channel's integration into ranges
+    added with integer atomics, and leaves a last sample without a partner."""
+    spec = synth.Spec("rmp", N, 2, 5001, bits, seed=13 + N, kind=synth.SYNTH_RANDMAX)
+    assert_exact(run(mw, spec, mw.ENGINE_PLAIN), oracle_for(spec, range(2)),
+                 f"randmax plain {bits} {N}")
+
+
 def test_int32_bound_at_max_integration(mw):
     """All samples (127, 127) at the largest allowed T: V_ii = 2,147,479,576."""
     T = mw.max_n_time(8)
