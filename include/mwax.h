@@ -72,6 +72,10 @@ typedef enum {
   MWAX_ENGINE_TENSOR = 0, /* unpack + tcgen05 tensor-core correlator + dump (default)   */
   MWAX_ENGINE_PLAIN = 1   /* CUDA-core int32 correlator, one launch per channel         */
 } mwax_engine;
+/* The plain engine's launch of a channel with too few 64x64 (32x32 up to 256
+ * inputs) tile pairs to fill the GPU cuts the integration into ranges whose
+ * partial sums are added with integer atomics; the channel's output is then
+ * zeroed first with a memset on the same stream. */
 
 /* One correlation job.  Zero-initialise, then set the shape fields; the
  * tuning fields may stay 0 (= chosen by the plan / autotuner). */
