@@ -70,10 +70,19 @@ __global__ void __launch_bounds__((P / 4) * (P / 4)) plain_kernel(const uint8_t 
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc_re[a][b] = acc_im[a][b] = 0;
 
-  // this CTA's range of the integration: [t_begin, t_end), Ts a multiple of 2
+  // this CTA's range of the integration: [t_begin, t_end), Ts a multiple of 2.
+  // 64 x 64 tiles load the next chunk's words into registers while the
+  // current one is multiplied (kIt words of each side per thread); 32 x 32
+  // tiles load each chunk just before storing it (the registers the early
+  // loads would hold cost more there than the latency they hide: measured).
+  constexpr int kIt = kTP * P / kThreads;
+  constexpr bool kPrefetch = P == 64;
   const int t_begin = blockIdx.y * Ts, t_end = min(T, t_begin + Ts);
-  for (int t0 = t_begin; t0 < t_end; t0 += 2 * kTP) {
-    for (int k = tid; k < kTP * P; k += kThreads) {
+  uint32_t na[kIt], nb[kIt];
+  auto fetch = [&](int t0) {  // this thread's words of the chunk at t0, into na / nb
+#pragma unroll
+    for (int m = 0; m < kIt; ++m) {
+      const int k = tid + m * kThreads;
       const int tp = k / P, l = k % P;
       const int t = t0 + 2 * tp;
       uint32_t wa = 0, wb = 0;
@@ -89,12 +98,46 @@ __global__ void __launch_bounds__((P / 4) * (P / 4)) plain_kernel(const uint8_t 
           if (second) wb |= sample_bytes(r0 + row_bytes, j0 + l, bits) << 16;
         }
       }
-      sA[tp][l] = wa;
-      sB[tp][l] = wb;
-      // C = [-im_t, re_t, -im_t+1, re_t+1]: bytes 1, 0, 3, 2 of (-B, B)
-      sC[tp][l] = __byte_perm(wb, __vneg4(wb), 0x2705);
+      na[m] = wa;
+      nb[m] = wb;
+    }
+  };
+  if (kPrefetch && t_begin < t_end) fetch(t_begin);
+  for (int t0 = t_begin; t0 < t_end; t0 += 2 * kTP) {
+    if constexpr (kPrefetch) {
+#pragma unroll
+      for (int m = 0; m < kIt; ++m) {
+        const int k = tid + m * kThreads;
+        const int tp = k / P, l = k % P;
+        sA[tp][l] = na[m];
+        sB[tp][l] = nb[m];
+        // C = [-im_t, re_t, -im_t+1, re_t+1]: bytes 1, 0, 3, 2 of (-B, B)
+        sC[tp][l] = __byte_perm(nb[m], __vneg4(nb[m]), 0x2705);
+      }
+    } else {
+      for (int k = tid; k < kTP * P; k += kThreads) {
+        const int tp = k / P, l = k % P;
+        const int t = t0 + 2 * tp;
+        uint32_t wa = 0, wb = 0;
+        if (t < t_end) {
+          const uint8_t *r0 = volt + (int64_t)t * row_bytes;
+          const bool second = t + 1 < t_end;
+          if (i0 + l < N) {
+            wa = sample_bytes(r0, i0 + l, bits);
+            if (second) wa |= sample_bytes(r0 + row_bytes, i0 + l, bits) << 16;
+          }
+          if (j0 + l < N) {
+            wb = sample_bytes(r0, j0 + l, bits);
+            if (second) wb |= sample_bytes(r0 + row_bytes, j0 + l, bits) << 16;
+          }
+        }
+        sA[tp][l] = wa;
+        sB[tp][l] = wb;
+        sC[tp][l] = __byte_perm(wb, __vneg4(wb), 0x2705);
+      }
     }
     __syncthreads();
+    if (kPrefetch && t0 + 2 * kTP < t_end) fetch(t0 + 2 * kTP);
 #pragma unroll 4
     for (int tp = 0; tp < kTP; ++tp) {
       const uint4 a = *reinterpret_cast<const uint4 *>(&sA[tp][ty * 4]);
